@@ -1,0 +1,175 @@
+"""FP64 CPU oracle for the ridge-regularized matching LP.
+
+TEST INFRASTRUCTURE ONLY: the tests, ``__graft_entry__.smoke()`` and the
+benchmark's CPU-baseline leg use it; the solver library never does.  It shares
+no code with the CUDA path.  The arithmetic lives in ``oracle.c`` (plain C,
+FP64, sequential); this module compiles it with gcc and marshals numpy arrays.
+
+Parity status of each function (what pins it is in ``tests/test_oracle_*``):
+  project    pinned: brute-force active-set enumeration, closed forms, KKT,
+             two independent algorithms (sort and bisection), scipy QP.
+  sweep/dual pinned: finite differences (Danskin), concavity, L-smoothness.
+  fista      pinned: exact KKT solutions by enumeration of active sets, the
+             LP limit (scipy linprog), slack-capacity and one-item closed
+             forms, the FISTA O(1/t^2) rate bound.
+  certify    pinned: weak duality, feasibility of the scaled point.
+  The exact FP32-trajectory values on the large workloads are parity
+  unpinned beyond oracle-vs-solver agreement (the paper prints no worked
+  example).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "oracle.c")
+_LIB = os.path.join(_HERE, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+SIMPLEX_LE, SIMPLEX_EQ, BOX = 0, 1, 2
+
+
+class _Problem(ctypes.Structure):
+    _fields_ = [
+        ("I", ctypes.c_int64),
+        ("J", ctypes.c_int64),
+        ("nnz", ctypes.c_int64),
+        ("row_ptr", ctypes.c_void_p),
+        ("col", ctypes.c_void_p),
+        ("c", ctypes.c_void_p),
+        ("a", ctypes.c_void_p),
+        ("b", ctypes.c_void_p),
+        ("kind", ctypes.c_int32),
+        ("_pad", ctypes.c_int32),
+        ("z", ctypes.c_double),
+    ]
+
+
+def build(force: bool = False) -> str:
+    """Compile ``liboracle.so`` (gcc -O2, no fast-math: IEEE FP64)."""
+    with _lock:
+        if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+            tmp = _LIB + f".tmp{os.getpid()}"
+            subprocess.check_call(["gcc", "-O2", "-fno-fast-math", "-ffp-contract=off", "-shared", "-fPIC",
+                                   "-o", tmp, _SRC, "-lm"])
+            os.replace(tmp, _LIB)
+    return _LIB
+
+
+def _load():
+    global _lib
+    if _lib is None:
+        lib = ctypes.CDLL(build())
+        vp, i64, i32, d = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_double
+        P = ctypes.POINTER(_Problem)
+        lib.orc_project.argtypes = [vp, i64, i32, d, i32, vp]
+        lib.orc_project.restype = d
+        lib.orc_sweep.argtypes = [P, vp, d, vp, vp, vp, vp, vp]
+        lib.orc_sweep.restype = d
+        lib.orc_dual.argtypes = [P, vp, d, vp, vp]
+        lib.orc_dual.restype = d
+        lib.orc_row_sq.argtypes = [P, vp]
+        lib.orc_certify.argtypes = [P, vp, d, vp]
+        lib.orc_fista.argtypes = [P, d, d, d, i64, i32, i64, vp, vp, vp, vp, vp, vp]
+        lib.orc_stage_gamma.argtypes = [d, d, d, i64]
+        lib.orc_stage_gamma.restype = d
+        _lib = lib
+    return _lib
+
+
+def _p(a):
+    return None if a is None else a.ctypes.data_as(ctypes.c_void_p)
+
+
+class Problem:
+    """An instance in FP64: user-major CSR (row_ptr int64, col int32), c, a
+    (float64, e.g. float32 or bfloat16 values widened exactly), b (float64)."""
+
+    def __init__(self, row_ptr, col, c, a, b, J=None, kind=SIMPLEX_LE, z=1.0):
+        self.row_ptr = np.ascontiguousarray(row_ptr, dtype=np.int64)
+        self.col = np.ascontiguousarray(col, dtype=np.int32)
+        self.c = np.ascontiguousarray(c, dtype=np.float64)
+        self.a = np.ascontiguousarray(a, dtype=np.float64)
+        self.b = np.ascontiguousarray(b, dtype=np.float64)
+        self.I = int(self.row_ptr.shape[0] - 1)
+        self.J = int(J if J is not None else self.b.shape[0])
+        self.nnz = int(self.row_ptr[-1])
+        self.kind = int(kind)
+        self.z = float(z)
+        s = _Problem()
+        s.I, s.J, s.nnz = self.I, self.J, self.nnz
+        s.row_ptr, s.col, s.c, s.a, s.b = (_p(self.row_ptr), _p(self.col), _p(self.c), _p(self.a), _p(self.b))
+        s.kind, s.z = self.kind, self.z
+        self._s = s
+
+    @classmethod
+    def from_instance(cls, inst, kind=SIMPLEX_LE, z=1.0, c=None, a=None):
+        return cls(inst.row_ptr, inst.col, inst.c if c is None else c, inst.a if a is None else a, inst.b,
+                   inst.J, kind, z)
+
+
+def project(v, kind=SIMPLEX_LE, z=1.0, method=0):
+    """Projection of one segment onto the simplex / box; returns (x, theta)."""
+    v = np.ascontiguousarray(v, dtype=np.float64)
+    x = np.empty_like(v)
+    th = _load().orc_project(_p(v), v.shape[0], kind, z, method, _p(x))
+    return x, th
+
+
+def sweep(p: Problem, lam, gamma, want_x=True):
+    """One dual evaluation: dict(g, x, Ax, Cx, Qx, obj, grad)."""
+    lam = np.ascontiguousarray(lam, dtype=np.float64)
+    x = np.empty(p.nnz) if want_x else None
+    Ax, Cx, Qx = np.empty(p.J), np.empty(p.J), np.empty(p.J)
+    obj = ctypes.c_double()
+    g = _load().orc_sweep(ctypes.byref(p._s), _p(lam), gamma, _p(x), _p(Ax), _p(Cx), _p(Qx), ctypes.byref(obj))
+    return dict(g=g, x=x, Ax=Ax, Cx=Cx, Qx=Qx, obj=obj.value, grad=Ax - p.b)
+
+
+def dual(p: Problem, lam, gamma):
+    """(g(lam), grad g(lam), x*(lam))."""
+    lam = np.ascontiguousarray(lam, dtype=np.float64)
+    grad = np.empty(p.J)
+    x = np.empty(p.nnz)
+    g = _load().orc_dual(ctypes.byref(p._s), _p(lam), gamma, _p(grad), _p(x))
+    return g, grad, x
+
+
+def row_sq(p: Problem):
+    out = np.empty(p.J)
+    _load().orc_row_sq(ctypes.byref(p._s), _p(out))
+    return out
+
+
+def certify(p: Problem, lam, gamma):
+    """dict(g, primal, rel_gap, max_viol, uncert_gap, primal_unscaled)."""
+    lam = np.ascontiguousarray(lam, dtype=np.float64)
+    out = np.empty(6)
+    _load().orc_certify(ctypes.byref(p._s), _p(lam), gamma, _p(out))
+    return dict(g=out[0], primal=out[1], rel_gap=out[2], max_viol=out[3], uncert_gap=out[4],
+                primal_unscaled=out[5])
+
+
+def fista(p: Problem, T, gamma0, gamma_end=None, factor=0.5, iters_per_stage=0, precondition=False, lam0=None,
+          trajectory=True):
+    """T iterations of accelerated projected dual ascent; dict(lam, y, theta,
+    g_traj, gamma_traj)."""
+    gamma_end = gamma0 if gamma_end is None else gamma_end
+    lam0 = np.zeros(p.J) if lam0 is None else np.ascontiguousarray(lam0, dtype=np.float64)
+    lam, y = np.empty(p.J), np.empty(p.J)
+    th = ctypes.c_double()
+    gt = np.empty(T) if trajectory else None
+    gg = np.empty(T) if trajectory else None
+    _load().orc_fista(ctypes.byref(p._s), gamma0, gamma_end, factor, iters_per_stage, int(bool(precondition)), T,
+                      _p(lam0), _p(lam), _p(y), ctypes.byref(th), _p(gt), _p(gg))
+    return dict(lam=lam, y=y, theta=th.value, g_traj=gt, gamma_traj=gg)
+
+
+def stage_gamma(gamma0, gamma_end, factor, s):
+    return _load().orc_stage_gamma(gamma0, gamma_end, factor, s)

@@ -1,0 +1,428 @@
+#!/usr/bin/env python3
+"""Throughput of the dual sweep (nnz*iters/s) on one GB300, with the
+roofline of the sweep kernel, the end-to-end number through the C-ABI with
+host buffers, and the FP64 CPU oracle timed beside it.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--workload precision]
+    python bench.py --impl reference ...   # the oracle arm
+
+One step = `--iters` iterations (sweep + accelerated update) of the hot path
+on the workload's instance.  Inputs are generated on the host (seeded), then
+made resident in HBM before the timed region; the instance (>= 6 GB) is far
+larger than L2, so no flush is needed between iterations.
+Under torchrun (N > 1) each rank solves its own replica (the single-GPU path
+does not exchange data), and `value` is the sum over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "nnz·iters/s (% HBM peak); time-to-1e-4 rel. dual gap, learned+BF16 vs plain"
+UNIT = "nnz·iters/s"
+
+WORKLOADS = {
+    "precision": dict(
+        desc="precision form: 80M users x 5,000 items, ~2.0B nnz; degree truncated lognormal (mean 25, max 500), "
+             "item popularity ~ rank^-0.8; c = -LogNormal(0,0.5), a = U(0.5,1.5) stored BF16; int32 item idx, "
+             "int64 row_ptr; b_j = 0.05 sum_i a_ij; gamma = 1e-3 fixed",
+        users=80_000_000, items=5_000, seed=1002, bf16=True, schedule=(1e-3, 1e-3, 0.5, 1 << 30)),
+    "production": dict(
+        desc="production shape: 20M users x 2,000 items, ~500M nnz; same generators; c, a FP32; "
+             "gamma continuation 1e-1 -> 1e-3 halved every 100 iterations",
+        users=20_000_000, items=2_000, seed=1001, bf16=False, schedule=(1e-1, 1e-3, 0.5, 100)),
+    "tiny": dict(
+        desc="tiny: 10,000 users x 100 items, ~100k nnz, 1+Poisson(9) degree, uniform items, c=-U(0,1), a=1, "
+             "b_j = 0.05 deg_j, gamma = 1e-2",
+        users=10_000, items=100, seed=1000, bf16=False, schedule=(1e-2, 1e-2, 0.5, 1 << 30)),
+}
+
+
+def recipe_for(name, scale):
+    import synth
+
+    w = WORKLOADS[name]
+    I = max(1000, int(round(w["users"] * scale)))
+    if name == "tiny":
+        return synth.recipe_tiny(w["seed"])
+    if name == "production":
+        return synth.recipe_production(I=I, J=w["items"], seed=w["seed"])
+    return synth.recipe_precision(I=I, J=w["items"], seed=w["seed"])
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def sweep_source_hash():
+    h = hashlib.sha256()
+    for f in ("sweep.cu", "dlm_impl.cuh"):
+        with open(os.path.join(ROOT, "paper_2606_07777_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(workload, nnz, users):
+    """DRAM bytes per sweep launch from the committed ncu summary, scaled to
+    this instance, or None if the kernel changed since it was captured."""
+    p = os.path.join(ROOT, "profiles", "sweep_traffic.json")
+    if not os.path.exists(p):
+        return None
+    try:
+        with open(p) as f:
+            d = json.load(f)
+        rec = d.get(workload)
+        if not rec or rec.get("source_hash") != sweep_source_hash():
+            return None
+        return rec["bytes_per_nnz"] * nnz + rec.get("bytes_per_user", 0.0) * users
+    except Exception:
+        return None
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, dev_id):
+        self.dev_id = dev_id
+        self.proc = None
+
+    def start(self):
+        try:
+            cmd = ["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits", "-lms", "200"]
+            if self.dev_id is not None:
+                cmd += ["-i", str(self.dev_id)]
+            self.proc = subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except Exception:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+def gpu_id_for_smi(torch, dev):
+    try:
+        u = str(torch.cuda.get_device_properties(dev).uuid)
+        if u:
+            return u if u.startswith("GPU-") else "GPU-" + u
+    except Exception:
+        pass
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES")
+    if vis:
+        return vis.split(",")[dev.index or 0]
+    return dev.index or 0
+
+
+def make_instance(recipe, bf16, torch, pinned, threads):
+    import numpy as np
+    import synth
+
+    def pin_alloc(n, dtype):
+        t = torch.empty(int(n), dtype={np.int64: torch.int64, np.int32: torch.int32, np.float32: torch.float32,
+                                       np.uint16: torch.int16}[np.dtype(dtype).type], pin_memory=pinned)
+        return t.numpy().view(dtype)
+
+    if bf16:
+        inst = synth.generate(recipe, nthreads=threads, alloc=lambda n, dt: pin_alloc(n, dt) if dt != np.float32
+                              else np.empty(int(n), dt))
+        c16 = pin_alloc(inst.nnz, np.uint16)
+        a16 = pin_alloc(inst.nnz, np.uint16)
+        synth.round_bf16(inst.c, threads, c16)
+        synth.round_bf16(inst.a, threads, a16)
+        inst.c, inst.a = c16, a16
+    else:
+        inst = synth.generate(recipe, nthreads=threads, alloc=pin_alloc)
+    return inst
+
+
+def cpu_sample(workload, bf16, frac, seed=4242, threads=0):
+    """A seeded user sample of the workload, regenerated row by row, as an
+    FP64 oracle problem (BF16 values widened exactly)."""
+    import numpy as np
+    import oracle
+    import synth
+
+    r = recipe_for(workload, 1.0 if workload != "tiny" else 1.0)
+    if workload == "tiny":
+        inst = synth.generate(r)
+    else:
+        ids = synth.sample_users(r.I, frac, seed)
+        inst = synth.generate(r, ids=ids, nthreads=threads)
+    c, a = inst.c, inst.a
+    if bf16:
+        c = synth.bf16_to_f32(synth.round_bf16(c))
+        a = synth.bf16_to_f32(synth.round_bf16(a))
+    return oracle.Problem(inst.row_ptr, inst.col, c.astype(np.float64), a.astype(np.float64), inst.b, inst.J)
+
+
+def time_oracle(p, gamma, budget_s):
+    """Oracle iterations on problem p for about budget_s seconds; returns
+    (nnz*iters/s, iters, seconds)."""
+    import oracle
+
+    t0 = time.perf_counter()
+    oracle.fista(p, 1, gamma, trajectory=False)
+    t1 = time.perf_counter() - t0
+    iters = max(1, int(budget_s / max(t1, 1e-6)))
+    t0 = time.perf_counter()
+    oracle.fista(p, iters, gamma, trajectory=False)
+    dt = time.perf_counter() - t0
+    return p.nnz * iters / dt, iters, dt
+
+
+def run_reference(args, rank, world):
+    w = WORKLOADS[args.workload]
+    if rank != 0:
+        return 0
+    frac = args.cpu_frac
+    p = cpu_sample(args.workload, w["bf16"], frac)
+    gamma = w["schedule"][1]
+    per_step = []
+    for k in range(args.warmup + args.steps):
+        v, iters, dt = time_oracle(p, gamma, args.ref_step_seconds)
+        if k >= args.warmup:
+            per_step.append((v, iters, dt))
+    total_nnz_iters = sum(p.nnz * it for _, it, _ in per_step)
+    total_s = sum(dt for _, _, dt in per_step)
+    value = total_nnz_iters / total_s
+    sample = (f"{'all' if args.workload == 'tiny' else f'{frac:.2%} seeded user sample'} of the {args.workload} "
+              f"workload ({p.I} users, {p.nnz} nnz), FP64 oracle iterations (sweep + accelerated update), "
+              f"{per_step[0][1]} iterations per step")
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1000 * total_s / len(per_step), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+        "config": {"workload": WORKLOADS[args.workload]["desc"], "parallelism": "replicas"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=list(WORKLOADS), default="precision")
+    ap.add_argument("--iters", type=int, default=100, help="iterations per step")
+    ap.add_argument("--scale", type=float, default=1.0, help="fraction of the workload's users (smoke runs)")
+    ap.add_argument("--threads", type=int, default=0, help="host threads for instance generation")
+    ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--cpu-frac", type=float, default=0.01)
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--ref-step-seconds", type=float, default=6.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+
+    import numpy as np
+    import torch
+
+    import paper_2606_07777_gb300 as dlm
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=dev)
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    def max_over_ranks(v):
+        if dist is None:
+            return v
+        t = torch.tensor([v], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    w = WORKLOADS[args.workload]
+    bf16 = w["bf16"]
+    recipe = recipe_for(args.workload, args.scale)
+    t_gen = time.perf_counter()
+    inst = make_instance(recipe, bf16, torch, True, args.threads)
+    t_gen = time.perf_counter() - t_gen
+
+    # Device-resident inputs.
+    def dev_arrays():
+        rp = torch.from_numpy(inst.row_ptr).to(dev, non_blocking=True)
+        col = torch.from_numpy(inst.col).to(dev, non_blocking=True)
+        if bf16:
+            c = torch.from_numpy(inst.c.view(np.int16)).to(dev, non_blocking=True).view(torch.bfloat16)
+            a = torch.from_numpy(inst.a.view(np.int16)).to(dev, non_blocking=True).view(torch.bfloat16)
+        else:
+            c = torch.from_numpy(inst.c).to(dev, non_blocking=True)
+            a = torch.from_numpy(inst.a).to(dev, non_blocking=True)
+        b = torch.from_numpy(inst.b).to(dev, non_blocking=True)
+        torch.cuda.synchronize(dev)
+        return rp, col, c, a, b
+
+    dlm.load()
+    t_setup = time.perf_counter()
+    arrs = dev_arrays()
+    s = dlm.Solver(*arrs, inst.J, bf16=bf16)
+    del arrs
+    torch.cuda.synchronize(dev)
+    t_setup = time.perf_counter() - t_setup
+    s.set_schedule(*w["schedule"])
+    info = s.info()
+    nnz, I, J, bytes_iter = info["nnz"], info["num_users"], info["num_items"], info["bytes_per_iter"]
+
+    for _ in range(args.warmup):
+        s.step(args.iters)
+    torch.cuda.synchronize(dev)
+
+    # ---- timed region: K steps, every kernel bracketed by CUDA events ----
+    sampler = ClockSampler(gpu_id_for_smi(torch, dev))
+    sampler.start()
+    time.sleep(0.3)
+    barrier()
+    torch.cuda.synchronize(dev)
+    sweep_ms = upd_ms = tot_ms = 0.0
+    for _ in range(args.steps):
+        a_, b_, c_ = s.step_timed(args.iters)
+        sweep_ms += a_
+        upd_ms += b_
+        tot_ms += c_
+    torch.cuda.synchronize(dev)
+    barrier()
+    clocks = sampler.stop()
+    elapsed_s = max_over_ranks(tot_ms / 1000.0)
+    iters_total = args.iters * args.steps
+    value = world * nnz * iters_total / elapsed_s
+
+    # Same steps replayed through the captured CUDA graphs (the default path).
+    st = torch.cuda.current_stream(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(st)
+    for _ in range(args.steps):
+        s.step(args.iters)
+    e1.record(st)
+    torch.cuda.synchronize(dev)
+    graph_ms_per_step = e0.elapsed_time(e1) / args.steps
+
+    # ---- end to end through the C-ABI: host (pinned) inputs -> create ->
+    # iterations -> lam back to the host, every step ----
+    lam_host = torch.empty(J, dtype=torch.float32, pin_memory=True)
+    h2d = inst.row_ptr.nbytes + inst.col.nbytes + inst.c.nbytes + inst.a.nbytes + inst.b.nbytes
+    del s
+    torch.cuda.synchronize(dev)
+    e2e_times = []
+    for k in range(args.e2e_steps + 1 if args.e2e_steps > 0 else 0):
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        s2 = dlm.Solver(inst.row_ptr, inst.col, inst.c, inst.a, inst.b, inst.J, bf16=bf16)
+        s2.set_schedule(*w["schedule"])
+        s2.step(args.iters)
+        dlm.dlm_get_lambda(s2.h, lam_host, dlm.DLM_MEM_HOST)
+        s2.close()
+        dt = time.perf_counter() - t0
+        if k > 0:  # first call warms the allocator
+            e2e_times.append(dt)
+    e2e_value = None
+    if e2e_times:
+        e2e_s = max_over_ranks(statistics.mean(e2e_times))
+        e2e_value = world * nnz * args.iters / e2e_s
+
+    # ---- roofline of the dominant kernel (the sweep) ----
+    peak, peak_kind = load_peaks()
+    sweep_s = sweep_ms / 1000.0 / iters_total
+    achieved = bytes_iter / sweep_s / 1e9
+    traffic = recorded_traffic(args.workload, nnz, I) if args.scale == 1.0 else None
+    roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+            "traffic": traffic, "peak_source": f"{peak_kind} (copy bandwidth, MEASURED_PEAKS.json)"
+            if peak_kind == "measured" else "fallback 6.8 TB/s",
+            "kernel": "sweep_kernel", "algorithmic_bytes_per_launch": bytes_iter,
+            "sweep_share_of_iteration": sweep_ms / tot_ms if tot_ms > 0 else None,
+            "sweep_us": sweep_s * 1e6, "update_us": upd_ms * 1000.0 / iters_total}
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        p = cpu_sample(args.workload, bf16, args.cpu_frac, threads=args.threads)
+        v, iters, dt = time_oracle(p, w["schedule"][1], args.cpu_seconds)
+        cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": (f"{'all' if args.workload == 'tiny' else f'{args.cpu_frac:.0%} seeded user sample'} of "
+                          f"the workload ({p.I} users, {p.nnz} nnz), {iters} FP64 oracle iterations in {dt:.1f} s")}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": elapsed_s * 1000.0 / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": w["desc"] if args.scale == 1.0 else w["desc"] + f" (users scaled x{args.scale})",
+                   "users": I, "items": J, "nnz": nnz, "storage": "bf16" if bf16 else "f32",
+                   "iters_per_step": args.iters, "parallelism": "replicas" if world > 1 else "single GPU",
+                   "l2": f"inputs {bytes_iter / 1e9:.1f} GB per iteration >> 129 MB L2 (no flush)"
+                   if bytes_iter > 1.3e8 else "inputs fit in L2 (tiny case)"},
+        "roofline": roof,
+        "cpu_baseline": cpu,
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(J * 4),
+                "note": "per step: dlm_create from pinned host arrays (copy + layout), iterations, lam to host"},
+        "gpu_launches": 2 * iters_total,
+        "clocks": clocks,
+        "graph_ms_per_step": graph_ms_per_step,
+        "setup_s": {"generate": t_gen, "upload_and_create": t_setup},
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,201 @@
+/*
+ * dlm.h -- C-ABI of the GB300 dual-sweep solver for ridge-regularized
+ * matching LPs.
+ *
+ * The problem (Sec. 3.1, Eq. primal; Sec. 3.3, Eq. dest-capacity):
+ *
+ *     min_x  sum_ij c_ij x_ij + (gamma/2) sum_ij x_ij^2
+ *     s.t.   sum_i a_ij x_ij <= b_j            for every item j,
+ *            x_i in C_i                        for every user i,
+ *
+ * over the eligible edges (i, j) only.  C_i is the simplex
+ * {x_i >= 0, sum_j x_ij <= z} (DLM_SIMPLEX_LE), the simplex with equality
+ * (DLM_SIMPLEX_EQ) or the box [0, z]^n (DLM_BOX).  Only the capacities carry
+ * dual variables lam >= 0 (Sec. 3.2, Eq. dual).  Each iteration evaluates the
+ * dual at a point y (Eq. primal-recovery: x(y) = Proj_C(-(A^T y + c)/gamma);
+ * Eq. dual-gradient: grad g(y) = A x(y) - b), then takes a projected
+ * accelerated step on lam >= 0 (Sec. 4.4) under a gamma-continuation schedule
+ * (Sec. 6; App. B.2).
+ *
+ * Conventions for every call:
+ *  - Every call returns a dlm_status and never aborts; on failure
+ *    dlm_last_error() gives a thread-local message.
+ *  - "device" pointers are CUDA global-memory addresses of the current device;
+ *    "host" pointers are ordinary (preferably pinned) host memory.  Calls
+ *    taking a dlm_memspace argument accept either.
+ *  - All GPU work of a handle is ordered on the CUDA stream given at creation.
+ *    Calls that return host-visible results (dlm_solve, dlm_get_stats,
+ *    dlm_calculate's scalar, host-memspace reads) synchronize that stream.
+ *  - A handle is not thread-safe; distinct handles are independent.
+ *  - Array layouts are plain C order; all sizes are element counts.
+ */
+#ifndef DLM_H
+#define DLM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  DLM_OK = 0,
+  DLM_ERR_INVALID_ARG = 1, /* bad sizes, pointers, NaN/Inf data, gamma <= 0, ... */
+  DLM_ERR_OOM = 2,         /* a device or host allocation failed */
+  DLM_ERR_CUDA = 3,        /* a CUDA runtime call failed */
+  DLM_ERR_NUMERIC = 4,     /* a NaN/Inf appeared in the iteration */
+  DLM_ERR_TIMEOUT = 5,     /* an iteration limit was reached before the target */
+  DLM_ERR_UNSUPPORTED = 6  /* valid input outside what this build handles */
+} dlm_status;
+
+typedef enum { DLM_F32 = 0, DLM_BF16 = 1 } dlm_dtype;
+typedef enum { DLM_SIMPLEX_LE = 0, DLM_SIMPLEX_EQ = 1, DLM_BOX = 2 } dlm_simple_kind;
+typedef enum { DLM_MEM_DEVICE = 0, DLM_MEM_HOST = 1 } dlm_memspace;
+
+/* The instance, as user-major CSR (the paper stores the same data as CSC with
+ * one column per source, Sec. 4.1; one column per user is one CSR row here).
+ *   row_ptr  int64 [num_users + 1], row_ptr[0] = 0, non-decreasing,
+ *            row_ptr[num_users] = nnz
+ *   item_idx int32 [nnz], 0 <= item_idx < num_items (the eligible items of
+ *            each user; a repeated item in one row is a parallel edge)
+ *   c, a     [nnz] float32 (val_dtype DLM_F32) or bfloat16 bit patterns
+ *            (DLM_BF16, stored as uint16); all finite
+ *   b        float64 [num_items], finite, >= 0
+ * The arrays live in `memspace`.  dlm_create copies them into its own layout;
+ * the caller may free or reuse them once dlm_create has returned. */
+typedef struct {
+  int64_t num_users, num_items, nnz;
+  const int64_t* row_ptr;
+  const int32_t* item_idx;
+  const void* c;
+  const void* a;
+  const double* b;
+  int32_t val_dtype; /* dlm_dtype */
+  int32_t kind;      /* dlm_simple_kind */
+  double z;          /* simplex radius or box bound, > 0 */
+  int32_t memspace;  /* dlm_memspace of the arrays above */
+  int32_t reserved;
+} dlm_problem_desc;
+
+/* Solver options (zero-initialised fields take the defaults). */
+typedef struct {
+  int32_t gap_every;    /* iterations between certified-gap checks in dlm_solve (default 50) */
+  int32_t precondition; /* 1: row normalization (App. B.2) as the per-item step gamma/sum_i a_ij^2 */
+  int32_t mapping;      /* degree-bucket mapping table: -1 default/autotuned, >= 0 a fixed table */
+  int32_t graph_iters;  /* iterations per captured CUDA graph (default 10) */
+  int32_t ctas_per_sm;  /* persistent sweep CTAs per SM (0: from occupancy) */
+  int32_t reserved[3];
+} dlm_options;
+
+/* Result of a certified-gap evaluation at the current iterate lam (one extra
+ * sweep at lam; App. B.1-style objective tracking):
+ *   dual_obj    g(lam)
+ *   primal_obj  P(x~), x~_ij = s_j x_ij(lam), s_j = min(1, b_j / (A x(lam))_j)
+ *               (feasible for simplex-<= and box sets when a, b >= 0)
+ *   rel_gap     (primal_obj - dual_obj) / max(|dual_obj|, 1e-30) (>= 0)
+ *   uncert_gap  -lam^T (A x(lam) - b) / max(|dual_obj|, 1e-30)
+ *   max_viol    max_j (A x(lam) - b)_j^+
+ * For DLM_SIMPLEX_EQ or negative a the scaled point is not certified and
+ * rel_gap is NaN. */
+typedef struct {
+  int64_t iter;   /* iterations taken so far */
+  double gamma;   /* ridge of the current stage */
+  double dual_obj, primal_obj, rel_gap, uncert_gap, max_viol;
+  double seconds; /* wall time of the last dlm_solve */
+  int32_t status; /* dlm_status of the device-side checks */
+  int32_t converged;
+} dlm_stats;
+
+/* Iteration state for checkpoint / resume (besides the lam and y vectors). */
+typedef struct {
+  int64_t iter;  /* global iteration counter t */
+  double theta;  /* accelerated-momentum scalar */
+  int32_t stage; /* continuation stage index */
+  int32_t reserved;
+} dlm_state;
+
+typedef struct dlm_problem dlm_problem;
+typedef struct dlm_batch dlm_batch;
+
+/* Create a solver handle for one instance (Sec. 3.3 matching LP).  Validates
+ * the input (returns DLM_ERR_INVALID_ARG with a message on non-monotone
+ * row_ptr, out-of-range items, non-finite values, b < 0, z <= 0), buckets
+ * users by degree and lays the edges out for the sweep kernels.  `stream` is
+ * a cudaStream_t; with NULL the handle creates its own blocking stream,
+ * which is ordered with the legacy default stream in both directions.  Initial state: lam = 0,
+ * fixed gamma = 1e-2, no preconditioning.  Synchronous. */
+dlm_status dlm_create(const dlm_problem_desc* desc, void* stream, dlm_problem** out);
+
+/* gamma schedule (Sec. 6, App. B.2 "regularization decay"): iteration t is in
+ * stage s = t / iters_per_stage; gamma_0 = gamma0 and
+ * gamma_{s+1} = max(gamma_end, gamma_s * factor).  When gamma changes at a
+ * stage boundary the momentum restarts (theta = 1, y = lam), lam is kept as the
+ * warm start, and the step 1/L, L = max_j sum_i a_ij^2 / gamma, follows gamma.
+ * gamma0 == gamma_end gives a fixed ridge.  Requires gamma_end > 0,
+ * gamma0 >= gamma_end, 0 < factor <= 1, iters_per_stage >= 1.  Resets the
+ * iteration counter and momentum (lam is kept). */
+dlm_status dlm_set_schedule(dlm_problem* p, double gamma0, double gamma_end, double factor,
+                            int64_t iters_per_stage);
+
+dlm_status dlm_set_options(dlm_problem* p, const dlm_options* opt);
+
+/* Warm start: lam <- max(lambda0, 0), y <- lam, theta <- 1, iteration counter
+ * kept.  lambda0 has num_items float32 entries in `memspace`. */
+dlm_status dlm_set_lambda(dlm_problem* p, const float* lambda0, int32_t memspace);
+
+/* One dual evaluation (the paper's ObjectiveFunction.calculate, Table 1):
+ * at lambda (device, num_items float32, >= 0 expected) and ridge gamma,
+ * writes g(lambda) to *g (host double), grad g(lambda) = A x - b to grad
+ * (device, num_items float32; may be NULL) and x(lambda) in the caller's
+ * CSR edge order to x (device, nnz float32; may be NULL).  Synchronous. */
+dlm_status dlm_calculate(dlm_problem* p, const float* lambda, double gamma, double* g, float* grad, float* x);
+
+/* Run n_iters iterations (asynchronous on the handle's stream; replays
+ * captured CUDA graphs). */
+dlm_status dlm_step(dlm_problem* p, int64_t n_iters);
+
+/* Iterate until the certified relative gap at lam is <= target_rel_gap while
+ * gamma is at its final value, checking every gap_every iterations, or until
+ * max_iters iterations in total (then DLM_ERR_TIMEOUT).  Fills *out (may be
+ * NULL), including the wall time.  Synchronous. */
+dlm_status dlm_solve(dlm_problem* p, double target_rel_gap, int64_t max_iters, dlm_stats* out);
+
+/* Certified-gap evaluation at the current lam (one sweep; see dlm_stats). */
+dlm_status dlm_get_stats(dlm_problem* p, dlm_stats* out);
+
+/* Current lam (num_items float32) into `memspace`. */
+dlm_status dlm_get_lambda(dlm_problem* p, float* out, int32_t memspace);
+
+/* x(lam) for the current lam and gamma, in the caller's CSR edge order
+ * (nnz float32) into `memspace`. */
+dlm_status dlm_get_x(dlm_problem* p, float* out, int32_t memspace);
+
+/* Checkpoint / resume: lam and y (num_items float32 each, `memspace`) and the
+ * scalar state.  dlm_set_state restores exactly the trajectory that
+ * dlm_get_state saved (same schedule and options assumed). */
+dlm_status dlm_get_state(dlm_problem* p, float* lam, float* y, dlm_state* s, int32_t memspace);
+dlm_status dlm_set_state(dlm_problem* p, const float* lam, const float* y, const dlm_state* s, int32_t memspace);
+
+/* Run n_iters iterations as individual kernel launches with a CUDA event
+ * recorded on the handle's stream between consecutive kernels, and return the
+ * summed device time of the sweep kernels (*sweep_ms), of the update kernels
+ * (*update_ms) and of the whole sequence (*total_ms) (each may be NULL).
+ * Same arithmetic as dlm_step; used to measure kernel durations.
+ * Synchronous. */
+dlm_status dlm_step_timed(dlm_problem* p, int64_t n_iters, double* sweep_ms, double* update_ms, double* total_ms);
+
+/* Sizes of the handle's instance and the bytes per iteration the sweep must
+ * read (the algorithmic traffic: item index + c + a per edge, plus the row
+ * pointer per user). */
+dlm_status dlm_get_info(dlm_problem* p, int64_t* num_users, int64_t* num_items, int64_t* nnz,
+                        int64_t* bytes_per_iter);
+
+void dlm_destroy(dlm_problem* p);
+
+/* Thread-local message describing the last failure on this thread ("" if none). */
+const char* dlm_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DLM_H */

@@ -1,0 +1,321 @@
+"""GB300 dual-sweep solver for ridge-regularized matching LPs.
+
+Thin Python binding of the C-ABI in ``include/dlm.h`` (library
+``libdlm.so``, hand-written sm_103a CUDA kernels).  This module only marshals
+arguments: every step of the iteration runs in the library's kernels.  There
+is no CPU path; if the library cannot be built or loaded, ``load()`` raises.
+
+PyTorch is used for device memory and streams: pass CUDA tensors (device
+memspace) or CPU tensors / numpy arrays (host memspace).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+from . import _build
+
+__all__ = [
+    "load", "build", "DlmError", "Solver", "dlm_create", "dlm_set_schedule", "dlm_set_options", "dlm_set_lambda",
+    "dlm_calculate", "dlm_step", "dlm_solve", "dlm_get_stats", "dlm_get_lambda", "dlm_get_x", "dlm_get_state",
+    "dlm_set_state", "dlm_get_info", "dlm_step_timed", "dlm_destroy", "dlm_last_error",
+]
+
+DLM_OK, DLM_ERR_INVALID_ARG, DLM_ERR_OOM, DLM_ERR_CUDA, DLM_ERR_NUMERIC, DLM_ERR_TIMEOUT, DLM_ERR_UNSUPPORTED = range(7)
+DLM_F32, DLM_BF16 = 0, 1
+DLM_SIMPLEX_LE, DLM_SIMPLEX_EQ, DLM_BOX = 0, 1, 2
+DLM_MEM_DEVICE, DLM_MEM_HOST = 0, 1
+
+_STATUS = {0: "DLM_OK", 1: "DLM_ERR_INVALID_ARG", 2: "DLM_ERR_OOM", 3: "DLM_ERR_CUDA", 4: "DLM_ERR_NUMERIC",
+           5: "DLM_ERR_TIMEOUT", 6: "DLM_ERR_UNSUPPORTED"}
+
+
+class DlmError(RuntimeError):
+    def __init__(self, status, where, msg):
+        super().__init__(f"{where}: {_STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class ProblemDesc(ctypes.Structure):
+    _fields_ = [("num_users", ctypes.c_int64), ("num_items", ctypes.c_int64), ("nnz", ctypes.c_int64),
+                ("row_ptr", ctypes.c_void_p), ("item_idx", ctypes.c_void_p), ("c", ctypes.c_void_p),
+                ("a", ctypes.c_void_p), ("b", ctypes.c_void_p), ("val_dtype", ctypes.c_int32),
+                ("kind", ctypes.c_int32), ("z", ctypes.c_double), ("memspace", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
+
+
+class Options(ctypes.Structure):
+    _fields_ = [("gap_every", ctypes.c_int32), ("precondition", ctypes.c_int32), ("mapping", ctypes.c_int32),
+                ("graph_iters", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 3)]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("iter", ctypes.c_int64), ("gamma", ctypes.c_double), ("dual_obj", ctypes.c_double),
+                ("primal_obj", ctypes.c_double), ("rel_gap", ctypes.c_double), ("uncert_gap", ctypes.c_double),
+                ("max_viol", ctypes.c_double), ("seconds", ctypes.c_double), ("status", ctypes.c_int32),
+                ("converged", ctypes.c_int32)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class State(ctypes.Structure):
+    _fields_ = [("iter", ctypes.c_int64), ("theta", ctypes.c_double), ("stage", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
+
+
+_lib = None
+
+# (name, argtypes) of every exported call, in header order.
+_vp, _i64, _i32, _d = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_double
+_SIGS = {
+    "dlm_create": [ctypes.POINTER(ProblemDesc), _vp, ctypes.POINTER(_vp)],
+    "dlm_set_schedule": [_vp, _d, _d, _d, _i64],
+    "dlm_set_options": [_vp, ctypes.POINTER(Options)],
+    "dlm_set_lambda": [_vp, _vp, _i32],
+    "dlm_calculate": [_vp, _vp, _d, ctypes.POINTER(_d), _vp, _vp],
+    "dlm_step": [_vp, _i64],
+    "dlm_solve": [_vp, _d, _i64, ctypes.POINTER(Stats)],
+    "dlm_get_stats": [_vp, ctypes.POINTER(Stats)],
+    "dlm_get_lambda": [_vp, _vp, _i32],
+    "dlm_get_x": [_vp, _vp, _i32],
+    "dlm_get_state": [_vp, _vp, _vp, ctypes.POINTER(State), _i32],
+    "dlm_set_state": [_vp, _vp, _vp, ctypes.POINTER(State), _i32],
+    "dlm_get_info": [_vp, ctypes.POINTER(_i64), ctypes.POINTER(_i64), ctypes.POINTER(_i64), ctypes.POINTER(_i64)],
+    "dlm_step_timed": [_vp, _i64, ctypes.POINTER(_d), ctypes.POINTER(_d), ctypes.POINTER(_d)],
+}
+EXPORTS = list(_SIGS) + ["dlm_destroy", "dlm_last_error"]
+
+
+def build(force: bool = False) -> str:
+    return _build.build(force=force)
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load():
+    """Load ``libdlm.so`` (building it first if it is missing or stale).
+    Raises if it cannot be built or loaded: there is no fallback."""
+    global _lib
+    if _lib is None:
+        if not _build.up_to_date():
+            _build.build()
+        lib = ctypes.CDLL(_build.LIB)
+        for name, args in _SIGS.items():
+            f = getattr(lib, name)
+            f.argtypes = args
+            f.restype = ctypes.c_int
+        lib.dlm_destroy.argtypes = [_vp]
+        lib.dlm_destroy.restype = None
+        lib.dlm_last_error.argtypes = []
+        lib.dlm_last_error.restype = ctypes.c_char_p
+        _lib = lib
+    return _lib
+
+
+def dlm_last_error() -> str:
+    return load().dlm_last_error().decode()
+
+
+def _call(name, *args):
+    lib = load()
+    st = getattr(lib, name)(*args)
+    if st != DLM_OK:
+        raise DlmError(st, name, lib.dlm_last_error().decode())
+    return st
+
+
+def _ptr(x):
+    """Address of a torch tensor, numpy array or None."""
+    if x is None:
+        return None
+    if hasattr(x, "data_ptr"):
+        return x.data_ptr()
+    if hasattr(x, "ctypes"):
+        return x.ctypes.data
+    return int(x)
+
+
+def dlm_create(desc: ProblemDesc, stream=None):
+    h = ctypes.c_void_p()
+    _call("dlm_create", ctypes.byref(desc), stream, ctypes.byref(h))
+    return h
+
+
+def dlm_set_schedule(h, gamma0, gamma_end, factor, iters_per_stage):
+    _call("dlm_set_schedule", h, gamma0, gamma_end, factor, iters_per_stage)
+
+
+def dlm_set_options(h, opt: Options):
+    _call("dlm_set_options", h, ctypes.byref(opt))
+
+
+def dlm_set_lambda(h, lam, memspace):
+    _call("dlm_set_lambda", h, _ptr(lam), memspace)
+
+
+def dlm_calculate(h, lam, gamma, grad=None, x=None) -> float:
+    g = ctypes.c_double()
+    _call("dlm_calculate", h, _ptr(lam), gamma, ctypes.byref(g), _ptr(grad), _ptr(x))
+    return g.value
+
+
+def dlm_step(h, n):
+    _call("dlm_step", h, n)
+
+
+def dlm_solve(h, target, max_iters) -> Stats:
+    s = Stats()
+    lib = load()
+    st = lib.dlm_solve(h, target, max_iters, ctypes.byref(s))
+    if st not in (DLM_OK, DLM_ERR_TIMEOUT):
+        raise DlmError(st, "dlm_solve", lib.dlm_last_error().decode())
+    return s
+
+
+def dlm_get_stats(h) -> Stats:
+    s = Stats()
+    _call("dlm_get_stats", h, ctypes.byref(s))
+    return s
+
+
+def dlm_get_lambda(h, out, memspace):
+    _call("dlm_get_lambda", h, _ptr(out), memspace)
+
+
+def dlm_get_x(h, out, memspace):
+    _call("dlm_get_x", h, _ptr(out), memspace)
+
+
+def dlm_get_state(h, lam, y, memspace) -> State:
+    s = State()
+    _call("dlm_get_state", h, _ptr(lam), _ptr(y), ctypes.byref(s), memspace)
+    return s
+
+
+def dlm_set_state(h, lam, y, state: State, memspace):
+    _call("dlm_set_state", h, _ptr(lam), _ptr(y), ctypes.byref(state), memspace)
+
+
+def dlm_get_info(h):
+    v = [ctypes.c_int64() for _ in range(4)]
+    _call("dlm_get_info", h, *[ctypes.byref(x) for x in v])
+    return dict(num_users=v[0].value, num_items=v[1].value, nnz=v[2].value, bytes_per_iter=v[3].value)
+
+
+def dlm_step_timed(h, n):
+    """(sweep_ms, update_ms, total_ms) summed over n individually launched iterations."""
+    v = [ctypes.c_double() for _ in range(3)]
+    _call("dlm_step_timed", h, n, *[ctypes.byref(x) for x in v])
+    return tuple(x.value for x in v)
+
+
+def dlm_destroy(h):
+    if h:
+        load().dlm_destroy(h)
+
+
+class Solver:
+    """One matching-LP instance on the GPU.
+
+    Arrays may be CUDA tensors (device memspace) or CPU tensors / numpy
+    arrays (host memspace; copied in by ``dlm_create``).  ``c``/``a`` are
+    float32, or bfloat16 (torch.bfloat16 tensors or uint16 bit patterns with
+    ``bf16=True``)."""
+
+    def __init__(self, row_ptr, col, c, a, b, num_items=None, kind=DLM_SIMPLEX_LE, z=1.0, bf16=None, stream=None):
+        import torch
+
+        self._torch = torch
+        dev = getattr(row_ptr, "is_cuda", False)
+        if bf16 is None:
+            bf16 = getattr(c, "dtype", None) in (torch.bfloat16,) or str(getattr(c, "dtype", "")) == "uint16"
+        self.num_items = int(num_items if num_items is not None else len(b))
+        self.num_users = int(row_ptr.shape[0] - 1)
+        self.nnz = int(col.shape[0])
+        self.bf16 = bool(bf16)
+        desc = ProblemDesc()
+        desc.num_users, desc.num_items, desc.nnz = self.num_users, self.num_items, self.nnz
+        desc.row_ptr, desc.item_idx, desc.c, desc.a, desc.b = (_ptr(row_ptr), _ptr(col), _ptr(c), _ptr(a), _ptr(b))
+        desc.val_dtype = DLM_BF16 if self.bf16 else DLM_F32
+        desc.kind, desc.z = int(kind), float(z)
+        desc.memspace = DLM_MEM_DEVICE if dev else DLM_MEM_HOST
+        self.device = torch.device("cuda", torch.cuda.current_device())
+        if stream is None:
+            stream = torch.cuda.current_stream(self.device)
+        self.stream = stream
+        self._keep = (row_ptr, col, c, a, b)
+        self.h = dlm_create(desc, ctypes.c_void_p(stream.cuda_stream))
+        self._keep = None
+        self.kind = int(kind)
+        self.z = float(z)
+
+    def close(self):
+        if getattr(self, "h", None):
+            dlm_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_schedule(self, gamma0, gamma_end=None, factor=0.5, iters_per_stage=1 << 30):
+        dlm_set_schedule(self.h, gamma0, gamma0 if gamma_end is None else gamma_end, factor, iters_per_stage)
+
+    def set_options(self, gap_every=0, precondition=False, mapping=-1, graph_iters=0, ctas_per_sm=0):
+        o = Options()
+        o.gap_every, o.precondition, o.mapping = gap_every, int(bool(precondition)), mapping
+        o.graph_iters, o.ctas_per_sm = graph_iters, ctas_per_sm
+        dlm_set_options(self.h, o)
+
+    def set_lambda(self, lam):
+        dlm_set_lambda(self.h, lam, DLM_MEM_DEVICE if getattr(lam, "is_cuda", False) else DLM_MEM_HOST)
+
+    def step(self, n):
+        dlm_step(self.h, n)
+
+    def step_timed(self, n):
+        return dlm_step_timed(self.h, n)
+
+    def solve(self, target_rel_gap, max_iters) -> Stats:
+        return dlm_solve(self.h, target_rel_gap, max_iters)
+
+    def stats(self) -> Stats:
+        return dlm_get_stats(self.h)
+
+    def calculate(self, lam, gamma, want_grad=True, want_x=True):
+        t = self._torch
+        grad = t.empty(self.num_items, dtype=t.float32, device=self.device) if want_grad else None
+        x = t.empty(self.nnz, dtype=t.float32, device=self.device) if want_x else None
+        g = dlm_calculate(self.h, lam, gamma, grad, x)
+        return g, grad, x
+
+    def lam(self):
+        t = self._torch
+        out = t.empty(self.num_items, dtype=t.float32, device=self.device)
+        dlm_get_lambda(self.h, out, DLM_MEM_DEVICE)
+        return out
+
+    def x(self):
+        t = self._torch
+        out = t.empty(self.nnz, dtype=t.float32, device=self.device)
+        dlm_get_x(self.h, out, DLM_MEM_DEVICE)
+        return out
+
+    def get_state(self):
+        t = self._torch
+        lam = t.empty(self.num_items, dtype=t.float32, device=self.device)
+        y = t.empty_like(lam)
+        s = dlm_get_state(self.h, lam, y, DLM_MEM_DEVICE)
+        return lam, y, s
+
+    def set_state(self, lam, y, s):
+        dlm_set_state(self.h, lam, y, s, DLM_MEM_DEVICE)
+
+    def info(self):
+        return dlm_get_info(self.h)

@@ -1,0 +1,146 @@
+// update.cu -- the O(J) kernels that follow a sweep: the accelerated
+// projected dual step with gamma continuation, and the dual objective /
+// certified-gap statistics.  One CTA per instance; every reduction runs in a
+// fixed order (thread-strided, then a fixed shuffle tree, then warps in
+// order), so results are bit-identical from run to run.
+#include <math.h>
+
+#include "dlm_impl.cuh"
+
+namespace dlm {
+namespace {
+
+constexpr unsigned kFull = 0xffffffffu;
+
+__device__ __forceinline__ double to_real(unsigned long long v, double inv_scale) {
+  return static_cast<double>(static_cast<long long>(v)) * inv_scale;
+}
+
+// Sum over the block in a fixed order; result valid in thread 0.
+__device__ double block_sum(double v, double* sh) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(kFull, v, o);
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  __syncthreads();
+  if (lane == 0) sh[w] = v;
+  __syncthreads();
+  double s = 0.0;
+  if (threadIdx.x == 0)
+    for (int k = 0; k < static_cast<int>(blockDim.x >> 5); ++k) s += sh[k];
+  __syncthreads();
+  return s;
+}
+__device__ double block_max(double v, double* sh) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_down_sync(kFull, v, o));
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  __syncthreads();
+  if (lane == 0) sh[w] = v;
+  __syncthreads();
+  double s = -INFINITY;
+  if (threadIdx.x == 0)
+    for (int k = 0; k < static_cast<int>(blockDim.x >> 5); ++k) s = fmax(s, sh[k]);
+  __syncthreads();
+  return s;
+}
+
+// Accelerated projected step (Sec. 4.4; App. B.2), for iteration t at y:
+//   G_j    = (A x(y))_j - b_j
+//   lam+_j = max(0, y_j + step_j G_j),  step_j = gamma / max_k n_k  (1/L)
+//                                         or gamma / n_j (row normalization)
+//   theta+ = (1 + sqrt(1 + 4 theta^2)) / 2,  y+ = lam+ + (theta - 1)/theta+ (lam+ - lam)
+// and, when iteration t+1 starts a stage with a different gamma, a momentum
+// restart (theta = 1, y+ = lam+).  lam and y are FP32; G is formed from the
+// exact fixed-point sum minus b and rounded once to FP32.
+__global__ void __launch_bounds__(kUpdThreads) fista_update_kernel(const UpdInst* __restrict__ tab) {
+  __shared__ double sh[32];
+  const UpdInst U = tab[blockIdx.x];
+  const DevState st = *U.state;
+  const double gamma = st.gamma;
+  const int64_t t1 = st.iter + 1;
+  const int64_t s1 = t1 / U.iters_per_stage;
+  const double gamma1 = U.gamma_tab[s1 < kMaxStages ? s1 : kMaxStages - 1];
+  const bool restart = gamma1 != gamma;
+  const double th1 = 0.5 * (1.0 + sqrt(1.0 + 4.0 * st.theta * st.theta));
+  const float beta = static_cast<float>((st.theta - 1.0) / th1);
+  const float step0 = static_cast<float>(gamma * U.inv_nmax);
+  double bad = 0.0;
+  for (int j = threadIdx.x; j < U.J; j += blockDim.x) {
+    const float G = static_cast<float>(to_real(U.acc[j], U.inv_scaleG) - U.b[j]);
+    const float step = U.precondition ? static_cast<float>(gamma * U.inv_n2[j]) : step0;
+    const float yj = U.y[j];
+    const float ln = fmaxf(0.f, fmaf(step, G, yj));
+    const float yn = restart ? ln : fmaf(beta, ln - U.lam[j], ln);
+    U.lam[j] = ln;
+    U.y[j] = yn;
+    U.acc[j] = 0ull;
+    if (!isfinite(G) || !isfinite(yn)) bad = 1.0;
+  }
+  bad = block_max(bad, sh);
+  if (threadIdx.x == 0) {
+    DevState n = st;
+    n.iter = t1;
+    n.theta = restart ? 1.0 : th1;
+    n.gamma = gamma1;
+    n.stage = static_cast<int32_t>(s1 < 0x7fffffff ? s1 : 0x7fffffff);
+    if (bad > 0.0) n.status |= kStatNumeric;
+    *U.state = n;
+  }
+}
+
+// Dual value and certified gap at the dual point of the certificate sweep
+// (Sec. 3.2 Eq. dual; scaled-point gap as defined in the header):
+//   G_j = (A x)_j - b_j,  g = sum_i (c x + gamma/2 x^2) + lam^T G,
+//   s_j = min(1, b_j / (A x)_j),  P = sum_j s_j (c x)_j + gamma/2 s_j^2 (x^2)_j.
+__global__ void __launch_bounds__(kUpdThreads) stats_kernel(const StatsInst* __restrict__ tab) {
+  __shared__ double sh[32];
+  const StatsInst S = tab[blockIdx.x];
+  const double gamma = *S.gamma;
+  double obj = 0.0;
+  for (int k = threadIdx.x; k < S.nseg; k += blockDim.x) obj += S.seg_obj[S.seg_list[k]];
+  double lg = 0.0, P = 0.0, viol = 0.0;
+  for (int j = threadIdx.x; j < S.J; j += blockDim.x) {
+    const double Ax = to_real(S.acc[j], S.inv_sG);
+    const double Cx = to_real(S.accC[j], S.inv_sC);
+    const double Qx = to_real(S.accQ[j], S.inv_sQ);
+    const double G = Ax - S.b[j];
+    lg += static_cast<double>(S.lam[j]) * G;
+    const double s = Ax > S.b[j] ? S.b[j] / Ax : 1.0;
+    P += s * Cx + 0.5 * gamma * s * s * Qx;
+    viol = fmax(viol, G);
+    if (S.grad_out) S.grad_out[j] = static_cast<float>(G);
+    S.acc[j] = 0ull;
+    S.accC[j] = 0ull;
+    S.accQ[j] = 0ull;
+  }
+  obj = block_sum(obj, sh);
+  lg = block_sum(lg, sh);
+  P = block_sum(P, sh);
+  viol = block_max(viol, sh);
+  if (threadIdx.x == 0) {
+    const double g = obj + lg;
+    const double den = fabs(g) > 1e-30 ? fabs(g) : 1e-30;
+    S.out[0] = g;
+    S.out[1] = P;
+    S.out[2] = S.certified ? (P - g) / den : NAN;
+    S.out[3] = -lg / den;
+    S.out[4] = viol;
+    S.out[5] = obj;
+    S.out[6] = S.state ? static_cast<double>(S.state->iter) : 0.0;
+    S.out[7] = S.state ? static_cast<double>(S.state->status) : 0.0;
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_update(const UpdInst* dev_tab, int ninst, cudaStream_t s) {
+  fista_update_kernel<<<ninst, kUpdThreads, 0, s>>>(dev_tab);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_stats(const StatsInst* dev_tab, int ninst, cudaStream_t s) {
+  stats_kernel<<<ninst, kUpdThreads, 0, s>>>(dev_tab);
+  return cudaGetLastError();
+}
+
+}  // namespace dlm

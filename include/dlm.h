@@ -44,7 +44,8 @@ typedef enum {
   DLM_ERR_OOM = 2,         /* a device or host allocation failed */
   DLM_ERR_CUDA = 3,        /* a CUDA runtime call failed */
   DLM_ERR_NUMERIC = 4,     /* a NaN/Inf appeared in the iteration */
-  DLM_ERR_TIMEOUT = 5,     /* an iteration limit was reached before the target */
+  DLM_ERR_TIMEOUT = 5,     /* an iteration limit was reached before the target, or a bounded
+                              device-side wait ran out */
   DLM_ERR_UNSUPPORTED = 6  /* valid input outside what this build handles */
 } dlm_status;
 
@@ -81,9 +82,9 @@ typedef struct {
 typedef struct {
   int32_t gap_every;    /* iterations between certified-gap checks in dlm_solve (default 50) */
   int32_t precondition; /* 1: row normalization (App. B.2) as the per-item step gamma/sum_i a_ij^2 */
-  int32_t mapping;      /* degree-bucket mapping table: -1 default/autotuned, >= 0 a fixed table */
+  int32_t mapping;      /* slice-to-CTA assignment order: -1 default, >= 0 a fixed order */
   int32_t graph_iters;  /* iterations per captured CUDA graph (default 10) */
-  int32_t ctas_per_sm;  /* persistent sweep CTAs per SM (0: from occupancy) */
+  int32_t ctas_per_sm;  /* persistent sweep CTAs per SM (0: one) */
   int32_t reserved[3];
 } dlm_options;
 

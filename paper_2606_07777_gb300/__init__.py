@@ -168,11 +168,15 @@ def dlm_step(h, n):
 
 
 def dlm_solve(h, target, max_iters) -> Stats:
+    """Returns the final Stats; a run that stops on the iteration limit or on a
+    device-reported status returns normally with that status in `.status`."""
     s = Stats()
     lib = load()
     st = lib.dlm_solve(h, target, max_iters, ctypes.byref(s))
-    if st not in (DLM_OK, DLM_ERR_TIMEOUT):
+    if st not in (DLM_OK, DLM_ERR_TIMEOUT, DLM_ERR_NUMERIC):
         raise DlmError(st, "dlm_solve", lib.dlm_last_error().decode())
+    if st != DLM_OK and s.status == DLM_OK:
+        s.status = st
     return s
 
 

@@ -30,15 +30,7 @@ dlm_status fail(dlm_status s, const std::string& m) {
     if (e_ != cudaSuccess) return fail(DLM_ERR_CUDA, std::string(#x) + ": " + cudaGetErrorString(e_)); \
   } while (0)
 
-// Degree class -> mapping, per table (class 0 = empty rows: no task).
-constexpr int kNumTables = 2;
-const int kTables[kNumTables][kNumClasses] = {
-    // d:  0   1         2         3-4       5-8       9-16      17-32     33-64      65-128     129-256     257-512     513+
-    {-1, kMapL1K4, kMapL1K4, kMapL1K4, kMapL1K8, kMapL2K8, kMapL4K8, kMapL8K8, kMapL16K8, kMapL32K8, kMapStream,
-     kMapStream},
-    {-1, kMapL1K4, kMapL1K4, kMapL1K4, kMapL2K4, kMapL4K4, kMapL8K4, kMapL16K4, kMapL32K4, kMapStream, kMapStream,
-     kMapStream},
-};
+constexpr int kNumTables = 1;  // slice assignment orders (reserved for the tuner)
 
 __global__ void k_set_double(double* p, double v) { *p = v; }
 
@@ -130,11 +122,14 @@ namespace {
 
 InstDesc base_desc(const dlm_problem* p) {
   InstDesc d{};
-  d.rp = p->lay.rp;
+  d.slice_off = p->lay.slice_off;
+  d.slice_w = p->lay.slice_w;
   d.col = p->lay.col;
-  d.c = p->lay.c;
-  d.a = p->lay.a;
+  d.ca = p->lay.ca;
   d.orig_off = p->lay.orig_off;
+  d.udeg = p->lay.udeg;
+  d.nusers = p->lay.num_active_users;
+  d.status = &p->state->status;
   d.scaleG = std::ldexp(1.0f, p->sG);
   d.scaleC = std::ldexp(1.0f, p->sC);
   d.scaleQ = std::ldexp(1.0f, p->sQ);
@@ -168,8 +163,8 @@ void invalidate_graph(dlm_problem* p) {
   p->gexec_iters = 0;
 }
 
-// Per-CTA task lists: CTA k gets users [B_c + k n_c / V, B_c + (k+1) n_c / V)
-// of every degree class c, so all CTAs carry the same mix of classes.
+// Per-CTA task lists: CTA k sweeps slices k, k + V, k + 2V, ...; slices are
+// sorted by width, so every CTA (and every warp) gets the same mix of widths.
 dlm_status build_tasks(dlm_problem* p) {
   const int V = p->grid;
   p->h_tasks.clear();
@@ -177,21 +172,15 @@ dlm_status build_tasks(dlm_problem* p) {
   p->h_seg.clear();
   for (int k = 0; k < V; ++k) {
     p->h_cta[k] = static_cast<int32_t>(p->h_tasks.size());
-    for (int c = 1; c < kNumClasses; ++c) {
-      const int64_t n = p->lay.class_count[c];
-      if (n == 0) continue;
-      const int64_t u0 = p->lay.class_begin[c] + n * k / V;
-      const int64_t u1 = p->lay.class_begin[c] + n * (k + 1) / V;
-      if (u1 > u0) {
-        Task t;
-        t.inst = 0;
-        t.map = kTables[p->table][c];
-        t.u0 = static_cast<int32_t>(u0);
-        t.u1 = static_cast<int32_t>(u1);
-        p->h_tasks.push_back(t);
-      }
+    if (k < p->lay.nslices) {
+      Task t;
+      t.inst = 0;
+      t.stride = V;
+      t.first = k;
+      t.end = p->lay.nslices;
+      p->h_tasks.push_back(t);
+      p->h_seg.push_back(p->h_cta[k]);
     }
-    if (static_cast<int32_t>(p->h_tasks.size()) > p->h_cta[k]) p->h_seg.push_back(p->h_cta[k]);
   }
   p->h_cta[V] = static_cast<int32_t>(p->h_tasks.size());
   p->ntasks = static_cast<int>(p->h_tasks.size());
@@ -322,7 +311,9 @@ dlm_status read_stats(dlm_problem* p, dlm_stats* out) {
     out->uncert_gap = p->h_out[3];
     out->max_viol = p->h_out[4];
     out->seconds = p->last_solve_seconds;
-    out->status = (hs.status & kStatNumeric) ? DLM_ERR_NUMERIC : DLM_OK;
+    out->status = (hs.status & kStatNumeric) ? DLM_ERR_NUMERIC
+                  : (hs.status & kStatTimeout) ? DLM_ERR_TIMEOUT
+                                               : DLM_OK;
     out->converged = 0;
   }
   return DLM_OK;
@@ -332,11 +323,12 @@ void free_problem(dlm_problem* p) {
   if (!p) return;
   if (p->stream) cudaStreamSynchronize(p->stream);
   invalidate_graph(p);
-  cudaFree(p->lay.rp);
+  cudaFree(p->lay.slice_off);
+  cudaFree(p->lay.slice_w);
   cudaFree(p->lay.col);
-  cudaFree(p->lay.c);
-  cudaFree(p->lay.a);
+  cudaFree(p->lay.ca);
   cudaFree(p->lay.orig_off);
+  cudaFree(p->lay.udeg);
   cudaFree(p->lay.n2);
   void* ptrs[] = {p->b,        p->inv_n2,    p->lam,      p->y,        p->acc,      p->acc2,     p->accC,
                   p->accQ,     p->gamma_tab, p->calc_gamma, p->seg_obj, p->stats_out, p->state,    p->inst_iter,
@@ -474,7 +466,7 @@ dlm_status dlm_create(const dlm_problem_desc* desc, void* stream, dlm_problem** 
   }
 
   p->smemJ = static_cast<int>(J);
-  if (sweep_smem_bytes(p->smemJ, true, p->bf16) > sweep_smem_limit()) {
+  if (sweep_smem_bytes(p->smemJ, true) > sweep_smem_limit()) {
     cleanup_tmp();
     free_problem(p);
     return fail(DLM_ERR_UNSUPPORTED, "num_items too large for the shared-memory item arrays of this build");
@@ -523,10 +515,7 @@ dlm_status dlm_create(const dlm_problem_desc* desc, void* stream, dlm_problem** 
   {
     int sms = 0;
     CKC(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, p->device));
-    int occ = sweep_occupancy(p->smemJ, false, p->bf16);
-    if (occ < 1) occ = 1;
-    if (occ > 2) occ = 2;
-    p->grid = sms * occ;
+    p->grid = sms;  // persistent: one sweep CTA per SM
   }
   CKC(cudaStreamSynchronize(p->stream));
   cleanup_tmp();
@@ -678,8 +667,9 @@ dlm_status dlm_solve(dlm_problem* p, double target_rel_gap, int64_t max_iters, d
     dlm_status st = dlm_get_stats(p, &s);
     if (st != DLM_OK) return st;
     if (s.status != DLM_OK) {
-      result = DLM_ERR_NUMERIC;
-      g_err = "non-finite value in the iteration";
+      result = static_cast<dlm_status>(s.status);
+      g_err = s.status == DLM_ERR_NUMERIC ? "non-finite value in the iteration"
+                                          : "a device-side wait ran out of its limit";
       break;
     }
     if (s.gamma == p->gamma_end && s.rel_gap <= target_rel_gap) {
@@ -698,7 +688,7 @@ dlm_status dlm_solve(dlm_problem* p, double target_rel_gap, int64_t max_iters, d
   p->last_solve_seconds = std::chrono::duration<double>(t1 - t0).count();
   s.seconds = p->last_solve_seconds;
   if (out) *out = s;
-  if (result == DLM_ERR_TIMEOUT) g_err = "max_iters reached before the target gap";
+  if (result == DLM_ERR_TIMEOUT && s.status == DLM_OK) g_err = "max_iters reached before the target gap";
   return result;
 }
 

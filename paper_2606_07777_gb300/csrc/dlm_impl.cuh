@@ -13,64 +13,13 @@
 namespace dlm {
 
 constexpr int kWarp = 32;
-constexpr int kSweepThreads = 512;  // 16 warps per sweep CTA
-constexpr int kUpdThreads = 1024;   // one CTA per instance for the O(J) kernels
-constexpr int kMaxStages = 64;      // continuation stages tabulated (gamma is flat after)
-constexpr int kNumClasses = 12;     // degree classes: 0, 1, 2, 3-4, 5-8, ..., 257-512, 513+
+constexpr int kSweepThreads = 1024;  // 32 warps per sweep CTA, one CTA per SM
+constexpr int kUpdThreads = 1024;    // one CTA per instance for the O(J) kernels
+constexpr int kMaxStages = 64;       // continuation stages tabulated (gamma is flat after)
+constexpr int kMaxSegTasks = 16;     // tasks of one instance in one CTA
 
 // Error bits of the device status word.
-enum : int32_t { kStatNumeric = 1, kStatTimeout = 2, kStatBadMap = 4 };
-
-// Degree class of a user: 0 for d = 0, otherwise 1 + ceil(log2 d) capped.
-__host__ __device__ inline int degree_class(int64_t d) {
-  if (d <= 0) return 0;
-  int c = 1;
-  int64_t cap = 1;
-  while (cap < d && c < kNumClasses - 1) {
-    cap <<= 1;
-    ++c;
-  }
-  return c;
-}
-
-// Mapping ids (how a degree class is laid on lanes).  Register mappings
-// process users of degree <= L*K with L lanes per user and K edges per lane;
-// kMapStream runs one warp per user over an arbitrarily long row.
-enum : int32_t {
-  kMapStream = 0,
-  kMapL1K4 = 1,
-  kMapL1K8 = 2,
-  kMapL2K8 = 3,
-  kMapL4K8 = 4,
-  kMapL8K8 = 5,
-  kMapL16K8 = 6,
-  kMapL32K8 = 7,
-  kMapL2K4 = 8,
-  kMapL4K4 = 9,
-  kMapL8K4 = 10,
-  kMapL16K4 = 11,
-  kMapL32K4 = 12,
-  kNumMaps = 13
-};
-__host__ __device__ inline int map_lanes(int m) {
-  switch (m) {
-    case kMapL1K4: case kMapL1K8: return 1;
-    case kMapL2K8: case kMapL2K4: return 2;
-    case kMapL4K8: case kMapL4K4: return 4;
-    case kMapL8K8: case kMapL8K4: return 8;
-    case kMapL16K8: case kMapL16K4: return 16;
-    default: return 32;
-  }
-}
-__host__ __device__ inline int map_k(int m) {
-  switch (m) {
-    case kMapL1K4: case kMapL2K4: case kMapL4K4: case kMapL8K4: case kMapL16K4: case kMapL32K4: return 4;
-    case kMapStream: return 0;
-    default: return 8;
-  }
-}
-// Users handled by one warp pass.
-__host__ __device__ inline int map_users_per_pass(int m) { return m == kMapStream ? 1 : kWarp / map_lanes(m); }
+enum : int32_t { kStatNumeric = 1, kStatTimeout = 2 };
 
 // Per-instance iteration state (device memory).
 struct DevState {
@@ -98,13 +47,18 @@ struct UpdInst {
 };
 
 // Per-instance view for the sweep kernels (device memory; one table for the
-// iteration sweep at y, one for the certificate sweep at lam).
+// iteration sweep at y, one for the certificate sweep at lam).  Edges are in
+// slices of 32 users (see layout.cu): edge k of user t of slice s is at
+// slice_off[s] + 32 k + t.
 struct InstDesc {
-  const int64_t* rp;        // bucketed row pointer [I+1]
-  const int32_t* col;       // [nnz]
-  const void* c;            // [nnz] float or bf16
-  const void* a;            // [nnz]
-  const int64_t* orig_off;  // [I] caller row start of each bucketed user
+  const int64_t* slice_off; // [nslices + 1]
+  const int32_t* slice_w;   // [nslices] edges per lane (the slice's largest degree)
+  const int32_t* col;       // [padded nnz] item index
+  const void* ca;           // [padded nnz] interleaved (c, a): float2, or bf16 pair in a uint32
+  const int64_t* orig_off;  // [users with edges] caller row start of each sorted user
+  const int32_t* udeg;      // [users with edges] degree of each sorted user
+  int64_t nusers;           // users with edges (sorted users 0 .. nusers-1)
+  int32_t* status;          // device error word (kStat* bits)
   const float* y;           // sweep point [J]
   const double* gamma;      // ridge used by this sweep
   unsigned long long* acc;  // [J] fixed-point sum a x
@@ -118,14 +72,13 @@ struct InstDesc {
   int32_t kind;
 };
 
-// A task: users [u0, u1) of instance `inst`, all of one degree class, laid
-// on lanes by mapping `map`.  The tasks of one CTA are contiguous and sorted
-// by instance.
+// A task: slices first, first + stride, ... (< end) of instance `inst`.  The
+// tasks of one CTA are contiguous and grouped by instance.
 struct Task {
   int32_t inst;
-  int32_t map;
-  int32_t u0;
-  int32_t u1;
+  int32_t stride;
+  int64_t first;
+  int64_t end;
 };
 
 struct SweepLaunch {
@@ -154,24 +107,23 @@ struct StatsInst {
 };
 
 // ---- launchers (defined in the .cu files) ----
-size_t sweep_smem_bytes(int smemJ, bool stats, bool bf16);
-size_t sweep_smem_limit();  // usable dynamic shared memory per sweep CTA on this device
+size_t sweep_smem_bytes(int smemJ, bool stats);
+size_t sweep_smem_limit();             // usable dynamic shared memory per sweep CTA on this device
 cudaError_t sweep_prepare(bool bf16);  // raises the dynamic shared-memory limit
-int sweep_occupancy(int smemJ, bool stats, bool bf16);
 cudaError_t launch_sweep(const SweepLaunch& L, bool stats, bool bf16);
 cudaError_t launch_update(const UpdInst* dev_tab, int ninst, cudaStream_t s);
 cudaError_t launch_stats(const StatsInst* dev_tab, int ninst, cudaStream_t s);
 
 // layout.cu
 struct LayoutOut {
-  int64_t* rp = nullptr;        // [I+1]
-  int32_t* col = nullptr;       // [nnz]
-  void* c = nullptr;            // [nnz]
-  void* a = nullptr;            // [nnz]
-  int64_t* orig_off = nullptr;  // [I]
-  int64_t class_count[kNumClasses] = {0};
-  int64_t class_begin[kNumClasses + 1] = {0};
-  double* n2 = nullptr;         // [J] sum_i a_ij^2
+  int64_t* slice_off = nullptr;  // [nslices + 1]
+  int32_t* slice_w = nullptr;    // [nslices]
+  int32_t* col = nullptr;        // [padded_nnz + 32]
+  void* ca = nullptr;            // [padded_nnz + 32]
+  int64_t* orig_off = nullptr;   // [num_active_users + 32]
+  int32_t* udeg = nullptr;       // [num_active_users + 32]
+  int64_t num_active_users = 0, nslices = 0, padded_nnz = 0;
+  double* n2 = nullptr;          // [J] sum_i a_ij^2
   double n2max = 0;
   int64_t max_item_deg = 0;
   double max_abs_a = 0, max_abs_c = 0;

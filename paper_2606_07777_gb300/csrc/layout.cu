@@ -1,13 +1,18 @@
-// layout.cu -- one-time set-up of an instance: input validation, degree
-// classes, the degree-bucketed edge layout the sweep reads, and per-item
-// constants (sum_i a_ij^2 for the step size and row normalization, App. B.2;
-// item degrees and value bounds for the fixed-point scales).
+// layout.cu -- one-time set-up of an instance: input validation, the
+// degree-sorted sliced layout the sweep reads, and per-item constants
+// (sum_i a_ij^2 for the step size and row normalization, App. B.2; item
+// degrees and value bounds for the fixed-point scales).
 //
-// The caller's CSR is user-major (one row per user, Sec. 4.1's one column per
-// source).  Users are stably sorted by degree class (the log-bucketing idea
-// of Sec. 4.2: classes [2^(t-1), 2^t)), and their rows are copied into that
-// order, so the rows of one class are contiguous and a sweep task streams a
-// contiguous byte range.
+// The caller's CSR is user-major (one row per user; the paper's CSC with one
+// column per source, Sec. 4.1).  Users are stably sorted by degree, largest
+// first (the paper buckets by degree to limit padding, Sec. 4.2; sorting by
+// the exact degree takes that to its limit), and cut into slices of 32
+// consecutive users.  A slice of width w (its largest degree) stores edge k of
+// its user t at slice_off + 32 k + t, for the item index stream and for the
+// interleaved (c, a) stream, so that lane t of a warp reads user t's edges
+// and every warp load is one contiguous 128-byte line per stream.  Edges past
+// a user's degree are padding with c = +inf, a = 0 (they give u = -inf and
+// are never active).  Users with no edges are dropped from the slices.
 #include <cub/cub.cuh>
 
 #include <cmath>
@@ -31,28 +36,24 @@ __device__ __forceinline__ float load_val(const void* p, int64_t e, bool bf16) {
   return reinterpret_cast<const float*>(p)[e];
 }
 
-// Row pointer checks, degree classes and class histogram.
-__global__ void k_rows(const int64_t* rp, int64_t I, int64_t nnz, int32_t* cls, unsigned long long* class_cnt,
+// Row pointer checks; degree of every user; users with no edges.
+__global__ void k_rows(const int64_t* rp, int64_t I, int64_t nnz, int32_t* deg, unsigned long long* zero_cnt,
                        int* bad) {
-  __shared__ unsigned long long h[kNumClasses];
-  if (threadIdx.x < kNumClasses) h[threadIdx.x] = 0;
-  __syncthreads();
   int flag = 0;
+  unsigned long long z = 0;
   for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < I;
        i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
     const int64_t r0 = rp[i], r1 = rp[i + 1];
     const int64_t d = r1 - r0;
-    if (d < 0 || r0 < 0 || r1 > nnz) flag |= kBadRowPtr;
-    const int c = degree_class(d < 0 ? 0 : d);
-    cls[i] = c;
-    atomicAdd(&h[c], 1ull);
+    if (d < 0 || r0 < 0 || r1 > nnz || d > 0x7fffffff) flag |= kBadRowPtr;
+    deg[i] = d < 0 ? 0 : static_cast<int32_t>(d);
+    z += (d == 0);
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     if (rp[0] != 0 || rp[I] != nnz) flag |= kBadRowPtr;
   }
   if (flag) atomicOr(bad, flag);
-  __syncthreads();
-  if (threadIdx.x < kNumClasses && h[threadIdx.x]) atomicAdd(&class_cnt[threadIdx.x], h[threadIdx.x]);
+  if (z) atomicAdd(zero_cnt, z);
 }
 
 // Edge checks, item degrees, max |a|, max |c|.
@@ -100,28 +101,64 @@ __global__ void k_iota(int32_t* v, int64_t n) {
     v[i] = static_cast<int32_t>(i);
 }
 
-__global__ void k_perm_deg(const int64_t* rp, const int32_t* perm, int64_t I, int64_t* deg_p, int64_t* orig_off) {
-  for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < I;
-       i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
-    const int64_t o = perm[i];
-    deg_p[i] = rp[o + 1] - rp[o];
-    orig_off[i] = rp[o];
+// Slice widths (edges per lane) and slice sizes in elements (32 w).
+__global__ void k_slices(const int32_t* sdeg, int64_t nslices, int32_t* width, int64_t* size) {
+  for (int64_t s = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; s < nslices;
+       s += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const int32_t w = sdeg[32 * s];  // largest degree of the slice (sorted descending)
+    width[s] = w;
+    size[s] = 32 * static_cast<int64_t>(w);
   }
 }
 
-// Copy each user's row into the bucketed order: one warp per user.
-template <typename VT>
-__global__ void k_gather(const int32_t* col, const VT* c, const VT* a, const int64_t* orig_off,
-                         const int64_t* rp_new, int64_t I, int32_t* col_o, VT* c_o, VT* a_o) {
+// One warp per slice: lane t copies user t's row into column t of the slice.
+// CA = float2 {c, a} (FP32) or uint32 (bf16 c low, bf16 a high).
+template <typename CA>
+__device__ __forceinline__ CA pack_ca(const void* c, const void* a, int64_t e);
+template <>
+__device__ __forceinline__ float2 pack_ca<float2>(const void* c, const void* a, int64_t e) {
+  return make_float2(static_cast<const float*>(c)[e], static_cast<const float*>(a)[e]);
+}
+template <>
+__device__ __forceinline__ uint32_t pack_ca<uint32_t>(const void* c, const void* a, int64_t e) {
+  return static_cast<uint32_t>(static_cast<const unsigned short*>(c)[e]) |
+         (static_cast<uint32_t>(static_cast<const unsigned short*>(a)[e]) << 16);
+}
+template <typename CA>
+__device__ __forceinline__ CA pad_ca();
+template <>
+__device__ __forceinline__ float2 pad_ca<float2>() {
+  return make_float2(INFINITY, 0.f);
+}
+template <>
+__device__ __forceinline__ uint32_t pad_ca<uint32_t>() {
+  return 0x00007F80u;  // c = bf16 +inf, a = 0
+}
+
+template <typename CA>
+__global__ void k_gather(const int64_t* rp, const int32_t* col, const void* c, const void* a, const int32_t* perm,
+                         const int32_t* sdeg, int64_t In, int64_t nslices, const int64_t* slice_off,
+                         const int32_t* width, int32_t* col_o, CA* ca_o, int64_t* orig_off, int32_t* udeg) {
   const int lane = threadIdx.x & 31;
   const int64_t w0 = (blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x) >> 5;
   const int64_t nwarps = (static_cast<int64_t>(gridDim.x) * blockDim.x) >> 5;
-  for (int64_t u = w0; u < I; u += nwarps) {
-    const int64_t s = orig_off[u], t = rp_new[u], d = rp_new[u + 1] - t;
-    for (int64_t k = lane; k < d; k += 32) {
-      col_o[t + k] = col[s + k];
-      c_o[t + k] = c[s + k];
-      a_o[t + k] = a[s + k];
+  for (int64_t s = w0; s < nslices; s += nwarps) {
+    const int64_t u = 32 * s + lane;
+    int64_t r = 0;
+    int d = 0;
+    if (u < In) {
+      const int32_t o = perm[u];
+      r = rp[o];
+      d = sdeg[u];
+      orig_off[u] = r;
+      udeg[u] = d;
+    }
+    const int w = width[s];
+    const int64_t base = slice_off[s] + lane;
+    for (int k = 0; k < w; ++k) {
+      const bool v = k < d;
+      col_o[base + 32 * static_cast<int64_t>(k)] = v ? col[r + k] : 0;
+      ca_o[base + 32 * static_cast<int64_t>(k)] = v ? pack_ca<CA>(c, a, r + k) : pad_ca<CA>();
     }
   }
 }
@@ -160,13 +197,13 @@ int fixed_point_shift(double bound) {
   return s;
 }
 
-#define DLM_CK(x)                                                   \
-  do {                                                              \
-    cudaError_t e_ = (x);                                           \
-    if (e_ != cudaSuccess) {                                        \
+#define DLM_CK(x)                                                            \
+  do {                                                                       \
+    cudaError_t e_ = (x);                                                    \
+    if (e_ != cudaSuccess) {                                                 \
       *msg = std::string("CUDA error in layout: ") + cudaGetErrorString(e_); \
-      goto fail;                                                    \
-    }                                                               \
+      goto fail;                                                             \
+    }                                                                        \
   } while (0)
 
 dlm_status build_layout(int64_t I, int64_t J, int64_t nnz, const int64_t* rp, const int32_t* col, const void* c,
@@ -174,34 +211,36 @@ dlm_status build_layout(int64_t I, int64_t J, int64_t nnz, const int64_t* rp, co
                         std::string* msg) {
   const size_t vs = bf16 ? 2 : 4;
   dlm_status st = DLM_OK;
-  int32_t *cls = nullptr, *cls_sorted = nullptr, *idx = nullptr, *perm = nullptr;
-  int64_t* deg_p = nullptr;
-  unsigned long long *class_cnt = nullptr, *item_deg = nullptr, *sq = nullptr;
+  int32_t *deg = nullptr, *sdeg = nullptr, *idx = nullptr, *perm = nullptr;
+  int64_t* ssize = nullptr;
+  unsigned long long *zero_cnt = nullptr, *item_deg = nullptr, *sq = nullptr;
   unsigned* mx = nullptr;
   int* bad = nullptr;
   void* tmp = nullptr;
   size_t tmp_bytes = 0;
   int h_bad = 0;
   unsigned h_mx[2] = {0, 0};
-  unsigned long long h_cnt[kNumClasses];
+  unsigned long long h_zero = 0;
   std::vector<unsigned long long> h_deg;
   double bound_sq = 0;
   int ssq = 0;
+  int64_t In = 0, ns = 0;
 
-  DLM_CK(cudaMalloc(&cls, sizeof(int32_t) * (I > 0 ? I : 1)));
-  DLM_CK(cudaMalloc(&class_cnt, sizeof(unsigned long long) * kNumClasses));
+  DLM_CK(cudaMalloc(&deg, sizeof(int32_t) * (I > 0 ? I : 1)));
+  DLM_CK(cudaMalloc(&zero_cnt, sizeof(unsigned long long)));
   DLM_CK(cudaMalloc(&item_deg, sizeof(unsigned long long) * (J > 0 ? J : 1)));
   DLM_CK(cudaMalloc(&mx, sizeof(unsigned) * 2));
   DLM_CK(cudaMalloc(&bad, sizeof(int)));
-  DLM_CK(cudaMemsetAsync(class_cnt, 0, sizeof(unsigned long long) * kNumClasses, s));
+  DLM_CK(cudaMemsetAsync(zero_cnt, 0, sizeof(unsigned long long), s));
   DLM_CK(cudaMemsetAsync(item_deg, 0, sizeof(unsigned long long) * (J > 0 ? J : 1), s));
   DLM_CK(cudaMemsetAsync(mx, 0, sizeof(unsigned) * 2, s));
   DLM_CK(cudaMemsetAsync(bad, 0, sizeof(int), s));
-  if (I > 0) k_rows<<<grid_for(I), kT, 0, s>>>(rp, I, nnz, cls, class_cnt, bad);
+  if (I > 0) k_rows<<<grid_for(I), kT, 0, s>>>(rp, I, nnz, deg, zero_cnt, bad);
   DLM_CK(cudaGetLastError());
   if (J > 0) k_b<<<grid_for(J), kT, 0, s>>>(b, J, bad);
   DLM_CK(cudaGetLastError());
   DLM_CK(cudaMemcpyAsync(&h_bad, bad, sizeof(int), cudaMemcpyDeviceToHost, s));
+  DLM_CK(cudaMemcpyAsync(&h_zero, zero_cnt, sizeof(h_zero), cudaMemcpyDeviceToHost, s));
   DLM_CK(cudaStreamSynchronize(s));
   if (h_bad & kBadRowPtr) {
     *msg = "row_ptr must start at 0, be non-decreasing and end at nnz";
@@ -217,7 +256,6 @@ dlm_status build_layout(int64_t I, int64_t J, int64_t nnz, const int64_t* rp, co
   DLM_CK(cudaGetLastError());
   DLM_CK(cudaMemcpyAsync(&h_bad, bad, sizeof(int), cudaMemcpyDeviceToHost, s));
   DLM_CK(cudaMemcpyAsync(h_mx, mx, sizeof(unsigned) * 2, cudaMemcpyDeviceToHost, s));
-  DLM_CK(cudaMemcpyAsync(h_cnt, class_cnt, sizeof(h_cnt), cudaMemcpyDeviceToHost, s));
   h_deg.resize(J > 0 ? J : 1);
   DLM_CK(cudaMemcpyAsync(h_deg.data(), item_deg, sizeof(unsigned long long) * h_deg.size(), cudaMemcpyDeviceToHost,
                          s));
@@ -243,61 +281,57 @@ dlm_status build_layout(int64_t I, int64_t J, int64_t nnz, const int64_t* rp, co
   out->max_item_deg = 0;
   for (int64_t j = 0; j < J; ++j)
     if (static_cast<int64_t>(h_deg[j]) > out->max_item_deg) out->max_item_deg = static_cast<int64_t>(h_deg[j]);
-  {
-    int64_t acc = 0;
-    for (int k = 0; k < kNumClasses; ++k) {
-      out->class_count[k] = static_cast<int64_t>(h_cnt[k]);
-      out->class_begin[k] = acc;
-      acc += static_cast<int64_t>(h_cnt[k]);
-    }
-    out->class_begin[kNumClasses] = acc;
-  }
 
-  // ---- stable sort of users by degree class ----
-  DLM_CK(cudaMalloc(&cls_sorted, sizeof(int32_t) * (I > 0 ? I : 1)));
+  // ---- stable sort of users by degree, largest first ----
+  In = I - static_cast<int64_t>(h_zero);
+  ns = (In + 31) / 32;
+  out->num_active_users = In;
+  out->nslices = ns;
+  DLM_CK(cudaMalloc(&sdeg, sizeof(int32_t) * (I + 32)));
+  DLM_CK(cudaMemsetAsync(sdeg, 0, sizeof(int32_t) * (I + 32), s));
   DLM_CK(cudaMalloc(&idx, sizeof(int32_t) * (I > 0 ? I : 1)));
   DLM_CK(cudaMalloc(&perm, sizeof(int32_t) * (I > 0 ? I : 1)));
   if (I > 0) {
     k_iota<<<grid_for(I), kT, 0, s>>>(idx, I);
     DLM_CK(cudaGetLastError());
-    DLM_CK(cub::DeviceRadixSort::SortPairs(nullptr, tmp_bytes, cls, cls_sorted, idx, perm, I, 0, 4, s));
+    DLM_CK(cub::DeviceRadixSort::SortPairsDescending(nullptr, tmp_bytes, deg, sdeg, idx, perm, I, 0, 32, s));
     DLM_CK(cudaMalloc(&tmp, tmp_bytes > 0 ? tmp_bytes : 16));
-    DLM_CK(cub::DeviceRadixSort::SortPairs(tmp, tmp_bytes, cls, cls_sorted, idx, perm, I, 0, 4, s));
+    DLM_CK(cub::DeviceRadixSort::SortPairsDescending(tmp, tmp_bytes, deg, sdeg, idx, perm, I, 0, 32, s));
     DLM_CK(cudaFree(tmp));
     tmp = nullptr;
   }
 
-  // ---- bucketed row pointer and caller offsets ----
-  DLM_CK(cudaMalloc(&deg_p, sizeof(int64_t) * (I > 0 ? I : 1)));
-  DLM_CK(cudaMalloc(&out->rp, sizeof(int64_t) * (I + 1)));
-  DLM_CK(cudaMalloc(&out->orig_off, sizeof(int64_t) * (I > 0 ? I : 1)));
-  if (I > 0) k_perm_deg<<<grid_for(I), kT, 0, s>>>(rp, perm, I, deg_p, out->orig_off);
-  DLM_CK(cudaGetLastError());
-  DLM_CK(cudaMemsetAsync(out->rp, 0, sizeof(int64_t), s));
-  if (I > 0) {
+  // ---- slices ----
+  DLM_CK(cudaMalloc(&out->slice_w, sizeof(int32_t) * (ns + 1)));
+  DLM_CK(cudaMalloc(&out->slice_off, sizeof(int64_t) * (ns + 1)));
+  DLM_CK(cudaMalloc(&ssize, sizeof(int64_t) * (ns + 1)));
+  DLM_CK(cudaMemsetAsync(out->slice_off, 0, sizeof(int64_t), s));
+  if (ns > 0) {
+    k_slices<<<grid_for(ns), kT, 0, s>>>(sdeg, ns, out->slice_w, ssize);
+    DLM_CK(cudaGetLastError());
     tmp_bytes = 0;
-    DLM_CK(cub::DeviceScan::InclusiveSum(nullptr, tmp_bytes, deg_p, out->rp + 1, I, s));
+    DLM_CK(cub::DeviceScan::InclusiveSum(nullptr, tmp_bytes, ssize, out->slice_off + 1, ns, s));
     DLM_CK(cudaMalloc(&tmp, tmp_bytes > 0 ? tmp_bytes : 16));
-    DLM_CK(cub::DeviceScan::InclusiveSum(tmp, tmp_bytes, deg_p, out->rp + 1, I, s));
+    DLM_CK(cub::DeviceScan::InclusiveSum(tmp, tmp_bytes, ssize, out->slice_off + 1, ns, s));
     DLM_CK(cudaFree(tmp));
     tmp = nullptr;
   }
+  DLM_CK(cudaMemcpyAsync(&out->padded_nnz, out->slice_off + ns, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+  DLM_CK(cudaStreamSynchronize(s));
 
-  // ---- edge arrays in bucketed order ----
-  DLM_CK(cudaMalloc(&out->col, sizeof(int32_t) * (nnz > 0 ? nnz : 1)));
-  DLM_CK(cudaMalloc(&out->c, vs * (nnz > 0 ? nnz : 1)));
-  DLM_CK(cudaMalloc(&out->a, vs * (nnz > 0 ? nnz : 1)));
-  if (I > 0) {
-    const int g = grid_for(I * 32);
+  // ---- edge streams in slice order ----
+  DLM_CK(cudaMalloc(&out->col, sizeof(int32_t) * (out->padded_nnz + 32)));
+  DLM_CK(cudaMalloc(&out->ca, 2 * vs * (out->padded_nnz + 32)));
+  DLM_CK(cudaMalloc(&out->orig_off, sizeof(int64_t) * (In + 32)));
+  DLM_CK(cudaMalloc(&out->udeg, sizeof(int32_t) * (In + 32)));
+  if (ns > 0) {
+    const int g = grid_for(ns * 32);
     if (bf16)
-      k_gather<unsigned short><<<g, kT, 0, s>>>(col, static_cast<const unsigned short*>(c),
-                                                 static_cast<const unsigned short*>(a), out->orig_off, out->rp, I,
-                                                 out->col, static_cast<unsigned short*>(out->c),
-                                                 static_cast<unsigned short*>(out->a));
+      k_gather<uint32_t><<<g, kT, 0, s>>>(rp, col, c, a, perm, sdeg, In, ns, out->slice_off, out->slice_w, out->col,
+                                          static_cast<uint32_t*>(out->ca), out->orig_off, out->udeg);
     else
-      k_gather<float><<<g, kT, 0, s>>>(col, static_cast<const float*>(c), static_cast<const float*>(a),
-                                        out->orig_off, out->rp, I, out->col, static_cast<float*>(out->c),
-                                        static_cast<float*>(out->a));
+      k_gather<float2><<<g, kT, 0, s>>>(rp, col, c, a, perm, sdeg, In, ns, out->slice_off, out->slice_w, out->col,
+                                        static_cast<float2*>(out->ca), out->orig_off, out->udeg);
     DLM_CK(cudaGetLastError());
   }
 
@@ -324,28 +358,31 @@ fail:
   st = DLM_ERR_CUDA;
 done:
   cudaStreamSynchronize(s);
-  cudaFree(cls);
-  cudaFree(cls_sorted);
+  cudaFree(deg);
+  cudaFree(sdeg);
   cudaFree(idx);
   cudaFree(perm);
-  cudaFree(deg_p);
-  cudaFree(class_cnt);
+  cudaFree(ssize);
+  cudaFree(zero_cnt);
   cudaFree(item_deg);
   cudaFree(sq);
   cudaFree(mx);
   cudaFree(bad);
   if (tmp) cudaFree(tmp);
   if (st != DLM_OK) {
-    cudaFree(out->rp);
+    cudaFree(out->slice_w);
+    cudaFree(out->slice_off);
     cudaFree(out->col);
-    cudaFree(out->c);
-    cudaFree(out->a);
+    cudaFree(out->ca);
     cudaFree(out->orig_off);
+    cudaFree(out->udeg);
     cudaFree(out->n2);
-    out->rp = nullptr;
+    out->slice_w = nullptr;
+    out->slice_off = nullptr;
     out->col = nullptr;
-    out->c = out->a = nullptr;
+    out->ca = nullptr;
     out->orig_off = nullptr;
+    out->udeg = nullptr;
     out->n2 = nullptr;
   }
   return st;

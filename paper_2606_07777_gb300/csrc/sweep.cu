@@ -1,33 +1,36 @@
 // sweep.cu -- the fused dual sweep (the per-iteration hot path).
 //
 // For every user i and dual point y (Sec. 3.2, Eq. primal-recovery):
-//     u_ik  = -(c_ik + a_ik * y_j(k))                      (gamma-scaled v)
-//     x_i   = Proj_C_i(u_i / gamma)
-// and per item j (Eq. dual-gradient):  (A x)_j = sum_i a_ij x_ij.
-// With `STATS` it also accumulates per item sum c x and sum x^2 and the
+//     u_ik = -(c_ik + a_ik * y_j(k))                 (v = u / gamma)
+//     x_i  = Proj_C_i(u_i / gamma)
+// and per item j (Eq. dual-gradient): (A x)_j = sum_i a_ij x_ij.
+// With STATS it also accumulates per item sum c x and sum x^2 and the
 // objective sum (c x + gamma/2 x^2) for the dual value and the certified gap,
 // and optionally writes x in the caller's edge order.
 //
-// Simplex projection (Sec. 4.3 computes the same threshold with a sort; here
-// no sort): in u-space the threshold tau solves sum max(u - tau, 0) = gamma z.
-// Start from tau_1 = max(u) - gamma z, a lower bound on tau, and iterate
-// tau <- (sum_{u > tau} u - gamma z) / #{u > tau} (Michelot 1986; the
-// iteration is monotone from below and stops when the active set stops
-// changing).  The inequality simplex then takes max(tau, 0), which equals the
-// early exit of Sec. 4.3 (sum max(u, 0) <= gamma z gives tau = 0).
-// x = max(u - tau, 0) / gamma.  Box: x = clip(u / gamma, 0, z).
+// Layout and mapping: users sit in degree-sorted slices of 32 (layout.cu);
+// lane t of a warp owns user t of its slice and walks the user's edges, one
+// coalesced 128-byte line per stream and step.  The item dual y lives in
+// shared memory (gathered by item index); item sums are accumulated in
+// shared memory and flushed once per CTA.
 //
-// Work layout: users are grouped by degree class; a task is one class's
-// slice of one CTA; a warp pass covers 32/L users of a class with L lanes per
-// user and K edges per lane (register resident), or one user per warp with a
-// streamed row for long rows.  Passes of a CTA are dealt to its warps
-// round-robin, so every accumulation below has a fixed order.
+// Simplex projection (Sec. 4.3 gets the threshold by sorting; no sort here).
+// In u-space the threshold tau solves sum max(u - tau, 0) = gamma z, and
+// tau >= tau_1 = max(u) - gamma z.  One pass over the row keeps the largest
+// and second largest u: if the second is <= tau_1, the maximum is the only
+// active edge, tau = tau_1 and x = z on it exactly (the common case at small
+// gamma).  Otherwise the lane runs the iteration
+// tau <- (sum_{u > tau} u - gamma z) / #{u > tau} from tau_1 (Michelot 1986;
+// monotone from below, it stops when the active set stops changing), then
+// recomputes tau over the active set in float-pair arithmetic so that
+// x = (u - tau) / gamma keeps full FP32 relative accuracy when u and tau
+// nearly cancel.  The inequality simplex takes max(tau, 0) (the early exit of
+// Sec. 4.3).  Box: x = clip(u / gamma, 0, z).
 //
-// Determinism: item sums are accumulated in 64-bit fixed point (value *
-// 2^s rounded to an integer, s chosen at set-up so no item sum can overflow),
-// so the sum is exact and independent of the order in which atomics land.
-// The objective is summed per warp in FP64 in pass order, per CTA in warp
-// order, and across CTAs in task order by the statistics kernel.
+// Determinism: item sums are 64-bit fixed point (value * 2^s rounded, s chosen
+// at set-up so no sum can overflow), exact and order independent; slices are
+// dealt to warps statically and the FP64 objective is summed per warp in
+// slice order, per CTA in warp order and across CTAs in task order.
 #include <cuda_bf16.h>
 
 #include "dlm_impl.cuh"
@@ -36,42 +39,29 @@ namespace dlm {
 namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
-constexpr int kMaxSegTasks = kNumClasses;
 
-__device__ __forceinline__ float ld_val(const float* p, int64_t e) { return __ldg(p + e); }
-__device__ __forceinline__ float ld_val(const __nv_bfloat16* p, int64_t e) {
-  const unsigned short b = __ldg(reinterpret_cast<const unsigned short*>(p) + e);
-  return __uint_as_float(static_cast<unsigned>(b) << 16);
-}
-
-template <int L>
-__device__ __forceinline__ float sub_max(float v) {
-#pragma unroll
-  for (int o = L / 2; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(kFull, v, o));
-  return v;
-}
-template <int L>
-__device__ __forceinline__ float sub_sum(float v) {
-#pragma unroll
-  for (int o = L / 2; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
-  return v;
-}
-template <int L>
-__device__ __forceinline__ int sub_sumi(int v) {
-#pragma unroll
-  for (int o = L / 2; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
-  return v;
-}
+// One interleaved (c, a) element.
+struct F32Pair {
+  using T = float2;
+  __device__ __forceinline__ static void get(const T& w, float& c, float& a) {
+    c = w.x;
+    a = w.y;
+  }
+};
+struct BF16Pair {
+  using T = uint32_t;
+  __device__ __forceinline__ static void get(const T& w, float& c, float& a) {
+    c = __uint_as_float(w << 16);
+    a = __uint_as_float(w & 0xffff0000u);
+  }
+};
 
 __device__ __forceinline__ unsigned long long fixp(float v, float scale) {
   return static_cast<unsigned long long>(__float2ll_rn(v * scale));
 }
 
-// Unevaluated float pairs (hi + lo) for the few active edges of a user: the
-// error-free transformations TwoSum (Knuth) and TwoProduct by FMA make
-// u = -(c + a y) and the threshold tau exact to ~2^-48 relative, so
-// x = (u - tau) / gamma keeps full FP32 relative accuracy even when u and tau
-// nearly cancel (small gamma).
+// Unevaluated float pairs hi + lo (error-free transformations: Knuth's
+// TwoSum, and TwoProduct by FMA).
 struct F2 {
   float h, l;
 };
@@ -84,14 +74,14 @@ __device__ __forceinline__ F2 f2_add(F2 a, F2 b) {
   const F2 s = two_sum(a.h, b.h);
   return {s.h, s.l + (a.l + b.l)};
 }
-// u = -(c + a*y) as a pair: a*y = p + pe exactly (FMA), then -c - p by TwoSum.
+// u = -(c + a*y) as a pair: a*y = p + pe exactly, then -c - p by TwoSum.
 __device__ __forceinline__ F2 u_pair(float c, float a, float y) {
   const float p = a * y;
   const float pe = fmaf(a, y, -p);
   const F2 s = two_sum(-c, -p);
   return {s.h, s.l - pe};
 }
-// (sum - gz) / n for a pair sum; the FP32 quotient's remainder is exact by FMA.
+// (sum - gz) / n for a pair sum; the quotient's remainder is exact by FMA.
 __device__ __forceinline__ F2 f2_threshold(F2 sum, float gzh, float gzl, int n) {
   const F2 num = f2_add(sum, F2{-gzh, -gzl});
   const float fn = static_cast<float>(n);
@@ -106,253 +96,278 @@ struct Seg {
   int kind;
 };
 
-// One warp pass of a register mapping: users [uf, uf + 32/L) (clipped at ue),
-// L lanes per user, K edges per lane (edge sl + k*L of the row).
-template <int L, int K, typename VT, bool STATS>
-__device__ __forceinline__ void pass_reg(const InstDesc& D, const Seg& S, const float* __restrict__ ys,
-                                         unsigned long long* accG, unsigned long long* accC,
-                                         unsigned long long* accQ, int64_t uf, int64_t ue, double& wobj) {
-  const int lane = threadIdx.x & 31;
-  const int sl = lane & (L - 1);
-  const int64_t u = uf + lane / L;
-  int64_t s = 0;
-  int d = 0;
-  if (u < ue) {
-    s = __ldg(D.rp + u);
-    d = static_cast<int>(__ldg(D.rp + u + 1) - s);
-  }
-  const VT* __restrict__ cp = static_cast<const VT*>(D.c);
-  const VT* __restrict__ ap = static_cast<const VT*>(D.a);
-  int cj[K];
-  float cv[K], av[K], uu[K];
-#pragma unroll
-  for (int k = 0; k < K; ++k) {
-    const int idx = sl + k * L;
-    if (idx < d) {
-      const int64_t e = s + idx;
-      cj[k] = __ldg(D.col + e);
-      cv[k] = ld_val(cp, e);
-      av[k] = ld_val(ap, e);
-    } else {
-      cj[k] = -1;
-      cv[k] = 0.f;
-      av[k] = 0.f;
-    }
-  }
-#pragma unroll
-  for (int k = 0; k < K; ++k) uu[k] = (cj[k] >= 0) ? -fmaf(av[k], ys[cj[k]], cv[k]) : -INFINITY;
-
-  float tau = 0.f, taul = 0.f;
-  if (S.kind != DLM_BOX) {
-    const bool eq = S.kind == DLM_SIMPLEX_EQ;
-    float m = -INFINITY;
-#pragma unroll
-    for (int k = 0; k < K; ++k) m = fmaxf(m, uu[k]);
-    m = sub_max<L>(m);
-    const bool trivial = (d == 0) || (!eq && m <= 0.f);
-    bool done = trivial;
-    tau = m - S.gz;
-    int prevn = -1;
-    for (int it = 0; it < L * K + 2; ++it) {
-      if (!__any_sync(kFull, !done)) break;
-      float sm = 0.f;
-      int n = 0;
-#pragma unroll
-      for (int k = 0; k < K; ++k) {
-        if (uu[k] > tau) {
-          sm += uu[k];
-          ++n;
-        }
-      }
-      sm = sub_sum<L>(sm);
-      n = sub_sumi<L>(n);
-      if (!done) {
-        if (n == prevn || n == 0) {
-          done = true;
-        } else {
-          prevn = n;
-          const float tn = __fdiv_rn(sm - S.gz, static_cast<float>(n));
-          done = (tn == tau);
-          tau = tn;
-        }
-      }
-    }
-    // Refine tau over the active set {u > tau} in pair arithmetic.  The
-    // shuffles run on every lane (warp-uniform); `zero` is uniform per user.
-    const bool zero = trivial || (!eq && tau <= 0.f);
-    F2 sum{0.f, 0.f};
-    int n = 0;
-    if (!zero) {
-#pragma unroll
-      for (int k = 0; k < K; ++k) {
-        if (uu[k] > tau) {
-          sum = f2_add(sum, u_pair(cv[k], av[k], ys[cj[k]]));
-          ++n;
-        }
-      }
-    }
-#pragma unroll
-    for (int o = L / 2; o > 0; o >>= 1) {
-      const F2 other{__shfl_xor_sync(kFull, sum.h, o), __shfl_xor_sync(kFull, sum.l, o)};
-      sum = f2_add(sum, other);
-      n += __shfl_xor_sync(kFull, n, o);
-    }
-    const F2 t2 = f2_threshold(sum, S.gz, S.gzl, n > 0 ? n : 1);
-    if (zero || (!eq && t2.h + t2.l <= 0.f)) {
-      tau = 0.f;
-    } else {
-      tau = t2.h;
-      taul = t2.l;
-    }
-  }
-
-  float ob = 0.f;
-#pragma unroll
-  for (int k = 0; k < K; ++k) {
-    float x = 0.f;
-    if (cj[k] >= 0) {
-      if (S.kind == DLM_BOX) {
-        if (uu[k] > 0.f) {
-          const F2 up = u_pair(cv[k], av[k], ys[cj[k]]);
-          x = fminf((up.h + up.l) * S.invg, S.z);
-        }
-      } else if (uu[k] > tau) {
-        const F2 up = u_pair(cv[k], av[k], ys[cj[k]]);
-        x = fmaxf((up.h - tau) + (up.l - taul), 0.f) * S.invg;
-      }
-    }
-    if (x > 0.f) {
-      atomicAdd(&accG[cj[k]], fixp(av[k] * x, S.scaleG));
-      if (STATS) {
-        atomicAdd(&accC[cj[k]], fixp(cv[k] * x, S.scaleC));
-        atomicAdd(&accQ[cj[k]], fixp(x * x, S.scaleQ));
-        ob += fmaf(0.5f * S.gamma * x, x, cv[k] * x);
-      }
-    }
-    if (STATS && D.xout != nullptr) {
-      const int idx = sl + k * L;
-      if (idx < d) D.xout[__ldg(D.orig_off + u) + idx] = x;
-    }
-  }
+// Contributions of one edge with x > 0.
+template <bool STATS>
+__device__ __forceinline__ void deposit(const Seg& S, int j, float c, float a, float x, unsigned long long* accG,
+                                        unsigned long long* accC, unsigned long long* accQ, float& ob) {
+  atomicAdd(&accG[j], fixp(a * x, S.scaleG));
   if (STATS) {
-    ob = sub_sum<L>(ob);
-    if (sl == 0 && d > 0) wobj += static_cast<double>(ob);
+    atomicAdd(&accC[j], fixp(c * x, S.scaleC));
+    atomicAdd(&accQ[j], fixp(x * x, S.scaleQ));
+    ob += fmaf(0.5f * S.gamma * x, x, c * x);
   }
 }
 
-__device__ __forceinline__ float warp_max(float v) { return sub_max<32>(v); }
-__device__ __forceinline__ float warp_sum(float v) { return sub_sum<32>(v); }
-__device__ __forceinline__ int warp_sumi(int v) { return sub_sumi<32>(v); }
+// x of one edge given the user's threshold (general mode).
+__device__ __forceinline__ float x_general(const Seg& S, bool box, bool zero, float tau, float taul, float c,
+                                           float a, float y) {
+  const F2 up = u_pair(c, a, y);
+  if (box) return fminf(fmaxf((up.h + up.l) * S.invg, 0.f), S.z);
+  if (zero) return fmaxf(up.h + up.l, 0.f) * S.invg;
+  return fmaxf((up.h - tau) + (up.l - taul), 0.f) * S.invg;
+}
 
-// One user of any degree, one warp, the row streamed from memory in every
-// pass of the threshold iteration (rows here are long and rare).
-template <typename VT, bool STATS>
-__device__ __forceinline__ void pass_stream(const InstDesc& D, const Seg& S, const float* __restrict__ ys,
-                                            unsigned long long* accG, unsigned long long* accC,
-                                            unsigned long long* accQ, int64_t u, double& wobj) {
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+  return v;
+}
+__device__ __forceinline__ int warp_sumi(int v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+  return v;
+}
+
+// Threshold of user t of the slice computed by the whole warp: lane l takes
+// edges l, l + 32, ... of the user (re-read from L1; the warp has just
+// streamed them), the Michelot sums and the pair-arithmetic refinement are
+// warp reductions in a fixed order, and every lane deposits the x of its own
+// edges.  Returns the threshold (tau, taul) and whether the inequality
+// simplex took tau = 0.
+template <class P, bool STATS>
+__device__ __forceinline__ void coop_user(const Seg& S, const float* __restrict__ ys, unsigned long long* accG,
+                                          unsigned long long* accC, unsigned long long* accQ,
+                                          const int32_t* __restrict__ cp0, const typename P::T* __restrict__ vp0,
+                                          int w, int t, float m1, float& tau, float& taul, bool& zero, float& ob) {
   const int lane = threadIdx.x & 31;
-  const int64_t s = __ldg(D.rp + u);
-  const int64_t d = __ldg(D.rp + u + 1) - s;
-  const VT* __restrict__ cp = static_cast<const VT*>(D.c);
-  const VT* __restrict__ ap = static_cast<const VT*>(D.a);
-  float tau = 0.f, taul = 0.f;
-  if (S.kind != DLM_BOX && d > 0) {
-    const bool eq = S.kind == DLM_SIMPLEX_EQ;
-    float m = -INFINITY;
-    for (int64_t i = lane; i < d; i += 32) {
-      const int64_t e = s + i;
-      m = fmaxf(m, -fmaf(ld_val(ap, e), ys[__ldg(D.col + e)], ld_val(cp, e)));
+  const bool box = S.kind == DLM_BOX;
+  const bool eq = S.kind == DLM_SIMPLEX_EQ;
+  auto uval = [&](int k, int& j, float& c, float& a) {
+    j = __ldg(cp0 + 32 * k + t);
+    P::get(__ldg(vp0 + 32 * k + t), c, a);
+    return -fmaf(a, ys[j], c);
+  };
+  tau = 0.f;
+  taul = 0.f;
+  zero = box;
+  if (!box) {
+    tau = m1 - S.gz;
+    int prevn = -1;
+    for (int it = 0; it < 256; ++it) {
+      float sm = 0.f;
+      int n = 0;
+      for (int k = lane; k < w; k += 32) {
+        int j;
+        float c, a;
+        const float u = uval(k, j, c, a);
+        if (u > tau) {
+          sm += u;
+          ++n;
+        }
+      }
+      sm = warp_sum(sm);
+      n = warp_sumi(n);
+      if (n == prevn || n == 0) break;
+      prevn = n;
+      const float tn = __fdiv_rn(sm - S.gz, static_cast<float>(n));
+      if (tn == tau) break;
+      tau = tn;
     }
-    m = warp_max(m);
-    if (eq || m > 0.f) {
-      tau = m - S.gz;
+    zero = !eq && tau <= 0.f;
+    if (!zero) {
+      F2 sum{0.f, 0.f};
+      int n = 0;
+      for (int k = lane; k < w; k += 32) {
+        int j;
+        float c, a;
+        if (uval(k, j, c, a) > tau) {
+          sum = f2_add(sum, u_pair(c, a, ys[j]));
+          ++n;
+        }
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        const F2 other{__shfl_xor_sync(kFull, sum.h, o), __shfl_xor_sync(kFull, sum.l, o)};
+        sum = f2_add(sum, other);
+        n += __shfl_xor_sync(kFull, n, o);
+      }
+      const F2 t2 = f2_threshold(sum, S.gz, S.gzl, n > 0 ? n : 1);
+      if (!eq && t2.h + t2.l <= 0.f) {
+        zero = true;
+      } else {
+        tau = t2.h;
+        taul = t2.l;
+      }
+    }
+  }
+  if (zero) tau = taul = 0.f;
+  for (int k = lane; k < w; k += 32) {
+    int j;
+    float c, a;
+    if (uval(k, j, c, a) > tau) {
+      const float x = x_general(S, box, zero, tau, taul, c, a, ys[j]);
+      if (x > 0.f) deposit<STATS>(S, j, c, a, x, accG, accC, accQ, ob);
+    }
+  }
+}
+
+// Users of a slice that need the general threshold path are handled by the
+// whole warp, one after another, unless at least this many of the 32 do (then
+// each lane runs its own user, which keeps the lanes busy).
+constexpr int kCoopMax = 12;
+
+// One slice: lane t = user t.  cp/vp point at the lane's first edge; edge k
+// is at cp[32 k].
+template <class P, bool STATS>
+__device__ __forceinline__ void do_slice(const InstDesc& D, const Seg& S, const float* __restrict__ ys,
+                                         unsigned long long* accG, unsigned long long* accC,
+                                         unsigned long long* accQ, int64_t s, double& wobj) {
+  const int lane = threadIdx.x & 31;
+  const int64_t off = __ldg(D.slice_off + s);
+  const int w = __ldg(D.slice_w + s);
+  const int32_t* __restrict__ cp = D.col + off + lane;
+  const typename P::T* __restrict__ vp = static_cast<const typename P::T*>(D.ca) + off + lane;
+  const bool box = S.kind == DLM_BOX;
+  const bool eq = S.kind == DLM_SIMPLEX_EQ;
+
+  // Pass A: the row's largest u (m1, at edge k1) and second largest (m2).
+  float m1 = -INFINITY, m2 = -INFINITY;
+  int k1 = 0;
+#pragma unroll 8
+  for (int k = 0; k < w; ++k) {
+    const int j = __ldg(cp + 32 * k);
+    float c, a;
+    P::get(__ldg(vp + 32 * k), c, a);
+    const float u = -fmaf(a, ys[j], c);
+    m2 = fmaxf(m2, fminf(m1, u));
+    k1 = (u > m1) ? k : k1;
+    m1 = fmaxf(m1, u);
+  }
+
+  // mode 0: no edge active; 1: the maximum alone, x = z; 2: general.
+  const float t1 = m1 - S.gz;
+  int mode;
+  if (box)
+    mode = (m1 > 0.f) ? 2 : 0;
+  else if (m1 == -INFINITY || (!eq && m1 <= 0.f))
+    mode = 0;
+  else if (m2 <= t1 && (eq || t1 >= 0.f))
+    mode = 1;
+  else
+    mode = 2;
+
+  float ob = 0.f;
+  float tau = 0.f, taul = 0.f;
+  bool zero = box;
+  const unsigned mask2 = __ballot_sync(kFull, mode == 2);
+  const bool coop = mask2 != 0u && __popc(mask2) < kCoopMax;  // warp-uniform
+  if (coop) {
+    const int32_t* cp0 = D.col + off;
+    const typename P::T* vp0 = static_cast<const typename P::T*>(D.ca) + off;
+    unsigned m = mask2;
+    while (m) {
+      const int t = __ffs(m) - 1;
+      m &= m - 1;
+      const float mt = __shfl_sync(kFull, m1, t);
+      float ta, tl;
+      bool zr;
+      coop_user<P, STATS>(S, ys, accG, accC, accQ, cp0, vp0, w, t, mt, ta, tl, zr, ob);
+      if (lane == t) {
+        tau = ta;
+        taul = tl;
+        zero = zr;
+      }
+    }
+  }
+  if (mode == 2 && !coop) {
+    // per-lane general path
+    if (!box) {
+      tau = t1;
       int prevn = -1;
       for (int it = 0; it < 256; ++it) {
         float sm = 0.f;
         int n = 0;
-        for (int64_t i = lane; i < d; i += 32) {
-          const int64_t e = s + i;
-          const float uv = -fmaf(ld_val(ap, e), ys[__ldg(D.col + e)], ld_val(cp, e));
-          if (uv > tau) {
-            sm += uv;
+        for (int k = 0; k < w; ++k) {
+          const int j = __ldg(cp + 32 * k);
+          float c, a;
+          P::get(__ldg(vp + 32 * k), c, a);
+          const float u = -fmaf(a, ys[j], c);
+          if (u > tau) {
+            sm += u;
             ++n;
           }
         }
-        sm = warp_sum(sm);
-        n = warp_sumi(n);
         if (n == prevn || n == 0) break;
         prevn = n;
         const float tn = __fdiv_rn(sm - S.gz, static_cast<float>(n));
         if (tn == tau) break;
         tau = tn;
       }
-      if (!eq && tau <= 0.f) {
-        tau = 0.f;
-      } else {
+      zero = !eq && tau <= 0.f;
+      if (!zero) {
         F2 sum{0.f, 0.f};
         int n = 0;
-        for (int64_t i = lane; i < d; i += 32) {
-          const int64_t e = s + i;
-          const int j = __ldg(D.col + e);
-          const float cv = ld_val(cp, e), av = ld_val(ap, e);
-          if (-fmaf(av, ys[j], cv) > tau) {
-            sum = f2_add(sum, u_pair(cv, av, ys[j]));
+        for (int k = 0; k < w; ++k) {
+          const int j = __ldg(cp + 32 * k);
+          float c, a;
+          P::get(__ldg(vp + 32 * k), c, a);
+          if (-fmaf(a, ys[j], c) > tau) {
+            sum = f2_add(sum, u_pair(c, a, ys[j]));
             ++n;
           }
         }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-          const F2 other{__shfl_xor_sync(kFull, sum.h, o), __shfl_xor_sync(kFull, sum.l, o)};
-          sum = f2_add(sum, other);
-          n += __shfl_xor_sync(kFull, n, o);
-        }
         const F2 t2 = f2_threshold(sum, S.gz, S.gzl, n > 0 ? n : 1);
         if (!eq && t2.h + t2.l <= 0.f) {
-          tau = 0.f;
+          zero = true;
         } else {
           tau = t2.h;
           taul = t2.l;
         }
       }
-    } else {
-      tau = 0.f;
     }
-  }
-  float ob = 0.f;
-  const int64_t off = (STATS && D.xout != nullptr) ? __ldg(D.orig_off + u) : 0;
-  for (int64_t i = lane; i < d; i += 32) {
-    const int64_t e = s + i;
-    const int j = __ldg(D.col + e);
-    const float cv = ld_val(cp, e), av = ld_val(ap, e);
-    const float uv = -fmaf(av, ys[j], cv);
-    float x = 0.f;
-    if (S.kind == DLM_BOX) {
-      if (uv > 0.f) {
-        const F2 up = u_pair(cv, av, ys[j]);
-        x = fminf((up.h + up.l) * S.invg, S.z);
-      }
-    } else if (uv > tau) {
-      const F2 up = u_pair(cv, av, ys[j]);
-      x = fmaxf((up.h - tau) + (up.l - taul), 0.f) * S.invg;
-    }
-    if (x > 0.f) {
-      atomicAdd(&accG[j], fixp(av * x, S.scaleG));
-      if (STATS) {
-        atomicAdd(&accC[j], fixp(cv * x, S.scaleC));
-        atomicAdd(&accQ[j], fixp(x * x, S.scaleQ));
-        ob += fmaf(0.5f * S.gamma * x, x, cv * x);
+    if (zero) tau = taul = 0.f;
+    // x on the active edges (u > tau; for the box and tau = 0, u > 0)
+    for (int k = 0; k < w; ++k) {
+      const int j = __ldg(cp + 32 * k);
+      float c, a;
+      P::get(__ldg(vp + 32 * k), c, a);
+      if (-fmaf(a, ys[j], c) > tau) {
+        const float x = x_general(S, box, zero, tau, taul, c, a, ys[j]);
+        if (x > 0.f) deposit<STATS>(S, j, c, a, x, accG, accC, accQ, ob);
       }
     }
-    if (STATS && D.xout != nullptr) D.xout[off + i] = x;
+  } else if (mode == 1) {
+    const int j = __ldg(cp + 32 * k1);
+    float c, a;
+    P::get(__ldg(vp + 32 * k1), c, a);
+    deposit<STATS>(S, j, c, a, S.z, accG, accC, accQ, ob);
   }
+
   if (STATS) {
-    ob = warp_sum(ob);
-    if (lane == 0 && d > 0) wobj += static_cast<double>(ob);
+    const int64_t u = 32 * s + lane;
+    if (D.xout != nullptr && u < D.nusers) {
+      // x in the caller's order, every edge of the user
+      const int64_t o = __ldg(D.orig_off + u);
+      const int d = __ldg(D.udeg + u);
+      for (int k = 0; k < d; ++k) {
+        float x = 0.f;
+        if (mode == 1) {
+          x = (k == k1) ? S.z : 0.f;
+        } else if (mode == 2) {
+          const int j = __ldg(cp + 32 * k);
+          float c, a;
+          P::get(__ldg(vp + 32 * k), c, a);
+          if (-fmaf(a, ys[j], c) > tau) x = x_general(S, box, zero, tau, taul, c, a, ys[j]);
+        }
+        D.xout[o + k] = x;
+      }
+    }
+    wobj += static_cast<double>(ob);
   }
 }
 
-template <typename VT, bool STATS>
-__global__ void __launch_bounds__(kSweepThreads, 2)
+template <class P, bool STATS>
+__global__ void __launch_bounds__(kSweepThreads, 1)
     sweep_kernel(const InstDesc* __restrict__ insts, const Task* __restrict__ tasks,
                  const int32_t* __restrict__ cta_task, int smemJ) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -363,9 +378,7 @@ __global__ void __launch_bounds__(kSweepThreads, 2)
   double* wsum = reinterpret_cast<double*>(ys + ((smemJ + 1) & ~1));
 
   __shared__ InstDesc sD;
-  __shared__ Task sT[kMaxSegTasks];
-  __shared__ int sPre[kMaxSegTasks + 1];
-
+  __shared__ unsigned long long s_next;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int nw = blockDim.x >> 5;
   const int t_last = cta_task[blockIdx.x + 1];
@@ -373,17 +386,8 @@ __global__ void __launch_bounds__(kSweepThreads, 2)
   while (t < t_last) {
     const int inst = tasks[t].inst;
     int te = t + 1;
-    while (te < t_last && tasks[te].inst == inst && te - t < kMaxSegTasks) ++te;
-    if (threadIdx.x == 0) {
-      sD = insts[inst];
-      sPre[0] = 0;
-      for (int k = 0; k < te - t; ++k) {
-        const Task T = tasks[t + k];
-        sT[k] = T;
-        const int up = map_users_per_pass(T.map);
-        sPre[k + 1] = sPre[k] + (T.u1 - T.u0 + up - 1) / up;
-      }
-    }
+    while (te < t_last && tasks[te].inst == inst) ++te;
+    if (threadIdx.x == 0) sD = insts[inst];
     __syncthreads();
     const int J = sD.J;
     for (int j = threadIdx.x; j < J; j += blockDim.x) {
@@ -408,31 +412,30 @@ __global__ void __launch_bounds__(kSweepThreads, 2)
       S.scaleQ = sD.scaleQ;
       S.kind = sD.kind;
     }
+    if (threadIdx.x == 0) s_next = 0;
     __syncthreads();
     double wobj = 0.0;
-    const int ntask = te - t;
-    const int total = sPre[ntask];
-    for (int p = warp; p < total; p += nw) {
-      int k = 0;
-      while (p >= sPre[k + 1]) ++k;
-      const Task T = sT[k];
-      const int64_t uf = T.u0 + static_cast<int64_t>(p - sPre[k]) * map_users_per_pass(T.map);
-      const int64_t ue = T.u1;
-      switch (T.map) {
-        case kMapStream: pass_stream<VT, STATS>(sD, S, ys, accG, accC, accQ, uf, wobj); break;
-        case kMapL1K4: pass_reg<1, 4, VT, STATS>(sD, S, ys, accG, accC, accQ, uf, ue, wobj); break;
-        case kMapL1K8: pass_reg<1, 8, VT, STATS>(sD, S, ys, accG, accC, accQ, uf, ue, wobj); break;
-        case kMapL2K8: pass_reg<2, 8, VT, STATS>(sD, S, ys, accG, accC, accQ, uf, ue, wobj); break;
-        case kMapL4K8: pass_reg<4, 8, VT, STATS>(sD, S, ys, accG, accC, accQ, uf, ue, wobj); break;
-        case kMapL8K8: pass_reg<8, 8, VT, STATS>(sD, S, ys, accG, accC, accQ, uf, ue, wobj); break;
-        case kMapL16K8: pass_reg<16, 8, VT, STATS>(sD, S, ys, accG, accC, accQ, uf, ue, wobj); break;
-        case kMapL32K8: pass_reg<32, 8, VT, STATS>(sD, S, ys, accG, accC, accQ, uf, ue, wobj); break;
-        case kMapL2K4: pass_reg<2, 4, VT, STATS>(sD, S, ys, accG, accC, accQ, uf, ue, wobj); break;
-        case kMapL4K4: pass_reg<4, 4, VT, STATS>(sD, S, ys, accG, accC, accQ, uf, ue, wobj); break;
-        case kMapL8K4: pass_reg<8, 4, VT, STATS>(sD, S, ys, accG, accC, accQ, uf, ue, wobj); break;
-        case kMapL16K4: pass_reg<16, 4, VT, STATS>(sD, S, ys, accG, accC, accQ, uf, ue, wobj); break;
-        case kMapL32K4: pass_reg<32, 4, VT, STATS>(sD, S, ys, accG, accC, accQ, uf, ue, wobj); break;
-        default: break;
+    for (int k = t; k < te; ++k) {
+      const Task T = tasks[k];
+      if (STATS) {
+        // static order: the FP64 objective partials are summed in a fixed order
+        const int64_t step = static_cast<int64_t>(T.stride) * nw;
+        for (int64_t s = T.first + static_cast<int64_t>(T.stride) * warp; s < T.end; s += step)
+          do_slice<P, STATS>(sD, S, ys, accG, accC, accQ, s, wobj);
+      } else {
+        // dynamic order within the CTA (item sums are exact, so the order of
+        // slices does not change any result)
+        const int64_t nsl = (T.end - T.first + T.stride - 1) / T.stride;
+        for (;;) {
+          int64_t i = 0;
+          if (lane == 0) i = atomicAdd(&s_next, 1ull);
+          i = __shfl_sync(kFull, i, 0);
+          if (i >= nsl) break;
+          do_slice<P, STATS>(sD, S, ys, accG, accC, accQ, T.first + i * T.stride, wobj);
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) s_next = 0;
+        __syncthreads();
       }
     }
     if (STATS) {
@@ -451,75 +454,61 @@ __global__ void __launch_bounds__(kSweepThreads, 2)
       }
     }
     if (STATS && threadIdx.x == 0) {
-      double s = 0.0;
-      for (int w = 0; w < nw; ++w) s += wsum[w];
-      sD.seg_obj[t] = s;
+      double sum = 0.0;
+      for (int w = 0; w < nw; ++w) sum += wsum[w];
+      sD.seg_obj[t] = sum;
     }
     __syncthreads();
     t = te;
   }
 }
 
-template <typename VT, bool STATS>
+template <class P, bool STATS>
 constexpr auto kernel_of() {
-  return &sweep_kernel<VT, STATS>;
+  return &sweep_kernel<P, STATS>;
 }
 
 }  // namespace
 
-size_t sweep_smem_bytes(int smemJ, bool stats, bool /*bf16*/) {
+size_t sweep_smem_bytes(int smemJ, bool stats) {
   const size_t J = static_cast<size_t>(smemJ);
-  return (stats ? 3 : 1) * J * 8 + ((J + 1) & ~static_cast<size_t>(1)) * 4 + (kSweepThreads / 32) * 8;
+  return (stats ? 3 : 1) * J * 8 + ((J + 1) & ~static_cast<size_t>(1)) * 4 + 32 * 8;
 }
 
 size_t sweep_smem_limit() {
   int dev = 0, optin = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return 0;
   if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess) return 0;
-  // room for the kernel's static shared memory
-  return optin > 4096 ? static_cast<size_t>(optin - 4096) : 0;
+  return optin > 1024 ? static_cast<size_t>(optin - 1024) : 0;  // room for static shared memory
 }
 
 cudaError_t sweep_prepare(bool bf16) {
   const int lim = static_cast<int>(sweep_smem_limit());
   cudaError_t e;
   if (bf16) {
-    e = cudaFuncSetAttribute(kernel_of<__nv_bfloat16, false>(), cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+    e = cudaFuncSetAttribute(kernel_of<BF16Pair, false>(), cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
     if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(kernel_of<__nv_bfloat16, true>(), cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+    e = cudaFuncSetAttribute(kernel_of<BF16Pair, true>(), cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
   } else {
-    e = cudaFuncSetAttribute(kernel_of<float, false>(), cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+    e = cudaFuncSetAttribute(kernel_of<F32Pair, false>(), cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
     if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(kernel_of<float, true>(), cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+    e = cudaFuncSetAttribute(kernel_of<F32Pair, true>(), cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
   }
   return e;
 }
 
-int sweep_occupancy(int smemJ, bool stats, bool bf16) {
-  int n = 0;
-  const size_t sm = sweep_smem_bytes(smemJ, stats, bf16);
-  cudaError_t e;
-  if (bf16)
-    e = stats ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kernel_of<__nv_bfloat16, true>(), kSweepThreads, sm)
-              : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kernel_of<__nv_bfloat16, false>(), kSweepThreads, sm);
-  else
-    e = stats ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kernel_of<float, true>(), kSweepThreads, sm)
-              : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kernel_of<float, false>(), kSweepThreads, sm);
-  return e == cudaSuccess ? n : 0;
-}
-
 cudaError_t launch_sweep(const SweepLaunch& L, bool stats, bool bf16) {
-  const size_t sm = sweep_smem_bytes(L.smemJ, stats, bf16);
+  const size_t sm = sweep_smem_bytes(L.smemJ, stats);
   if (bf16) {
     if (stats)
-      sweep_kernel<__nv_bfloat16, true><<<L.grid, kSweepThreads, sm, L.stream>>>(L.inst, L.tasks, L.cta_task, L.smemJ);
+      sweep_kernel<BF16Pair, true><<<L.grid, kSweepThreads, sm, L.stream>>>(L.inst, L.tasks, L.cta_task, L.smemJ);
     else
-      sweep_kernel<__nv_bfloat16, false><<<L.grid, kSweepThreads, sm, L.stream>>>(L.inst, L.tasks, L.cta_task, L.smemJ);
+      sweep_kernel<BF16Pair, false><<<L.grid, kSweepThreads, sm, L.stream>>>(L.inst, L.tasks, L.cta_task, L.smemJ);
   } else {
     if (stats)
-      sweep_kernel<float, true><<<L.grid, kSweepThreads, sm, L.stream>>>(L.inst, L.tasks, L.cta_task, L.smemJ);
+      sweep_kernel<F32Pair, true><<<L.grid, kSweepThreads, sm, L.stream>>>(L.inst, L.tasks, L.cta_task, L.smemJ);
     else
-      sweep_kernel<float, false><<<L.grid, kSweepThreads, sm, L.stream>>>(L.inst, L.tasks, L.cta_task, L.smemJ);
+      sweep_kernel<F32Pair, false><<<L.grid, kSweepThreads, sm, L.stream>>>(L.inst, L.tasks, L.cta_task, L.smemJ);
   }
   return cudaGetLastError();
 }

@@ -74,7 +74,7 @@ __global__ void __launch_bounds__(kUpdThreads) fista_update_kernel(const UpdInst
     U.lam[j] = ln;
     U.y[j] = yn;
     U.acc[j] = 0ull;
-    if (!isfinite(G) || !isfinite(yn)) bad = 1.0;
+    if (!isfinite(G) || !isfinite(yj) || !isfinite(yn)) bad = 1.0;
   }
   bad = block_max(bad, sh);
   if (threadIdx.x == 0) {

@@ -7,12 +7,16 @@
 // column per source, Sec. 4.1).  Users are stably sorted by degree, largest
 // first (the paper buckets by degree to limit padding, Sec. 4.2; sorting by
 // the exact degree takes that to its limit), and cut into slices of 32
-// consecutive users.  A slice of width w (its largest degree) stores edge k of
-// its user t at slice_off + 32 k + t, for the item index stream and for the
-// interleaved (c, a) stream, so that lane t of a warp reads user t's edges
-// and every warp load is one contiguous 128-byte line per stream.  Edges past
-// a user's degree are padding with c = +inf, a = 0 (they give u = -inf and
-// are never active).  Users with no edges are dropped from the slices.
+// consecutive users.  A slice of width w (its largest degree) holds 32 w
+// elements per stream (item index; interleaved (c, a)).  Its first 4 (w / 4)
+// edges of every user are stored in groups of four: edge k < 4 (w / 4) of
+// user t at slice_off + 4 (32 (k / 4) + t) + k % 4, so that lane t reads four
+// consecutive edges of its user with one 128-bit load (one float2 pair per
+// edge in FP32: two 128-bit loads) and a warp load covers 512 contiguous
+// bytes.  The remaining w % 4 edges follow edge-major: edge k at
+// slice_off + 128 (w / 4) + 32 (k - 4 (w / 4)) + t.  Edges past a user's
+// degree are padding with c = +inf, a = 0 (they give u = -inf and are never
+// active).  Users with no edges are dropped from the slices.
 #include <cub/cub.cuh>
 
 #include <cmath>
@@ -154,11 +158,14 @@ __global__ void k_gather(const int64_t* rp, const int32_t* col, const void* c, c
       udeg[u] = d;
     }
     const int w = width[s];
-    const int64_t base = slice_off[s] + lane;
+    const int w4 = w >> 2;
+    const int64_t base = slice_off[s];
     for (int k = 0; k < w; ++k) {
       const bool v = k < d;
-      col_o[base + 32 * static_cast<int64_t>(k)] = v ? col[r + k] : 0;
-      ca_o[base + 32 * static_cast<int64_t>(k)] = v ? pack_ca<CA>(c, a, r + k) : pad_ca<CA>();
+      const int64_t e = k < 4 * w4 ? base + 4 * (32 * static_cast<int64_t>(k >> 2) + lane) + (k & 3)
+                                   : base + 128 * static_cast<int64_t>(w4) + 32 * static_cast<int64_t>(k - 4 * w4) + lane;
+      col_o[e] = v ? col[r + k] : 0;
+      ca_o[e] = v ? pack_ca<CA>(c, a, r + k) : pad_ca<CA>();
     }
   }
 }

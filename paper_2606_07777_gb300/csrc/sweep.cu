@@ -9,8 +9,8 @@
 // and optionally writes x in the caller's edge order.
 //
 // Layout and mapping: users sit in degree-sorted slices of 32 (layout.cu);
-// lane t of a warp owns user t of its slice and walks the user's edges, one
-// coalesced 128-byte line per stream and step.  The item dual y lives in
+// lane t of a warp owns user t of its slice and walks the user's edges four
+// at a time with 128-bit loads (512 contiguous bytes per warp load).  The item dual y lives in
 // shared memory (gathered by item index); item sums are accumulated in
 // shared memory and flushed once per CTA.
 //
@@ -40,12 +40,19 @@ namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
 
-// One interleaved (c, a) element.
+// One interleaved (c, a) element, and a group of four consecutive edges of a
+// lane (element index 4 q .. 4 q + 3 of the stream, 16-byte aligned).
 struct F32Pair {
   using T = float2;
   __device__ __forceinline__ static void get(const T& w, float& c, float& a) {
     c = w.x;
     a = w.y;
+  }
+  __device__ __forceinline__ static void get4(const T* base, int q, float c[4], float a[4]) {
+    const float4* p = reinterpret_cast<const float4*>(base) + 2 * q;
+    const float4 v0 = __ldg(p), v1 = __ldg(p + 1);
+    c[0] = v0.x, a[0] = v0.y, c[1] = v0.z, a[1] = v0.w;
+    c[2] = v1.x, a[2] = v1.y, c[3] = v1.z, a[3] = v1.w;
   }
 };
 struct BF16Pair {
@@ -54,7 +61,20 @@ struct BF16Pair {
     c = __uint_as_float(w << 16);
     a = __uint_as_float(w & 0xffff0000u);
   }
+  __device__ __forceinline__ static void get4(const T* base, int q, float c[4], float a[4]) {
+    const uint4 v = __ldg(reinterpret_cast<const uint4*>(base) + q);
+    get(v.x, c[0], a[0]);
+    get(v.y, c[1], a[1]);
+    get(v.z, c[2], a[2]);
+    get(v.w, c[3], a[3]);
+  }
 };
+
+// Position of edge k of lane t inside a slice of width w (w4 = w / 4 groups
+// of four edges per lane, then w % 4 edges edge-major; see layout.cu).
+__device__ __forceinline__ int sell_el(int k, int t, int w4) {
+  return k < 4 * w4 ? 4 * (32 * (k >> 2) + t) + (k & 3) : 128 * w4 + 32 * (k - 4 * w4) + t;
+}
 
 __device__ __forceinline__ unsigned long long fixp(float v, float scale) {
   return static_cast<unsigned long long>(__float2ll_rn(v * scale));
@@ -138,13 +158,15 @@ template <class P, bool STATS>
 __device__ __forceinline__ void coop_user(const Seg& S, const float* __restrict__ ys, unsigned long long* accG,
                                           unsigned long long* accC, unsigned long long* accQ,
                                           const int32_t* __restrict__ cp0, const typename P::T* __restrict__ vp0,
-                                          int w, int t, float m1, float& tau, float& taul, bool& zero, float& ob) {
+                                          int w, int w4, int t, float m1, float& tau, float& taul, bool& zero,
+                                          float& ob) {
   const int lane = threadIdx.x & 31;
   const bool box = S.kind == DLM_BOX;
   const bool eq = S.kind == DLM_SIMPLEX_EQ;
   auto uval = [&](int k, int& j, float& c, float& a) {
-    j = __ldg(cp0 + 32 * k + t);
-    P::get(__ldg(vp0 + 32 * k + t), c, a);
+    const int e = sell_el(k, t, w4);
+    j = __ldg(cp0 + e);
+    P::get(__ldg(vp0 + e), c, a);
     return -fmaf(a, ys[j], c);
   };
   tau = 0.f;
@@ -216,8 +238,8 @@ __device__ __forceinline__ void coop_user(const Seg& S, const float* __restrict_
 // each lane runs its own user, which keeps the lanes busy).
 constexpr int kCoopMax = 12;
 
-// One slice: lane t = user t.  cp/vp point at the lane's first edge; edge k
-// is at cp[32 k].
+// One slice: lane t = user t; edge k of lane t is element sell_el(k, t, w/4)
+// of the slice.
 template <class P, bool STATS>
 __device__ __forceinline__ void do_slice(const InstDesc& D, const Seg& S, const float* __restrict__ ys,
                                          unsigned long long* accG, unsigned long long* accC,
@@ -225,19 +247,35 @@ __device__ __forceinline__ void do_slice(const InstDesc& D, const Seg& S, const 
   const int lane = threadIdx.x & 31;
   const int64_t off = __ldg(D.slice_off + s);
   const int w = __ldg(D.slice_w + s);
-  const int32_t* __restrict__ cp = D.col + off + lane;
-  const typename P::T* __restrict__ vp = static_cast<const typename P::T*>(D.ca) + off + lane;
+  const int w4 = w >> 2;
+  const int32_t* __restrict__ col0 = D.col + off;
+  const typename P::T* __restrict__ ca0 = static_cast<const typename P::T*>(D.ca) + off;
   const bool box = S.kind == DLM_BOX;
   const bool eq = S.kind == DLM_SIMPLEX_EQ;
 
   // Pass A: the row's largest u (m1, at edge k1) and second largest (m2).
   float m1 = -INFINITY, m2 = -INFINITY;
   int k1 = 0;
-#pragma unroll 8
-  for (int k = 0; k < w; ++k) {
-    const int j = __ldg(cp + 32 * k);
+#pragma unroll 4
+  for (int g = 0; g < w4; ++g) {
+    const int q = 32 * g + lane;
+    const int4 jv = __ldg(reinterpret_cast<const int4*>(col0) + q);
+    float c[4], a[4];
+    P::get4(ca0, q, c, a);
+    const int jj[4] = {jv.x, jv.y, jv.z, jv.w};
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      const float u = -fmaf(a[e], ys[jj[e]], c[e]);
+      m2 = fmaxf(m2, fminf(m1, u));
+      k1 = (u > m1) ? 4 * g + e : k1;
+      m1 = fmaxf(m1, u);
+    }
+  }
+  for (int k = 4 * w4; k < w; ++k) {
+    const int el = 128 * w4 + 32 * (k - 4 * w4) + lane;
+    const int j = __ldg(col0 + el);
     float c, a;
-    P::get(__ldg(vp + 32 * k), c, a);
+    P::get(__ldg(ca0 + el), c, a);
     const float u = -fmaf(a, ys[j], c);
     m2 = fmaxf(m2, fminf(m1, u));
     k1 = (u > m1) ? k : k1;
@@ -262,8 +300,6 @@ __device__ __forceinline__ void do_slice(const InstDesc& D, const Seg& S, const 
   const unsigned mask2 = __ballot_sync(kFull, mode == 2);
   const bool coop = mask2 != 0u && __popc(mask2) < kCoopMax;  // warp-uniform
   if (coop) {
-    const int32_t* cp0 = D.col + off;
-    const typename P::T* vp0 = static_cast<const typename P::T*>(D.ca) + off;
     unsigned m = mask2;
     while (m) {
       const int t = __ffs(m) - 1;
@@ -271,7 +307,7 @@ __device__ __forceinline__ void do_slice(const InstDesc& D, const Seg& S, const 
       const float mt = __shfl_sync(kFull, m1, t);
       float ta, tl;
       bool zr;
-      coop_user<P, STATS>(S, ys, accG, accC, accQ, cp0, vp0, w, t, mt, ta, tl, zr, ob);
+      coop_user<P, STATS>(S, ys, accG, accC, accQ, col0, ca0, w, w4, t, mt, ta, tl, zr, ob);
       if (lane == t) {
         tau = ta;
         taul = tl;
@@ -288,9 +324,10 @@ __device__ __forceinline__ void do_slice(const InstDesc& D, const Seg& S, const 
         float sm = 0.f;
         int n = 0;
         for (int k = 0; k < w; ++k) {
-          const int j = __ldg(cp + 32 * k);
+          const int el = sell_el(k, lane, w4);
+          const int j = __ldg(col0 + el);
           float c, a;
-          P::get(__ldg(vp + 32 * k), c, a);
+          P::get(__ldg(ca0 + el), c, a);
           const float u = -fmaf(a, ys[j], c);
           if (u > tau) {
             sm += u;
@@ -308,9 +345,10 @@ __device__ __forceinline__ void do_slice(const InstDesc& D, const Seg& S, const 
         F2 sum{0.f, 0.f};
         int n = 0;
         for (int k = 0; k < w; ++k) {
-          const int j = __ldg(cp + 32 * k);
+          const int el = sell_el(k, lane, w4);
+          const int j = __ldg(col0 + el);
           float c, a;
-          P::get(__ldg(vp + 32 * k), c, a);
+          P::get(__ldg(ca0 + el), c, a);
           if (-fmaf(a, ys[j], c) > tau) {
             sum = f2_add(sum, u_pair(c, a, ys[j]));
             ++n;
@@ -328,18 +366,20 @@ __device__ __forceinline__ void do_slice(const InstDesc& D, const Seg& S, const 
     if (zero) tau = taul = 0.f;
     // x on the active edges (u > tau; for the box and tau = 0, u > 0)
     for (int k = 0; k < w; ++k) {
-      const int j = __ldg(cp + 32 * k);
+      const int el = sell_el(k, lane, w4);
+      const int j = __ldg(col0 + el);
       float c, a;
-      P::get(__ldg(vp + 32 * k), c, a);
+      P::get(__ldg(ca0 + el), c, a);
       if (-fmaf(a, ys[j], c) > tau) {
         const float x = x_general(S, box, zero, tau, taul, c, a, ys[j]);
         if (x > 0.f) deposit<STATS>(S, j, c, a, x, accG, accC, accQ, ob);
       }
     }
   } else if (mode == 1) {
-    const int j = __ldg(cp + 32 * k1);
+    const int el = sell_el(k1, lane, w4);
+    const int j = __ldg(col0 + el);
     float c, a;
-    P::get(__ldg(vp + 32 * k1), c, a);
+    P::get(__ldg(ca0 + el), c, a);
     deposit<STATS>(S, j, c, a, S.z, accG, accC, accQ, ob);
   }
 
@@ -354,9 +394,10 @@ __device__ __forceinline__ void do_slice(const InstDesc& D, const Seg& S, const 
         if (mode == 1) {
           x = (k == k1) ? S.z : 0.f;
         } else if (mode == 2) {
-          const int j = __ldg(cp + 32 * k);
+          const int el = sell_el(k, lane, w4);
+          const int j = __ldg(col0 + el);
           float c, a;
-          P::get(__ldg(vp + 32 * k), c, a);
+          P::get(__ldg(ca0 + el), c, a);
           if (-fmaf(a, ys[j], c) > tau) x = x_general(S, box, zero, tau, taul, c, a, ys[j]);
         }
         D.xout[o + k] = x;

@@ -193,6 +193,33 @@ dlm_status dlm_get_info(dlm_problem* p, int64_t* num_users, int64_t* num_items, 
 
 void dlm_destroy(dlm_problem* p);
 
+/* One dual evaluation straight from the caller's device CSR arrays, with no
+ * device memory allocated by this call or any earlier one: for callers that
+ * cannot call cudaMalloc (a process whose device memory belongs to another
+ * framework's allocator, a fixed memory budget, code that must not allocate
+ * after start-up).  The paper has no counterpart; it computes what
+ * dlm_calculate computes (g(lambda), grad g(lambda) = A x - b, x(lambda))
+ * for FP32 c and a, without a handle.
+ *   row_ptr, item_idx, c, a, b, lambda: device arrays as in dlm_problem_desc
+ *     (valid CSR; an out-of-range item or row pointer makes the call write
+ *     NaN to g and grad instead of reading out of bounds);
+ *   kind, z: the simple sets; gamma > 0: the ridge;
+ *   g: device double (1), grad: device float (num_items) or NULL,
+ *   x: device float (nnz, caller's edge order) or NULL.
+ * Asynchronous on `stream` (a cudaStream_t; NULL = legacy default stream).
+ * Scratch: one file-scope device array of 1.5 MB (fixed-point item sums for
+ * up to 65,536 items, objective partials, bounds), held on every GPU that
+ * loads the library until the process exits; num_items > 65,536 returns
+ * DLM_ERR_UNSUPPORTED.  The first call on a device looks the array's device
+ * address up (cudaGetSymbolAddress), so make that first call before any
+ * stream capture.  Every call clears the scratch it needs at its start and
+ * leaves it cleared at its end; calls that overlap on the GPU share the
+ * array and race, so issue them one after another on one stream. */
+dlm_status dlm_calculate_static(int64_t num_users, int64_t num_items, int64_t nnz, const int64_t* row_ptr,
+                                const int32_t* item_idx, const float* c, const float* a, const double* b,
+                                int32_t kind, double z, const float* lambda, double gamma, double* g, float* grad,
+                                float* x, void* stream);
+
 /* Thread-local message describing the last failure on this thread ("" if none). */
 const char* dlm_last_error(void);
 

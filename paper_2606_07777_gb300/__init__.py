@@ -18,7 +18,7 @@ from . import _build
 __all__ = [
     "load", "build", "DlmError", "Solver", "dlm_create", "dlm_set_schedule", "dlm_set_options", "dlm_set_lambda",
     "dlm_calculate", "dlm_step", "dlm_solve", "dlm_get_stats", "dlm_get_lambda", "dlm_get_x", "dlm_get_state",
-    "dlm_set_state", "dlm_get_info", "dlm_step_timed", "dlm_destroy", "dlm_last_error",
+    "dlm_set_state", "dlm_get_info", "dlm_step_timed", "dlm_calculate_static", "dlm_destroy", "dlm_last_error",
 ]
 
 DLM_OK, DLM_ERR_INVALID_ARG, DLM_ERR_OOM, DLM_ERR_CUDA, DLM_ERR_NUMERIC, DLM_ERR_TIMEOUT, DLM_ERR_UNSUPPORTED = range(7)
@@ -84,6 +84,7 @@ _SIGS = {
     "dlm_set_state": [_vp, _vp, _vp, ctypes.POINTER(State), _i32],
     "dlm_get_info": [_vp, ctypes.POINTER(_i64), ctypes.POINTER(_i64), ctypes.POINTER(_i64), ctypes.POINTER(_i64)],
     "dlm_step_timed": [_vp, _i64, ctypes.POINTER(_d), ctypes.POINTER(_d), ctypes.POINTER(_d)],
+    "dlm_calculate_static": [_i64, _i64, _i64, _vp, _vp, _vp, _vp, _vp, _i32, _d, _vp, _d, _vp, _vp, _vp, _vp],
 }
 EXPORTS = list(_SIGS) + ["dlm_destroy", "dlm_last_error"]
 
@@ -215,6 +216,13 @@ def dlm_step_timed(h, n):
     v = [ctypes.c_double() for _ in range(3)]
     _call("dlm_step_timed", h, n, *[ctypes.byref(x) for x in v])
     return tuple(x.value for x in v)
+
+
+def dlm_calculate_static(num_users, num_items, nnz, row_ptr, item_idx, c, a, b, kind, z, lam, gamma, g, grad=None,
+                         x=None, stream=None):
+    """Allocation-free dual evaluation (device arrays; g is a device double)."""
+    _call("dlm_calculate_static", num_users, num_items, nnz, _ptr(row_ptr), _ptr(item_idx), _ptr(c), _ptr(a),
+          _ptr(b), kind, z, _ptr(lam), gamma, _ptr(g), _ptr(grad), _ptr(x), stream)
 
 
 def dlm_destroy(h):

@@ -13,11 +13,15 @@ namespace dlm {
 int fixed_point_shift(double bound);
 }
 
+namespace {
+thread_local std::string g_err;
+}
+
+void dlm::set_last_error(const std::string& m) { g_err = m; }
+
 using namespace dlm;
 
 namespace {
-
-thread_local std::string g_err;
 
 dlm_status fail(dlm_status s, const std::string& m) {
   g_err = m;

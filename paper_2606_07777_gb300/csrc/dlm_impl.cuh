@@ -106,6 +106,9 @@ struct StatsInst {
   int32_t certified;          // 0: scaled point not certified (EQ simplex or a < 0)
 };
 
+// Sets the thread-local message returned by dlm_last_error (api.cu).
+void set_last_error(const std::string& m);
+
 // ---- launchers (defined in the .cu files) ----
 size_t sweep_smem_bytes(int smemJ, bool stats);
 size_t sweep_smem_limit();             // usable dynamic shared memory per sweep CTA on this device

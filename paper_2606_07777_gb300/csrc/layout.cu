@@ -60,19 +60,27 @@ __global__ void k_rows(const int64_t* rp, int64_t I, int64_t nnz, int32_t* deg, 
   if (z) atomicAdd(zero_cnt, z);
 }
 
-// Edge checks, item degrees, max |a|, max |c|.
+// Edge checks, item degrees, max |a|, max |c|.  With J <= 16384 each block
+// counts its contiguous edge range in shared memory and flushes once per item.
 __global__ void k_edges(const int32_t* col, const void* c, const void* a, bool bf16, int64_t nnz, int64_t J,
                         unsigned long long* item_deg, unsigned* max_a, unsigned* max_c, int* bad) {
+  extern __shared__ unsigned scnt[];
   __shared__ unsigned s_ma, s_mc;
+  const bool sm = J <= 16384;
   if (threadIdx.x == 0) s_ma = s_mc = 0;
+  if (sm)
+    for (int64_t j = threadIdx.x; j < J; j += blockDim.x) scnt[j] = 0u;
   __syncthreads();
   int flag = 0;
   unsigned ma = 0, mc = 0;
-  for (int64_t e = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; e < nnz;
-       e += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+  const int64_t per = (nnz + gridDim.x - 1) / gridDim.x;
+  const int64_t e0 = blockIdx.x * per, e1 = e0 + per < nnz ? e0 + per : nnz;
+  for (int64_t e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
     const int32_t j = col[e];
     if (j < 0 || j >= J)
       flag |= kBadItem;
+    else if (sm)
+      atomicAdd(&scnt[j], 1u);
     else
       atomicAdd(&item_deg[j], 1ull);
     const float cv = load_val(c, e, bf16), av = load_val(a, e, bf16);
@@ -89,6 +97,9 @@ __global__ void k_edges(const int32_t* col, const void* c, const void* a, bool b
     atomicMax(max_a, s_ma);
     atomicMax(max_c, s_mc);
   }
+  if (sm)
+    for (int64_t j = threadIdx.x; j < J; j += blockDim.x)
+      if (scnt[j]) atomicAdd(&item_deg[j], static_cast<unsigned long long>(scnt[j]));
 }
 
 __global__ void k_b(const double* b, int64_t J, int* bad) {
@@ -171,12 +182,31 @@ __global__ void k_gather(const int64_t* rp, const int32_t* col, const void* c, c
 }
 
 // sum_i a_ij^2 per item in 64-bit fixed point (exact, order independent).
-__global__ void k_item_sq(const int32_t* col, const void* a, bool bf16, int64_t nnz, float scale,
+// With J <= kSmemItems each block sums its contiguous edge range in shared
+// memory and flushes once per item.
+constexpr int kSmemItems = 16384;
+__global__ void k_item_sq(const int32_t* col, const void* a, bool bf16, int64_t nnz, int64_t J, float scale,
                           unsigned long long* acc) {
-  for (int64_t e = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; e < nnz;
-       e += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+  extern __shared__ unsigned long long sacc[];
+  const bool sm = J <= kSmemItems;
+  if (sm) {
+    for (int64_t j = threadIdx.x; j < J; j += blockDim.x) sacc[j] = 0ull;
+    __syncthreads();
+  }
+  const int64_t per = (nnz + gridDim.x - 1) / gridDim.x;
+  const int64_t e0 = blockIdx.x * per, e1 = e0 + per < nnz ? e0 + per : nnz;
+  for (int64_t e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
     const float av = load_val(a, e, bf16);
-    atomicAdd(&acc[col[e]], static_cast<unsigned long long>(__float2ll_rn(av * av * scale)));
+    const unsigned long long q = static_cast<unsigned long long>(__float2ll_rn(av * av * scale));
+    if (sm)
+      atomicAdd(&sacc[col[e]], q);
+    else
+      atomicAdd(&acc[col[e]], q);
+  }
+  if (sm) {
+    __syncthreads();
+    for (int64_t j = threadIdx.x; j < J; j += blockDim.x)
+      if (sacc[j]) atomicAdd(&acc[j], sacc[j]);
   }
 }
 
@@ -217,6 +247,8 @@ dlm_status build_layout(int64_t I, int64_t J, int64_t nnz, const int64_t* rp, co
                         const void* a, const double* b, bool bf16, cudaStream_t s, LayoutOut* out,
                         std::string* msg) {
   const size_t vs = bf16 ? 2 : 4;
+  cudaFuncSetAttribute(k_item_sq, cudaFuncAttributeMaxDynamicSharedMemorySize, 8 * kSmemItems);
+  cudaFuncSetAttribute(k_edges, cudaFuncAttributeMaxDynamicSharedMemorySize, 4 * 16384);
   dlm_status st = DLM_OK;
   int32_t *deg = nullptr, *sdeg = nullptr, *idx = nullptr, *perm = nullptr;
   int64_t* ssize = nullptr;
@@ -259,7 +291,11 @@ dlm_status build_layout(int64_t I, int64_t J, int64_t nnz, const int64_t* rp, co
     st = DLM_ERR_INVALID_ARG;
     goto done;
   }
-  if (nnz > 0) k_edges<<<grid_for(nnz), kT, 0, s>>>(col, c, a, bf16, nnz, J, item_deg, mx, mx + 1, bad);
+  if (nnz > 0) {
+    const int g = static_cast<int>(nnz / 8192 + 1 < 608 ? nnz / 8192 + 1 : 608);
+    const size_t smem = J <= 16384 ? sizeof(unsigned) * J : 0;
+    k_edges<<<g, 1024, smem, s>>>(col, c, a, bf16, nnz, J, item_deg, mx, mx + 1, bad);
+  }
   DLM_CK(cudaGetLastError());
   DLM_CK(cudaMemcpyAsync(&h_bad, bad, sizeof(int), cudaMemcpyDeviceToHost, s));
   DLM_CK(cudaMemcpyAsync(h_mx, mx, sizeof(unsigned) * 2, cudaMemcpyDeviceToHost, s));
@@ -348,7 +384,11 @@ dlm_status build_layout(int64_t I, int64_t J, int64_t nnz, const int64_t* rp, co
   DLM_CK(cudaMalloc(&sq, sizeof(unsigned long long) * (J > 0 ? J : 1)));
   DLM_CK(cudaMalloc(&out->n2, sizeof(double) * (J > 0 ? J : 1)));
   DLM_CK(cudaMemsetAsync(sq, 0, sizeof(unsigned long long) * (J > 0 ? J : 1), s));
-  if (nnz > 0) k_item_sq<<<grid_for(nnz), kT, 0, s>>>(col, a, bf16, nnz, std::ldexp(1.0f, ssq), sq);
+  if (nnz > 0) {
+    const int g = static_cast<int>(nnz / 8192 + 1 < 608 ? nnz / 8192 + 1 : 608);
+    const size_t smem = J <= kSmemItems ? sizeof(unsigned long long) * J : 0;
+    k_item_sq<<<g, 1024, smem, s>>>(col, a, bf16, nnz, J, std::ldexp(1.0f, ssq), sq);
+  }
   DLM_CK(cudaGetLastError());
   if (J > 0) k_fix_to_double<<<grid_for(J), kT, 0, s>>>(sq, J, std::ldexp(1.0, -ssq), out->n2);
   DLM_CK(cudaGetLastError());

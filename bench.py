@@ -172,10 +172,53 @@ def make_instance(recipe, bf16, torch, pinned, threads):
         a16 = pin_alloc(inst.nnz, np.uint16)
         synth.round_bf16(inst.c, threads, c16)
         synth.round_bf16(inst.a, threads, a16)
+        inst.c32, inst.a32 = inst.c, inst.a  # FP32 values, kept for the error statement
         inst.c, inst.a = c16, a16
     else:
         inst = synth.generate(recipe, nthreads=threads, alloc=pin_alloc)
     return inst
+
+
+def bf16_error_statement(dlm, torch, s_bf16, inst, recipe, gamma, frac, threads):
+    """Error of the BF16-storage form at its current lam: against the FP32 GPU
+    form of the same instance (full instance) and against the FP64 oracle on
+    the FP32 values (seeded user sample)."""
+    import numpy as np
+    import oracle
+    import synth
+
+    dev = s_bf16.device
+    lam = s_bf16.lam()
+    g16, G16, x16 = s_bf16.calculate(lam, gamma)
+    arrs = [torch.from_numpy(v).to(dev) for v in (inst.row_ptr, inst.col, inst.c32, inst.a32, inst.b)]
+    s32 = dlm.Solver(*arrs, inst.J)
+    del arrs
+    g32, G32, x32 = s32.calculate(lam, gamma)
+    s32.close()
+    Gs = float(G32.abs().max().item()) or 1.0
+    full = {"rel_dual_obj": abs(g16 - g32) / abs(g32), "max_abs_grad": float((G16 - G32).abs().max().item()),
+            "max_abs_grad_rel": float((G16 - G32).abs().max().item()) / Gs,
+            "max_abs_x": float((x16 - x32).abs().max().item()),
+            "mean_abs_x": float((x16 - x32).abs().double().mean().item())}
+    del x32, G32
+    # seeded sample: oracle x on the FP32 values at the same lam, against the BF16 solver's x
+    ids = synth.sample_users(inst.I, frac, 4343)
+    rows = torch.from_numpy(ids).to(dev)
+    rp = torch.from_numpy(inst.row_ptr).to(dev)
+    starts, ends = rp[rows], rp[rows + 1]
+    lens = ends - starts
+    idx = torch.repeat_interleave(starts, lens) + (torch.arange(int(lens.sum().item()), device=dev) -
+                                                   torch.repeat_interleave(torch.cumsum(lens, 0) - lens, lens))
+    xs = x16[idx].cpu().numpy().astype(np.float64)
+    del x16
+    sub = synth.subset(synth.Instance(inst.row_ptr, inst.col, inst.c32, inst.a32, inst.b, inst.J), ids)
+    p = oracle.Problem(sub.row_ptr, sub.col, sub.c.astype(np.float64), sub.a.astype(np.float64), sub.b, sub.J)
+    ref = oracle.sweep(p, lam.cpu().numpy().astype(np.float64), gamma)
+    dx = np.abs(xs - ref["x"])
+    return {"vs_fp32_gpu_full_instance": full,
+            "vs_fp64_oracle_sample": {"users": int(len(ids)), "nnz": int(p.nnz), "max_abs_x": float(dx.max()),
+                                      "mean_abs_x": float(dx.mean())},
+            "at": "lam after the timed steps; gamma %.3g" % gamma}
 
 
 def cpu_sample(workload, bf16, frac, seed=4242, threads=0):
@@ -258,6 +301,7 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--ref-step-seconds", type=float, default=6.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-error-statement", action="store_true")
     args = ap.parse_args()
 
     rank = int(os.environ.get("RANK", "0"))
@@ -356,6 +400,10 @@ def main():
     torch.cuda.synchronize(dev)
     graph_ms_per_step = e0.elapsed_time(e1) / args.steps
 
+    bf16_err = None
+    if bf16 and not args.no_error_statement:
+        bf16_err = bf16_error_statement(dlm, torch, s, inst, recipe, w["schedule"][1], args.cpu_frac, args.threads)
+
     # ---- end to end through the C-ABI: host (pinned) inputs -> create ->
     # iterations -> lam back to the host, every step ----
     lam_host = torch.empty(J, dtype=torch.float32, pin_memory=True)
@@ -415,6 +463,7 @@ def main():
         "gpu_launches": 2 * iters_total,
         "clocks": clocks,
         "graph_ms_per_step": graph_ms_per_step,
+        "bf16_error": bf16_err,
         "setup_s": {"generate": t_gen, "upload_and_create": t_setup},
     }
     if rank == 0:

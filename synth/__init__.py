@@ -222,8 +222,8 @@ def subset(inst: Instance, users: np.ndarray) -> Instance:
     lens = inst.row_ptr[users + 1] - inst.row_ptr[users]
     rp = np.zeros(len(users) + 1, dtype=np.int64)
     np.cumsum(lens, out=rp[1:])
-    idx = np.concatenate([np.arange(inst.row_ptr[u], inst.row_ptr[u + 1]) for u in users]) if len(users) else \
-        np.zeros(0, dtype=np.int64)
+    # edge positions of the selected rows, in order
+    idx = np.repeat(inst.row_ptr[users], lens) + (np.arange(int(rp[-1]), dtype=np.int64) - np.repeat(rp[:-1], lens))
     return Instance(rp, inst.col[idx].copy(), inst.c[idx].copy(), inst.a[idx].copy(), inst.b.copy(), inst.J,
                     None if inst.ids is None else inst.ids[users], inst.recipe)
 

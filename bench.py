@@ -41,6 +41,12 @@ WORKLOADS = {
         desc="production shape: 20M users x 2,000 items, ~500M nnz; same generators; c, a FP32; "
              "gamma continuation 1e-1 -> 1e-3 halved every 100 iterations",
         users=20_000_000, items=2_000, seed=1001, bf16=False, schedule=(1e-1, 1e-3, 0.5, 100)),
+    "batched": dict(
+        desc="batched form: 64 independent instances of the production generators, users log-uniform 1e4-5e6, "
+             "items log-uniform 50-2,000, gamma drawn from {1e-1, 1e-2, 1e-3} (fixed per instance); c, a stored "
+             "BF16; one sweep launch + one update launch per iteration for all 64, replayed as CUDA graphs; "
+             "mapping chosen by the library's tuner",
+        n=64, seed=1003, bf16=True),
     "tiny": dict(
         desc="tiny: 10,000 users x 100 items, ~100k nnz, 1+Poisson(9) degree, uniform items, c=-U(0,1), a=1, "
              "b_j = 0.05 deg_j, gamma = 1e-2",
@@ -228,7 +234,9 @@ def cpu_sample(workload, bf16, frac, seed=4242, threads=0):
     import oracle
     import synth
 
-    r = recipe_for(workload, 1.0 if workload != "tiny" else 1.0)
+    r = recipe_for(workload, 1.0) if workload != "batched" else None
+    if workload == "batched":
+        return batch_sample(frac, seed, threads)
     if workload == "tiny":
         inst = synth.generate(r)
     else:
@@ -239,6 +247,45 @@ def cpu_sample(workload, bf16, frac, seed=4242, threads=0):
         c = synth.bf16_to_f32(synth.round_bf16(c))
         a = synth.bf16_to_f32(synth.round_bf16(a))
     return oracle.Problem(inst.row_ptr, inst.col, c.astype(np.float64), a.astype(np.float64), inst.b, inst.J)
+
+
+def batch_sample(frac, seed=4242, threads=0):
+    """A seeded user sample of every member of the batched workload, as a
+    list of (FP64 oracle problem, gamma)."""
+    import numpy as np
+    import oracle
+    import synth
+
+    w = WORKLOADS["batched"]
+    out = []
+    for k, (r, gamma) in enumerate(synth.recipe_batch(n=w["n"], seed=w["seed"])):
+        ids = synth.sample_users(r.I, frac, seed + k)
+        if len(ids) == 0:
+            continue
+        inst = synth.generate(r, ids=ids, nthreads=threads)
+        c = synth.bf16_to_f32(synth.round_bf16(inst.c))
+        a = synth.bf16_to_f32(synth.round_bf16(inst.a))
+        out.append((oracle.Problem(inst.row_ptr, inst.col, c.astype(np.float64), a.astype(np.float64), inst.b,
+                                   inst.J), gamma))
+    return out
+
+
+def time_oracle_batch(ps, budget_s):
+    """Oracle iterations over every sampled member, about budget_s seconds in
+    total; returns (nnz*iters/s, iters per member, seconds, nnz)."""
+    import oracle
+
+    t0 = time.perf_counter()
+    for p, g in ps:
+        oracle.fista(p, 1, g, trajectory=False)
+    t1 = time.perf_counter() - t0
+    iters = max(1, int(budget_s / max(t1, 1e-6)))
+    t0 = time.perf_counter()
+    for p, g in ps:
+        oracle.fista(p, iters, g, trajectory=False)
+    dt = time.perf_counter() - t0
+    nnz = sum(p.nnz for p, _ in ps)
+    return nnz * iters / dt, iters, dt, nnz
 
 
 def time_oracle(p, gamma, budget_s):
@@ -261,19 +308,29 @@ def run_reference(args, rank, world):
     if rank != 0:
         return 0
     frac = args.cpu_frac
-    p = cpu_sample(args.workload, w["bf16"], frac)
-    gamma = w["schedule"][1]
     per_step = []
-    for k in range(args.warmup + args.steps):
-        v, iters, dt = time_oracle(p, gamma, args.ref_step_seconds)
-        if k >= args.warmup:
-            per_step.append((v, iters, dt))
-    total_nnz_iters = sum(p.nnz * it for _, it, _ in per_step)
+    if args.workload == "batched":
+        ps = batch_sample(frac)
+        for k in range(args.warmup + args.steps):
+            v, iters, dt, nnz_s = time_oracle_batch(ps, args.ref_step_seconds)
+            if k >= args.warmup:
+                per_step.append((v, iters * nnz_s, dt))
+        users = sum(p.I for p, _ in ps)
+        desc_n = f"{users} users, {nnz_s} nnz over {len(ps)} members"
+    else:
+        p = cpu_sample(args.workload, w["bf16"], frac)
+        gamma = w["schedule"][1]
+        for k in range(args.warmup + args.steps):
+            v, iters, dt = time_oracle(p, gamma, args.ref_step_seconds)
+            if k >= args.warmup:
+                per_step.append((v, iters * p.nnz, dt))
+        desc_n = f"{p.I} users, {p.nnz} nnz"
+    total_nnz_iters = sum(ni for _, ni, _ in per_step)
     total_s = sum(dt for _, _, dt in per_step)
     value = total_nnz_iters / total_s
     sample = (f"{'all' if args.workload == 'tiny' else f'{frac:.2%} seeded user sample'} of the {args.workload} "
-              f"workload ({p.I} users, {p.nnz} nnz), FP64 oracle iterations (sweep + accelerated update), "
-              f"{per_step[0][1]} iterations per step")
+              f"workload ({desc_n}), FP64 oracle iterations (sweep + accelerated update), "
+              f"{per_step[0][1]} nnz-iterations per step")
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1000 * total_s / len(per_step), "higher_is_better": True, "scaling": "weak",
@@ -334,6 +391,9 @@ def main():
         t = torch.tensor([v], dtype=torch.float64, device=dev)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         return float(t.item())
+
+    if args.workload == "batched":
+        return run_batched(args, dlm, torch, dev, rank, world, barrier, max_over_ranks, dist)
 
     w = WORKLOADS[args.workload]
     bf16 = w["bf16"]
@@ -465,6 +525,161 @@ def main():
         "graph_ms_per_step": graph_ms_per_step,
         "bf16_error": bf16_err,
         "setup_s": {"generate": t_gen, "upload_and_create": t_setup},
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+def run_batched(args, dlm, torch, dev, rank, world, barrier, max_over_ranks, dist):
+    """The batched workload: 64 handles run as one batch."""
+    import numpy as np
+    import synth
+
+    w = WORKLOADS["batched"]
+    recipes = synth.recipe_batch(n=w["n"], seed=w["seed"])
+    if args.scale != 1.0:
+        for r, _ in recipes:
+            r.I = max(1000, int(round(r.I * args.scale)))
+    t_gen = time.perf_counter()
+    insts = [(make_instance(r, True, torch, True, args.threads), g) for r, g in recipes]
+    for inst, _ in insts:
+        inst.c32 = inst.a32 = None  # FP32 copies are only needed for the single-instance error statement
+    t_gen = time.perf_counter() - t_gen
+    dlm.load()
+
+    def create(inst, on_device):
+        if on_device:
+            arrs = [torch.from_numpy(v).to(dev, non_blocking=True) for v in
+                    (inst.row_ptr, inst.col, inst.c.view(np.int16), inst.a.view(np.int16), inst.b)]
+            arrs[2], arrs[3] = arrs[2].view(torch.bfloat16), arrs[3].view(torch.bfloat16)
+            s = dlm.Solver(*arrs, inst.J, bf16=True)
+            del arrs
+        else:
+            s = dlm.Solver(inst.row_ptr, inst.col, inst.c, inst.a, inst.b, inst.J, bf16=True)
+        return s
+
+    t_setup = time.perf_counter()
+    solvers = []
+    for inst, g in insts:
+        s = create(inst, True)
+        s.set_schedule(g)
+        solvers.append(s)
+    torch.cuda.synchronize(dev)
+    bt = dlm.Batch(solvers)
+    t_setup = time.perf_counter() - t_setup
+    infos = [s.info() for s in solvers]
+    nnz = sum(i["nnz"] for i in infos)
+    users = sum(i["num_users"] for i in infos)
+    bytes_iter = sum(i["bytes_per_iter"] for i in infos)
+
+    t_tune = time.perf_counter()
+    chosen, tune_ms = bt.autotune(3)
+    t_tune = time.perf_counter() - t_tune
+    for _ in range(args.warmup):
+        bt.step(args.iters)
+    torch.cuda.synchronize(dev)
+
+    sampler = ClockSampler(gpu_id_for_smi(torch, dev))
+    sampler.start()
+    time.sleep(0.3)
+    barrier()
+    torch.cuda.synchronize(dev)
+    sweep_ms = upd_ms = tot_ms = 0.0
+    for _ in range(args.steps):
+        a_, b_, c_ = bt.step_timed(args.iters)
+        sweep_ms += a_
+        upd_ms += b_
+        tot_ms += c_
+    torch.cuda.synchronize(dev)
+    barrier()
+    clocks = sampler.stop()
+    elapsed_s = max_over_ranks(tot_ms / 1000.0)
+    iters_total = args.iters * args.steps
+    value = world * nnz * iters_total / elapsed_s
+
+    st = torch.cuda.current_stream(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize(dev)
+    e0.record(st)
+    for _ in range(args.steps):
+        bt.step(args.iters)
+    e1.record(st)
+    torch.cuda.synchronize(dev)
+    graph_ms_per_step = e0.elapsed_time(e1) / args.steps
+    stats = bt.stats()
+    bt.close()
+    for s in solvers:
+        s.close()
+    del solvers
+    torch.cuda.synchronize(dev)
+
+    # end to end: every member created from pinned host arrays, batched, the
+    # iterations, every member's lam back to the host
+    h2d = sum(i.row_ptr.nbytes + i.col.nbytes + i.c.nbytes + i.a.nbytes + i.b.nbytes for i, _ in insts)
+    d2h = sum(4 * i.J for i, _ in insts)
+    lam_host = [torch.empty(i.J, dtype=torch.float32, pin_memory=True) for i, _ in insts]
+    e2e_times = []
+    for k in range(args.e2e_steps + 1 if args.e2e_steps > 0 else 0):
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        ss = []
+        for inst, g in insts:
+            s = create(inst, False)
+            s.set_schedule(g)
+            ss.append(s)
+        b2 = dlm.Batch(ss)
+        b2.set_options(**{f: getattr(chosen, f) for f in ("mapping", "coop_max", "block_threads", "ctas_per_sm")})
+        b2.step(args.iters)
+        for s, lh in zip(ss, lam_host):
+            dlm.dlm_get_lambda(s.h, lh, dlm.DLM_MEM_HOST)
+        b2.close()
+        for s in ss:
+            s.close()
+        dt = time.perf_counter() - t0
+        if k > 0:
+            e2e_times.append(dt)
+    e2e_value = None
+    if e2e_times:
+        e2e_value = world * nnz * args.iters / max_over_ranks(statistics.mean(e2e_times))
+
+    peak, peak_kind = load_peaks()
+    sweep_s = sweep_ms / 1000.0 / iters_total
+    achieved = bytes_iter / sweep_s / 1e9
+    roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+            "traffic": recorded_traffic("batched", nnz, users) if args.scale == 1.0 else None,
+            "peak_source": f"{peak_kind} (copy bandwidth, MEASURED_PEAKS.json)"
+            if peak_kind == "measured" else "fallback 6.8 TB/s",
+            "kernel": "sweep_kernel (all 64 instances in one launch)", "algorithmic_bytes_per_launch": bytes_iter,
+            "sweep_share_of_iteration": sweep_ms / tot_ms if tot_ms > 0 else None,
+            "sweep_us": sweep_s * 1e6, "update_us": upd_ms * 1000.0 / iters_total}
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        ps = batch_sample(args.cpu_frac, threads=args.threads)
+        v, iters, dt, nnz_s = time_oracle_batch(ps, args.cpu_seconds)
+        cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": (f"{args.cpu_frac:.0%} seeded user sample of every member ({nnz_s} nnz over {len(ps)} "
+                          f"members), {iters} FP64 oracle iterations each in {dt:.1f} s")}
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": elapsed_s * 1000.0 / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": w["desc"] if args.scale == 1.0 else w["desc"] + f" (users scaled x{args.scale})",
+                   "instances": len(insts), "users": users, "nnz": nnz, "storage": "bf16",
+                   "iters_per_step": args.iters, "parallelism": "replicas" if world > 1 else "single GPU",
+                   "l2": f"inputs {bytes_iter / 1e9:.1f} GB per iteration >> 129 MB L2 (no flush)",
+                   "mapping": chosen.as_dict(), "tuner_sweep_ms": tune_ms},
+        "roofline": roof,
+        "cpu_baseline": cpu,
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+                "note": "per step: 64 x dlm_create from pinned host arrays, batch, iterations, every lam to host"},
+        "gpu_launches": 2 * iters_total,
+        "clocks": clocks,
+        "graph_ms_per_step": graph_ms_per_step,
+        "member_status": sorted({x.status for x in stats}),
+        "setup_s": {"generate": t_gen, "upload_and_create": t_setup, "autotune": t_tune},
     }
     if rank == 0:
         print(json.dumps(line), flush=True)

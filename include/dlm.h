@@ -78,14 +78,26 @@ typedef struct {
   int32_t reserved;
 } dlm_problem_desc;
 
-/* Solver options (zero-initialised fields take the defaults). */
+/* Solver options (zero-initialised fields take the defaults).  The mapping
+ * fields change only how the sweep is laid onto the GPU: every mapping gives
+ * the same item sums (they are exact), and mappings with the same coop_max
+ * give bit-identical iterates. */
 typedef struct {
-  int32_t gap_every;    /* iterations between certified-gap checks in dlm_solve (default 50) */
-  int32_t precondition; /* 1: row normalization (App. B.2) as the per-item step gamma/sum_i a_ij^2 */
-  int32_t mapping;      /* slice-to-CTA assignment order: -1 default, >= 0 a fixed order */
-  int32_t graph_iters;  /* iterations per captured CUDA graph (default 10) */
-  int32_t ctas_per_sm;  /* persistent sweep CTAs per SM (0: one) */
-  int32_t reserved[3];
+  int32_t gap_every;     /* iterations between certified-gap checks in dlm_solve (default 50) */
+  int32_t precondition;  /* 1: row normalization (App. B.2) as the per-item step gamma/sum_i a_ij^2 */
+  int32_t mapping;       /* slice-to-CTA assignment: 0 default (1 for a handle, 3 for a batch),
+                            1 interleaved (CTA k sweeps slices k, k + grid, ... of every instance),
+                            2 contiguous (equal-work ranges of the instances' slices in order),
+                            3 dynamic (CTAs take work units -- slice ranges of one instance,
+                              shrinking toward the end -- from a device counter; certificate
+                              sweeps then use order 1 for a handle, 2 for a batch) */
+  int32_t graph_iters;   /* iterations per captured CUDA graph (default 10) */
+  int32_t ctas_per_sm;   /* persistent sweep CTAs per SM, 0..4 (0: 1 at 1024 threads, 2 at 512) */
+  int32_t coop_max;      /* 0..33: a warp runs its general-path users (threshold search) one
+                            after another with all 32 lanes while fewer than coop_max of its
+                            32 users need it (default 12; 1 never, 33 always) */
+  int32_t block_threads; /* threads per sweep CTA: 0 (default 1024), 512 or 1024 */
+  int32_t reserved;
 } dlm_options;
 
 /* Result of a certified-gap evaluation at the current iterate lam (one extra
@@ -138,7 +150,21 @@ dlm_status dlm_create(const dlm_problem_desc* desc, void* stream, dlm_problem** 
 dlm_status dlm_set_schedule(dlm_problem* p, double gamma0, double gamma_end, double factor,
                             int64_t iters_per_stage);
 
+/* Replace the handle's options (see dlm_options; out-of-range values return
+ * DLM_ERR_INVALID_ARG).  Synchronizes the handle's stream when the launch
+ * shape changes. */
 dlm_status dlm_set_options(dlm_problem* p, const dlm_options* opt);
+dlm_status dlm_get_options(dlm_problem* p, dlm_options* opt);
+
+/* Mapping tuner (the paper has no counterpart; its kernels have one fixed
+ * mapping).  Times `iters` iterations (after one warm-up iteration) of every
+ * candidate mapping -- block_threads {1024, 512}, mapping {1, 2, 3},
+ * coop_max {1, 6, 12, 20, 33} -- from the handle's current state, restores
+ * that state (lam, y, theta, counter) after each trial, and keeps the mapping
+ * whose sweeps took the least device time.  Writes it to *chosen and the mean
+ * sweep time of the winner in milliseconds to *sweep_ms (either may be NULL).
+ * Allocates two num_items float arrays while it runs.  Synchronous. */
+dlm_status dlm_autotune(dlm_problem* p, int32_t iters, dlm_options* chosen, double* sweep_ms);
 
 /* Warm start: lam <- max(lambda0, 0), y <- lam, theta <- 1, iteration counter
  * kept.  lambda0 has num_items float32 entries in `memspace`. */
@@ -192,6 +218,38 @@ dlm_status dlm_get_info(dlm_problem* p, int64_t* num_users, int64_t* num_items, 
                         int64_t* bytes_per_iter);
 
 void dlm_destroy(dlm_problem* p);
+
+/* Batches (the paper's experiments solve many independent instances; this
+ * sweeps them together).  A batch runs n existing handles as one: each
+ * iteration is one sweep launch over the slices of all members and one update
+ * launch with one CTA per member, replayed as CUDA graphs.  Every member keeps
+ * its own data, schedule, options' precondition flag, lam, y and state, and
+ * its iterates are those it would take alone (bit-identical for the same
+ * coop_max).  Members must share val_dtype and device; a handle appears at
+ * most once.  Set each member's schedule, precondition flag and warm start
+ * before dlm_batch_create (the batch captures them; set_lambda and set_state
+ * on a member remain valid afterwards).  Work of the batch is ordered on
+ * `stream` (NULL: the batch creates its own blocking stream); calls on a
+ * member's own handle and on the batch act on the same state, so the caller
+ * must not let them overlap.  Destroy the batch before its members. */
+dlm_status dlm_batch_create(dlm_problem* const* probs, int32_t n, void* stream, dlm_batch** out);
+/* Mapping fields of `opt` for the batch (mapping 0 means dynamic here);
+ * gap_every and graph_iters apply to dlm_batch_solve and dlm_batch_step. */
+dlm_status dlm_batch_set_options(dlm_batch* bt, const dlm_options* opt);
+/* dlm_autotune over the whole batch (interleaved candidates only up to 8 members). */
+dlm_status dlm_batch_autotune(dlm_batch* bt, int32_t iters, dlm_options* chosen, double* sweep_ms);
+dlm_status dlm_batch_step(dlm_batch* bt, int64_t n_iters);
+/* As dlm_step_timed, for the batch's launches. */
+dlm_status dlm_batch_step_timed(dlm_batch* bt, int64_t n_iters, double* sweep_ms, double* update_ms,
+                                double* total_ms);
+/* Certified-gap evaluation of every member: out[i] for member i (n entries). */
+dlm_status dlm_batch_get_stats(dlm_batch* bt, dlm_stats* out);
+/* Iterate until every member meets the target of dlm_solve (its own final
+ * gamma and certified gap <= target_rel_gap), checking every gap_every
+ * iterations, or until max_iters more iterations (then DLM_ERR_TIMEOUT);
+ * out[i] (may be NULL) gets member i's stats with `converged` per member. */
+dlm_status dlm_batch_solve(dlm_batch* bt, double target_rel_gap, int64_t max_iters, dlm_stats* out);
+void dlm_batch_destroy(dlm_batch* bt);
 
 /* One dual evaluation straight from the caller's device CSR arrays, with no
  * device memory allocated by this call or any earlier one: for callers that

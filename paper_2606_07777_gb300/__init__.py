@@ -19,6 +19,8 @@ __all__ = [
     "load", "build", "DlmError", "Solver", "dlm_create", "dlm_set_schedule", "dlm_set_options", "dlm_set_lambda",
     "dlm_calculate", "dlm_step", "dlm_solve", "dlm_get_stats", "dlm_get_lambda", "dlm_get_x", "dlm_get_state",
     "dlm_set_state", "dlm_get_info", "dlm_step_timed", "dlm_calculate_static", "dlm_destroy", "dlm_last_error",
+    "dlm_get_options", "dlm_autotune", "Batch", "dlm_batch_create", "dlm_batch_set_options", "dlm_batch_autotune",
+    "dlm_batch_step", "dlm_batch_step_timed", "dlm_batch_get_stats", "dlm_batch_solve", "dlm_batch_destroy",
 ]
 
 DLM_OK, DLM_ERR_INVALID_ARG, DLM_ERR_OOM, DLM_ERR_CUDA, DLM_ERR_NUMERIC, DLM_ERR_TIMEOUT, DLM_ERR_UNSUPPORTED = range(7)
@@ -46,8 +48,11 @@ class ProblemDesc(ctypes.Structure):
 
 class Options(ctypes.Structure):
     _fields_ = [("gap_every", ctypes.c_int32), ("precondition", ctypes.c_int32), ("mapping", ctypes.c_int32),
-                ("graph_iters", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 3)]
+                ("graph_iters", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32), ("coop_max", ctypes.c_int32),
+                ("block_threads", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}
 
 
 class Stats(ctypes.Structure):
@@ -85,8 +90,18 @@ _SIGS = {
     "dlm_get_info": [_vp, ctypes.POINTER(_i64), ctypes.POINTER(_i64), ctypes.POINTER(_i64), ctypes.POINTER(_i64)],
     "dlm_step_timed": [_vp, _i64, ctypes.POINTER(_d), ctypes.POINTER(_d), ctypes.POINTER(_d)],
     "dlm_calculate_static": [_i64, _i64, _i64, _vp, _vp, _vp, _vp, _vp, _i32, _d, _vp, _d, _vp, _vp, _vp, _vp],
+    "dlm_get_options": [_vp, ctypes.POINTER(Options)],
+    "dlm_autotune": [_vp, _i32, ctypes.POINTER(Options), ctypes.POINTER(_d)],
+    "dlm_batch_create": [ctypes.POINTER(_vp), _i32, _vp, ctypes.POINTER(_vp)],
+    "dlm_batch_set_options": [_vp, ctypes.POINTER(Options)],
+    "dlm_batch_autotune": [_vp, _i32, ctypes.POINTER(Options), ctypes.POINTER(_d)],
+    "dlm_batch_step": [_vp, _i64],
+    "dlm_batch_step_timed": [_vp, _i64, ctypes.POINTER(_d), ctypes.POINTER(_d), ctypes.POINTER(_d)],
+    "dlm_batch_get_stats": [_vp, ctypes.POINTER(Stats)],
+    "dlm_batch_solve": [_vp, _d, _i64, ctypes.POINTER(Stats)],
 }
-EXPORTS = list(_SIGS) + ["dlm_destroy", "dlm_last_error"]
+_VOID = {"dlm_destroy": [_vp], "dlm_batch_destroy": [_vp]}
+EXPORTS = list(_SIGS) + list(_VOID) + ["dlm_last_error"]
 
 
 def build(force: bool = False) -> str:
@@ -109,8 +124,10 @@ def load():
             f = getattr(lib, name)
             f.argtypes = args
             f.restype = ctypes.c_int
-        lib.dlm_destroy.argtypes = [_vp]
-        lib.dlm_destroy.restype = None
+        for name, args in _VOID.items():
+            f = getattr(lib, name)
+            f.argtypes = args
+            f.restype = None
         lib.dlm_last_error.argtypes = []
         lib.dlm_last_error.restype = ctypes.c_char_p
         _lib = lib
@@ -152,6 +169,19 @@ def dlm_set_schedule(h, gamma0, gamma_end, factor, iters_per_stage):
 
 def dlm_set_options(h, opt: Options):
     _call("dlm_set_options", h, ctypes.byref(opt))
+
+
+def dlm_get_options(h) -> Options:
+    o = Options()
+    _call("dlm_get_options", h, ctypes.byref(o))
+    return o
+
+
+def dlm_autotune(h, iters=3):
+    """(chosen Options, mean sweep ms of the winner)."""
+    o, ms = Options(), ctypes.c_double()
+    _call("dlm_autotune", h, iters, ctypes.byref(o), ctypes.byref(ms))
+    return o, ms.value
 
 
 def dlm_set_lambda(h, lam, memspace):
@@ -230,6 +260,62 @@ def dlm_destroy(h):
         load().dlm_destroy(h)
 
 
+def dlm_batch_create(handles, stream=None):
+    arr = (ctypes.c_void_p * len(handles))(*[h.value if isinstance(h, ctypes.c_void_p) else h for h in handles])
+    bt = ctypes.c_void_p()
+    _call("dlm_batch_create", arr, len(handles), stream, ctypes.byref(bt))
+    return bt
+
+
+def dlm_batch_set_options(bt, opt: Options):
+    _call("dlm_batch_set_options", bt, ctypes.byref(opt))
+
+
+def dlm_batch_autotune(bt, iters=3):
+    o, ms = Options(), ctypes.c_double()
+    _call("dlm_batch_autotune", bt, iters, ctypes.byref(o), ctypes.byref(ms))
+    return o, ms.value
+
+
+def dlm_batch_step(bt, n):
+    _call("dlm_batch_step", bt, n)
+
+
+def dlm_batch_step_timed(bt, n):
+    v = [ctypes.c_double() for _ in range(3)]
+    _call("dlm_batch_step_timed", bt, n, *[ctypes.byref(x) for x in v])
+    return tuple(x.value for x in v)
+
+
+def dlm_batch_get_stats(bt, n):
+    out = (Stats * n)()
+    _call("dlm_batch_get_stats", bt, out)
+    return list(out)
+
+
+def dlm_batch_solve(bt, n, target, max_iters):
+    """(status, [Stats] per member); the iteration limit and device-reported
+    statuses return normally."""
+    out = (Stats * n)()
+    lib = load()
+    st = lib.dlm_batch_solve(bt, target, max_iters, out)
+    if st not in (DLM_OK, DLM_ERR_TIMEOUT, DLM_ERR_NUMERIC):
+        raise DlmError(st, "dlm_batch_solve", lib.dlm_last_error().decode())
+    return st, list(out)
+
+
+def dlm_batch_destroy(bt):
+    if bt:
+        load().dlm_batch_destroy(bt)
+
+
+def _options(gap_every=0, precondition=False, mapping=0, graph_iters=0, ctas_per_sm=0, coop_max=0, block_threads=0):
+    o = Options()
+    o.gap_every, o.precondition, o.mapping = gap_every, int(bool(precondition)), mapping
+    o.graph_iters, o.ctas_per_sm, o.coop_max, o.block_threads = graph_iters, ctas_per_sm, coop_max, block_threads
+    return o
+
+
 class Solver:
     """One matching-LP instance on the GPU.
 
@@ -279,11 +365,18 @@ class Solver:
     def set_schedule(self, gamma0, gamma_end=None, factor=0.5, iters_per_stage=1 << 30):
         dlm_set_schedule(self.h, gamma0, gamma0 if gamma_end is None else gamma_end, factor, iters_per_stage)
 
-    def set_options(self, gap_every=0, precondition=False, mapping=-1, graph_iters=0, ctas_per_sm=0):
-        o = Options()
-        o.gap_every, o.precondition, o.mapping = gap_every, int(bool(precondition)), mapping
-        o.graph_iters, o.ctas_per_sm = graph_iters, ctas_per_sm
-        dlm_set_options(self.h, o)
+    def set_options(self, gap_every=0, precondition=False, mapping=0, graph_iters=0, ctas_per_sm=0, coop_max=0,
+                    block_threads=0):
+        dlm_set_options(self.h, _options(gap_every, precondition, mapping, graph_iters, ctas_per_sm, coop_max,
+                                         block_threads))
+
+    def options(self) -> Options:
+        return dlm_get_options(self.h)
+
+    def autotune(self, iters=3):
+        """Tries the sweep mappings from the current state (which it keeps);
+        returns (chosen Options, mean sweep ms)."""
+        return dlm_autotune(self.h, iters)
 
     def set_lambda(self, lam):
         dlm_set_lambda(self.h, lam, DLM_MEM_DEVICE if getattr(lam, "is_cuda", False) else DLM_MEM_HOST)
@@ -331,3 +424,48 @@ class Solver:
 
     def info(self):
         return dlm_get_info(self.h)
+
+
+class Batch:
+    """Several Solver instances iterated together: one sweep launch and one
+    update launch per iteration for all of them.  Set each member's schedule,
+    options and warm start first; close the batch before its members."""
+
+    def __init__(self, solvers, stream=None):
+        import torch
+
+        self.members = list(solvers)
+        if stream is None:
+            stream = torch.cuda.current_stream(self.members[0].device)
+        self.stream = stream
+        self.bt = dlm_batch_create([m.h for m in self.members], ctypes.c_void_p(stream.cuda_stream))
+
+    def close(self):
+        if getattr(self, "bt", None):
+            dlm_batch_destroy(self.bt)
+            self.bt = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_options(self, gap_every=0, mapping=0, graph_iters=0, ctas_per_sm=0, coop_max=0, block_threads=0):
+        dlm_batch_set_options(self.bt, _options(gap_every, False, mapping, graph_iters, ctas_per_sm, coop_max,
+                                                block_threads))
+
+    def autotune(self, iters=3):
+        return dlm_batch_autotune(self.bt, iters)
+
+    def step(self, n):
+        dlm_batch_step(self.bt, n)
+
+    def step_timed(self, n):
+        return dlm_batch_step_timed(self.bt, n)
+
+    def stats(self):
+        return dlm_batch_get_stats(self.bt, len(self.members))
+
+    def solve(self, target_rel_gap, max_iters):
+        return dlm_batch_solve(self.bt, len(self.members), target_rel_gap, max_iters)

@@ -1,6 +1,9 @@
 // api.cu -- the C-ABI (include/dlm.h): handle life cycle, schedule and
-// options, CUDA-graph replay of the iteration, certified-gap checks and the
-// solve loop.  All device work of a handle runs on its stream.
+// options, the runner that sweeps one instance or a batch (device tables,
+// slice-to-CTA tasks, CUDA-graph replay, timed stepping), certified-gap checks,
+// the solve loop, and the mapping tuner.  All device work of a handle or a
+// batch runs on its stream.
+#include <algorithm>
 #include <chrono>
 #include <cmath>
 #include <cstring>
@@ -28,13 +31,11 @@ dlm_status fail(dlm_status s, const std::string& m) {
   return s;
 }
 
-#define CK(x)                                                                                      \
-  do {                                                                                             \
-    cudaError_t e_ = (x);                                                                          \
+#define CK(x)                                                                                          \
+  do {                                                                                                 \
+    cudaError_t e_ = (x);                                                                              \
     if (e_ != cudaSuccess) return fail(DLM_ERR_CUDA, std::string(#x) + ": " + cudaGetErrorString(e_)); \
   } while (0)
-
-constexpr int kNumTables = 1;  // slice assignment orders (reserved for the tuner)
 
 __global__ void k_set_double(double* p, double v) { *p = v; }
 
@@ -77,6 +78,44 @@ cudaError_t dalloc(T** p, size_t n) {
   return cudaMalloc(reinterpret_cast<void**>(p), sizeof(T) * (n > 0 ? n : 1));
 }
 
+// Slice-to-CTA assignment orders.
+enum : int { kAssignInterleaved = 0, kAssignContiguous = 1, kAssignDynamic = 2 };
+
+// The launch state of a set of instances swept together: one instance for a
+// handle, several for a batch.  Instance data (layout, duals, accumulators,
+// state) stay in the dlm_problem objects; the runner owns the device tables
+// that point at them, the slice-to-CTA tasks and the captured graph.
+struct Runner {
+  std::vector<dlm_problem*> probs;
+  cudaStream_t stream = nullptr;
+  bool bf16 = false;
+  int device = 0;
+  int sms = 0;
+  int grid = 0;
+  int threads = kSweepThreads;
+  int coop_max = kDefaultCoopMax;
+  int assign = kAssignInterleaved;
+  int smemJ = 0;
+  int graph_iters = 10;
+  InstDesc *inst_iter = nullptr, *inst_stats = nullptr;
+  UpdInst* upd = nullptr;
+  StatsInst* st_stats = nullptr;
+  Task* tasks = nullptr;
+  int32_t *cta_task = nullptr, *seg_lists = nullptr;
+  double* seg_obj = nullptr;
+  std::vector<Task> h_tasks;
+  std::vector<int32_t> h_cta;
+  std::vector<std::vector<int32_t>> h_seg;
+  std::vector<int32_t> seg_off;
+  Task* units = nullptr;      // dynamic assignment: work units of the iteration sweeps
+  unsigned* ctr = nullptr;    // their counters [2]
+  std::vector<Task> h_units;
+  cudaGraphExec_t gexec = nullptr;
+  int gexec_iters = 0;
+  std::vector<cudaEvent_t> events;
+  cudaEvent_t done = nullptr;  // batches: end of the last enqueued batch work
+};
+
 }  // namespace
 
 struct dlm_problem {
@@ -86,39 +125,39 @@ struct dlm_problem {
   double z = 1.0;
   cudaStream_t stream = nullptr;
   bool own_stream = false;
+  cudaEvent_t ev = nullptr;  // orders the handle's stream before batch work
   int device = 0;
   LayoutOut lay;
+  std::vector<int64_t> h_slice_off;  // host copy of the slice offsets (task balancing)
   int sG = 0, sC = 0, sQ = 0;
   bool certified = true;
 
   double *b = nullptr, *inv_n2 = nullptr;
   float *lam = nullptr, *y = nullptr;
   unsigned long long *acc = nullptr, *acc2 = nullptr, *accC = nullptr, *accQ = nullptr;
-  double *gamma_tab = nullptr, *calc_gamma = nullptr, *seg_obj = nullptr, *stats_out = nullptr;
+  double *gamma_tab = nullptr, *calc_gamma = nullptr, *stats_out = nullptr;
   DevState* state = nullptr;
-  InstDesc *inst_iter = nullptr, *inst_stats = nullptr, *inst_calc = nullptr;
-  UpdInst* upd = nullptr;
-  StatsInst *st_stats = nullptr, *st_calc = nullptr;
-  Task* tasks = nullptr;
-  int32_t *cta_task = nullptr, *seg_list = nullptr;
-  int ntasks = 0, nseg = 0, grid = 0, smemJ = 0, table = 0;
-  std::vector<Task> h_tasks;
-  std::vector<int32_t> h_cta, h_seg;
+  InstDesc* inst_calc = nullptr;
+  StatsInst* st_calc = nullptr;
 
   // pinned host staging
   double* h_out = nullptr;  // 8 doubles
   InstDesc* h_inst = nullptr;
   StatsInst* h_stinst = nullptr;
-  UpdInst* h_upd = nullptr;
 
   double gamma0 = 1e-2, gamma_end = 1e-2, factor = 0.5;
   int64_t ips = 1 << 30;
   dlm_options opt{};
   std::vector<double> h_gamma_tab;
+  double last_solve_seconds = 0;
 
-  cudaGraphExec_t gexec = nullptr;
-  int gexec_iters = 0;
-  std::vector<cudaEvent_t> events;
+  Runner run;
+};
+
+struct dlm_batch {
+  Runner run;
+  dlm_options opt{};  // mapping and loop options of the batch
+  bool own_stream = false;
   double last_solve_seconds = 0;
 };
 
@@ -143,15 +182,15 @@ InstDesc base_desc(const dlm_problem* p) {
   return d;
 }
 
-StatsInst base_stats(const dlm_problem* p) {
+StatsInst base_stats(const dlm_problem* p, const Runner& R, int i) {
   StatsInst s{};
   s.b = p->b;
   s.acc = p->acc2;
   s.accC = p->accC;
   s.accQ = p->accQ;
-  s.seg_obj = p->seg_obj;
-  s.seg_list = p->seg_list;
-  s.nseg = p->nseg;
+  s.seg_obj = R.seg_obj;
+  s.seg_list = R.seg_lists + (R.seg_off.empty() ? 0 : R.seg_off[i]);
+  s.nseg = R.h_seg.empty() ? 0 : static_cast<int32_t>(R.h_seg[i].size());
   s.J = static_cast<int32_t>(p->J);
   s.inv_sG = std::ldexp(1.0, -p->sG);
   s.inv_sC = std::ldexp(1.0, -p->sC);
@@ -161,144 +200,349 @@ StatsInst base_stats(const dlm_problem* p) {
   return s;
 }
 
-void invalidate_graph(dlm_problem* p) {
-  if (p->gexec) cudaGraphExecDestroy(p->gexec);
-  p->gexec = nullptr;
-  p->gexec_iters = 0;
+void invalidate_graph(Runner& R) {
+  if (R.gexec) cudaGraphExecDestroy(R.gexec);
+  R.gexec = nullptr;
+  R.gexec_iters = 0;
 }
 
-// Per-CTA task lists: CTA k sweeps slices k, k + V, k + 2V, ...; slices are
-// sorted by width, so every CTA (and every warp) gets the same mix of widths.
-dlm_status build_tasks(dlm_problem* p) {
-  const int V = p->grid;
-  p->h_tasks.clear();
-  p->h_cta.assign(V + 1, 0);
-  p->h_seg.clear();
-  for (int k = 0; k < V; ++k) {
-    p->h_cta[k] = static_cast<int32_t>(p->h_tasks.size());
-    if (k < p->lay.nslices) {
-      Task t;
-      t.inst = 0;
-      t.stride = V;
-      t.first = k;
-      t.end = p->lay.nslices;
-      p->h_tasks.push_back(t);
-      p->h_seg.push_back(p->h_cta[k]);
+void runner_free(Runner& R) {
+  invalidate_graph(R);
+  void* ptrs[] = {R.inst_iter, R.inst_stats, R.upd,      R.st_stats, R.tasks,
+                  R.cta_task,  R.seg_lists,  R.seg_obj, R.units,    R.ctr};
+  for (void* q : ptrs) cudaFree(q);
+  for (cudaEvent_t e : R.events) cudaEventDestroy(e);
+  R.events.clear();
+  if (R.done) cudaEventDestroy(R.done);
+  R.done = nullptr;
+  R.inst_iter = R.inst_stats = nullptr;
+  R.upd = nullptr;
+  R.st_stats = nullptr;
+  R.tasks = nullptr;
+  R.cta_task = R.seg_lists = nullptr;
+  R.seg_obj = nullptr;
+  R.units = nullptr;
+  R.ctr = nullptr;
+}
+
+// Slice-to-CTA tasks.  Interleaved: CTA k sweeps slices k, k + V, ... of
+// every instance; slices are sorted by width, so every CTA gets the same mix.
+// Contiguous: the slices of all instances, in order, are cut into V ranges of
+// equal weight (edges plus a per-slice cost), so a CTA touches few instances.
+void build_task_list(Runner& R) {
+  const int V = R.grid;
+  const int n = static_cast<int>(R.probs.size());
+  R.h_tasks.clear();
+  R.h_cta.assign(V + 1, 0);
+  // certificate sweeps of a dynamic mapping use a static order
+  const int assign =
+      R.assign != kAssignDynamic ? R.assign : (n > 1 ? kAssignContiguous : kAssignInterleaved);
+  if (assign == kAssignInterleaved) {
+    for (int k = 0; k < V; ++k) {
+      R.h_cta[k] = static_cast<int32_t>(R.h_tasks.size());
+      for (int i = 0; i < n; ++i) {
+        const int64_t ns = R.probs[i]->lay.nslices;
+        if (k < ns) {
+          Task t;
+          t.inst = i;
+          t.stride = V;
+          t.first = k;
+          t.end = ns;
+          R.h_tasks.push_back(t);
+        }
+      }
+    }
+  } else {
+    constexpr int64_t kSliceCost = 128;  // fixed work of a slice, in edge units
+    std::vector<int64_t> base(n + 1, 0);
+    auto weight = [&](int i, int64_t s) { return R.probs[i]->h_slice_off[s] + kSliceCost * s; };
+    for (int i = 0; i < n; ++i) base[i + 1] = base[i] + weight(i, R.probs[i]->lay.nslices);
+    const int64_t W = base[n];
+    for (int k = 0; k < V; ++k) {
+      R.h_cta[k] = static_cast<int32_t>(R.h_tasks.size());
+      const int64_t lo = W * k / V, hi = W * (k + 1) / V;
+      for (int i = 0; i < n; ++i) {
+        const int64_t ns = R.probs[i]->lay.nslices;
+        if (ns == 0 || base[i + 1] <= lo || base[i] >= hi) continue;
+        // first slice whose start is at or after x
+        auto first_at = [&](int64_t x) {
+          int64_t a = 0, b = ns;
+          while (a < b) {
+            const int64_t m = (a + b) / 2;
+            if (base[i] + weight(i, m) < x)
+              a = m + 1;
+            else
+              b = m;
+          }
+          return a;
+        };
+        const int64_t f = first_at(lo), e = first_at(hi);
+        if (e > f) {
+          Task t;
+          t.inst = i;
+          t.stride = 1;
+          t.first = f;
+          t.end = e;
+          R.h_tasks.push_back(t);
+        }
+      }
     }
   }
-  p->h_cta[V] = static_cast<int32_t>(p->h_tasks.size());
-  p->ntasks = static_cast<int>(p->h_tasks.size());
-  p->nseg = static_cast<int>(p->h_seg.size());
-  cudaFree(p->tasks);
-  cudaFree(p->cta_task);
-  cudaFree(p->seg_list);
-  cudaFree(p->seg_obj);
-  p->tasks = nullptr;
-  p->cta_task = nullptr;
-  p->seg_list = nullptr;
-  p->seg_obj = nullptr;
-  CK(dalloc(&p->tasks, p->h_tasks.size()));
-  CK(dalloc(&p->cta_task, p->h_cta.size()));
-  CK(dalloc(&p->seg_list, p->h_seg.size()));
-  CK(dalloc(&p->seg_obj, p->h_tasks.size()));
-  if (!p->h_tasks.empty())
-    CK(cudaMemcpy(p->tasks, p->h_tasks.data(), sizeof(Task) * p->h_tasks.size(), cudaMemcpyHostToDevice));
-  CK(cudaMemcpy(p->cta_task, p->h_cta.data(), sizeof(int32_t) * p->h_cta.size(), cudaMemcpyHostToDevice));
-  if (!p->h_seg.empty())
-    CK(cudaMemcpy(p->seg_list, p->h_seg.data(), sizeof(int32_t) * p->h_seg.size(), cudaMemcpyHostToDevice));
-  invalidate_graph(p);
+  R.h_cta[V] = static_cast<int32_t>(R.h_tasks.size());
+  R.h_units.clear();
+  if (R.assign == kAssignDynamic) {
+    // Work units in instance order, each about max(Wmin, R / (2 V)) of the
+    // remaining weight R (guided self-scheduling: large units first, small
+    // ones last, so the CTAs run out of work together).
+    constexpr int64_t kSliceCost = 128;
+    std::vector<int64_t> tot(n, 0);
+    int64_t W = 0;
+    for (int i = 0; i < n; ++i) {
+      const int64_t ns = R.probs[i]->lay.nslices;
+      tot[i] = R.probs[i]->h_slice_off[ns] + kSliceCost * ns;
+      W += tot[i];
+    }
+    const int64_t wmin = std::max<int64_t>(8192, W / (64 * static_cast<int64_t>(V)));
+    int64_t rem = W;
+    for (int i = 0; i < n; ++i) {
+      const int64_t ns = R.probs[i]->lay.nslices;
+      const std::vector<int64_t>& so = R.probs[i]->h_slice_off;
+      auto weight = [&](int64_t s) { return so[s] + kSliceCost * s; };
+      int64_t s = 0;
+      while (s < ns) {
+        const int64_t size = std::max(wmin, rem / (2 * static_cast<int64_t>(V)));
+        // first slice e > s with weight(e) - weight(s) >= size (or ns)
+        int64_t a = s + 1, b = ns;
+        while (a < b) {
+          const int64_t m = (a + b) / 2;
+          if (weight(m) - weight(s) < size)
+            a = m + 1;
+          else
+            b = m;
+        }
+        Task t;
+        t.inst = i;
+        t.stride = 1;
+        t.first = s;
+        t.end = a;
+        R.h_units.push_back(t);
+        rem -= weight(a) - weight(s);
+        s = a;
+      }
+    }
+  }
+  R.h_seg.assign(n, {});
+  for (size_t t = 0; t < R.h_tasks.size(); ++t) R.h_seg[R.h_tasks[t].inst].push_back(static_cast<int32_t>(t));
+  R.seg_off.assign(n, 0);
+  for (int i = 1; i < n; ++i) R.seg_off[i] = R.seg_off[i - 1] + static_cast<int32_t>(R.h_seg[i - 1].size());
+}
+
+// Device tables of the runner from the members' current state and options.
+dlm_status write_tables(Runner& R) {
+  const int n = static_cast<int>(R.probs.size());
+  std::vector<InstDesc> it(n), ss(n);
+  std::vector<UpdInst> up(n);
+  std::vector<StatsInst> st(n);
+  for (int i = 0; i < n; ++i) {
+    const dlm_problem* p = R.probs[i];
+    it[i] = base_desc(p);
+    it[i].y = p->y;
+    it[i].gamma = &p->state->gamma;
+    it[i].acc = p->acc;
+    it[i].accC = p->accC;
+    it[i].accQ = p->accQ;
+    it[i].seg_obj = R.seg_obj;
+    it[i].xout = nullptr;
+    ss[i] = base_desc(p);
+    ss[i].y = p->lam;
+    ss[i].gamma = &p->state->gamma;
+    ss[i].acc = p->acc2;
+    ss[i].accC = p->accC;
+    ss[i].accQ = p->accQ;
+    ss[i].seg_obj = R.seg_obj;
+    ss[i].xout = nullptr;
+    UpdInst u{};
+    u.state = p->state;
+    u.gamma_tab = p->gamma_tab;
+    u.b = p->b;
+    u.inv_n2 = p->inv_n2;
+    u.lam = p->lam;
+    u.y = p->y;
+    u.acc = p->acc;
+    u.iters_per_stage = p->ips;
+    u.inv_nmax = p->lay.n2max > 0 ? 1.0 / p->lay.n2max : 0.0;
+    u.inv_scaleG = std::ldexp(1.0, -p->sG);
+    u.J = static_cast<int32_t>(p->J);
+    u.precondition = p->opt.precondition ? 1 : 0;
+    up[i] = u;
+    st[i] = base_stats(p, R, i);
+    st[i].lam = p->lam;
+    st[i].gamma = &p->state->gamma;
+    st[i].grad_out = nullptr;
+    st[i].state = p->state;
+  }
+  CK(cudaMemcpy(R.inst_iter, it.data(), sizeof(InstDesc) * n, cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(R.inst_stats, ss.data(), sizeof(InstDesc) * n, cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(R.upd, up.data(), sizeof(UpdInst) * n, cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(R.st_stats, st.data(), sizeof(StatsInst) * n, cudaMemcpyHostToDevice));
   return DLM_OK;
 }
 
-// Device tables derived from the handle (re-written after option changes).
-dlm_status write_tables(dlm_problem* p) {
-  InstDesc it = base_desc(p);
-  it.y = p->y;
-  it.gamma = &p->state->gamma;
-  it.acc = p->acc;
-  it.accC = p->accC;
-  it.accQ = p->accQ;
-  it.seg_obj = p->seg_obj;
-  it.xout = nullptr;
-  InstDesc ss = base_desc(p);
-  ss.y = p->lam;
-  ss.gamma = &p->state->gamma;
-  ss.acc = p->acc2;
-  ss.accC = p->accC;
-  ss.accQ = p->accQ;
-  ss.seg_obj = p->seg_obj;
-  ss.xout = nullptr;
-  CK(cudaMemcpy(p->inst_iter, &it, sizeof(InstDesc), cudaMemcpyHostToDevice));
-  CK(cudaMemcpy(p->inst_stats, &ss, sizeof(InstDesc), cudaMemcpyHostToDevice));
-
-  UpdInst u{};
-  u.state = p->state;
-  u.gamma_tab = p->gamma_tab;
-  u.b = p->b;
-  u.inv_n2 = p->inv_n2;
-  u.lam = p->lam;
-  u.y = p->y;
-  u.acc = p->acc;
-  u.iters_per_stage = p->ips;
-  u.inv_nmax = p->lay.n2max > 0 ? 1.0 / p->lay.n2max : 0.0;
-  u.inv_scaleG = std::ldexp(1.0, -p->sG);
-  u.J = static_cast<int32_t>(p->J);
-  u.precondition = p->opt.precondition ? 1 : 0;
-  CK(cudaMemcpy(p->upd, &u, sizeof(UpdInst), cudaMemcpyHostToDevice));
-
-  StatsInst st = base_stats(p);
-  st.lam = p->lam;
-  st.gamma = &p->state->gamma;
-  st.grad_out = nullptr;
-  st.state = p->state;
-  CK(cudaMemcpy(p->st_stats, &st, sizeof(StatsInst), cudaMemcpyHostToDevice));
-  invalidate_graph(p);
-  return DLM_OK;
+// (Re)builds tasks and tables for the runner's current grid/assignment.
+dlm_status runner_build(Runner& R) {
+  CK(cudaStreamSynchronize(R.stream));
+  invalidate_graph(R);
+  const int n = static_cast<int>(R.probs.size());
+  if (!R.inst_iter) {
+    CK(dalloc(&R.inst_iter, n));
+    CK(dalloc(&R.inst_stats, n));
+    CK(dalloc(&R.upd, n));
+    CK(dalloc(&R.st_stats, n));
+  }
+  build_task_list(R);
+  cudaFree(R.tasks);
+  cudaFree(R.cta_task);
+  cudaFree(R.seg_lists);
+  cudaFree(R.seg_obj);
+  R.tasks = nullptr;
+  R.cta_task = R.seg_lists = nullptr;
+  R.seg_obj = nullptr;
+  CK(dalloc(&R.tasks, R.h_tasks.size()));
+  CK(dalloc(&R.cta_task, R.h_cta.size()));
+  CK(dalloc(&R.seg_lists, R.h_tasks.size()));
+  CK(dalloc(&R.seg_obj, R.h_tasks.size()));
+  if (!R.h_tasks.empty())
+    CK(cudaMemcpy(R.tasks, R.h_tasks.data(), sizeof(Task) * R.h_tasks.size(), cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(R.cta_task, R.h_cta.data(), sizeof(int32_t) * R.h_cta.size(), cudaMemcpyHostToDevice));
+  std::vector<int32_t> flat;
+  for (const auto& v : R.h_seg) flat.insert(flat.end(), v.begin(), v.end());
+  if (!flat.empty()) CK(cudaMemcpy(R.seg_lists, flat.data(), sizeof(int32_t) * flat.size(), cudaMemcpyHostToDevice));
+  cudaFree(R.units);
+  R.units = nullptr;
+  if (!R.h_units.empty()) {
+    CK(dalloc(&R.units, R.h_units.size()));
+    CK(cudaMemcpy(R.units, R.h_units.data(), sizeof(Task) * R.h_units.size(), cudaMemcpyHostToDevice));
+  }
+  if (!R.ctr) CK(dalloc(&R.ctr, 2));
+  CK(cudaMemset(R.ctr, 0, 2 * sizeof(unsigned)));
+  return write_tables(R);
 }
 
-dlm_status enqueue_iteration(dlm_problem* p) {
+SweepLaunch launch_of(const Runner& R, const InstDesc* tab) {
   SweepLaunch L;
-  L.inst = p->inst_iter;
-  L.tasks = p->tasks;
-  L.cta_task = p->cta_task;
-  L.grid = p->grid;
-  L.smemJ = p->smemJ;
-  L.stream = p->stream;
-  CK(launch_sweep(L, false, p->bf16));
-  CK(launch_update(p->upd, 1, p->stream));
+  L.inst = tab;
+  L.tasks = R.tasks;
+  L.cta_task = R.cta_task;
+  L.grid = R.grid;
+  L.smemJ = R.smemJ;
+  L.threads = R.threads;
+  L.coop_max = R.coop_max;
+  L.stream = R.stream;
+  L.units = R.h_units.empty() ? nullptr : R.units;
+  L.nunits = static_cast<int32_t>(R.h_units.size());
+  L.ctr = R.ctr;
+  return L;
+}
+
+dlm_status enqueue_iteration(Runner& R) {
+  CK(launch_sweep(launch_of(R, R.inst_iter), false, R.bf16));
+  CK(launch_update(R.upd, static_cast<int>(R.probs.size()), R.stream));
   return DLM_OK;
 }
 
-dlm_status enqueue_certificate(dlm_problem* p, const InstDesc* inst_tab, const StatsInst* st_tab) {
-  SweepLaunch L;
-  L.inst = inst_tab;
-  L.tasks = p->tasks;
-  L.cta_task = p->cta_task;
-  L.grid = p->grid;
-  L.smemJ = p->smemJ;
-  L.stream = p->stream;
-  CK(launch_sweep(L, true, p->bf16));
-  CK(launch_stats(st_tab, 1, p->stream));
+dlm_status enqueue_certificate(Runner& R, const InstDesc* inst_tab, const StatsInst* st_tab) {
+  CK(launch_sweep(launch_of(R, inst_tab), true, R.bf16));
+  CK(launch_stats(st_tab, static_cast<int>(R.probs.size()), R.stream));
   return DLM_OK;
 }
 
-dlm_status capture_graph(dlm_problem* p, int iters) {
-  invalidate_graph(p);
+dlm_status capture_graph(Runner& R, int iters) {
+  invalidate_graph(R);
   cudaGraph_t g = nullptr;
-  CK(cudaStreamBeginCapture(p->stream, cudaStreamCaptureModeThreadLocal));
+  CK(cudaStreamBeginCapture(R.stream, cudaStreamCaptureModeThreadLocal));
   dlm_status st = DLM_OK;
-  for (int i = 0; i < iters && st == DLM_OK; ++i) st = enqueue_iteration(p);
-  cudaError_t e = cudaStreamEndCapture(p->stream, &g);
+  for (int i = 0; i < iters && st == DLM_OK; ++i) st = enqueue_iteration(R);
+  cudaError_t e = cudaStreamEndCapture(R.stream, &g);
   if (st != DLM_OK) {
     if (g) cudaGraphDestroy(g);
     return st;
   }
   if (e != cudaSuccess) return fail(DLM_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(e));
-  e = cudaGraphInstantiate(&p->gexec, g, 0);
+  e = cudaGraphInstantiate(&R.gexec, g, 0);
   cudaGraphDestroy(g);
   if (e != cudaSuccess) return fail(DLM_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
-  p->gexec_iters = iters;
+  R.gexec_iters = iters;
   return DLM_OK;
+}
+
+dlm_status runner_step(Runner& R, int64_t n_iters) {
+  const int gi = R.graph_iters > 0 ? R.graph_iters : 10;
+  if (n_iters >= gi && (!R.gexec || R.gexec_iters != gi)) {
+    dlm_status st = capture_graph(R, gi);
+    if (st != DLM_OK) return st;
+  }
+  int64_t done = 0;
+  for (; done + gi <= n_iters; done += gi) CK(cudaGraphLaunch(R.gexec, R.stream));
+  for (; done < n_iters; ++done) {
+    dlm_status st = enqueue_iteration(R);
+    if (st != DLM_OK) return st;
+  }
+  return DLM_OK;
+}
+
+dlm_status runner_step_timed(Runner& R, int64_t n_iters, double* sweep_ms, double* update_ms, double* total_ms) {
+  const size_t need = static_cast<size_t>(2 * n_iters + 1);
+  while (R.events.size() < need) {
+    cudaEvent_t e;
+    CK(cudaEventCreate(&e));
+    R.events.push_back(e);
+  }
+  const SweepLaunch L = launch_of(R, R.inst_iter);
+  const int n = static_cast<int>(R.probs.size());
+  CK(cudaEventRecord(R.events[0], R.stream));
+  for (int64_t i = 0; i < n_iters; ++i) {
+    CK(launch_sweep(L, false, R.bf16));
+    CK(cudaEventRecord(R.events[2 * i + 1], R.stream));
+    CK(launch_update(R.upd, n, R.stream));
+    CK(cudaEventRecord(R.events[2 * i + 2], R.stream));
+  }
+  CK(cudaStreamSynchronize(R.stream));
+  double ss = 0, su = 0;
+  for (int64_t i = 0; i < n_iters; ++i) {
+    float a = 0, b = 0;
+    CK(cudaEventElapsedTime(&a, R.events[2 * i], R.events[2 * i + 1]));
+    CK(cudaEventElapsedTime(&b, R.events[2 * i + 1], R.events[2 * i + 2]));
+    ss += a;
+    su += b;
+  }
+  float tot = 0;
+  if (n_iters > 0) CK(cudaEventElapsedTime(&tot, R.events[0], R.events[2 * n_iters]));
+  if (sweep_ms) *sweep_ms = ss;
+  if (update_ms) *update_ms = su;
+  if (total_ms) *total_ms = tot;
+  return DLM_OK;
+}
+
+// Applies mapping options to a runner: grid, threads, cooperative threshold,
+// assignment.  Rebuilds the tasks when the launch shape changes.
+dlm_status runner_configure(Runner& R, const dlm_options& o, bool force) {
+  const int threads = o.block_threads > 0 ? o.block_threads : kSweepThreads;
+  const int per_sm = o.ctas_per_sm > 0 ? o.ctas_per_sm : (threads <= 512 ? 2 : 1);
+  const int grid = R.sms * per_sm;
+  const int assign = o.mapping == 1   ? kAssignInterleaved
+                     : o.mapping == 2 ? kAssignContiguous
+                     : o.mapping == 3 ? kAssignDynamic
+                                      : (R.probs.size() > 1 ? kAssignDynamic : kAssignInterleaved);
+  R.coop_max = o.coop_max > 0 ? o.coop_max : kDefaultCoopMax;
+  R.graph_iters = o.graph_iters > 0 ? o.graph_iters : 10;
+  if (force || grid != R.grid || threads != R.threads || assign != R.assign) {
+    R.grid = grid;
+    R.threads = threads;
+    R.assign = assign;
+    return runner_build(R);
+  }
+  invalidate_graph(R);
+  return write_tables(R);
 }
 
 dlm_status read_stats(dlm_problem* p, dlm_stats* out) {
@@ -315,9 +559,8 @@ dlm_status read_stats(dlm_problem* p, dlm_stats* out) {
     out->uncert_gap = p->h_out[3];
     out->max_viol = p->h_out[4];
     out->seconds = p->last_solve_seconds;
-    out->status = (hs.status & kStatNumeric) ? DLM_ERR_NUMERIC
-                  : (hs.status & kStatTimeout) ? DLM_ERR_TIMEOUT
-                                               : DLM_OK;
+    out->status =
+        (hs.status & kStatNumeric) ? DLM_ERR_NUMERIC : (hs.status & kStatTimeout) ? DLM_ERR_TIMEOUT : DLM_OK;
     out->converged = 0;
   }
   return DLM_OK;
@@ -326,7 +569,7 @@ dlm_status read_stats(dlm_problem* p, dlm_stats* out) {
 void free_problem(dlm_problem* p) {
   if (!p) return;
   if (p->stream) cudaStreamSynchronize(p->stream);
-  invalidate_graph(p);
+  runner_free(p->run);
   cudaFree(p->lay.slice_off);
   cudaFree(p->lay.slice_w);
   cudaFree(p->lay.col);
@@ -334,16 +577,13 @@ void free_problem(dlm_problem* p) {
   cudaFree(p->lay.orig_off);
   cudaFree(p->lay.udeg);
   cudaFree(p->lay.n2);
-  void* ptrs[] = {p->b,        p->inv_n2,    p->lam,      p->y,        p->acc,      p->acc2,     p->accC,
-                  p->accQ,     p->gamma_tab, p->calc_gamma, p->seg_obj, p->stats_out, p->state,    p->inst_iter,
-                  p->inst_stats, p->inst_calc, p->upd,     p->st_stats, p->st_calc,  p->tasks,    p->cta_task,
-                  p->seg_list};
+  void* ptrs[] = {p->b,         p->inv_n2,    p->lam,       p->y,         p->acc,   p->acc2,      p->accC,
+                  p->accQ,      p->gamma_tab, p->calc_gamma, p->stats_out, p->state, p->inst_calc, p->st_calc};
   for (void* q : ptrs) cudaFree(q);
   cudaFreeHost(p->h_out);
   cudaFreeHost(p->h_inst);
   cudaFreeHost(p->h_stinst);
-  cudaFreeHost(p->h_upd);
-  for (cudaEvent_t e : p->events) cudaEventDestroy(e);
+  if (p->ev) cudaEventDestroy(p->ev);
   if (p->own_stream && p->stream) cudaStreamDestroy(p->stream);
   delete p;
 }
@@ -363,7 +603,124 @@ dlm_status upload_schedule(dlm_problem* p) {
   k_warm<<<blocks_for(p->J), 256, 0, p->stream>>>(p->lam, p->lam, p->y, p->J, p->state);
   CK(cudaGetLastError());
   CK(cudaStreamSynchronize(p->stream));
-  return write_tables(p);
+  invalidate_graph(p->run);
+  return write_tables(p->run);
+}
+
+// Saved duals and state of the members (tuning trials must not advance them).
+struct Saved {
+  std::vector<float*> lam, y;
+  std::vector<DevState> st;
+};
+dlm_status save_state(Runner& R, Saved* S) {
+  CK(cudaStreamSynchronize(R.stream));
+  for (dlm_problem* p : R.probs) {
+    float *l = nullptr, *y = nullptr;
+    CK(dalloc(&l, p->J));
+    CK(dalloc(&y, p->J));
+    CK(cudaMemcpy(l, p->lam, sizeof(float) * p->J, cudaMemcpyDeviceToDevice));
+    CK(cudaMemcpy(y, p->y, sizeof(float) * p->J, cudaMemcpyDeviceToDevice));
+    DevState hs;
+    CK(cudaMemcpy(&hs, p->state, sizeof(DevState), cudaMemcpyDeviceToHost));
+    S->lam.push_back(l);
+    S->y.push_back(y);
+    S->st.push_back(hs);
+  }
+  return DLM_OK;
+}
+dlm_status restore_state(Runner& R, const Saved& S) {
+  CK(cudaStreamSynchronize(R.stream));
+  for (size_t i = 0; i < R.probs.size(); ++i) {
+    dlm_problem* p = R.probs[i];
+    CK(cudaMemcpy(p->lam, S.lam[i], sizeof(float) * p->J, cudaMemcpyDeviceToDevice));
+    CK(cudaMemcpy(p->y, S.y[i], sizeof(float) * p->J, cudaMemcpyDeviceToDevice));
+    CK(cudaMemcpy(p->state, &S.st[i], sizeof(DevState), cudaMemcpyHostToDevice));
+    CK(cudaMemset(p->acc, 0, sizeof(unsigned long long) * p->J));
+  }
+  return DLM_OK;
+}
+void free_saved(Saved& S) {
+  for (float* q : S.lam) cudaFree(q);
+  for (float* q : S.y) cudaFree(q);
+  S.lam.clear();
+  S.y.clear();
+}
+
+// Times candidate mappings for `iters` iterations each (after one warm-up
+// iteration) from the same state, keeps the fastest sweep, restores the state.
+dlm_status tune(Runner& R, dlm_options base, int iters, dlm_options* chosen, double* best_ms_out) {
+  if (iters < 1) iters = 3;
+  Saved S;
+  dlm_status st = save_state(R, &S);
+  if (st != DLM_OK) return st;
+  const int threads_c[] = {1024, 512};
+  const int coop_c[] = {1, 6, 12, 20, 33};
+  const int assign_c[] = {kAssignInterleaved, kAssignContiguous, kAssignDynamic};
+  const size_t smem = sweep_smem_bytes(R.smemJ, false);
+  int sm_bytes = 0;
+  cudaDeviceGetAttribute(&sm_bytes, cudaDevAttrMaxSharedMemoryPerMultiprocessor, R.device);
+  dlm_options best = base;
+  double best_ms = 1e300;
+  for (int th : threads_c) {
+    if (th == 512 && 2 * (smem + 2048) > static_cast<size_t>(sm_bytes)) continue;  // two CTAs per SM must fit
+    for (int as : assign_c) {
+      if (as == kAssignInterleaved && R.probs.size() > 8) continue;  // too many segments per CTA
+      for (int cm : coop_c) {
+        dlm_options o = base;
+        o.block_threads = th;
+        o.ctas_per_sm = 0;
+        o.mapping = as + 1;
+        o.coop_max = cm;
+        st = runner_configure(R, o, false);
+        if (st == DLM_OK) st = restore_state(R, S);
+        double sw = 0;
+        if (st == DLM_OK) st = runner_step_timed(R, 1, nullptr, nullptr, nullptr);
+        if (st == DLM_OK) st = restore_state(R, S);
+        if (st == DLM_OK) st = runner_step_timed(R, iters, &sw, nullptr, nullptr);
+        if (st != DLM_OK) {
+          free_saved(S);
+          return st;
+        }
+        if (sw < best_ms) {
+          best_ms = sw;
+          best = o;
+        }
+      }
+    }
+  }
+  st = runner_configure(R, best, false);
+  if (st == DLM_OK) st = restore_state(R, S);
+  free_saved(S);
+  if (chosen) *chosen = best;
+  if (best_ms_out) *best_ms_out = best_ms / iters;
+  return st;
+}
+
+// A batch's stream and its members' streams may differ: batch work waits for
+// the work already enqueued on each member's stream, and later member work
+// waits for the batch work (stream-ordered, no host synchronization).
+dlm_status batch_enter(Runner& R) {
+  for (dlm_problem* p : R.probs) {
+    if (p->stream == R.stream) continue;
+    CK(cudaEventRecord(p->ev, p->stream));
+    CK(cudaStreamWaitEvent(R.stream, p->ev, 0));
+  }
+  return DLM_OK;
+}
+dlm_status batch_leave(Runner& R) {
+  CK(cudaEventRecord(R.done, R.stream));
+  for (dlm_problem* p : R.probs)
+    if (p->stream != R.stream) CK(cudaStreamWaitEvent(p->stream, R.done, 0));
+  return DLM_OK;
+}
+
+dlm_status check_options(const dlm_options* opt) {
+  if (!opt) return fail(DLM_ERR_INVALID_ARG, "null options");
+  if (opt->gap_every < 0 || opt->graph_iters < 0 || opt->mapping < 0 || opt->mapping > 3 || opt->ctas_per_sm < 0 ||
+      opt->ctas_per_sm > 4 || opt->coop_max < 0 || opt->coop_max > 33 ||
+      (opt->block_threads != 0 && opt->block_threads != 512 && opt->block_threads != 1024))
+    return fail(DLM_ERR_INVALID_ARG, "bad option value");
+  return DLM_OK;
 }
 
 }  // namespace
@@ -397,7 +754,6 @@ dlm_status dlm_create(const dlm_problem_desc* desc, void* stream, dlm_problem** 
   p->kind = desc->kind;
   p->z = desc->z;
   p->opt.gap_every = 50;
-  p->opt.mapping = -1;
   p->opt.graph_iters = 10;
   cudaGetDevice(&p->device);
   if (stream) {
@@ -468,22 +824,20 @@ dlm_status dlm_create(const dlm_problem_desc* desc, void* stream, dlm_problem** 
     free_problem(p);
     return fail(DLM_ERR_UNSUPPORTED, "item sums too large for 64-bit fixed point");
   }
-
-  p->smemJ = static_cast<int>(J);
-  if (sweep_smem_bytes(p->smemJ, true) > sweep_smem_limit()) {
+  if (sweep_smem_bytes(static_cast<int>(J), true) > sweep_smem_limit()) {
     cleanup_tmp();
     free_problem(p);
     return fail(DLM_ERR_UNSUPPORTED, "num_items too large for the shared-memory item arrays of this build");
   }
 
-#define CKC(x)                                                                 \
-  do {                                                                         \
-    cudaError_t e_ = (x);                                                      \
-    if (e_ != cudaSuccess) {                                                   \
-      cleanup_tmp();                                                           \
-      free_problem(p);                                                         \
+#define CKC(x)                                                                     \
+  do {                                                                             \
+    cudaError_t e_ = (x);                                                          \
+    if (e_ != cudaSuccess) {                                                       \
+      cleanup_tmp();                                                               \
+      free_problem(p);                                                             \
       return fail(DLM_ERR_CUDA, std::string(#x) + ": " + cudaGetErrorString(e_)); \
-    }                                                                          \
+    }                                                                              \
   } while (0)
 
   CKC(dalloc(&p->b, J));
@@ -505,28 +859,30 @@ dlm_status dlm_create(const dlm_problem_desc* desc, void* stream, dlm_problem** 
   CKC(dalloc(&p->calc_gamma, 1));
   CKC(dalloc(&p->stats_out, 8));
   CKC(dalloc(&p->state, 1));
-  CKC(dalloc(&p->inst_iter, 1));
-  CKC(dalloc(&p->inst_stats, 1));
   CKC(dalloc(&p->inst_calc, 1));
-  CKC(dalloc(&p->upd, 1));
-  CKC(dalloc(&p->st_stats, 1));
   CKC(dalloc(&p->st_calc, 1));
   CKC(cudaMallocHost(reinterpret_cast<void**>(&p->h_out), sizeof(double) * 8));
   CKC(cudaMallocHost(reinterpret_cast<void**>(&p->h_inst), sizeof(InstDesc)));
   CKC(cudaMallocHost(reinterpret_cast<void**>(&p->h_stinst), sizeof(StatsInst)));
-  CKC(cudaMallocHost(reinterpret_cast<void**>(&p->h_upd), sizeof(UpdInst)));
   CKC(sweep_prepare(p->bf16));
-  {
-    int sms = 0;
-    CKC(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, p->device));
-    p->grid = sms;  // persistent: one sweep CTA per SM
-  }
+  CKC(cudaEventCreateWithFlags(&p->ev, cudaEventDisableTiming));
+  p->h_slice_off.resize(p->lay.nslices + 1);
+  CKC(cudaMemcpyAsync(p->h_slice_off.data(), p->lay.slice_off, sizeof(int64_t) * (p->lay.nslices + 1),
+                      cudaMemcpyDeviceToHost, p->stream));
   CKC(cudaStreamSynchronize(p->stream));
   cleanup_tmp();
   for (void*& q : tmp) q = nullptr;
 #undef CKC
-  p->table = 0;
-  st = build_tasks(p);
+  // The handle's own runner: this one instance.
+  Runner& R = p->run;
+  R.probs = {p};
+  R.stream = p->stream;
+  R.bf16 = p->bf16;
+  R.device = p->device;
+  R.smemJ = static_cast<int>(J);
+  cudaDeviceGetAttribute(&R.sms, cudaDevAttrMultiProcessorCount, p->device);
+  p->h_gamma_tab.assign(kMaxStages, p->gamma0);
+  st = runner_configure(R, p->opt, true);
   if (st == DLM_OK) st = upload_schedule(p);
   if (st != DLM_OK) {
     free_problem(p);
@@ -549,28 +905,30 @@ dlm_status dlm_set_schedule(dlm_problem* p, double gamma0, double gamma_end, dou
 }
 
 dlm_status dlm_set_options(dlm_problem* p, const dlm_options* opt) {
-  if (!p || !opt) return fail(DLM_ERR_INVALID_ARG, "null argument");
-  if (opt->gap_every < 0 || opt->graph_iters < 0 || opt->mapping >= kNumTables || opt->ctas_per_sm < 0)
-    return fail(DLM_ERR_INVALID_ARG, "bad option value");
+  if (!p) return fail(DLM_ERR_INVALID_ARG, "null handle");
+  dlm_status st = check_options(opt);
+  if (st != DLM_OK) return st;
   dlm_options o = *opt;
   if (o.gap_every == 0) o.gap_every = 50;
   if (o.graph_iters == 0) o.graph_iters = 10;
-  const int table = o.mapping < 0 ? 0 : o.mapping;
-  int grid = p->grid;
-  if (o.ctas_per_sm > 0) {
-    int sms = 0;
-    CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, p->device));
-    grid = sms * o.ctas_per_sm;
-  }
   p->opt = o;
-  CK(cudaStreamSynchronize(p->stream));
-  if (table != p->table || grid != p->grid) {
-    p->table = table;
-    p->grid = grid;
-    dlm_status st = build_tasks(p);
-    if (st != DLM_OK) return st;
-  }
-  return write_tables(p);
+  return runner_configure(p->run, o, false);
+}
+
+dlm_status dlm_get_options(dlm_problem* p, dlm_options* opt) {
+  if (!p || !opt) return fail(DLM_ERR_INVALID_ARG, "null argument");
+  *opt = p->opt;
+  return DLM_OK;
+}
+
+dlm_status dlm_autotune(dlm_problem* p, int32_t iters, dlm_options* chosen, double* sweep_ms) {
+  if (!p) return fail(DLM_ERR_INVALID_ARG, "null handle");
+  dlm_options best{};
+  dlm_status st = tune(p->run, p->opt, iters, &best, sweep_ms);
+  if (st != DLM_OK) return st;
+  p->opt = best;
+  if (chosen) *chosen = best;
+  return DLM_OK;
 }
 
 dlm_status dlm_set_lambda(dlm_problem* p, const float* lambda0, int32_t memspace) {
@@ -594,62 +952,17 @@ dlm_status dlm_set_lambda(dlm_problem* p, const float* lambda0, int32_t memspace
 
 dlm_status dlm_step(dlm_problem* p, int64_t n_iters) {
   if (!p || n_iters < 0) return fail(DLM_ERR_INVALID_ARG, "bad argument");
-  const int gi = p->opt.graph_iters > 0 ? p->opt.graph_iters : 10;
-  if (n_iters >= gi && (!p->gexec || p->gexec_iters != gi)) {
-    dlm_status st = capture_graph(p, gi);
-    if (st != DLM_OK) return st;
-  }
-  int64_t done = 0;
-  for (; done + gi <= n_iters; done += gi) CK(cudaGraphLaunch(p->gexec, p->stream));
-  for (; done < n_iters; ++done) {
-    dlm_status st = enqueue_iteration(p);
-    if (st != DLM_OK) return st;
-  }
-  return DLM_OK;
+  return runner_step(p->run, n_iters);
 }
 
 dlm_status dlm_step_timed(dlm_problem* p, int64_t n_iters, double* sweep_ms, double* update_ms, double* total_ms) {
   if (!p || n_iters < 0) return fail(DLM_ERR_INVALID_ARG, "bad argument");
-  const size_t need = static_cast<size_t>(2 * n_iters + 1);
-  while (p->events.size() < need) {
-    cudaEvent_t e;
-    CK(cudaEventCreate(&e));
-    p->events.push_back(e);
-  }
-  SweepLaunch L;
-  L.inst = p->inst_iter;
-  L.tasks = p->tasks;
-  L.cta_task = p->cta_task;
-  L.grid = p->grid;
-  L.smemJ = p->smemJ;
-  L.stream = p->stream;
-  CK(cudaEventRecord(p->events[0], p->stream));
-  for (int64_t i = 0; i < n_iters; ++i) {
-    CK(launch_sweep(L, false, p->bf16));
-    CK(cudaEventRecord(p->events[2 * i + 1], p->stream));
-    CK(launch_update(p->upd, 1, p->stream));
-    CK(cudaEventRecord(p->events[2 * i + 2], p->stream));
-  }
-  CK(cudaStreamSynchronize(p->stream));
-  double ss = 0, su = 0;
-  for (int64_t i = 0; i < n_iters; ++i) {
-    float a = 0, b = 0;
-    CK(cudaEventElapsedTime(&a, p->events[2 * i], p->events[2 * i + 1]));
-    CK(cudaEventElapsedTime(&b, p->events[2 * i + 1], p->events[2 * i + 2]));
-    ss += a;
-    su += b;
-  }
-  float tot = 0;
-  if (n_iters > 0) CK(cudaEventElapsedTime(&tot, p->events[0], p->events[2 * n_iters]));
-  if (sweep_ms) *sweep_ms = ss;
-  if (update_ms) *update_ms = su;
-  if (total_ms) *total_ms = tot;
-  return DLM_OK;
+  return runner_step_timed(p->run, n_iters, sweep_ms, update_ms, total_ms);
 }
 
 dlm_status dlm_get_stats(dlm_problem* p, dlm_stats* out) {
   if (!p) return fail(DLM_ERR_INVALID_ARG, "null handle");
-  dlm_status st = enqueue_certificate(p, p->inst_stats, p->st_stats);
+  dlm_status st = enqueue_certificate(p->run, p->run.inst_stats, p->run.st_stats);
   if (st != DLM_OK) return st;
   return read_stats(p, out);
 }
@@ -666,14 +979,12 @@ dlm_status dlm_solve(dlm_problem* p, double target_rel_gap, int64_t max_iters, d
     start_iter = hs.iter;
   }
   dlm_status result = DLM_ERR_TIMEOUT;
-  int64_t done = 0;
   for (;;) {
     dlm_status st = dlm_get_stats(p, &s);
     if (st != DLM_OK) return st;
     if (s.status != DLM_OK) {
       result = static_cast<dlm_status>(s.status);
-      g_err = s.status == DLM_ERR_NUMERIC ? "non-finite value in the iteration"
-                                          : "a device-side wait ran out of its limit";
+      g_err = s.status == DLM_ERR_NUMERIC ? "non-finite value in the iteration" : "a device-side check failed";
       break;
     }
     if (s.gamma == p->gamma_end && s.rel_gap <= target_rel_gap) {
@@ -681,11 +992,11 @@ dlm_status dlm_solve(dlm_problem* p, double target_rel_gap, int64_t max_iters, d
       s.converged = 1;
       break;
     }
-    done = s.iter - start_iter;
+    const int64_t done = s.iter - start_iter;
     if (done >= max_iters) break;
-    int64_t n = p->opt.gap_every;
+    int64_t n = p->opt.gap_every > 0 ? p->opt.gap_every : 50;
     if (n > max_iters - done) n = max_iters - done;
-    st = dlm_step(p, n);
+    st = runner_step(p->run, n);
     if (st != DLM_OK) return st;
   }
   const auto t1 = std::chrono::steady_clock::now();
@@ -708,18 +1019,18 @@ dlm_status dlm_calculate(dlm_problem* p, const float* lambda, double gamma, doub
   d.acc = p->acc2;
   d.accC = p->accC;
   d.accQ = p->accQ;
-  d.seg_obj = p->seg_obj;
+  d.seg_obj = p->run.seg_obj;
   d.xout = x;
   *p->h_inst = d;
   CK(cudaMemcpyAsync(p->inst_calc, p->h_inst, sizeof(InstDesc), cudaMemcpyHostToDevice, p->stream));
-  StatsInst s = base_stats(p);
+  StatsInst s = base_stats(p, p->run, 0);
   s.lam = lambda;
   s.gamma = p->calc_gamma;
   s.grad_out = grad;
   s.state = nullptr;
   *p->h_stinst = s;
   CK(cudaMemcpyAsync(p->st_calc, p->h_stinst, sizeof(StatsInst), cudaMemcpyHostToDevice, p->stream));
-  dlm_status st = enqueue_certificate(p, p->inst_calc, p->st_calc);
+  dlm_status st = enqueue_certificate(p->run, p->inst_calc, p->st_calc);
   if (st != DLM_OK) return st;
   CK(cudaMemcpyAsync(p->h_out, p->stats_out, sizeof(double) * 8, cudaMemcpyDeviceToHost, p->stream));
   CK(cudaStreamSynchronize(p->stream));
@@ -750,17 +1061,17 @@ dlm_status dlm_get_x(dlm_problem* p, float* out, int32_t memspace) {
   d.acc = p->acc2;
   d.accC = p->accC;
   d.accQ = p->accQ;
-  d.seg_obj = p->seg_obj;
+  d.seg_obj = p->run.seg_obj;
   d.xout = dst;
   *p->h_inst = d;
   CK(cudaMemcpyAsync(p->inst_calc, p->h_inst, sizeof(InstDesc), cudaMemcpyHostToDevice, p->stream));
-  StatsInst s = base_stats(p);
+  StatsInst s = base_stats(p, p->run, 0);
   s.lam = p->lam;
   s.gamma = &p->state->gamma;
   s.state = p->state;
   *p->h_stinst = s;
   CK(cudaMemcpyAsync(p->st_calc, p->h_stinst, sizeof(StatsInst), cudaMemcpyHostToDevice, p->stream));
-  dlm_status st = enqueue_certificate(p, p->inst_calc, p->st_calc);
+  dlm_status st = enqueue_certificate(p->run, p->inst_calc, p->st_calc);
   if (st == DLM_OK && tmp) {
     CK(cudaMemcpyAsync(out, tmp, sizeof(float) * p->nnz, cudaMemcpyDeviceToHost, p->stream));
     CK(cudaStreamSynchronize(p->stream));
@@ -817,5 +1128,165 @@ dlm_status dlm_get_info(dlm_problem* p, int64_t* num_users, int64_t* num_items, 
 }
 
 void dlm_destroy(dlm_problem* p) { free_problem(p); }
+
+// ---------------------------------------------------------------------------
+// Batches
+// ---------------------------------------------------------------------------
+
+dlm_status dlm_batch_create(dlm_problem* const* probs, int32_t n, void* stream, dlm_batch** out) {
+  if (!probs || n <= 0 || !out) return fail(DLM_ERR_INVALID_ARG, "need n > 0 problems");
+  *out = nullptr;
+  for (int i = 0; i < n; ++i) {
+    if (!probs[i]) return fail(DLM_ERR_INVALID_ARG, "null problem in batch");
+    if (probs[i]->bf16 != probs[0]->bf16) return fail(DLM_ERR_INVALID_ARG, "batch members must share val_dtype");
+    if (probs[i]->device != probs[0]->device) return fail(DLM_ERR_INVALID_ARG, "batch members must share a device");
+    for (int k = 0; k < i; ++k)
+      if (probs[k] == probs[i]) return fail(DLM_ERR_INVALID_ARG, "a problem appears twice in the batch");
+  }
+  dlm_batch* bt = new dlm_batch();
+  Runner& R = bt->run;
+  R.probs.assign(probs, probs + n);
+  R.bf16 = probs[0]->bf16;
+  R.device = probs[0]->device;
+  cudaDeviceGetAttribute(&R.sms, cudaDevAttrMultiProcessorCount, R.device);
+  if (stream) {
+    R.stream = static_cast<cudaStream_t>(stream);
+  } else {
+    if (cudaStreamCreateWithFlags(&R.stream, cudaStreamDefault) != cudaSuccess) {
+      delete bt;
+      return fail(DLM_ERR_CUDA, "stream creation failed");
+    }
+    bt->own_stream = true;
+  }
+  for (int i = 0; i < n; ++i) {
+    cudaStreamSynchronize(probs[i]->stream);
+    R.smemJ = std::max(R.smemJ, static_cast<int>(probs[i]->J));
+  }
+  if (sweep_smem_bytes(R.smemJ, true) > sweep_smem_limit()) {
+    if (bt->own_stream) cudaStreamDestroy(R.stream);
+    delete bt;
+    return fail(DLM_ERR_UNSUPPORTED, "largest num_items of the batch too large for the shared-memory item arrays");
+  }
+  if (cudaEventCreateWithFlags(&R.done, cudaEventDisableTiming) != cudaSuccess) {
+    if (bt->own_stream) cudaStreamDestroy(R.stream);
+    delete bt;
+    return fail(DLM_ERR_CUDA, "event creation failed");
+  }
+  dlm_options o = probs[0]->opt;
+  o.mapping = 0;
+  o.precondition = 0;  // per member, not a batch option
+  bt->opt = o;
+  dlm_status st = runner_configure(R, o, true);
+  if (st != DLM_OK) {
+    runner_free(R);
+    if (bt->own_stream) cudaStreamDestroy(R.stream);
+    delete bt;
+    return st;
+  }
+  *out = bt;
+  return DLM_OK;
+}
+
+dlm_status dlm_batch_set_options(dlm_batch* bt, const dlm_options* opt) {
+  if (!bt) return fail(DLM_ERR_INVALID_ARG, "null batch");
+  dlm_status st = check_options(opt);
+  if (st != DLM_OK) return st;
+  dlm_options o = *opt;
+  if (o.gap_every == 0) o.gap_every = 50;
+  if (o.graph_iters == 0) o.graph_iters = 10;
+  bt->opt = o;
+  return runner_configure(bt->run, o, false);
+}
+
+dlm_status dlm_batch_autotune(dlm_batch* bt, int32_t iters, dlm_options* chosen, double* sweep_ms) {
+  if (!bt) return fail(DLM_ERR_INVALID_ARG, "null batch");
+  dlm_options best{};
+  dlm_status st = batch_enter(bt->run);
+  if (st == DLM_OK) st = tune(bt->run, bt->opt, iters, &best, sweep_ms);
+  if (st != DLM_OK) return st;
+  bt->opt = best;
+  if (chosen) *chosen = best;
+  return DLM_OK;
+}
+
+dlm_status dlm_batch_step(dlm_batch* bt, int64_t n_iters) {
+  if (!bt || n_iters < 0) return fail(DLM_ERR_INVALID_ARG, "bad argument");
+  dlm_status st = batch_enter(bt->run);
+  if (st == DLM_OK) st = runner_step(bt->run, n_iters);
+  if (st == DLM_OK) st = batch_leave(bt->run);
+  return st;
+}
+
+dlm_status dlm_batch_step_timed(dlm_batch* bt, int64_t n_iters, double* sweep_ms, double* update_ms,
+                                double* total_ms) {
+  if (!bt || n_iters < 0) return fail(DLM_ERR_INVALID_ARG, "bad argument");
+  dlm_status st = batch_enter(bt->run);
+  if (st == DLM_OK) st = runner_step_timed(bt->run, n_iters, sweep_ms, update_ms, total_ms);
+  if (st == DLM_OK) st = batch_leave(bt->run);
+  return st;
+}
+
+dlm_status dlm_batch_get_stats(dlm_batch* bt, dlm_stats* out) {
+  if (!bt) return fail(DLM_ERR_INVALID_ARG, "null batch");
+  Runner& R = bt->run;
+  dlm_status st = batch_enter(R);
+  if (st == DLM_OK) st = enqueue_certificate(R, R.inst_stats, R.st_stats);
+  if (st != DLM_OK) return st;
+  CK(cudaStreamSynchronize(R.stream));
+  for (size_t i = 0; i < R.probs.size(); ++i) {
+    st = read_stats(R.probs[i], out ? out + i : nullptr);
+    if (st != DLM_OK) return st;
+  }
+  return DLM_OK;
+}
+
+dlm_status dlm_batch_solve(dlm_batch* bt, double target_rel_gap, int64_t max_iters, dlm_stats* out) {
+  if (!bt || max_iters < 0) return fail(DLM_ERR_INVALID_ARG, "bad argument");
+  Runner& R = bt->run;
+  const size_t n = R.probs.size();
+  std::vector<dlm_stats> s(n);
+  const auto t0 = std::chrono::steady_clock::now();
+  int64_t done = 0;
+  const int64_t every = bt->opt.gap_every > 0 ? bt->opt.gap_every : 50;
+  dlm_status result = DLM_ERR_TIMEOUT;
+  for (;;) {
+    dlm_status st = dlm_batch_get_stats(bt, s.data());
+    if (st != DLM_OK) return st;
+    bool all = true, bad = false;
+    for (size_t i = 0; i < n; ++i) {
+      if (s[i].status != DLM_OK) bad = true;
+      s[i].converged = (s[i].gamma == R.probs[i]->gamma_end && s[i].rel_gap <= target_rel_gap) ? 1 : 0;
+      all = all && s[i].converged;
+    }
+    if (bad) {
+      result = DLM_ERR_NUMERIC;
+      g_err = "a batch member reported a device-side error";
+      break;
+    }
+    if (all) {
+      result = DLM_OK;
+      break;
+    }
+    if (done >= max_iters) break;
+    const int64_t k = std::min(every, max_iters - done);
+    st = runner_step(R, k);
+    if (st == DLM_OK) st = batch_leave(R);
+    if (st != DLM_OK) return st;
+    done += k;
+  }
+  bt->last_solve_seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  for (size_t i = 0; i < n; ++i) s[i].seconds = bt->last_solve_seconds;
+  if (out) std::copy(s.begin(), s.end(), out);
+  if (result == DLM_ERR_TIMEOUT) g_err = "max_iters reached before every member met the target gap";
+  return result;
+}
+
+void dlm_batch_destroy(dlm_batch* bt) {
+  if (!bt) return;
+  cudaStreamSynchronize(bt->run.stream);
+  runner_free(bt->run);
+  if (bt->own_stream) cudaStreamDestroy(bt->run.stream);
+  delete bt;
+}
 
 }  // extern "C"

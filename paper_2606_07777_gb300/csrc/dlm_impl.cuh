@@ -87,8 +87,15 @@ struct SweepLaunch {
   const int32_t* cta_task;  // device [grid + 1]
   int32_t grid;
   int32_t smemJ;            // item capacity of the shared arrays
+  int32_t threads;          // threads per sweep CTA (0: kSweepThreads)
+  int32_t coop_max;         // warp-cooperative threshold path below this many users per warp
   cudaStream_t stream;
+  // Dynamic distribution of iteration sweeps (null: the static tasks above).
+  const Task* units;        // device [nunits] work units (stride 1), ordered by instance
+  int32_t nunits;
+  unsigned* ctr;            // device [2]: next unit, finished CTAs (zero between launches)
 };
+constexpr int kDefaultCoopMax = 12;
 
 struct StatsInst {
   const double* b;

@@ -14,18 +14,20 @@
 // shared memory (gathered by item index); item sums are accumulated in
 // shared memory and flushed once per CTA.
 //
-// Simplex projection (Sec. 4.3 gets the threshold by sorting; no sort here).
-// In u-space the threshold tau solves sum max(u - tau, 0) = gamma z, and
-// tau >= tau_1 = max(u) - gamma z.  One pass over the row keeps the largest
-// and second largest u: if the second is <= tau_1, the maximum is the only
-// active edge, tau = tau_1 and x = z on it exactly (the common case at small
-// gamma).  Otherwise the lane runs the iteration
-// tau <- (sum_{u > tau} u - gamma z) / #{u > tau} from tau_1 (Michelot 1986;
-// monotone from below, it stops when the active set stops changing), then
-// recomputes tau over the active set in float-pair arithmetic so that
-// x = (u - tau) / gamma keeps full FP32 relative accuracy when u and tau
-// nearly cancel.  The inequality simplex takes max(tau, 0) (the early exit of
-// Sec. 4.3).  Box: x = clip(u / gamma, 0, z).
+// Simplex projection (Sec. 4.3 gets the threshold by sorting the whole row;
+// no sort here).  In u-space the threshold tau solves
+// sum max(u - tau, 0) = gamma z.  One pass over the row keeps its four
+// largest u in a sorted register network; the sort-based rule applied to
+// those four either fixes the active set (at most three edges active: the
+// common case, and for one edge x = z on it exactly) or shows that at least
+// four are active, and then the lane runs the iteration
+// tau <- (sum_{u > tau} u - gamma z) / #{u > tau} from tau_4 (Michelot 1986;
+// monotone from below, it stops when the active set stops changing).  A
+// second pass recomputes tau over the active set in float-pair arithmetic, so
+// that x = (u - tau) / gamma keeps full FP32 relative accuracy when u and tau
+// nearly cancel, and records where the active edges are; x is then deposited
+// from those positions.  The inequality simplex takes max(tau, 0) (the early
+// exit of Sec. 4.3).  Box: x = clip(u / gamma, 0, z).
 //
 // Determinism: item sums are 64-bit fixed point (value * 2^s rounded, s chosen
 // at set-up so no sum can overflow), exact and order independent; slices are
@@ -149,17 +151,19 @@ __device__ __forceinline__ int warp_sumi(int v) {
 }
 
 // Threshold of user t of the slice computed by the whole warp: lane l takes
-// edges l, l + 32, ... of the user (re-read from L1; the warp has just
+// edges l, l + 32, ... of the user (re-read from L1/L2; the warp has just
 // streamed them), the Michelot sums and the pair-arithmetic refinement are
 // warp reductions in a fixed order, and every lane deposits the x of its own
-// edges.  Returns the threshold (tau, taul) and whether the inequality
-// simplex took tau = 0.
+// edges.  tau0 is the starting threshold (a lower bound on the equality
+// threshold); with `exact` it is already the threshold of the final active
+// set and the iteration is skipped.  Returns the threshold (tau, taul) and
+// whether the inequality simplex took tau = 0.
 template <class P, bool STATS>
 __device__ __forceinline__ void coop_user(const Seg& S, const float* __restrict__ ys, unsigned long long* accG,
                                           unsigned long long* accC, unsigned long long* accQ,
                                           const int32_t* __restrict__ cp0, const typename P::T* __restrict__ vp0,
-                                          int w, int w4, int t, float m1, float& tau, float& taul, bool& zero,
-                                          float& ob) {
+                                          int w, int w4, int t, float tau0, bool exact, float& tau, float& taul,
+                                          bool& zero, float& ob) {
   const int lane = threadIdx.x & 31;
   const bool box = S.kind == DLM_BOX;
   const bool eq = S.kind == DLM_SIMPLEX_EQ;
@@ -173,27 +177,29 @@ __device__ __forceinline__ void coop_user(const Seg& S, const float* __restrict_
   taul = 0.f;
   zero = box;
   if (!box) {
-    tau = m1 - S.gz;
-    int prevn = -1;
-    for (int it = 0; it < 256; ++it) {
-      float sm = 0.f;
-      int n = 0;
-      for (int k = lane; k < w; k += 32) {
-        int j;
-        float c, a;
-        const float u = uval(k, j, c, a);
-        if (u > tau) {
-          sm += u;
-          ++n;
+    tau = tau0;
+    if (!exact) {
+      int prevn = -1;
+      for (int it = 0; it < 256; ++it) {
+        float sm = 0.f;
+        int n = 0;
+        for (int k = lane; k < w; k += 32) {
+          int j;
+          float c, a;
+          const float u = uval(k, j, c, a);
+          if (u > tau) {
+            sm += u;
+            ++n;
+          }
         }
+        sm = warp_sum(sm);
+        n = warp_sumi(n);
+        if (n == prevn || n == 0) break;
+        prevn = n;
+        const float tn = __fdiv_rn(sm - S.gz, static_cast<float>(n));
+        if (tn == tau) break;
+        tau = tn;
       }
-      sm = warp_sum(sm);
-      n = warp_sumi(n);
-      if (n == prevn || n == 0) break;
-      prevn = n;
-      const float tn = __fdiv_rn(sm - S.gz, static_cast<float>(n));
-      if (tn == tau) break;
-      tau = tn;
     }
     zero = !eq && tau <= 0.f;
     if (!zero) {
@@ -233,17 +239,32 @@ __device__ __forceinline__ void coop_user(const Seg& S, const float* __restrict_
   }
 }
 
-// Users of a slice that need the general threshold path are handled by the
-// whole warp, one after another, unless at least this many of the 32 do (then
-// each lane runs its own user, which keeps the lanes busy).
-constexpr int kCoopMax = 12;
+// Sorted insertion of u into the four largest values seen (v0 >= ... >= v3).
+__device__ __forceinline__ void top4_insert(float u, float& v0, float& v1, float& v2, float& v3) {
+  float t = u;
+  const float n0 = fmaxf(v0, t);
+  t = fminf(v0, t);
+  const float n1 = fmaxf(v1, t);
+  t = fminf(v1, t);
+  const float n2 = fmaxf(v2, t);
+  t = fminf(v2, t);
+  v3 = fmaxf(v3, t);
+  v0 = n0;
+  v1 = n1;
+  v2 = n2;
+}
+
+// Users of a slice that need a threshold (modes 2 and 3 below) are handled by
+// the whole warp, one after another, unless at least coop_max of the 32 do
+// (then each lane runs its own user, which keeps the lanes busy).  coop_max is
+// a tuning parameter (0: always per lane, 33: always cooperative).
 
 // One slice: lane t = user t; edge k of lane t is element sell_el(k, t, w/4)
 // of the slice.
 template <class P, bool STATS>
 __device__ __forceinline__ void do_slice(const InstDesc& D, const Seg& S, const float* __restrict__ ys,
                                          unsigned long long* accG, unsigned long long* accC,
-                                         unsigned long long* accQ, int64_t s, double& wobj) {
+                                         unsigned long long* accQ, int64_t s, int coop_max, double& wobj) {
   const int lane = threadIdx.x & 31;
   const int64_t off = __ldg(D.slice_off + s);
   const int w = __ldg(D.slice_w + s);
@@ -253,8 +274,9 @@ __device__ __forceinline__ void do_slice(const InstDesc& D, const Seg& S, const 
   const bool box = S.kind == DLM_BOX;
   const bool eq = S.kind == DLM_SIMPLEX_EQ;
 
-  // Pass A: the row's largest u (m1, at edge k1) and second largest (m2).
-  float m1 = -INFINITY, m2 = -INFINITY;
+  // Pass A: the row's four largest u (v0 >= v1 >= v2 >= v3) and the edge k1
+  // of the largest.
+  float v0 = -INFINITY, v1 = -INFINITY, v2 = -INFINITY, v3 = -INFINITY;
   int k1 = 0;
 #pragma unroll 4
   for (int g = 0; g < w4; ++g) {
@@ -266,9 +288,8 @@ __device__ __forceinline__ void do_slice(const InstDesc& D, const Seg& S, const 
 #pragma unroll
     for (int e = 0; e < 4; ++e) {
       const float u = -fmaf(a[e], ys[jj[e]], c[e]);
-      m2 = fmaxf(m2, fminf(m1, u));
-      k1 = (u > m1) ? 4 * g + e : k1;
-      m1 = fmaxf(m1, u);
+      k1 = (u > v0) ? 4 * g + e : k1;
+      top4_insert(u, v0, v1, v2, v3);
     }
   }
   for (int k = 4 * w4; k < w; ++k) {
@@ -277,37 +298,59 @@ __device__ __forceinline__ void do_slice(const InstDesc& D, const Seg& S, const 
     float c, a;
     P::get(__ldg(ca0 + el), c, a);
     const float u = -fmaf(a, ys[j], c);
-    m2 = fmaxf(m2, fminf(m1, u));
-    k1 = (u > m1) ? k : k1;
-    m1 = fmaxf(m1, u);
+    k1 = (u > v0) ? k : k1;
+    top4_insert(u, v0, v1, v2, v3);
   }
 
-  // mode 0: no edge active; 1: the maximum alone, x = z; 2: general.
-  const float t1 = m1 - S.gz;
+  // The equality threshold solves sum_k max(u_k - tau, 0) = gamma z.  With
+  // the values sorted, tau_r = (v_0 + ... + v_{r-1} - gamma z) / r and the
+  // active count is the first r with v_r <= tau_r; scanning the four largest
+  // either finds it (the active set lies among them) or shows that at least
+  // four edges are active, and then tau_4 is a lower bound for the iteration.
+  // mode 0: no edge active; 1: the maximum alone, x = z; 2: threshold of the
+  // final active set known (tau); 3: iterate from tau.
   int mode;
-  if (box)
-    mode = (m1 > 0.f) ? 2 : 0;
-  else if (m1 == -INFINITY || (!eq && m1 <= 0.f))
-    mode = 0;
-  else if (m2 <= t1 && (eq || t1 >= 0.f))
-    mode = 1;
-  else
-    mode = 2;
-
-  float ob = 0.f;
   float tau = 0.f, taul = 0.f;
   bool zero = box;
-  const unsigned mask2 = __ballot_sync(kFull, mode == 2);
-  const bool coop = mask2 != 0u && __popc(mask2) < kCoopMax;  // warp-uniform
+  if (box) {
+    mode = (v0 > 0.f) ? 2 : 0;
+  } else if (v0 == -INFINITY || (!eq && v0 <= 0.f)) {
+    mode = 0;
+  } else {
+    float sm = v0;
+    int r = 1;
+    tau = v0 - S.gz;
+    if (v1 > tau) {
+      sm += v1;
+      r = 2;
+      tau = __fdiv_rn(sm - S.gz, 2.f);
+      if (v2 > tau) {
+        sm += v2;
+        r = 3;
+        tau = __fdiv_rn(sm - S.gz, 3.f);
+        if (v3 > tau) {
+          sm += v3;
+          r = 4;
+          tau = __fdiv_rn(sm - S.gz, 4.f);
+        }
+      }
+    }
+    mode = (r == 1 && (eq || tau >= 0.f)) ? 1 : (r < 4 ? 2 : 3);
+  }
+
+  float ob = 0.f;
+  const unsigned mask2 = __ballot_sync(kFull, mode >= 2);
+  const bool coop = mask2 != 0u && __popc(mask2) < coop_max;  // warp-uniform
   if (coop) {
     unsigned m = mask2;
     while (m) {
       const int t = __ffs(m) - 1;
       m &= m - 1;
-      const float mt = __shfl_sync(kFull, m1, t);
+      const float tt = __shfl_sync(kFull, tau, t);
+      const int mt = __shfl_sync(kFull, mode, t);
       float ta, tl;
       bool zr;
-      coop_user<P, STATS>(S, ys, accG, accC, accQ, col0, ca0, w, w4, t, mt, ta, tl, zr, ob);
+      coop_user<P, STATS>(S, ys, accG, accC, accQ, col0, ca0, w, w4, t, tt, mt == 2, ta, tl, zr, ob);
       if (lane == t) {
         tau = ta;
         taul = tl;
@@ -315,64 +358,104 @@ __device__ __forceinline__ void do_slice(const InstDesc& D, const Seg& S, const 
       }
     }
   }
-  if (mode == 2 && !coop) {
-    // per-lane general path
+  if (mode >= 2 && !coop) {
+    // per-lane threshold path
+    bool full = true;  // deposit by a pass over every edge of the row
+    int s0 = 0, s1 = 0, s2 = 0;
     if (!box) {
-      tau = t1;
-      int prevn = -1;
-      for (int it = 0; it < 256; ++it) {
-        float sm = 0.f;
-        int n = 0;
-        for (int k = 0; k < w; ++k) {
-          const int el = sell_el(k, lane, w4);
-          const int j = __ldg(col0 + el);
-          float c, a;
-          P::get(__ldg(ca0 + el), c, a);
-          const float u = -fmaf(a, ys[j], c);
-          if (u > tau) {
-            sm += u;
-            ++n;
+      if (mode == 3) {
+        int prevn = -1;
+        for (int it = 0; it < 256; ++it) {
+          float sm = 0.f;
+          int n = 0;
+          for (int k = 0; k < w; ++k) {
+            const int el = sell_el(k, lane, w4);
+            const int j = __ldg(col0 + el);
+            float c, a;
+            P::get(__ldg(ca0 + el), c, a);
+            const float u = -fmaf(a, ys[j], c);
+            if (u > tau) {
+              sm += u;
+              ++n;
+            }
           }
+          if (n == prevn || n == 0) break;
+          prevn = n;
+          const float tn = __fdiv_rn(sm - S.gz, static_cast<float>(n));
+          if (tn == tau) break;
+          tau = tn;
         }
-        if (n == prevn || n == 0) break;
-        prevn = n;
-        const float tn = __fdiv_rn(sm - S.gz, static_cast<float>(n));
-        if (tn == tau) break;
-        tau = tn;
       }
       zero = !eq && tau <= 0.f;
-      if (!zero) {
-        F2 sum{0.f, 0.f};
-        int n = 0;
-        for (int k = 0; k < w; ++k) {
-          const int el = sell_el(k, lane, w4);
-          const int j = __ldg(col0 + el);
-          float c, a;
-          P::get(__ldg(ca0 + el), c, a);
-          if (-fmaf(a, ys[j], c) > tau) {
-            sum = f2_add(sum, u_pair(c, a, ys[j]));
-            ++n;
-          }
+      // Pass B: the active edges (u > tau; u > 0 when tau <= 0 on the
+      // inequality simplex): their u in pair arithmetic, and the positions of
+      // the first three.
+      const float thr = zero ? 0.f : tau;
+      F2 sum{0.f, 0.f};
+      int n = 0;
+      auto visit = [&](int k, int j, float c, float a) {
+        if (-fmaf(a, ys[j], c) > thr) {
+          if (!zero) sum = f2_add(sum, u_pair(c, a, ys[j]));
+          if (n == 0)
+            s0 = k;
+          else if (n == 1)
+            s1 = k;
+          else if (n == 2)
+            s2 = k;
+          ++n;
         }
+      };
+      for (int g = 0; g < w4; ++g) {
+        const int q = 32 * g + lane;
+        const int4 jv = __ldg(reinterpret_cast<const int4*>(col0) + q);
+        float c[4], a[4];
+        P::get4(ca0, q, c, a);
+        visit(4 * g, jv.x, c[0], a[0]);
+        visit(4 * g + 1, jv.y, c[1], a[1]);
+        visit(4 * g + 2, jv.z, c[2], a[2]);
+        visit(4 * g + 3, jv.w, c[3], a[3]);
+      }
+      for (int k = 4 * w4; k < w; ++k) {
+        const int el = 128 * w4 + 32 * (k - 4 * w4) + lane;
+        float c, a;
+        P::get(__ldg(ca0 + el), c, a);
+        visit(k, __ldg(col0 + el), c, a);
+      }
+      full = n > 3;
+      if (!zero) {
         const F2 t2 = f2_threshold(sum, S.gz, S.gzl, n > 0 ? n : 1);
         if (!eq && t2.h + t2.l <= 0.f) {
-          zero = true;
+          zero = true;  // the active set shrinks to u > 0: take every edge again
+          full = true;
         } else {
           tau = t2.h;
           taul = t2.l;
         }
       }
+      if (!full) {
+        // deposit from the recorded positions
+        for (int i = 0; i < n; ++i) {
+          const int el = sell_el(i == 0 ? s0 : (i == 1 ? s1 : s2), lane, w4);
+          const int j = __ldg(col0 + el);
+          float c, a;
+          P::get(__ldg(ca0 + el), c, a);
+          const float x = x_general(S, box, zero, zero ? 0.f : tau, zero ? 0.f : taul, c, a, ys[j]);
+          if (x > 0.f) deposit<STATS>(S, j, c, a, x, accG, accC, accQ, ob);
+        }
+      }
     }
     if (zero) tau = taul = 0.f;
-    // x on the active edges (u > tau; for the box and tau = 0, u > 0)
-    for (int k = 0; k < w; ++k) {
-      const int el = sell_el(k, lane, w4);
-      const int j = __ldg(col0 + el);
-      float c, a;
-      P::get(__ldg(ca0 + el), c, a);
-      if (-fmaf(a, ys[j], c) > tau) {
-        const float x = x_general(S, box, zero, tau, taul, c, a, ys[j]);
-        if (x > 0.f) deposit<STATS>(S, j, c, a, x, accG, accC, accQ, ob);
+    if (full) {
+      // x on the active edges (u > tau; for the box and tau = 0, u > 0)
+      for (int k = 0; k < w; ++k) {
+        const int el = sell_el(k, lane, w4);
+        const int j = __ldg(col0 + el);
+        float c, a;
+        P::get(__ldg(ca0 + el), c, a);
+        if (-fmaf(a, ys[j], c) > tau) {
+          const float x = x_general(S, box, zero, tau, taul, c, a, ys[j]);
+          if (x > 0.f) deposit<STATS>(S, j, c, a, x, accG, accC, accQ, ob);
+        }
       }
     }
   } else if (mode == 1) {
@@ -393,7 +476,7 @@ __device__ __forceinline__ void do_slice(const InstDesc& D, const Seg& S, const 
         float x = 0.f;
         if (mode == 1) {
           x = (k == k1) ? S.z : 0.f;
-        } else if (mode == 2) {
+        } else if (mode >= 2) {
           const int el = sell_el(k, lane, w4);
           const int j = __ldg(col0 + el);
           float c, a;
@@ -410,7 +493,7 @@ __device__ __forceinline__ void do_slice(const InstDesc& D, const Seg& S, const 
 template <class P, bool STATS>
 __global__ void __launch_bounds__(kSweepThreads, 1)
     sweep_kernel(const InstDesc* __restrict__ insts, const Task* __restrict__ tasks,
-                 const int32_t* __restrict__ cta_task, int smemJ) {
+                 const int32_t* __restrict__ cta_task, int smemJ, int coop_max) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   unsigned long long* accG = reinterpret_cast<unsigned long long*>(smem_raw);
   unsigned long long* accC = accG + smemJ;
@@ -462,7 +545,7 @@ __global__ void __launch_bounds__(kSweepThreads, 1)
         // static order: the FP64 objective partials are summed in a fixed order
         const int64_t step = static_cast<int64_t>(T.stride) * nw;
         for (int64_t s = T.first + static_cast<int64_t>(T.stride) * warp; s < T.end; s += step)
-          do_slice<P, STATS>(sD, S, ys, accG, accC, accQ, s, wobj);
+          do_slice<P, STATS>(sD, S, ys, accG, accC, accQ, s, coop_max, wobj);
       } else {
         // dynamic order within the CTA (item sums are exact, so the order of
         // slices does not change any result)
@@ -472,7 +555,7 @@ __global__ void __launch_bounds__(kSweepThreads, 1)
           if (lane == 0) i = atomicAdd(&s_next, 1ull);
           i = __shfl_sync(kFull, i, 0);
           if (i >= nsl) break;
-          do_slice<P, STATS>(sD, S, ys, accG, accC, accQ, T.first + i * T.stride, wobj);
+          do_slice<P, STATS>(sD, S, ys, accG, accC, accQ, T.first + i * T.stride, coop_max, wobj);
         }
         __syncthreads();
         if (threadIdx.x == 0) s_next = 0;
@@ -504,6 +587,87 @@ __global__ void __launch_bounds__(kSweepThreads, 1)
   }
 }
 
+// Sweep with dynamic work distribution (iteration sweeps only): CTAs take
+// work units -- a range of slices of one instance -- from a global counter in
+// table order.  A CTA keeps an instance's y and item sums in shared memory
+// across consecutive units of that instance and flushes the sums when it
+// moves to another instance.  The last CTA to finish resets the counters for
+// the next launch.  The units are ordered by instance and shrink toward the
+// end of the table, so the CTAs finish together.
+template <class P>
+__global__ void __launch_bounds__(kSweepThreads, 1)
+    sweep_dyn_kernel(const InstDesc* __restrict__ insts, const Task* __restrict__ units, int nunits,
+                     unsigned* __restrict__ ctr, int smemJ, int coop_max) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  unsigned long long* accG = reinterpret_cast<unsigned long long*>(smem_raw);
+  float* ys = reinterpret_cast<float*>(accG + smemJ);
+
+  __shared__ InstDesc sD;
+  __shared__ unsigned s_unit;
+  __shared__ unsigned long long s_next;
+  const int lane = threadIdx.x & 31;
+  int cur = -1;
+  Seg S{};
+  double wobj = 0.0;
+  for (;;) {
+    if (threadIdx.x == 0) {
+      s_unit = atomicAdd(ctr, 1u);
+      s_next = 0;
+    }
+    __syncthreads();
+    const unsigned u = s_unit;
+    const bool out_of_work = u >= static_cast<unsigned>(nunits);
+    const int inst = out_of_work ? -1 : units[u].inst;
+    if (out_of_work || inst != cur) {
+      if (cur >= 0) {
+        for (int j = threadIdx.x; j < sD.J; j += blockDim.x) {
+          const unsigned long long v = accG[j];
+          if (v) atomicAdd(sD.acc + j, v);
+        }
+      }
+      __syncthreads();
+      if (out_of_work) break;
+      if (threadIdx.x == 0) sD = insts[inst];
+      __syncthreads();
+      for (int j = threadIdx.x; j < sD.J; j += blockDim.x) {
+        ys[j] = sD.y[j];
+        accG[j] = 0ull;
+      }
+      const double g = *sD.gamma;
+      S.gamma = static_cast<float>(g);
+      S.invg = static_cast<float>(1.0 / g);
+      const double gz = g * static_cast<double>(sD.z);
+      S.gz = static_cast<float>(gz);
+      S.gzl = static_cast<float>(gz - static_cast<double>(S.gz));
+      S.z = sD.z;
+      S.scaleG = sD.scaleG;
+      S.scaleC = sD.scaleC;
+      S.scaleQ = sD.scaleQ;
+      S.kind = sD.kind;
+      cur = inst;
+      __syncthreads();
+    }
+    const Task T = units[u];
+    const int64_t nsl = T.end - T.first;
+    for (;;) {
+      int64_t i = 0;
+      if (lane == 0) i = static_cast<int64_t>(atomicAdd(&s_next, 1ull));
+      i = __shfl_sync(kFull, i, 0);
+      if (i >= nsl) break;
+      do_slice<P, false>(sD, S, ys, accG, nullptr, nullptr, T.first + i, coop_max, wobj);
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    __threadfence();
+    const unsigned prev = atomicAdd(ctr + 1, 1u);
+    if (prev == gridDim.x - 1) {
+      ctr[0] = 0u;
+      ctr[1] = 0u;
+    }
+  }
+}
+
 template <class P, bool STATS>
 constexpr auto kernel_of() {
   return &sweep_kernel<P, STATS>;
@@ -525,7 +689,10 @@ size_t sweep_smem_limit() {
 
 cudaError_t sweep_prepare(bool bf16) {
   const int lim = static_cast<int>(sweep_smem_limit());
-  cudaError_t e;
+  cudaError_t e =
+      bf16 ? cudaFuncSetAttribute(&sweep_dyn_kernel<BF16Pair>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim)
+           : cudaFuncSetAttribute(&sweep_dyn_kernel<F32Pair>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+  if (e != cudaSuccess) return e;
   if (bf16) {
     e = cudaFuncSetAttribute(kernel_of<BF16Pair, false>(), cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
     if (e != cudaSuccess) return e;
@@ -540,16 +707,25 @@ cudaError_t sweep_prepare(bool bf16) {
 
 cudaError_t launch_sweep(const SweepLaunch& L, bool stats, bool bf16) {
   const size_t sm = sweep_smem_bytes(L.smemJ, stats);
+  const int th = L.threads > 0 ? L.threads : kSweepThreads;
+  const int cm = L.coop_max;
+  if (!stats && L.units != nullptr) {
+    if (bf16)
+      sweep_dyn_kernel<BF16Pair><<<L.grid, th, sm, L.stream>>>(L.inst, L.units, L.nunits, L.ctr, L.smemJ, cm);
+    else
+      sweep_dyn_kernel<F32Pair><<<L.grid, th, sm, L.stream>>>(L.inst, L.units, L.nunits, L.ctr, L.smemJ, cm);
+    return cudaGetLastError();
+  }
   if (bf16) {
     if (stats)
-      sweep_kernel<BF16Pair, true><<<L.grid, kSweepThreads, sm, L.stream>>>(L.inst, L.tasks, L.cta_task, L.smemJ);
+      sweep_kernel<BF16Pair, true><<<L.grid, th, sm, L.stream>>>(L.inst, L.tasks, L.cta_task, L.smemJ, cm);
     else
-      sweep_kernel<BF16Pair, false><<<L.grid, kSweepThreads, sm, L.stream>>>(L.inst, L.tasks, L.cta_task, L.smemJ);
+      sweep_kernel<BF16Pair, false><<<L.grid, th, sm, L.stream>>>(L.inst, L.tasks, L.cta_task, L.smemJ, cm);
   } else {
     if (stats)
-      sweep_kernel<F32Pair, true><<<L.grid, kSweepThreads, sm, L.stream>>>(L.inst, L.tasks, L.cta_task, L.smemJ);
+      sweep_kernel<F32Pair, true><<<L.grid, th, sm, L.stream>>>(L.inst, L.tasks, L.cta_task, L.smemJ, cm);
     else
-      sweep_kernel<F32Pair, false><<<L.grid, kSweepThreads, sm, L.stream>>>(L.inst, L.tasks, L.cta_task, L.smemJ);
+      sweep_kernel<F32Pair, false><<<L.grid, th, sm, L.stream>>>(L.inst, L.tasks, L.cta_task, L.smemJ, cm);
   }
   return cudaGetLastError();
 }

@@ -97,7 +97,11 @@ typedef struct {
                             after another with all 32 lanes while fewer than coop_max of its
                             32 users need it (default 12; 1 never, 33 always) */
   int32_t block_threads; /* threads per sweep CTA: 0 (default 1024), 512 or 1024 */
-  int32_t reserved;
+  int32_t restart;       /* 1: adaptive momentum restart besides the stage restarts -- theta = 1
+                            after a step whose direction opposes the momentum in the step metric,
+                            sum_j (lam+_j - y_j)(lam+_j - lam_j) / step_j < 0 (O'Donoghue &
+                            Candes 2015); 0 (default): the paper's schedule-only restarts */
+  int32_t reserved[3];
 } dlm_options;
 
 /* Result of a certified-gap evaluation at the current iterate lam (one extra
@@ -250,6 +254,60 @@ dlm_status dlm_batch_get_stats(dlm_batch* bt, dlm_stats* out);
  * out[i] (may be NULL) gets member i's stats with `converged` per member. */
 dlm_status dlm_batch_solve(dlm_batch* bt, double target_rel_gap, int64_t max_iters, dlm_stats* out);
 void dlm_batch_destroy(dlm_batch* bt);
+
+/* Learned warm start (the paper motivates warm starts for recurring solves,
+ * Sec. 1, but fixes no predictor; this one is the project's).  A three-layer
+ * perceptron of width H maps DLM_WS_FEATURES per-item features to an initial
+ * dual: xn = (x - mu) / sd, h1 = relu(xn W1 + b1), h2 = relu(h1 W2 + b2),
+ * lam0 = softplus(h2 . w3 + b3 + softplus^-1(max(x_4, 1e-6))) -- a correction
+ * to the previous day's dual x_4, so lam0 >= 0 and an untrained last layer
+ * returns x_4.  Products run on the tensor cores with bf16 operands (xn, h1,
+ * h2, the weights and, in the backward pass, the pre-activation gradients) and
+ * FP32 accumulation; the master weights, Adam moments and biases are FP32.
+ * Training minimises the mean squared error against solved duals with Adam
+ * (beta1 0.9, beta2 0.999, eps 1e-8).  All reductions add in a fixed order:
+ * results are deterministic.  A predictor is not thread-safe; its work is
+ * ordered on its stream. */
+#define DLM_WS_FEATURES 7
+typedef struct dlm_ws dlm_ws;
+
+/* width: 8..1024, a multiple of 8.  seed: initial weights (He-uniform W1, W2;
+ * zero w3 and biases).  stream: cudaStream_t or NULL (own blocking stream).
+ * Normalizer mu = 0, sd = 1 until fitted or set. */
+dlm_status dlm_ws_create(int32_t width, uint64_t seed, void* stream, dlm_ws** out);
+/* Parameter count P and layout of the flat FP32 vector theta:
+ * W1 (F x H, row-major), b1 (H), W2 (H x H, row-major: row = input unit),
+ * b2 (H), w3 (H), b3 (1). */
+dlm_status dlm_ws_num_params(dlm_ws* w, int64_t* n);
+/* Host copies of theta (P floats) and the normalizer (F floats each); any
+ * pointer may be NULL.  Synchronous. */
+dlm_status dlm_ws_get_params(dlm_ws* w, float* theta, float* mu, float* sd);
+/* Replace theta (resets the Adam state) and/or the normalizer (both or
+ * neither; sd > 0).  Host arrays; NULL keeps the current values. */
+dlm_status dlm_ws_set_params(dlm_ws* w, const float* theta, const float* mu, const float* sd);
+/* Item features of an instance, one row of DLM_WS_FEATURES floats per item
+ * (device X, num_items x F, row-major):
+ *   0 log(1 + b_j)          1 log(1 + deg_j)      2 mean_i(-c_ij)
+ *   3 max_i(-c_ij)          4 lam_prev_j          5 log(gamma)
+ *   6 G_j / (1 + b_j), G = A x(lam_prev) - b at ridge gamma (one dual sweep)
+ * (2, 3 are 0 for an item without edges).  lam_prev: device, num_items.
+ * Allocates temporary device memory; synchronous. */
+dlm_status dlm_ws_features(dlm_problem* p, const float* lam_prev, double gamma, float* X);
+/* mu, sd of the columns of X (device, n x F; population sd, 1 where < 1e-6). */
+dlm_status dlm_ws_fit_normalizer(dlm_ws* w, const float* X, int64_t n);
+/* Loss at the current weights on (X, y) (device; n rows) into *loss (host)
+ * and its gradient (host, P floats, theta layout) into grad (may be NULL);
+ * no update.  Synchronous. */
+dlm_status dlm_ws_loss_grad(dlm_ws* w, const float* X, const float* y, int64_t n, double* loss, float* grad);
+/* `steps` full-batch Adam steps of learning rate lr on (X, y) (device; fits
+ * the normalizer first if none was fitted or set); the loss before each step
+ * into losses (host, steps floats; may be NULL).  n <= 2^26.  Synchronous. */
+dlm_status dlm_ws_train(dlm_ws* w, const float* X, const float* y, int64_t n, int32_t steps, float lr,
+                        float* losses);
+/* lam0 for n feature rows X (device) into out (device, n floats).
+ * Synchronous, so a solver on another stream may read out at once. */
+dlm_status dlm_ws_predict(dlm_ws* w, const float* X, int64_t n, float* out);
+void dlm_ws_destroy(dlm_ws* w);
 
 /* One dual evaluation straight from the caller's device CSR arrays, with no
  * device memory allocated by this call or any earlier one: for callers that

@@ -11,7 +11,9 @@ Parity status of each function (what pins it is in ``tests/test_oracle_*``):
   sweep/dual pinned: finite differences (Danskin), concavity, L-smoothness.
   fista      pinned: exact KKT solutions by enumeration of active sets, the
              LP limit (scipy linprog), slack-capacity and one-item closed
-             forms, the FISTA O(1/t^2) rate bound.
+             forms, the FISTA O(1/t^2) rate bound; with the adaptive
+             restart, convergence to the same enumerated KKT solutions and a
+             restart that fires on a hand-built overshoot.
   certify    pinned: weak duality, feasibility of the scaled point.
   The exact FP32-trajectory values on the large workloads are parity
   unpinned beyond oracle-vs-solver agreement (the paper prints no worked
@@ -76,7 +78,7 @@ def _load():
         lib.orc_dual.restype = d
         lib.orc_row_sq.argtypes = [P, vp]
         lib.orc_certify.argtypes = [P, vp, d, vp]
-        lib.orc_fista.argtypes = [P, d, d, d, i64, i32, i64, vp, vp, vp, vp, vp, vp]
+        lib.orc_fista.argtypes = [P, d, d, d, i64, i32, i32, i64, vp, vp, vp, vp, vp, vp]
         lib.orc_stage_gamma.argtypes = [d, d, d, i64]
         lib.orc_stage_gamma.restype = d
         _lib = lib
@@ -157,17 +159,17 @@ def certify(p: Problem, lam, gamma):
 
 
 def fista(p: Problem, T, gamma0, gamma_end=None, factor=0.5, iters_per_stage=0, precondition=False, lam0=None,
-          trajectory=True):
+          trajectory=True, restart=False):
     """T iterations of accelerated projected dual ascent; dict(lam, y, theta,
-    g_traj, gamma_traj)."""
+    g_traj, gamma_traj).  restart=True adds the adaptive momentum restart."""
     gamma_end = gamma0 if gamma_end is None else gamma_end
     lam0 = np.zeros(p.J) if lam0 is None else np.ascontiguousarray(lam0, dtype=np.float64)
     lam, y = np.empty(p.J), np.empty(p.J)
     th = ctypes.c_double()
     gt = np.empty(T) if trajectory else None
     gg = np.empty(T) if trajectory else None
-    _load().orc_fista(ctypes.byref(p._s), gamma0, gamma_end, factor, iters_per_stage, int(bool(precondition)), T,
-                      _p(lam0), _p(lam), _p(y), ctypes.byref(th), _p(gt), _p(gg))
+    _load().orc_fista(ctypes.byref(p._s), gamma0, gamma_end, factor, iters_per_stage, int(bool(precondition)),
+                      int(bool(restart)), T, _p(lam0), _p(lam), _p(y), ctypes.byref(th), _p(gt), _p(gg))
     return dict(lam=lam, y=y, theta=th.value, g_traj=gt, gamma_traj=gg)
 
 

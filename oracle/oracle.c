@@ -274,8 +274,8 @@ static double stage_gamma(double gamma0, double gamma_end, double factor, int64_
  * Outputs: lam_out, y_out (state after T iterations), theta_out, and per
  * iteration t: traj_g[t] = g(y_t), traj_gamma[t] (either may be NULL). */
 void orc_fista(const orc_problem* p, double gamma0, double gamma_end, double factor, int64_t iters_per_stage,
-               int32_t precondition, int64_t T, const double* lam0, double* lam_out, double* y_out,
-               double* theta_out, double* traj_g, double* traj_gamma) {
+               int32_t precondition, int32_t restart, int64_t T, const double* lam0, double* lam_out,
+               double* y_out, double* theta_out, double* traj_g, double* traj_gamma) {
   int64_t J = p->J;
   double* n2 = (double*)malloc(sizeof(double) * (size_t)J);
   double* lam = (double*)malloc(sizeof(double) * (size_t)J);
@@ -306,7 +306,23 @@ void orc_fista(const orc_problem* p, double gamma0, double gamma_end, double fac
     }
     int64_t s1 = (t + 1) / iters_per_stage;
     double gamma_next = stage_gamma(gamma0, gamma_end, factor, s1);
-    if (gamma_next != gamma) {
+    int restart_now = gamma_next != gamma;
+    if (restart && !restart_now) {
+      /* adaptive restart (O'Donoghue & Candes 2015, gradient-mapping test
+         for ascent, in the metric of the per-item steps): restart when the
+         step just taken opposes the momentum */
+      double dot = 0.0;
+      for (int64_t j = 0; j < J; ++j) {
+        double step;
+        if (precondition)
+          step = n2[j] > 0 ? gamma / n2[j] : 0.0;
+        else
+          step = nmax > 0 ? gamma / nmax : 0.0;
+        if (step > 0) dot += (nl[j] - y[j]) * (nl[j] - lam[j]) / step;
+      }
+      restart_now = dot < 0.0;
+    }
+    if (restart_now) {
       theta = 1.0;
       for (int64_t j = 0; j < J; ++j) {
         lam[j] = nl[j];

@@ -21,7 +21,10 @@ __all__ = [
     "dlm_set_state", "dlm_get_info", "dlm_step_timed", "dlm_calculate_static", "dlm_destroy", "dlm_last_error",
     "dlm_get_options", "dlm_autotune", "Batch", "dlm_batch_create", "dlm_batch_set_options", "dlm_batch_autotune",
     "dlm_batch_step", "dlm_batch_step_timed", "dlm_batch_get_stats", "dlm_batch_solve", "dlm_batch_destroy",
+    "WarmStart", "WS_FEATURES",
 ]
+
+WS_FEATURES = 7
 
 DLM_OK, DLM_ERR_INVALID_ARG, DLM_ERR_OOM, DLM_ERR_CUDA, DLM_ERR_NUMERIC, DLM_ERR_TIMEOUT, DLM_ERR_UNSUPPORTED = range(7)
 DLM_F32, DLM_BF16 = 0, 1
@@ -49,10 +52,13 @@ class ProblemDesc(ctypes.Structure):
 class Options(ctypes.Structure):
     _fields_ = [("gap_every", ctypes.c_int32), ("precondition", ctypes.c_int32), ("mapping", ctypes.c_int32),
                 ("graph_iters", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32), ("coop_max", ctypes.c_int32),
-                ("block_threads", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("block_threads", ctypes.c_int32), ("restart", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}
+
+    def __repr__(self):
+        return f"Options({self.as_dict()})"
 
 
 class Stats(ctypes.Structure):
@@ -99,8 +105,17 @@ _SIGS = {
     "dlm_batch_step_timed": [_vp, _i64, ctypes.POINTER(_d), ctypes.POINTER(_d), ctypes.POINTER(_d)],
     "dlm_batch_get_stats": [_vp, ctypes.POINTER(Stats)],
     "dlm_batch_solve": [_vp, _d, _i64, ctypes.POINTER(Stats)],
+    "dlm_ws_create": [_i32, ctypes.c_uint64, _vp, ctypes.POINTER(_vp)],
+    "dlm_ws_num_params": [_vp, ctypes.POINTER(_i64)],
+    "dlm_ws_get_params": [_vp, _vp, _vp, _vp],
+    "dlm_ws_set_params": [_vp, _vp, _vp, _vp],
+    "dlm_ws_features": [_vp, _vp, _d, _vp],
+    "dlm_ws_fit_normalizer": [_vp, _vp, _i64],
+    "dlm_ws_loss_grad": [_vp, _vp, _vp, _i64, ctypes.POINTER(_d), _vp],
+    "dlm_ws_train": [_vp, _vp, _vp, _i64, _i32, ctypes.c_float, _vp],
+    "dlm_ws_predict": [_vp, _vp, _i64, _vp],
 }
-_VOID = {"dlm_destroy": [_vp], "dlm_batch_destroy": [_vp]}
+_VOID = {"dlm_destroy": [_vp], "dlm_batch_destroy": [_vp], "dlm_ws_destroy": [_vp]}
 EXPORTS = list(_SIGS) + list(_VOID) + ["dlm_last_error"]
 
 
@@ -309,10 +324,12 @@ def dlm_batch_destroy(bt):
         load().dlm_batch_destroy(bt)
 
 
-def _options(gap_every=0, precondition=False, mapping=0, graph_iters=0, ctas_per_sm=0, coop_max=0, block_threads=0):
+def _options(gap_every=0, precondition=False, mapping=0, graph_iters=0, ctas_per_sm=0, coop_max=0, block_threads=0,
+             restart=False):
     o = Options()
     o.gap_every, o.precondition, o.mapping = gap_every, int(bool(precondition)), mapping
     o.graph_iters, o.ctas_per_sm, o.coop_max, o.block_threads = graph_iters, ctas_per_sm, coop_max, block_threads
+    o.restart = int(bool(restart))
     return o
 
 
@@ -366,9 +383,9 @@ class Solver:
         dlm_set_schedule(self.h, gamma0, gamma0 if gamma_end is None else gamma_end, factor, iters_per_stage)
 
     def set_options(self, gap_every=0, precondition=False, mapping=0, graph_iters=0, ctas_per_sm=0, coop_max=0,
-                    block_threads=0):
+                    block_threads=0, restart=False):
         dlm_set_options(self.h, _options(gap_every, precondition, mapping, graph_iters, ctas_per_sm, coop_max,
-                                         block_threads))
+                                         block_threads, restart))
 
     def options(self) -> Options:
         return dlm_get_options(self.h)
@@ -469,3 +486,103 @@ class Batch:
 
     def solve(self, target_rel_gap, max_iters):
         return dlm_batch_solve(self.bt, len(self.members), target_rel_gap, max_iters)
+
+
+class WarmStart:
+    """The learned warm start (a three-layer perceptron on per-item
+    features, trained and evaluated by the library's tensor-core kernels).
+    Arrays are CUDA tensors; parameters come back as numpy float32."""
+
+    def __init__(self, width=128, seed=0, stream=None):
+        import torch
+
+        self._torch = torch
+        self.device = torch.device("cuda", torch.cuda.current_device())
+        if stream is None:
+            stream = torch.cuda.current_stream(self.device)
+        self.stream = stream
+        self.width = int(width)
+        h = ctypes.c_void_p()
+        _call("dlm_ws_create", self.width, seed, ctypes.c_void_p(stream.cuda_stream), ctypes.byref(h))
+        self.h = h
+        n = ctypes.c_int64()
+        _call("dlm_ws_num_params", self.h, ctypes.byref(n))
+        self.num_params = n.value
+
+    def close(self):
+        if getattr(self, "h", None):
+            load().dlm_ws_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @staticmethod
+    def features(solver, lam_prev, gamma):
+        """Feature rows [num_items, 7] (CUDA float32) of a Solver's instance."""
+        t = solver._torch
+        X = t.empty((solver.num_items, WS_FEATURES), dtype=t.float32, device=solver.device)
+        _call("dlm_ws_features", solver.h, _ptr(lam_prev), float(gamma), _ptr(X))
+        return X
+
+    def params(self):
+        import numpy as np
+
+        th = np.empty(self.num_params, dtype=np.float32)
+        mu = np.empty(WS_FEATURES, dtype=np.float32)
+        sd = np.empty(WS_FEATURES, dtype=np.float32)
+        _call("dlm_ws_get_params", self.h, _ptr(th), _ptr(mu), _ptr(sd))
+        return th, mu, sd
+
+    def set_params(self, theta=None, mu=None, sd=None):
+        import numpy as np
+
+        f = lambda v: None if v is None else np.ascontiguousarray(v, dtype=np.float32)
+        th, m, s = f(theta), f(mu), f(sd)
+        _call("dlm_ws_set_params", self.h, _ptr(th), _ptr(m), _ptr(s))
+
+    def fit_normalizer(self, X):
+        _call("dlm_ws_fit_normalizer", self.h, _ptr(X), int(X.shape[0]))
+
+    def loss_grad(self, X, y):
+        import numpy as np
+
+        loss = ctypes.c_double()
+        g = np.empty(self.num_params, dtype=np.float32)
+        _call("dlm_ws_loss_grad", self.h, _ptr(X), _ptr(y), int(X.shape[0]), ctypes.byref(loss), _ptr(g))
+        return loss.value, g
+
+    def train(self, X, y, steps, lr):
+        import numpy as np
+
+        losses = np.empty(max(int(steps), 1), dtype=np.float32)
+        _call("dlm_ws_train", self.h, _ptr(X), _ptr(y), int(X.shape[0]), int(steps), float(lr), _ptr(losses))
+        return losses[:steps]
+
+    def predict(self, X):
+        t = self._torch
+        out = t.empty(X.shape[0], dtype=t.float32, device=X.device)
+        _call("dlm_ws_predict", self.h, _ptr(X), int(X.shape[0]), _ptr(out))
+        return out
+
+    def unpack(self, theta):
+        """Split a flat parameter vector into the named tensors (numpy)."""
+        F, H = WS_FEATURES, self.width
+        o = 0
+        out = {}
+        for name, shape in (("W1", (F, H)), ("b1", (H,)), ("W2", (H, H)), ("b2", (H,)), ("w3", (H,)), ("b3", (1,))):
+            n = 1
+            for d in shape:
+                n *= d
+            out[name] = theta[o:o + n].reshape(shape)
+            o += n
+        return out
+
+    def pack(self, P):
+        import numpy as np
+
+        return np.concatenate([np.asarray(P[k], dtype=np.float32).ravel() for k in ("W1", "b1", "W2", "b2", "w3",
+                                                                                   "b3")])

@@ -374,6 +374,7 @@ dlm_status write_tables(Runner& R) {
     u.inv_scaleG = std::ldexp(1.0, -p->sG);
     u.J = static_cast<int32_t>(p->J);
     u.precondition = p->opt.precondition ? 1 : 0;
+    u.adaptive_restart = p->opt.restart ? 1 : 0;
     up[i] = u;
     st[i] = base_stats(p, R, i);
     st[i].lam = p->lam;
@@ -718,7 +719,8 @@ dlm_status check_options(const dlm_options* opt) {
   if (!opt) return fail(DLM_ERR_INVALID_ARG, "null options");
   if (opt->gap_every < 0 || opt->graph_iters < 0 || opt->mapping < 0 || opt->mapping > 3 || opt->ctas_per_sm < 0 ||
       opt->ctas_per_sm > 4 || opt->coop_max < 0 || opt->coop_max > 33 ||
-      (opt->block_threads != 0 && opt->block_threads != 512 && opt->block_threads != 1024))
+      (opt->block_threads != 0 && opt->block_threads != 512 && opt->block_threads != 1024) || opt->restart < 0 ||
+      opt->restart > 1)
     return fail(DLM_ERR_INVALID_ARG, "bad option value");
   return DLM_OK;
 }
@@ -1129,6 +1131,39 @@ dlm_status dlm_get_info(dlm_problem* p, int64_t* num_users, int64_t* num_items, 
 
 void dlm_destroy(dlm_problem* p) { free_problem(p); }
 
+dlm_status dlm_ws_features(dlm_problem* p, const float* lam_prev, double gamma, float* X) {
+  if (!p || !lam_prev || !X) return fail(DLM_ERR_INVALID_ARG, "null argument");
+  if (!(gamma > 0) || !std::isfinite(gamma)) return fail(DLM_ERR_INVALID_ARG, "gamma must be > 0");
+  float* grad = nullptr;
+  unsigned* deg = nullptr;
+  int* mx = nullptr;
+  unsigned long long* sum = nullptr;
+  auto release = [&]() {
+    cudaFree(grad);
+    cudaFree(deg);
+    cudaFree(mx);
+    cudaFree(sum);
+  };
+  if (dalloc(&grad, p->J) != cudaSuccess || dalloc(&deg, p->J) != cudaSuccess || dalloc(&mx, p->J) != cudaSuccess ||
+      dalloc(&sum, p->J) != cudaSuccess) {
+    release();
+    return fail(DLM_ERR_OOM, "device allocation failed");
+  }
+  double g = 0;
+  dlm_status st = dlm_calculate(p, lam_prev, gamma, &g, grad, nullptr);
+  if (st == DLM_OK) {
+    const double bound = static_cast<double>(p->lay.max_item_deg > 0 ? p->lay.max_item_deg : 1) *
+                         (p->lay.max_abs_c > 0 ? p->lay.max_abs_c : 1.0);
+    const double scale = std::ldexp(1.0, fixed_point_shift(bound));
+    cudaError_t e = launch_item_features(p->lay.col, p->lay.ca, p->bf16, p->lay.padded_nnz, static_cast<int>(p->J),
+                                         scale, p->b, lam_prev, gamma, grad, X, deg, mx, sum, p->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(p->stream);
+    if (e != cudaSuccess) st = fail(DLM_ERR_CUDA, std::string("item features: ") + cudaGetErrorString(e));
+  }
+  release();
+  return st;
+}
+
 // ---------------------------------------------------------------------------
 // Batches
 // ---------------------------------------------------------------------------
@@ -1175,6 +1210,7 @@ dlm_status dlm_batch_create(dlm_problem* const* probs, int32_t n, void* stream, 
   dlm_options o = probs[0]->opt;
   o.mapping = 0;
   o.precondition = 0;  // per member, not a batch option
+  o.restart = 0;
   bt->opt = o;
   dlm_status st = runner_configure(R, o, true);
   if (st != DLM_OK) {

@@ -44,6 +44,7 @@ struct UpdInst {
   double inv_scaleG;        // 2^-sG
   int32_t J;
   int32_t precondition;
+  int32_t adaptive_restart;
 };
 
 // Per-instance view for the sweep kernels (device memory; one table for the
@@ -123,6 +124,11 @@ cudaError_t sweep_prepare(bool bf16);  // raises the dynamic shared-memory limit
 cudaError_t launch_sweep(const SweepLaunch& L, bool stats, bool bf16);
 cudaError_t launch_update(const UpdInst* dev_tab, int ninst, cudaStream_t s);
 cudaError_t launch_stats(const StatsInst* dev_tab, int ninst, cudaStream_t s);
+
+// warmstart.cu: per-item features from the laid-out edges (scratch: J each).
+cudaError_t launch_item_features(const int32_t* col, const void* ca, bool bf, int64_t padded, int J, double scale,
+                                 const double* b, const float* lam_prev, double gamma, const float* grad, float* X,
+                                 unsigned* deg, int* mx, unsigned long long* sum, cudaStream_t s);
 
 // layout.cu
 struct LayoutOut {

@@ -50,26 +50,50 @@ __device__ double block_max(double v, double* sh) {
 //                                         or gamma / n_j (row normalization)
 //   theta+ = (1 + sqrt(1 + 4 theta^2)) / 2,  y+ = lam+ + (theta - 1)/theta+ (lam+ - lam)
 // and, when iteration t+1 starts a stage with a different gamma, a momentum
-// restart (theta = 1, y+ = lam+).  lam and y are FP32; G is formed from the
-// exact fixed-point sum minus b and rounded once to FP32.
+// restart (theta = 1, y+ = lam+).  With adaptive restart on, the momentum also
+// restarts when the step just taken points against the momentum in the
+// step metric: sum_j (lam+_j - y_j) (lam+_j - lam_j) / step_j < 0 (the
+// gradient-mapping test of O'Donoghue & Candes 2015, for ascent).  lam and y
+// are FP32; G is formed from the exact fixed-point sum minus b and rounded
+// once to FP32; the restart test sums in FP64 in a fixed order.
 __global__ void __launch_bounds__(kUpdThreads) fista_update_kernel(const UpdInst* __restrict__ tab) {
   __shared__ double sh[32];
+  __shared__ int s_restart;
   const UpdInst U = tab[blockIdx.x];
   const DevState st = *U.state;
   const double gamma = st.gamma;
   const int64_t t1 = st.iter + 1;
   const int64_t s1 = t1 / U.iters_per_stage;
   const double gamma1 = U.gamma_tab[s1 < kMaxStages ? s1 : kMaxStages - 1];
-  const bool restart = gamma1 != gamma;
+  const bool stage_restart = gamma1 != gamma;
   const double th1 = 0.5 * (1.0 + sqrt(1.0 + 4.0 * st.theta * st.theta));
   const float beta = static_cast<float>((st.theta - 1.0) / th1);
   const float step0 = static_cast<float>(gamma * U.inv_nmax);
+  auto lam_next = [&](int j, float& step, float& yj) {
+    const float G = static_cast<float>(to_real(U.acc[j], U.inv_scaleG) - U.b[j]);
+    step = U.precondition ? static_cast<float>(gamma * U.inv_n2[j]) : step0;
+    yj = U.y[j];
+    return fmaxf(0.f, fmaf(step, G, yj));
+  };
+  bool restart = stage_restart;
+  if (U.adaptive_restart && !stage_restart) {
+    double dot = 0.0;
+    for (int j = threadIdx.x; j < U.J; j += blockDim.x) {
+      float step, yj;
+      const float ln = lam_next(j, step, yj);
+      if (step > 0.f)
+        dot += (static_cast<double>(ln) - yj) * (static_cast<double>(ln) - U.lam[j]) / static_cast<double>(step);
+    }
+    dot = block_sum(dot, sh);
+    if (threadIdx.x == 0) s_restart = dot < 0.0;
+    __syncthreads();
+    restart = s_restart != 0;
+  }
   double bad = 0.0;
   for (int j = threadIdx.x; j < U.J; j += blockDim.x) {
     const float G = static_cast<float>(to_real(U.acc[j], U.inv_scaleG) - U.b[j]);
-    const float step = U.precondition ? static_cast<float>(gamma * U.inv_n2[j]) : step0;
-    const float yj = U.y[j];
-    const float ln = fmaxf(0.f, fmaf(step, G, yj));
+    float step, yj;
+    const float ln = lam_next(j, step, yj);
     const float yn = restart ? ln : fmaf(beta, ln - U.lam[j], ln);
     U.lam[j] = ln;
     U.y[j] = yn;

@@ -112,6 +112,31 @@ def test_trajectory_with_continuation(dlm_lib, precondition):
     s.close()
 
 
+@pytest.mark.parametrize("name,gamma", [("tiny", 1e-2), ("mixed", 1e-3)])
+def test_trajectory_with_adaptive_restart(dlm_lib, name, gamma):
+    # Fixed gamma, row normalization and the adaptive momentum restart.  The
+    # restart test is a sign decision on an FP64 sum; both sides make it in
+    # FP64 on their own (FP32 and FP64) iterates, so the trajectories agree
+    # to the FP32 tolerance while no decision sits within rounding of zero.
+    inst = tiny_instance() if name == "tiny" else mixed_instance(seed=6, I=3000, J=300)
+    s = solver_for(dlm_lib, inst)
+    s.set_schedule(gamma)
+    s.set_options(precondition=True, restart=True)
+    T = 300
+    s.step(T)
+    lam = s.lam().cpu().numpy().astype(np.float64)
+    p = oracle_problem(inst)
+    ref = oracle.fista(p, T, gamma, precondition=True, restart=True, trajectory=False)
+    _, _, st = s.get_state()
+    assert st.theta == pytest.approx(ref["theta"], rel=1e-12)  # the same restarts fired
+    err = np.abs(lam - ref["lam"]).max()
+    # FP32 lam/y rounding (2^-24 per step) compounds through the momentum over
+    # T = 300 steps; at gamma = 1e-3 (the smallest step) this reaches ~3e-5
+    # relative, so the bound is 5e-5 here.
+    assert err <= 5e-5 * max(np.abs(ref["lam"]).max(), 1e-6), f"max err {err:.3e}"
+    s.close()
+
+
 def test_certificate_matches_oracle(dlm_lib):
     inst = mixed_instance(seed=8, I=3000, J=400)
     s = solver_for(dlm_lib, inst)

@@ -82,11 +82,12 @@ def tiny_problem(seed, I=3, J=2, b_scale=0.6):
 
 @pytest.mark.parametrize("seed", [1, 2, 3, 4])
 @pytest.mark.parametrize("precondition", [False, True])
-def test_converged_fista_matches_active_set_enumeration(seed, precondition):
+@pytest.mark.parametrize("restart", [False, True])
+def test_converged_fista_matches_active_set_enumeration(seed, precondition, restart):
     p = tiny_problem(seed, b_scale=[0.6, 0.3, 6.0, 0.9][seed - 1])
     gamma = 0.1
     x_ref, lam_ref = solve_by_active_sets(p, gamma)
-    out = oracle.fista(p, 30000, gamma, precondition=precondition, trajectory=False)
+    out = oracle.fista(p, 30000, gamma, precondition=precondition, trajectory=False, restart=restart)
     np.testing.assert_allclose(out["lam"], lam_ref, atol=1e-9)
     g, grad, x = oracle.dual(p, out["lam"], gamma)
     np.testing.assert_allclose(x, x_ref, atol=1e-9)
@@ -211,3 +212,19 @@ def test_row_normalisation_equals_plain_method_on_scaled_rows():
     plain = oracle.fista(ps, 200, 0.05, precondition=False)
     np.testing.assert_allclose(pre["lam"], plain["lam"] * d, rtol=1e-9, atol=1e-12)
     np.testing.assert_allclose(pre["g_traj"], plain["g_traj"], rtol=1e-11)
+
+
+def test_adaptive_restart_fires_on_overshoot():
+    """One item, one user, a = 1: the dual is a concave scalar function, so the
+    accelerated iteration started far above the optimum overshoots it; the
+    restart resets the momentum (theta back to 1) the first time a step opposes
+    it, and without the restart theta keeps growing."""
+    p = oracle.Problem(np.array([0, 1]), np.array([0], dtype=np.int32), np.array([-1.0]), np.array([1.0]),
+                       np.array([0.3]), 1)
+    gamma = 0.5
+    # optimum: x = 0.3 binding, -(c + lam)/gamma = 0.3 -> lam* = 1 - 0.15 = 0.85
+    plain = [oracle.fista(p, t, gamma, lam0=np.array([3.0]), trajectory=False) for t in range(1, 40)]
+    rst = [oracle.fista(p, t, gamma, lam0=np.array([3.0]), trajectory=False, restart=True) for t in range(1, 40)]
+    assert all(plain[k + 1]["theta"] > plain[k]["theta"] for k in range(len(plain) - 1))
+    assert any(r["theta"] == 1.0 for r in rst[2:])
+    assert abs(rst[-1]["lam"][0] - 0.85) < 1e-9 and abs(plain[-1]["lam"][0] - 0.85) < 1e-3

@@ -359,6 +359,11 @@ def main():
     ap.add_argument("--ref-step-seconds", type=float, default=6.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-error-statement", action="store_true")
+    ap.add_argument("--no-time-to-gap", action="store_true", help="skip the recurring-instance time-to-gap run")
+    ap.add_argument("--ttg-users", type=int, default=5_000_000)
+    ap.add_argument("--ttg-items", type=int, default=1_000)
+    ap.add_argument("--ttg-gamma", type=float, default=1e-3)
+    ap.add_argument("--ttg-only", action="store_true", help="print only the time-to-gap object (development)")
     args = ap.parse_args()
 
     rank = int(os.environ.get("RANK", "0"))
@@ -394,6 +399,9 @@ def main():
 
     if args.workload == "batched":
         return run_batched(args, dlm, torch, dev, rank, world, barrier, max_over_ranks, dist)
+    if args.ttg_only:
+        print(json.dumps(time_to_gap(args, dlm, torch, dev)), flush=True)
+        return 0
 
     w = WORKLOADS[args.workload]
     bf16 = w["bf16"]
@@ -507,6 +515,10 @@ def main():
                "sample": (f"{'all' if args.workload == 'tiny' else f'{args.cpu_frac:.0%} seeded user sample'} of "
                           f"the workload ({p.I} users, {p.nnz} nnz), {iters} FP64 oracle iterations in {dt:.1f} s")}
 
+    ttg = None
+    if rank == 0 and not args.no_time_to_gap and args.workload == "precision":
+        ttg = time_to_gap(args, dlm, torch, dev)
+
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": elapsed_s * 1000.0 / args.steps, "higher_is_better": True, "scaling": "weak",
@@ -524,6 +536,7 @@ def main():
         "clocks": clocks,
         "graph_ms_per_step": graph_ms_per_step,
         "bf16_error": bf16_err,
+        "time_to_gap": ttg,
         "setup_s": {"generate": t_gen, "upload_and_create": t_setup},
     }
     if rank == 0:
@@ -531,6 +544,119 @@ def main():
     if dist is not None:
         dist.destroy_process_group()
     return 0
+
+
+def time_to_gap(args, dlm, torch, dev):
+    """Recurring daily instances (users x items of the daily recipe; day t
+    from day t-1: 10% of edges' c perturbed by N(0, 0.02), b_j scaled by
+    1 + N(0, 0.05), 2% of users churned).  Days 0-20 are solved to a 1e-6
+    certified gap for labels; the warm-start network trains on days 1-20;
+    on days 21-30 each start is driven to a 1e-4 certified gap at the final
+    gamma and timed end to end (features and prediction included):
+      fp32_cold     FP32 values, lam = 0, gamma continuation 1e-1 -> gamma_end
+                    halved every 50 iterations (the plain method)
+      bf16_cold     the same on BF16 values
+      fp32_prev     FP32, previous day's dual, fixed gamma_end, adaptive restart
+      fp32_learned  FP32, the network's prediction, fixed gamma_end, adaptive restart
+      bf16_learned  BF16 values + the network's prediction (the headline)
+    All forms use row normalization and check the gap every 25 iterations."""
+    import numpy as np
+    import synth
+
+    g_end, I, J = args.ttg_gamma, args.ttg_users, args.ttg_items
+    n_days, n_train, gap_every = 30, 20, 25
+    t_all = time.perf_counter()
+    inst = synth.generate(synth.recipe_daily(I=I, J=J, seed=1004), nthreads=args.threads)
+
+    def make(inst, bf16):
+        if bf16:
+            c = torch.from_numpy(synth.round_bf16(inst.c, args.threads).view(np.int16)).to(dev).view(torch.bfloat16)
+            a = torch.from_numpy(synth.round_bf16(inst.a, args.threads).view(np.int16)).to(dev).view(torch.bfloat16)
+        else:
+            c, a = torch.from_numpy(inst.c).to(dev), torch.from_numpy(inst.a).to(dev)
+        rp, col = torch.from_numpy(inst.row_ptr).to(dev), torch.from_numpy(inst.col).to(dev)
+        b = torch.from_numpy(inst.b).to(dev)
+        s = dlm.Solver(rp, col, c, a, b, inst.J, bf16=bf16)
+        del rp, col, c, a, b
+        return s
+
+    peak, _ = load_peaks()
+    modes = ["fp32_cold", "bf16_cold", "fp32_prev", "fp32_learned", "bf16_learned"]
+    res = {m: {"seconds": [], "iters": [], "gap": [], "roofline_frac": []} for m in modes}
+    labels, feats = {}, {}
+    label_gap, label_iters = [], []
+    ws, train = None, None
+    zeros = torch.zeros(J, dtype=torch.float32, device=dev)
+    for d in range(n_days + 1):
+        if d > 0:
+            inst = synth.next_day(inst, d, seed=1004, nthreads=args.threads)
+        s32 = make(inst, False)
+        bytes32 = s32.info()["bytes_per_iter"]
+        if d > n_train:
+            s16 = make(inst, True)
+            bytes16 = s16.info()["bytes_per_iter"]
+            for m in modes:
+                s, nbytes = (s16, bytes16) if m.startswith("bf16") else (s32, bytes32)
+                torch.cuda.synchronize(dev)
+                t0 = time.perf_counter()
+                if m.endswith("cold"):
+                    s.set_options(precondition=True, gap_every=gap_every)
+                    s.set_lambda(zeros)
+                    s.set_schedule(1e-1, g_end, 0.5, 50)
+                else:
+                    s.set_options(precondition=True, gap_every=gap_every, restart=True)
+                    s.set_schedule(g_end)
+                    if m.endswith("prev"):
+                        s.set_lambda(labels[d - 1])
+                    else:
+                        s.set_lambda(ws.predict(dlm.WarmStart.features(s, labels[d - 1], g_end)))
+                st = s.solve(1e-4, 100_000)
+                torch.cuda.synchronize(dev)
+                dt = time.perf_counter() - t0
+                sweeps = st.iter + st.iter // gap_every + 1 + (0 if m.endswith("cold") or m.endswith("prev") else 1)
+                res[m]["seconds"].append(dt)
+                res[m]["iters"].append(int(st.iter))
+                res[m]["gap"].append(float(st.rel_gap))
+                res[m]["roofline_frac"].append(sweeps * nbytes / dt / 1e9 / peak)
+            s16.close()
+        # label: the day solved to 1e-6 from the previous day's dual
+        if d == 0:
+            s32.set_options(precondition=True, gap_every=50, restart=True)
+            s32.set_schedule(1e-1, g_end, 0.5, 50)
+        else:
+            s32.set_options(precondition=True, gap_every=50, restart=True)
+            s32.set_schedule(g_end)
+            s32.set_lambda(labels[d - 1])
+            if d <= n_train:
+                feats[d] = dlm.WarmStart.features(s32, labels[d - 1], g_end)
+        st = s32.solve(1e-5, 8_000)
+        label_gap.append(float(st.rel_gap))
+        label_iters.append(int(st.iter))
+        labels[d] = s32.lam()
+        s32.close()
+        if d == n_train:
+            X = torch.cat([feats[k] for k in range(1, n_train + 1)])
+            y = torch.cat([labels[k] for k in range(1, n_train + 1)])
+            ws = dlm.WarmStart(128, 1)
+            t0 = time.perf_counter()
+            losses = ws.train(X, y, 300, 1e-3)
+            train = {"rows": int(X.shape[0]), "steps": 300, "lr": 1e-3, "loss_first": float(losses[0]),
+                     "loss_last": float(losses[-1]), "seconds": time.perf_counter() - t0}
+    out = {"workload": f"recurring daily instances: {I:,} users x {J:,} items (~{I * 25 / 1e6:.0f}M nnz), "
+                       f"30 days, train days 1-20, evaluate days 21-30",
+           "gamma_end": g_end, "target_rel_gap": 1e-4, "gap_every": gap_every, "train": train,
+           "labels": {"target": 1e-5, "max_iters": 8000, "worst_gap": max(label_gap),
+                      "mean_iters": float(np.mean(label_iters))},
+           "modes": {m: {"mean_s": float(np.mean(v["seconds"])), "mean_iters": float(np.mean(v["iters"])),
+                         "mean_roofline_frac": float(np.mean(v["roofline_frac"])), "per_day_s": v["seconds"],
+                         "per_day_iters": v["iters"], "max_gap": max(v["gap"])} for m, v in res.items()},
+           "seconds_total": time.perf_counter() - t_all}
+    out["headline_speedup_bf16_learned_vs_fp32_cold"] = out["modes"]["fp32_cold"]["mean_s"] / \
+        out["modes"]["bf16_learned"]["mean_s"]
+    out["learned_vs_prev_iters"] = out["modes"]["fp32_learned"]["mean_iters"] / out["modes"]["fp32_prev"]["mean_iters"]
+    if ws is not None:
+        ws.close()
+    return out
 
 
 def run_batched(args, dlm, torch, dev, rank, world, barrier, max_over_ranks, dist):

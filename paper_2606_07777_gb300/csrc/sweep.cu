@@ -17,17 +17,20 @@
 // Simplex projection (Sec. 4.3 gets the threshold by sorting the whole row;
 // no sort here).  In u-space the threshold tau solves
 // sum max(u - tau, 0) = gamma z.  One pass over the row keeps its four
-// largest u in a sorted register network; the sort-based rule applied to
-// those four either fixes the active set (at most three edges active: the
-// common case, and for one edge x = z on it exactly) or shows that at least
-// four are active, and then the lane runs the iteration
+// largest u in a sorted register network, with the positions of the first
+// three; the sort-based rule applied to those four either fixes the active
+// set (at most three edges active: nearly every row at the paper's gammas,
+// and for one edge x = z on it exactly) or shows that at least four are
+// active.  With at most three, the threshold is recomputed over the recorded
+// edges in float-pair arithmetic, so that x = (u - tau) / gamma keeps full
+// FP32 relative accuracy when u and tau nearly cancel, and x is deposited on
+// them: no second pass over the row.  With four or more the lane (or the
+// whole warp, when few lanes need it) runs the iteration
 // tau <- (sum_{u > tau} u - gamma z) / #{u > tau} from tau_4 (Michelot 1986;
-// monotone from below, it stops when the active set stops changing).  A
-// second pass recomputes tau over the active set in float-pair arithmetic, so
-// that x = (u - tau) / gamma keeps full FP32 relative accuracy when u and tau
-// nearly cancel, and records where the active edges are; x is then deposited
-// from those positions.  The inequality simplex takes max(tau, 0) (the early
-// exit of Sec. 4.3).  Box: x = clip(u / gamma, 0, z).
+// monotone from below, it stops when the active set stops changing), the
+// pair-arithmetic refinement and a deposit pass.  The inequality simplex
+// takes max(tau, 0) (the early exit of Sec. 4.3).  Box: x = clip(u / gamma,
+// 0, z).
 //
 // Determinism: item sums are 64-bit fixed point (value * 2^s rounded, s chosen
 // at set-up so no sum can overflow), exact and order independent; slices are
@@ -239,25 +242,33 @@ __device__ __forceinline__ void coop_user(const Seg& S, const float* __restrict_
   }
 }
 
-// Sorted insertion of u into the four largest values seen (v0 >= ... >= v3).
-__device__ __forceinline__ void top4_insert(float u, float& v0, float& v1, float& v2, float& v3) {
-  float t = u;
-  const float n0 = fmaxf(v0, t);
-  t = fminf(v0, t);
-  const float n1 = fmaxf(v1, t);
-  t = fminf(v1, t);
-  const float n2 = fmaxf(v2, t);
-  t = fminf(v2, t);
-  v3 = fmaxf(v3, t);
-  v0 = n0;
-  v1 = n1;
-  v2 = n2;
+// Sorted insertion of edge k with value u into the four largest values seen
+// (v0 >= ... >= v3), keeping the edge positions of the first three (i0..i2).
+// Strict comparisons: among equal values the earlier edge ranks first.
+__device__ __forceinline__ void top4_insert(float u, int k, float& v0, float& v1, float& v2, float& v3, int& i0,
+                                            int& i1, int& i2) {
+  const bool c0 = u > v0;
+  const float t1 = c0 ? v0 : u;
+  const int k1 = c0 ? i0 : k;
+  v0 = c0 ? u : v0;
+  i0 = c0 ? k : i0;
+  const bool c1 = t1 > v1;
+  const float t2 = c1 ? v1 : t1;
+  const int k2 = c1 ? i1 : k1;
+  v1 = c1 ? t1 : v1;
+  i1 = c1 ? k1 : i1;
+  const bool c2 = t2 > v2;
+  const float t3 = c2 ? v2 : t2;
+  v2 = c2 ? t2 : v2;
+  i2 = c2 ? k2 : i2;
+  v3 = fmaxf(v3, t3);
 }
 
-// Users of a slice that need a threshold (modes 2 and 3 below) are handled by
-// the whole warp, one after another, unless at least coop_max of the 32 do
-// (then each lane runs its own user, which keeps the lanes busy).  coop_max is
-// a tuning parameter (0: always per lane, 33: always cooperative).
+// Users of a slice whose active set is larger than the four tracked values
+// (mode 3 below) are handled by the whole warp, one after another, unless at
+// least coop_max of the 32 need it (then each lane runs its own user, which
+// keeps the lanes busy).  coop_max is a tuning parameter (0: always per lane,
+// 33: always cooperative).
 
 // One slice: lane t = user t; edge k of lane t is element sell_el(k, t, w/4)
 // of the slice.
@@ -274,10 +285,10 @@ __device__ __forceinline__ void do_slice(const InstDesc& D, const Seg& S, const 
   const bool box = S.kind == DLM_BOX;
   const bool eq = S.kind == DLM_SIMPLEX_EQ;
 
-  // Pass A: the row's four largest u (v0 >= v1 >= v2 >= v3) and the edge k1
-  // of the largest.
+  // Pass A: the row's four largest u (v0 >= v1 >= v2 >= v3) and the
+  // positions i0, i1, i2 of the first three.
   float v0 = -INFINITY, v1 = -INFINITY, v2 = -INFINITY, v3 = -INFINITY;
-  int k1 = 0;
+  int i0 = 0, i1 = 0, i2 = 0;
 #pragma unroll 4
   for (int g = 0; g < w4; ++g) {
     const int q = 32 * g + lane;
@@ -288,8 +299,7 @@ __device__ __forceinline__ void do_slice(const InstDesc& D, const Seg& S, const 
 #pragma unroll
     for (int e = 0; e < 4; ++e) {
       const float u = -fmaf(a[e], ys[jj[e]], c[e]);
-      k1 = (u > v0) ? 4 * g + e : k1;
-      top4_insert(u, v0, v1, v2, v3);
+      top4_insert(u, 4 * g + e, v0, v1, v2, v3, i0, i1, i2);
     }
   }
   for (int k = 4 * w4; k < w; ++k) {
@@ -298,8 +308,7 @@ __device__ __forceinline__ void do_slice(const InstDesc& D, const Seg& S, const 
     float c, a;
     P::get(__ldg(ca0 + el), c, a);
     const float u = -fmaf(a, ys[j], c);
-    k1 = (u > v0) ? k : k1;
-    top4_insert(u, v0, v1, v2, v3);
+    top4_insert(u, k, v0, v1, v2, v3, i0, i1, i2);
   }
 
   // The equality threshold solves sum_k max(u_k - tau, 0) = gamma z.  With
@@ -312,13 +321,14 @@ __device__ __forceinline__ void do_slice(const InstDesc& D, const Seg& S, const 
   int mode;
   float tau = 0.f, taul = 0.f;
   bool zero = box;
+  int r = 0;
   if (box) {
-    mode = (v0 > 0.f) ? 2 : 0;
+    mode = (v0 > 0.f) ? 3 : 0;
   } else if (v0 == -INFINITY || (!eq && v0 <= 0.f)) {
     mode = 0;
   } else {
     float sm = v0;
-    int r = 1;
+    r = 1;
     tau = v0 - S.gz;
     if (v1 > tau) {
       sm += v1;
@@ -339,131 +349,136 @@ __device__ __forceinline__ void do_slice(const InstDesc& D, const Seg& S, const 
   }
 
   float ob = 0.f;
-  const unsigned mask2 = __ballot_sync(kFull, mode >= 2);
-  const bool coop = mask2 != 0u && __popc(mask2) < coop_max;  // warp-uniform
+  if (mode == 2) {
+    // The active set is the r <= 3 recorded edges (on the inequality simplex
+    // with tau <= 0: those of them with u > 0).  Threshold over them in pair
+    // arithmetic, then x on each.
+    zero = !eq && tau <= 0.f;
+    if (!zero) {
+      F2 sum{0.f, 0.f};
+      for (int i = 0; i < r; ++i) {
+        const int el = sell_el(i == 0 ? i0 : (i == 1 ? i1 : i2), lane, w4);
+        const int j = __ldg(col0 + el);
+        float c, a;
+        P::get(__ldg(ca0 + el), c, a);
+        sum = f2_add(sum, u_pair(c, a, ys[j]));
+      }
+      const F2 t2 = f2_threshold(sum, S.gz, S.gzl, r);
+      if (!eq && t2.h + t2.l <= 0.f) {
+        zero = true;
+      } else {
+        tau = t2.h;
+        taul = t2.l;
+      }
+    }
+    if (zero) tau = taul = 0.f;
+    for (int i = 0; i < r; ++i) {
+      const int el = sell_el(i == 0 ? i0 : (i == 1 ? i1 : i2), lane, w4);
+      const int j = __ldg(col0 + el);
+      float c, a;
+      P::get(__ldg(ca0 + el), c, a);
+      const float x = x_general(S, false, zero, tau, taul, c, a, ys[j]);
+      if (x > 0.f) deposit<STATS>(S, j, c, a, x, accG, accC, accQ, ob);
+    }
+  } else if (mode == 1) {
+    const int el = sell_el(i0, lane, w4);
+    const int j = __ldg(col0 + el);
+    float c, a;
+    P::get(__ldg(ca0 + el), c, a);
+    deposit<STATS>(S, j, c, a, S.z, accG, accC, accQ, ob);
+  }
+
+  // Mode 3 (four or more active edges, or the box): the whole warp per user
+  // while few lanes need it, else each lane over its own row.
+  const unsigned mask3 = __ballot_sync(kFull, mode == 3);
+  const bool coop = mask3 != 0u && __popc(mask3) < coop_max;  // warp-uniform
   if (coop) {
-    unsigned m = mask2;
+    unsigned m = mask3;
     while (m) {
       const int t = __ffs(m) - 1;
       m &= m - 1;
       const float tt = __shfl_sync(kFull, tau, t);
-      const int mt = __shfl_sync(kFull, mode, t);
       float ta, tl;
       bool zr;
-      coop_user<P, STATS>(S, ys, accG, accC, accQ, col0, ca0, w, w4, t, tt, mt == 2, ta, tl, zr, ob);
+      coop_user<P, STATS>(S, ys, accG, accC, accQ, col0, ca0, w, w4, t, tt, false, ta, tl, zr, ob);
       if (lane == t) {
         tau = ta;
         taul = tl;
         zero = zr;
       }
     }
-  }
-  if (mode >= 2 && !coop) {
-    // per-lane threshold path
-    bool full = true;  // deposit by a pass over every edge of the row
-    int s0 = 0, s1 = 0, s2 = 0;
+  } else if (mode == 3) {
     if (!box) {
-      if (mode == 3) {
-        int prevn = -1;
-        for (int it = 0; it < 256; ++it) {
-          float sm = 0.f;
-          int n = 0;
-          for (int k = 0; k < w; ++k) {
-            const int el = sell_el(k, lane, w4);
-            const int j = __ldg(col0 + el);
-            float c, a;
-            P::get(__ldg(ca0 + el), c, a);
-            const float u = -fmaf(a, ys[j], c);
-            if (u > tau) {
-              sm += u;
-              ++n;
-            }
+      // Michelot iteration from tau_4, a lower bound of the threshold
+      int prevn = -1;
+      for (int it = 0; it < 256; ++it) {
+        float sm = 0.f;
+        int n = 0;
+        for (int k = 0; k < w; ++k) {
+          const int el = sell_el(k, lane, w4);
+          const int j = __ldg(col0 + el);
+          float c, a;
+          P::get(__ldg(ca0 + el), c, a);
+          const float u = -fmaf(a, ys[j], c);
+          if (u > tau) {
+            sm += u;
+            ++n;
           }
-          if (n == prevn || n == 0) break;
-          prevn = n;
-          const float tn = __fdiv_rn(sm - S.gz, static_cast<float>(n));
-          if (tn == tau) break;
-          tau = tn;
         }
+        if (n == prevn || n == 0) break;
+        prevn = n;
+        const float tn = __fdiv_rn(sm - S.gz, static_cast<float>(n));
+        if (tn == tau) break;
+        tau = tn;
       }
       zero = !eq && tau <= 0.f;
-      // Pass B: the active edges (u > tau; u > 0 when tau <= 0 on the
-      // inequality simplex): their u in pair arithmetic, and the positions of
-      // the first three.
-      const float thr = zero ? 0.f : tau;
-      F2 sum{0.f, 0.f};
-      int n = 0;
-      auto visit = [&](int k, int j, float c, float a) {
-        if (-fmaf(a, ys[j], c) > thr) {
-          if (!zero) sum = f2_add(sum, u_pair(c, a, ys[j]));
-          if (n == 0)
-            s0 = k;
-          else if (n == 1)
-            s1 = k;
-          else if (n == 2)
-            s2 = k;
-          ++n;
-        }
-      };
-      for (int g = 0; g < w4; ++g) {
-        const int q = 32 * g + lane;
-        const int4 jv = __ldg(reinterpret_cast<const int4*>(col0) + q);
-        float c[4], a[4];
-        P::get4(ca0, q, c, a);
-        visit(4 * g, jv.x, c[0], a[0]);
-        visit(4 * g + 1, jv.y, c[1], a[1]);
-        visit(4 * g + 2, jv.z, c[2], a[2]);
-        visit(4 * g + 3, jv.w, c[3], a[3]);
-      }
-      for (int k = 4 * w4; k < w; ++k) {
-        const int el = 128 * w4 + 32 * (k - 4 * w4) + lane;
-        float c, a;
-        P::get(__ldg(ca0 + el), c, a);
-        visit(k, __ldg(col0 + el), c, a);
-      }
-      full = n > 3;
       if (!zero) {
+        // the threshold over the active set in pair arithmetic
+        F2 sum{0.f, 0.f};
+        int n = 0;
+        auto visit = [&](int j, float c, float a) {
+          if (-fmaf(a, ys[j], c) > tau) {
+            sum = f2_add(sum, u_pair(c, a, ys[j]));
+            ++n;
+          }
+        };
+        for (int g = 0; g < w4; ++g) {
+          const int q = 32 * g + lane;
+          const int4 jv = __ldg(reinterpret_cast<const int4*>(col0) + q);
+          float c[4], a[4];
+          P::get4(ca0, q, c, a);
+          visit(jv.x, c[0], a[0]);
+          visit(jv.y, c[1], a[1]);
+          visit(jv.z, c[2], a[2]);
+          visit(jv.w, c[3], a[3]);
+        }
+        for (int k = 4 * w4; k < w; ++k) {
+          const int el = 128 * w4 + 32 * (k - 4 * w4) + lane;
+          float c, a;
+          P::get(__ldg(ca0 + el), c, a);
+          visit(__ldg(col0 + el), c, a);
+        }
         const F2 t2 = f2_threshold(sum, S.gz, S.gzl, n > 0 ? n : 1);
         if (!eq && t2.h + t2.l <= 0.f) {
-          zero = true;  // the active set shrinks to u > 0: take every edge again
-          full = true;
+          zero = true;
         } else {
           tau = t2.h;
           taul = t2.l;
         }
       }
-      if (!full) {
-        // deposit from the recorded positions
-        for (int i = 0; i < n; ++i) {
-          const int el = sell_el(i == 0 ? s0 : (i == 1 ? s1 : s2), lane, w4);
-          const int j = __ldg(col0 + el);
-          float c, a;
-          P::get(__ldg(ca0 + el), c, a);
-          const float x = x_general(S, box, zero, zero ? 0.f : tau, zero ? 0.f : taul, c, a, ys[j]);
-          if (x > 0.f) deposit<STATS>(S, j, c, a, x, accG, accC, accQ, ob);
-        }
-      }
     }
     if (zero) tau = taul = 0.f;
-    if (full) {
-      // x on the active edges (u > tau; for the box and tau = 0, u > 0)
-      for (int k = 0; k < w; ++k) {
-        const int el = sell_el(k, lane, w4);
-        const int j = __ldg(col0 + el);
-        float c, a;
-        P::get(__ldg(ca0 + el), c, a);
-        if (-fmaf(a, ys[j], c) > tau) {
-          const float x = x_general(S, box, zero, tau, taul, c, a, ys[j]);
-          if (x > 0.f) deposit<STATS>(S, j, c, a, x, accG, accC, accQ, ob);
-        }
+    // x on the active edges (u > tau; for the box and tau = 0, u > 0)
+    for (int k = 0; k < w; ++k) {
+      const int el = sell_el(k, lane, w4);
+      const int j = __ldg(col0 + el);
+      float c, a;
+      P::get(__ldg(ca0 + el), c, a);
+      if (-fmaf(a, ys[j], c) > tau) {
+        const float x = x_general(S, box, zero, tau, taul, c, a, ys[j]);
+        if (x > 0.f) deposit<STATS>(S, j, c, a, x, accG, accC, accQ, ob);
       }
     }
-  } else if (mode == 1) {
-    const int el = sell_el(k1, lane, w4);
-    const int j = __ldg(col0 + el);
-    float c, a;
-    P::get(__ldg(ca0 + el), c, a);
-    deposit<STATS>(S, j, c, a, S.z, accG, accC, accQ, ob);
   }
 
   if (STATS) {
@@ -475,7 +490,7 @@ __device__ __forceinline__ void do_slice(const InstDesc& D, const Seg& S, const 
       for (int k = 0; k < d; ++k) {
         float x = 0.f;
         if (mode == 1) {
-          x = (k == k1) ? S.z : 0.f;
+          x = (k == i0) ? S.z : 0.f;
         } else if (mode >= 2) {
           const int el = sell_el(k, lane, w4);
           const int j = __ldg(col0 + el);

@@ -112,28 +112,55 @@ def test_trajectory_with_continuation(dlm_lib, precondition):
     s.close()
 
 
-@pytest.mark.parametrize("name,gamma", [("tiny", 1e-2), ("mixed", 1e-3)])
-def test_trajectory_with_adaptive_restart(dlm_lib, name, gamma):
-    # Fixed gamma, row normalization and the adaptive momentum restart.  The
-    # restart test is a sign decision on an FP64 sum; both sides make it in
-    # FP64 on their own (FP32 and FP64) iterates, so the trajectories agree
-    # to the FP32 tolerance while no decision sits within rounding of zero.
-    inst = tiny_instance() if name == "tiny" else mixed_instance(seed=6, I=3000, J=300)
+def test_trajectory_with_adaptive_restart(dlm_lib):
+    # Fixed gamma, row normalization and the adaptive momentum restart on the
+    # 10,000 x 100 instance.  The restart test is a sign decision on an FP64
+    # sum that both sides make on their own (FP32 and FP64) iterates; here no
+    # decision sits within rounding of zero, so the trajectories agree to the
+    # FP32 tolerance and the same restarts fire.
+    inst = tiny_instance()
     s = solver_for(dlm_lib, inst)
-    s.set_schedule(gamma)
+    s.set_schedule(1e-2)
     s.set_options(precondition=True, restart=True)
     T = 300
     s.step(T)
     lam = s.lam().cpu().numpy().astype(np.float64)
     p = oracle_problem(inst)
-    ref = oracle.fista(p, T, gamma, precondition=True, restart=True, trajectory=False)
+    ref = oracle.fista(p, T, 1e-2, precondition=True, restart=True, trajectory=False)
     _, _, st = s.get_state()
-    assert st.theta == pytest.approx(ref["theta"], rel=1e-12)  # the same restarts fired
+    assert st.theta == pytest.approx(ref["theta"], rel=1e-12)
     err = np.abs(lam - ref["lam"]).max()
-    # FP32 lam/y rounding (2^-24 per step) compounds through the momentum over
-    # T = 300 steps; at gamma = 1e-3 (the smallest step) this reaches ~3e-5
-    # relative, so the bound is 5e-5 here.
-    assert err <= 5e-5 * max(np.abs(ref["lam"]).max(), 1e-6), f"max err {err:.3e}"
+    assert err <= 1e-5 * max(np.abs(ref["lam"]).max(), 1e-6), f"max err {err:.3e}"
+    s.close()
+
+
+def test_adaptive_restart_converges_to_the_oracle_optimum(dlm_lib):
+    # On a heavier instance a restart decision can fall within rounding of
+    # zero and then fire one step apart on the two sides, after which the
+    # trajectories differ by more than FP32 drift.  What is fixed is the limit,
+    # so both runs are driven to convergence and compared there: the dual
+    # value, and the FP64 certificate of the GPU's own iterate.  Both carry
+    # the floor of FP32 storage at a fixed point: the iteration stops moving
+    # lam_j once |step_j G_j| < ulp(lam_j) / 2, which leaves lam_j off by up to
+    # ulp(lam_j) / (2 step_j h_j) for a dual curvature h_j; on items with few
+    # fractional users that reaches ~1e-4 relative in lam and a few 1e-6 in
+    # the certified gap on this instance.
+    inst = mixed_instance(seed=6, I=1500, J=150)
+    s = solver_for(dlm_lib, inst)
+    s.set_schedule(1e-2)
+    s.set_options(precondition=True, restart=True)
+    T = 2500
+    s.step(T)
+    lam = s.lam().cpu().numpy().astype(np.float64)
+    p = oracle_problem(inst)
+    ref = oracle.fista(p, T, 1e-2, precondition=True, restart=True, trajectory=False)["lam"]
+    cert_ref = oracle.certify(p, ref, 1e-2)
+    assert cert_ref["rel_gap"] <= 1e-7  # the reference has converged
+    assert oracle.certify(p, lam, 1e-2)["rel_gap"] <= 1e-5
+    g, _, _ = s.calculate(torch.from_numpy(lam.astype(np.float32)).cuda(), 1e-2, want_grad=False, want_x=False)
+    assert abs(g - cert_ref["g"]) <= 1e-5 * abs(cert_ref["g"])
+    err = np.abs(lam - ref).max()
+    assert err <= 2e-4 * max(np.abs(ref).max(), 1e-6), f"max err {err:.3e}"
     s.close()
 
 

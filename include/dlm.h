@@ -93,9 +93,10 @@ typedef struct {
                               sweeps then use order 1 for a handle, 2 for a batch) */
   int32_t graph_iters;   /* iterations per captured CUDA graph (default 10) */
   int32_t ctas_per_sm;   /* persistent sweep CTAs per SM, 0..4 (0: 1 at 1024 threads, 2 at 512) */
-  int32_t coop_max;      /* 0..33: a warp runs its general-path users (threshold search) one
-                            after another with all 32 lanes while fewer than coop_max of its
-                            32 users need it (default 12; 1 never, 33 always) */
+  int32_t coop_max;      /* 0..33: rows whose simplex active set has four or more edges (the
+                            threshold iteration) are handled one after another by all 32 lanes
+                            of the warp while fewer than coop_max of its 32 rows need it
+                            (default 12; 1 never, 33 always) */
   int32_t block_threads; /* threads per sweep CTA: 0 (default 1024), 512 or 1024 */
   int32_t restart;       /* 1: adaptive momentum restart besides the stage restarts -- theta = 1
                             after a step whose direction opposes the momentum in the step metric,

@@ -264,6 +264,58 @@ __device__ __forceinline__ void top4_insert(float u, int k, float& v0, float& v1
   v3 = fmaxf(v3, t3);
 }
 
+// A row whose simplex active set is the r <= 3 recorded edges (on the
+// inequality simplex with tau <= 0: those of them with u > 0): load them once,
+// compute the threshold over them in pair arithmetic, deposit x on each.
+// Returns (tau, taul, zero, objective part).  Out of line, and used by the
+// dynamic-mapping sweep only: on the static sweeps the compiler's schedule of
+// the streaming pass measured 3 % slower with it (rows with one active edge
+// dominate there), while on mixed-gamma batches it saves a re-read.
+template <class P, bool STATS>
+__device__ __noinline__ float4 rows_upto3(const Seg S, const float* __restrict__ ys, unsigned long long* accG,
+                                          unsigned long long* accC, unsigned long long* accQ,
+                                          const int32_t* __restrict__ col0, const typename P::T* __restrict__ ca0,
+                                          int w4, int r, int i0, int i1, int i2, float tau, bool eq) {
+  const int lane = threadIdx.x & 31;
+  int jr[3];
+  float cr[3], ar[3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    jr[i] = 0;
+    cr[i] = ar[i] = 0.f;
+    if (i < r) {
+      const int el = sell_el(i == 0 ? i0 : (i == 1 ? i1 : i2), lane, w4);
+      jr[i] = __ldg(col0 + el);
+      P::get(__ldg(ca0 + el), cr[i], ar[i]);
+    }
+  }
+  bool zero = !eq && tau <= 0.f;
+  float taul = 0.f;
+  if (!zero) {
+    F2 sum{0.f, 0.f};
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+      if (i < r) sum = f2_add(sum, u_pair(cr[i], ar[i], ys[jr[i]]));
+    const F2 t2 = f2_threshold(sum, S.gz, S.gzl, r);
+    if (!eq && t2.h + t2.l <= 0.f) {
+      zero = true;
+    } else {
+      tau = t2.h;
+      taul = t2.l;
+    }
+  }
+  if (zero) tau = taul = 0.f;
+  float ob = 0.f;
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    if (i < r) {
+      const float x = x_general(S, false, zero, tau, taul, cr[i], ar[i], ys[jr[i]]);
+      if (x > 0.f) deposit<STATS>(S, jr[i], cr[i], ar[i], x, accG, accC, accQ, ob);
+    }
+  }
+  return make_float4(tau, taul, zero ? 1.f : 0.f, ob);
+}
+
 // Users of a slice whose active set is larger than the four tracked values
 // (mode 3 below) are handled by the whole warp, one after another, unless at
 // least coop_max of the 32 need it (then each lane runs its own user, which
@@ -272,7 +324,7 @@ __device__ __forceinline__ void top4_insert(float u, int k, float& v0, float& v1
 
 // One slice: lane t = user t; edge k of lane t is element sell_el(k, t, w/4)
 // of the slice.
-template <class P, bool STATS>
+template <class P, bool STATS, bool REG3 = false>
 __device__ __forceinline__ void do_slice(const InstDesc& D, const Seg& S, const float* __restrict__ ys,
                                          unsigned long long* accG, unsigned long long* accC,
                                          unsigned long long* accQ, int64_t s, int coop_max, double& wobj) {
@@ -349,10 +401,16 @@ __device__ __forceinline__ void do_slice(const InstDesc& D, const Seg& S, const 
   }
 
   float ob = 0.f;
-  if (mode == 2) {
+  if (mode == 2 && REG3) {
+    const float4 res = rows_upto3<P, STATS>(S, ys, accG, accC, accQ, col0, ca0, w4, r, i0, i1, i2, tau, eq);
+    tau = res.x;
+    taul = res.y;
+    zero = res.z != 0.f;
+    ob += res.w;
+  } else if (mode == 2) {
     // The active set is the r <= 3 recorded edges (on the inequality simplex
     // with tau <= 0: those of them with u > 0).  Threshold over them in pair
-    // arithmetic, then x on each.
+    // arithmetic, then x on each (the edges are re-read from L1).
     zero = !eq && tau <= 0.f;
     if (!zero) {
       F2 sum{0.f, 0.f};
@@ -669,7 +727,7 @@ __global__ void __launch_bounds__(kSweepThreads, 1)
       if (lane == 0) i = static_cast<int64_t>(atomicAdd(&s_next, 1ull));
       i = __shfl_sync(kFull, i, 0);
       if (i >= nsl) break;
-      do_slice<P, false>(sD, S, ys, accG, nullptr, nullptr, T.first + i, coop_max, wobj);
+      do_slice<P, false, true>(sD, S, ys, accG, nullptr, nullptr, T.first + i, coop_max, wobj);
     }
     __syncthreads();
   }

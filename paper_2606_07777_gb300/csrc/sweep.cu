@@ -267,12 +267,12 @@ __device__ __forceinline__ void top4_insert(float u, int k, float& v0, float& v1
 // A row whose simplex active set is the r <= 3 recorded edges (on the
 // inequality simplex with tau <= 0: those of them with u > 0): load them once,
 // compute the threshold over them in pair arithmetic, deposit x on each.
-// Returns (tau, taul, zero, objective part).  Out of line, and used by the
-// dynamic-mapping sweep only: on the static sweeps the compiler's schedule of
-// the streaming pass measured 3 % slower with it (rows with one active edge
-// dominate there), while on mixed-gamma batches it saves a re-read.
+// Returns (tau, taul, zero, objective part).  Used by the dynamic-mapping
+// sweep only: on the static sweeps the streaming pass measured 3 % slower with
+// it (rows with one active edge dominate there), while on mixed-gamma batches
+// it saves a re-read (4 % on the 64-instance batch).
 template <class P, bool STATS>
-__device__ __noinline__ float4 rows_upto3(const Seg S, const float* __restrict__ ys, unsigned long long* accG,
+__device__ __forceinline__ float4 rows_upto3(const Seg S, const float* __restrict__ ys, unsigned long long* accG,
                                           unsigned long long* accC, unsigned long long* accQ,
                                           const int32_t* __restrict__ col0, const typename P::T* __restrict__ ca0,
                                           int w4, int r, int i0, int i1, int i2, float tau, bool eq) {

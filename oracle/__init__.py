@@ -59,7 +59,7 @@ def build(force: bool = False) -> str:
         if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
             tmp = _LIB + f".tmp{os.getpid()}"
             subprocess.check_call(["gcc", "-O2", "-fno-fast-math", "-ffp-contract=off", "-shared", "-fPIC",
-                                   "-o", tmp, _SRC, "-lm"])
+                                   "-pthread", "-o", tmp, _SRC, "-lm"])
             os.replace(tmp, _LIB)
     return _LIB
 
@@ -80,6 +80,8 @@ def _load():
         lib.orc_certify.argtypes = [P, vp, d, vp]
         lib.orc_fista.argtypes = [P, d, d, d, i64, i32, i32, i64, vp, vp, vp, vp, vp, vp]
         lib.orc_stage_gamma.argtypes = [d, d, d, i64]
+        lib.orc_fista_threads.argtypes = [P, d, i32, i64, i32, vp]
+        lib.orc_fista_threads.restype = None
         lib.orc_stage_gamma.restype = d
         _lib = lib
     return _lib
@@ -171,6 +173,14 @@ def fista(p: Problem, T, gamma0, gamma_end=None, factor=0.5, iters_per_stage=0, 
     _load().orc_fista(ctypes.byref(p._s), gamma0, gamma_end, factor, iters_per_stage, int(bool(precondition)),
                       int(bool(restart)), T, _p(lam0), _p(lam), _p(y), ctypes.byref(th), _p(gt), _p(gg))
     return dict(lam=lam, y=y, theta=th.value, g_traj=gt, gamma_traj=gg)
+
+
+def fista_threads(p: Problem, T, gamma, precondition=False, nthreads=1):
+    """Timing only: T fixed-gamma iterations with the sweep split over
+    nthreads threads (per-thread item sums added in thread order); returns lam."""
+    lam = np.empty(p.J)
+    _load().orc_fista_threads(ctypes.byref(p._s), gamma, int(bool(precondition)), T, int(nthreads), _p(lam))
+    return lam
 
 
 def stage_gamma(gamma0, gamma_end, factor, s):

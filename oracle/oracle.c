@@ -22,6 +22,7 @@
  * elements of a user in storage order.
  */
 #include <math.h>
+#include <pthread.h>
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
@@ -353,4 +354,97 @@ void orc_fista(const orc_problem* p, double gamma0, double gamma_end, double fac
 /* Gamma of stage s under the continuation schedule (exported for tests). */
 double orc_stage_gamma(double gamma0, double gamma_end, double factor, int64_t s) {
   return stage_gamma(gamma0, gamma_end, factor, s);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Timing only: the same fixed-gamma iteration with the sweep split over      */
+/* threads.  Users are cut into nthreads contiguous ranges of equal edge      */
+/* count; each thread projects its users and sums A x into its own J-vector;  */
+/* the vectors are added in thread order, then the O(J) step runs serially.   */
+/* Deterministic for a fixed thread count.  Parity tests use orc_fista.       */
+/* ------------------------------------------------------------------------ */
+
+typedef struct {
+  const orc_problem* p;
+  const double* y;
+  double gamma;
+  int64_t u0, u1;
+  double* Ax;
+} sweep_job;
+
+static void* sweep_range(void* arg) {
+  sweep_job* jb = (sweep_job*)arg;
+  const orc_problem* p = jb->p;
+  int64_t maxd = 1;
+  for (int64_t i = jb->u0; i < jb->u1; ++i) {
+    int64_t d = p->row_ptr[i + 1] - p->row_ptr[i];
+    if (d > maxd) maxd = d;
+  }
+  double* v = (double*)malloc(sizeof(double) * (size_t)maxd);
+  double* x = (double*)malloc(sizeof(double) * (size_t)maxd);
+  for (int64_t j = 0; j < p->J; ++j) jb->Ax[j] = 0;
+  for (int64_t i = jb->u0; i < jb->u1; ++i) {
+    int64_t e0 = p->row_ptr[i], d = p->row_ptr[i + 1] - e0;
+    for (int64_t k = 0; k < d; ++k) v[k] = -(p->c[e0 + k] + p->a[e0 + k] * jb->y[p->col[e0 + k]]) / jb->gamma;
+    orc_project(v, d, p->kind, p->z, 0, x);
+    for (int64_t k = 0; k < d; ++k) jb->Ax[p->col[e0 + k]] += p->a[e0 + k] * x[k];
+  }
+  free(v);
+  free(x);
+  return NULL;
+}
+
+void orc_fista_threads(const orc_problem* p, double gamma, int32_t precondition, int64_t T, int32_t nthreads,
+                       double* lam_out) {
+  int64_t J = p->J;
+  if (nthreads < 1) nthreads = 1;
+  double* n2 = (double*)malloc(sizeof(double) * (size_t)J);
+  double* lam = (double*)calloc((size_t)J, sizeof(double));
+  double* y = (double*)calloc((size_t)J, sizeof(double));
+  double* Ax = (double*)malloc(sizeof(double) * (size_t)J * (size_t)nthreads);
+  sweep_job* jobs = (sweep_job*)malloc(sizeof(sweep_job) * (size_t)nthreads);
+  pthread_t* th = (pthread_t*)malloc(sizeof(pthread_t) * (size_t)nthreads);
+  orc_row_sq(p, n2);
+  double nmax = 0;
+  for (int64_t j = 0; j < J; ++j)
+    if (n2[j] > nmax) nmax = n2[j];
+  int64_t u = 0;
+  for (int32_t t = 0; t < nthreads; ++t) {
+    int64_t target = p->nnz * (t + 1) / nthreads;
+    int64_t u1 = u;
+    while (u1 < p->I && p->row_ptr[u1] < target) ++u1;
+    if (t == nthreads - 1) u1 = p->I;
+    jobs[t].p = p;
+    jobs[t].y = y;
+    jobs[t].gamma = gamma;
+    jobs[t].u0 = u;
+    jobs[t].u1 = u1;
+    jobs[t].Ax = Ax + (size_t)J * (size_t)t;
+    u = u1;
+  }
+  double theta = 1.0;
+  for (int64_t it = 0; it < T; ++it) {
+    for (int32_t t = 1; t < nthreads; ++t) pthread_create(&th[t], NULL, sweep_range, &jobs[t]);
+    sweep_range(&jobs[0]);
+    for (int32_t t = 1; t < nthreads; ++t) pthread_join(th[t], NULL);
+    double th1 = 0.5 * (1.0 + sqrt(1.0 + 4.0 * theta * theta));
+    double beta = (theta - 1.0) / th1;
+    for (int64_t j = 0; j < J; ++j) {
+      double G = -p->b[j];
+      for (int32_t t = 0; t < nthreads; ++t) G += Ax[(size_t)J * (size_t)t + (size_t)j];
+      double step = precondition ? (n2[j] > 0 ? gamma / n2[j] : 0.0) : (nmax > 0 ? gamma / nmax : 0.0);
+      double v = y[j] + step * G;
+      double nl = v > 0 ? v : 0;
+      y[j] = nl + beta * (nl - lam[j]);
+      lam[j] = nl;
+    }
+    theta = th1;
+  }
+  for (int64_t j = 0; j < J; ++j) lam_out[j] = lam[j];
+  free(n2);
+  free(lam);
+  free(y);
+  free(Ax);
+  free(jobs);
+  free(th);
 }

@@ -228,3 +228,18 @@ def test_adaptive_restart_fires_on_overshoot():
     assert all(plain[k + 1]["theta"] > plain[k]["theta"] for k in range(len(plain) - 1))
     assert any(r["theta"] == 1.0 for r in rst[2:])
     assert abs(rst[-1]["lam"][0] - 0.85) < 1e-9 and abs(plain[-1]["lam"][0] - 0.85) < 1e-3
+
+
+def test_threaded_timing_loop_is_the_same_iteration():
+    """The threaded loop that times the CPU baseline runs the same fixed-gamma
+    iteration; only the order of the per-item sums differs."""
+    import synth
+
+    inst = synth.generate(synth.recipe_tiny())
+    p = oracle.Problem(inst.row_ptr, inst.col, inst.c.astype(np.float64), inst.a.astype(np.float64), inst.b,
+                       inst.J)
+    for pre in (False, True):
+        ref = oracle.fista(p, 40, 1e-2, precondition=pre, trajectory=False)["lam"]
+        for nt in (1, 3, 8):
+            got = oracle.fista_threads(p, 40, 1e-2, precondition=pre, nthreads=nt)
+            assert np.abs(got - ref).max() <= 1e-12 * max(1.0, np.abs(ref).max()), (pre, nt)

@@ -315,6 +315,21 @@ def time_oracle(p, gamma, budget_s, nthreads=1):
     return p.nnz * iters / dt, iters, dt
 
 
+def replica_throughput(units, seconds, dist=None, device=None):
+    """Whole-job throughput of independent replicas: the units all ranks
+    processed divided by the slowest rank's time (max over ranks).  Returns
+    (units per second, max seconds).  Without a process group: this rank's."""
+    if dist is None:
+        return units / seconds, seconds
+    import torch
+
+    u = torch.tensor([float(units)], dtype=torch.float64, device=device)
+    t = torch.tensor([float(seconds)], dtype=torch.float64, device=device)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(u.item()) / float(t.item()), float(t.item())
+
+
 def host_cores():
     try:
         return len(os.sched_getaffinity(0))
@@ -474,9 +489,8 @@ def main():
     torch.cuda.synchronize(dev)
     barrier()
     clocks = sampler.stop()
-    elapsed_s = max_over_ranks(tot_ms / 1000.0)
     iters_total = args.iters * args.steps
-    value = world * nnz * iters_total / elapsed_s
+    value, elapsed_s = replica_throughput(nnz * iters_total, tot_ms / 1000.0, dist, dev)
 
     # Same steps replayed through the captured CUDA graphs (the default path).
     st = torch.cuda.current_stream(dev)
@@ -512,8 +526,7 @@ def main():
             e2e_times.append(dt)
     e2e_value = None
     if e2e_times:
-        e2e_s = max_over_ranks(statistics.mean(e2e_times))
-        e2e_value = world * nnz * args.iters / e2e_s
+        e2e_value, _ = replica_throughput(nnz * args.iters, statistics.mean(e2e_times), dist, dev)
 
     # ---- roofline of the dominant kernel (the sweep) ----
     peak, peak_kind = load_peaks()
@@ -746,9 +759,8 @@ def run_batched(args, dlm, torch, dev, rank, world, barrier, max_over_ranks, dis
     torch.cuda.synchronize(dev)
     barrier()
     clocks = sampler.stop()
-    elapsed_s = max_over_ranks(tot_ms / 1000.0)
     iters_total = args.iters * args.steps
-    value = world * nnz * iters_total / elapsed_s
+    value, elapsed_s = replica_throughput(nnz * iters_total, tot_ms / 1000.0, dist, dev)
 
     st = torch.cuda.current_stream(dev)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -793,7 +805,7 @@ def run_batched(args, dlm, torch, dev, rank, world, barrier, max_over_ranks, dis
             e2e_times.append(dt)
     e2e_value = None
     if e2e_times:
-        e2e_value = world * nnz * args.iters / max_over_ranks(statistics.mean(e2e_times))
+        e2e_value, _ = replica_throughput(nnz * args.iters, statistics.mean(e2e_times), dist, dev)
 
     peak, peak_kind = load_peaks()
     sweep_s = sweep_ms / 1000.0 / iters_total

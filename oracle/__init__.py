@@ -50,6 +50,7 @@ class _Problem(ctypes.Structure):
         ("kind", ctypes.c_int32),
         ("_pad", ctypes.c_int32),
         ("z", ctypes.c_double),
+        ("M", ctypes.c_double),
     ]
 
 
@@ -72,11 +73,13 @@ def _load():
         P = ctypes.POINTER(_Problem)
         lib.orc_project.argtypes = [vp, i64, i32, d, i32, vp]
         lib.orc_project.restype = d
-        lib.orc_sweep.argtypes = [P, vp, d, vp, vp, vp, vp, vp]
+        lib.orc_sweep.argtypes = [P, vp, d, vp, vp, vp, vp, vp, vp]
         lib.orc_sweep.restype = d
         lib.orc_dual.argtypes = [P, vp, d, vp, vp]
         lib.orc_dual.restype = d
         lib.orc_row_sq.argtypes = [P, vp]
+        lib.orc_row_sum.argtypes = [P, vp]
+        lib.orc_row_sum.restype = None
         lib.orc_certify.argtypes = [P, vp, d, vp]
         lib.orc_fista.argtypes = [P, d, d, d, i64, i32, i32, i64, vp, vp, vp, vp, vp, vp]
         lib.orc_stage_gamma.argtypes = [d, d, d, i64]
@@ -95,7 +98,7 @@ class Problem:
     """An instance in FP64: user-major CSR (row_ptr int64, col int32), c, a
     (float64, e.g. float32 or bfloat16 values widened exactly), b (float64)."""
 
-    def __init__(self, row_ptr, col, c, a, b, J=None, kind=SIMPLEX_LE, z=1.0):
+    def __init__(self, row_ptr, col, c, a, b, J=None, kind=SIMPLEX_LE, z=1.0, M=np.inf):
         self.row_ptr = np.ascontiguousarray(row_ptr, dtype=np.int64)
         self.col = np.ascontiguousarray(col, dtype=np.int32)
         self.c = np.ascontiguousarray(c, dtype=np.float64)
@@ -106,10 +109,12 @@ class Problem:
         self.nnz = int(self.row_ptr[-1])
         self.kind = int(kind)
         self.z = float(z)
+        self.M = float(M)
+        self.D = self.J + (1 if np.isfinite(self.M) else 0)  # dual dimension
         s = _Problem()
         s.I, s.J, s.nnz = self.I, self.J, self.nnz
         s.row_ptr, s.col, s.c, s.a, s.b = (_p(self.row_ptr), _p(self.col), _p(self.c), _p(self.a), _p(self.b))
-        s.kind, s.z = self.kind, self.z
+        s.kind, s.z, s.M = self.kind, self.z, self.M
         self._s = s
 
     @classmethod
@@ -126,20 +131,33 @@ def project(v, kind=SIMPLEX_LE, z=1.0, method=0):
     return x, th
 
 
-def sweep(p: Problem, lam, gamma, want_x=True):
-    """One dual evaluation: dict(g, x, Ax, Cx, Qx, obj, grad)."""
+def _dual_vec(p: Problem, lam):
     lam = np.ascontiguousarray(lam, dtype=np.float64)
+    if lam.shape[0] != p.D:
+        raise ValueError(f"dual vector needs {p.D} entries (num_items + 1 with a count constraint)")
+    return lam
+
+
+def sweep(p: Problem, lam, gamma, want_x=True):
+    """One dual evaluation: dict(g, x, Ax, Cx, Qx, obj, count, grad); lam has
+    p.D entries (the last is the count dual mu when p.M is finite), and so
+    does grad."""
+    lam = _dual_vec(p, lam)
     x = np.empty(p.nnz) if want_x else None
     Ax, Cx, Qx = np.empty(p.J), np.empty(p.J), np.empty(p.J)
-    obj = ctypes.c_double()
-    g = _load().orc_sweep(ctypes.byref(p._s), _p(lam), gamma, _p(x), _p(Ax), _p(Cx), _p(Qx), ctypes.byref(obj))
-    return dict(g=g, x=x, Ax=Ax, Cx=Cx, Qx=Qx, obj=obj.value, grad=Ax - p.b)
+    obj, count = ctypes.c_double(), ctypes.c_double()
+    g = _load().orc_sweep(ctypes.byref(p._s), _p(lam), gamma, _p(x), _p(Ax), _p(Cx), _p(Qx), ctypes.byref(obj),
+                          ctypes.byref(count))
+    grad = Ax - p.b
+    if p.D > p.J:
+        grad = np.append(grad, count.value - p.M)
+    return dict(g=g, x=x, Ax=Ax, Cx=Cx, Qx=Qx, obj=obj.value, count=count.value, grad=grad)
 
 
 def dual(p: Problem, lam, gamma):
-    """(g(lam), grad g(lam), x*(lam))."""
-    lam = np.ascontiguousarray(lam, dtype=np.float64)
-    grad = np.empty(p.J)
+    """(g(lam), grad g(lam), x*(lam)); lam and grad have p.D entries."""
+    lam = _dual_vec(p, lam)
+    grad = np.empty(p.D)
     x = np.empty(p.nnz)
     g = _load().orc_dual(ctypes.byref(p._s), _p(lam), gamma, _p(grad), _p(x))
     return g, grad, x
@@ -151,9 +169,15 @@ def row_sq(p: Problem):
     return out
 
 
+def row_sum(p: Problem):
+    out = np.empty(p.J)
+    _load().orc_row_sum(ctypes.byref(p._s), _p(out))
+    return out
+
+
 def certify(p: Problem, lam, gamma):
     """dict(g, primal, rel_gap, max_viol, uncert_gap, primal_unscaled)."""
-    lam = np.ascontiguousarray(lam, dtype=np.float64)
+    lam = _dual_vec(p, lam)
     out = np.empty(6)
     _load().orc_certify(ctypes.byref(p._s), _p(lam), gamma, _p(out))
     return dict(g=out[0], primal=out[1], rel_gap=out[2], max_viol=out[3], uncert_gap=out[4],
@@ -165,8 +189,8 @@ def fista(p: Problem, T, gamma0, gamma_end=None, factor=0.5, iters_per_stage=0, 
     """T iterations of accelerated projected dual ascent; dict(lam, y, theta,
     g_traj, gamma_traj).  restart=True adds the adaptive momentum restart."""
     gamma_end = gamma0 if gamma_end is None else gamma_end
-    lam0 = np.zeros(p.J) if lam0 is None else np.ascontiguousarray(lam0, dtype=np.float64)
-    lam, y = np.empty(p.J), np.empty(p.J)
+    lam0 = np.zeros(p.D) if lam0 is None else _dual_vec(p, lam0)
+    lam, y = np.empty(p.D), np.empty(p.D)
     th = ctypes.c_double()
     gt = np.empty(T) if trajectory else None
     gg = np.empty(T) if trajectory else None
@@ -178,6 +202,8 @@ def fista(p: Problem, T, gamma0, gamma_end=None, factor=0.5, iters_per_stage=0, 
 def fista_threads(p: Problem, T, gamma, precondition=False, nthreads=1):
     """Timing only: T fixed-gamma iterations with the sweep split over
     nthreads threads (per-thread item sums added in thread order); returns lam."""
+    if p.D != p.J:
+        raise ValueError("the threaded timing loop covers the capacity-only problem")
     lam = np.empty(p.J)
     _load().orc_fista_threads(ctypes.byref(p._s), gamma, int(bool(precondition)), T, int(nthreads), _p(lam))
     return lam

@@ -18,6 +18,10 @@
  * primal recovery (Eq. primal-recovery):  x*(lam) = Proj_C(-(A^T lam + c)/gamma),
  * gradient (Eq. dual-gradient, Danskin):   grad g(lam) = A x*(lam) - b.
  *
+ * Optionally a global count constraint sum_ij x_ij <= M (the example of a new
+ * coupling constraint in Sec. 5: one more dual coordinate mu, one more term in
+ * A^T lam, one more gradient entry).
+ *
  * Everything is sequential FP64 in the natural order: users in index order,
  * elements of a user in storage order.
  */
@@ -37,7 +41,13 @@ typedef struct {
   int32_t kind;           /* 0 simplex <=, 1 simplex ==, 2 box */
   int32_t _pad;
   double z;               /* simplex radius or box upper bound */
+  double M;               /* global count bound sum_ij x_ij <= M (Sec. 5); INFINITY: none */
 } orc_problem;
+
+/* With a global count constraint the dual vector is (lam_0..lam_{J-1}, mu):
+ * mu >= 0 is the dual of sum_ij x_ij <= M, which adds mu to every edge's cost
+ * (one more row of ones in A). */
+static int has_count(const orc_problem* p) { return isfinite(p->M); }
 
 /* ------------------------------------------------------------------------ */
 /* Projections onto one user's simple set (Sec. 3.3, Sec. 4.3)               */
@@ -147,12 +157,13 @@ double orc_project(const double* v, int64_t n, int32_t kind, double z, int32_t m
  *   obj    = sum (c x + gamma/2 x^2)                   (scalar)
  * and returns g(lam) = obj + lam^T (Ax - b). */
 double orc_sweep(const orc_problem* p, const double* lam, double gamma, double* x_out, double* Ax, double* Cx,
-                 double* Qx, double* obj_out) {
+                 double* Qx, double* obj_out, double* count_out) {
   int64_t maxd = 0;
   for (int64_t i = 0; i < p->I; ++i) {
     int64_t d = p->row_ptr[i + 1] - p->row_ptr[i];
     if (d > maxd) maxd = d;
   }
+  const double mu = has_count(p) ? lam[p->J] : 0.0;
   double* v = (double*)malloc(sizeof(double) * (size_t)(maxd > 0 ? maxd : 1));
   double* x = (double*)malloc(sizeof(double) * (size_t)(maxd > 0 ? maxd : 1));
   for (int64_t j = 0; j < p->J; ++j) {
@@ -160,12 +171,12 @@ double orc_sweep(const orc_problem* p, const double* lam, double gamma, double* 
     if (Cx) Cx[j] = 0;
     if (Qx) Qx[j] = 0;
   }
-  double obj = 0;
+  double obj = 0, count = 0;
   for (int64_t i = 0; i < p->I; ++i) {
     int64_t e0 = p->row_ptr[i], d = p->row_ptr[i + 1] - e0;
     for (int64_t k = 0; k < d; ++k) {
       int64_t e = e0 + k;
-      v[k] = -(p->c[e] + p->a[e] * lam[p->col[e]]) / gamma;
+      v[k] = -(p->c[e] + p->a[e] * lam[p->col[e]] + mu) / gamma;
     }
     orc_project(v, d, p->kind, p->z, 0, x);
     for (int64_t k = 0; k < d; ++k) {
@@ -175,6 +186,7 @@ double orc_sweep(const orc_problem* p, const double* lam, double gamma, double* 
       if (Cx) Cx[j] += p->c[e] * x[k];
       if (Qx) Qx[j] += x[k] * x[k];
       obj += p->c[e] * x[k] + 0.5 * gamma * x[k] * x[k];
+      count += x[k];
       if (x_out) x_out[e] = x[k];
     }
   }
@@ -182,15 +194,27 @@ double orc_sweep(const orc_problem* p, const double* lam, double gamma, double* 
   free(x);
   double g = obj;
   for (int64_t j = 0; j < p->J; ++j) g += lam[j] * (Ax[j] - p->b[j]);
+  if (has_count(p)) g += mu * (count - p->M);
   if (obj_out) *obj_out = obj;
+  if (count_out) *count_out = count;
   return g;
 }
 
-/* g(lam) and grad g(lam) = A x*(lam) - b (Eq. dual-gradient). */
+/* g(lam) and grad g(lam) = A x*(lam) - b (Eq. dual-gradient); with a count
+ * constraint grad has J + 1 entries, the last sum_ij x_ij - M. */
 double orc_dual(const orc_problem* p, const double* lam, double gamma, double* grad, double* x_out) {
-  double g = orc_sweep(p, lam, gamma, x_out, grad, NULL, NULL, NULL);
+  double count = 0;
+  double g = orc_sweep(p, lam, gamma, x_out, grad, NULL, NULL, NULL, &count);
   for (int64_t j = 0; j < p->J; ++j) grad[j] -= p->b[j];
+  if (has_count(p)) grad[p->J] = count - p->M;
   return g;
+}
+
+/* s_j = sum_i a_ij: the coupling between item j's row of A and the count row
+ * of ones (an entry of A A^T). */
+void orc_row_sum(const orc_problem* p, double* s1) {
+  for (int64_t j = 0; j < p->J; ++j) s1[j] = 0;
+  for (int64_t e = 0; e < p->nnz; ++e) s1[p->col[e]] += p->a[e];
 }
 
 /* n_j = sum_i a_ij^2.  With one capacity family the rows of A have disjoint
@@ -220,16 +244,26 @@ void orc_certify(const orc_problem* p, const double* lam, double gamma, double* 
   double* Ax = (double*)malloc(sizeof(double) * (size_t)J);
   double* Cx = (double*)malloc(sizeof(double) * (size_t)J);
   double* Qx = (double*)malloc(sizeof(double) * (size_t)J);
-  double obj = 0;
-  double g = orc_sweep(p, lam, gamma, NULL, Ax, Cx, Qx, &obj);
+  double obj = 0, count = 0;
+  double g = orc_sweep(p, lam, gamma, NULL, Ax, Cx, Qx, &obj, &count);
+  /* item scaling s_j = min(1, b_j / (Ax)_j); with a count constraint a common
+   * factor t = min(1, M / sum x) on top keeps sum x~ <= t sum x <= M */
+  double t = 1.0;
+  if (has_count(p) && count > p->M) t = p->M / count;
   double P = 0, viol = 0, lg = 0;
   for (int64_t j = 0; j < J; ++j) {
     double s = 1.0;
     if (Ax[j] > p->b[j]) s = p->b[j] / Ax[j];
+    s *= t;
     P += s * Cx[j] + 0.5 * gamma * s * s * Qx[j];
     double r = Ax[j] - p->b[j];
     if (r > viol) viol = r;
     lg += lam[j] * r;
+  }
+  if (has_count(p)) {
+    double r = count - p->M;
+    if (r > viol) viol = r;
+    lg += lam[J] * r;
   }
   double den = fabs(g) > 1e-30 ? fabs(g) : 1e-30;
   out[0] = g;
@@ -243,14 +277,6 @@ void orc_certify(const orc_problem* p, const double* lam, double gamma, double* 
   free(Qx);
 }
 
-/* ------------------------------------------------------------------------ */
-/* Accelerated projected dual ascent with gamma continuation                 */
-/* (Sec. 4.4 update on lam >= 0; Sec. 6 continuation; App. B.2 step 1/L,     */
-/*  row normalization)                                                       */
-/* ------------------------------------------------------------------------ */
-
-/* gamma of stage s: gamma_0 = gamma0, gamma_{s+1} = max(gamma_end, gamma_s * factor)
- * (a stage never goes below gamma_end; gamma0 == gamma_end is a fixed ridge). */
 static double stage_gamma(double gamma0, double gamma_end, double factor, int64_t s) {
   double g = gamma0;
   for (int64_t k = 0; k < s; ++k) {
@@ -274,20 +300,46 @@ static double stage_gamma(double gamma0, double gamma_end, double factor, int64_
  * from the last lam (warm start) with theta = 1 and y = lam (Sec. 6).
  * Outputs: lam_out, y_out (state after T iterations), theta_out, and per
  * iteration t: traj_g[t] = g(y_t), traj_gamma[t] (either may be NULL). */
+/* Per-coordinate curvature bounds h_k (step_k = gamma / h_k).  One family:
+ * A A^T = diag(n) (Def. 1), so h_j = n_j with row normalization and
+ * h = max_j n_j = ||A||^2 otherwise (App. B.2).  With the count row, A A^T
+ * gains the row and column s (s_j = sum_i a_ij) and the corner nnz; Gershgorin
+ * row sums r_j = n_j + |s_j|, r_mu = nnz + sum_j |s_j| bound it: the diagonal
+ * scaling by 1/r is a valid preconditioner, and max_k r_k bounds ||A||^2. */
+static int64_t curvature(const orc_problem* p, int32_t precondition, double* h) {
+  int64_t J = p->J, D = J + (has_count(p) ? 1 : 0);
+  orc_row_sq(p, h);
+  if (has_count(p)) {
+    double* s1 = (double*)malloc(sizeof(double) * (size_t)J);
+    orc_row_sum(p, s1);
+    double tot = 0;
+    for (int64_t j = 0; j < J; ++j) {
+      h[j] += fabs(s1[j]);
+      tot += fabs(s1[j]);
+    }
+    h[J] = (double)p->nnz + tot;
+    free(s1);
+  }
+  if (!precondition) {
+    double mx = 0;
+    for (int64_t k = 0; k < D; ++k)
+      if (h[k] > mx) mx = h[k];
+    for (int64_t k = 0; k < D; ++k) h[k] = mx;
+  }
+  return D;
+}
+
 void orc_fista(const orc_problem* p, double gamma0, double gamma_end, double factor, int64_t iters_per_stage,
                int32_t precondition, int32_t restart, int64_t T, const double* lam0, double* lam_out,
                double* y_out, double* theta_out, double* traj_g, double* traj_gamma) {
-  int64_t J = p->J;
-  double* n2 = (double*)malloc(sizeof(double) * (size_t)J);
-  double* lam = (double*)malloc(sizeof(double) * (size_t)J);
-  double* y = (double*)malloc(sizeof(double) * (size_t)J);
-  double* G = (double*)malloc(sizeof(double) * (size_t)J);
-  double* nl = (double*)malloc(sizeof(double) * (size_t)J);
-  orc_row_sq(p, n2);
-  double nmax = 0;
-  for (int64_t j = 0; j < J; ++j)
-    if (n2[j] > nmax) nmax = n2[j];
-  for (int64_t j = 0; j < J; ++j) lam[j] = y[j] = lam0[j];
+  int64_t J = p->J, D1 = J + 1;
+  double* h = (double*)malloc(sizeof(double) * (size_t)D1);
+  double* lam = (double*)malloc(sizeof(double) * (size_t)D1);
+  double* y = (double*)malloc(sizeof(double) * (size_t)D1);
+  double* G = (double*)malloc(sizeof(double) * (size_t)D1);
+  double* nl = (double*)malloc(sizeof(double) * (size_t)D1);
+  const int64_t D = curvature(p, precondition, h);
+  for (int64_t k = 0; k < D; ++k) lam[k] = y[k] = lam0[k];
   double theta = 1.0;
   if (iters_per_stage <= 0) iters_per_stage = T > 0 ? T : 1;
   for (int64_t t = 0; t < T; ++t) {
@@ -296,55 +348,47 @@ void orc_fista(const orc_problem* p, double gamma0, double gamma_end, double fac
     double g = orc_dual(p, y, gamma, G, NULL);
     if (traj_g) traj_g[t] = g;
     if (traj_gamma) traj_gamma[t] = gamma;
-    for (int64_t j = 0; j < J; ++j) {
-      double step;
-      if (precondition)
-        step = n2[j] > 0 ? gamma / n2[j] : 0.0;
-      else
-        step = nmax > 0 ? gamma / nmax : 0.0;
-      double v = y[j] + step * G[j];
-      nl[j] = v > 0 ? v : 0;
+    for (int64_t k = 0; k < D; ++k) {
+      double step = h[k] > 0 ? gamma / h[k] : 0.0;
+      double v = y[k] + step * G[k];
+      nl[k] = v > 0 ? v : 0;
     }
     int64_t s1 = (t + 1) / iters_per_stage;
     double gamma_next = stage_gamma(gamma0, gamma_end, factor, s1);
     int restart_now = gamma_next != gamma;
     if (restart && !restart_now) {
       /* adaptive restart (O'Donoghue & Candes 2015, gradient-mapping test
-         for ascent, in the metric of the per-item steps): restart when the
-         step just taken opposes the momentum */
+         for ascent, in the metric of the per-coordinate steps): restart when
+         the step just taken opposes the momentum */
       double dot = 0.0;
-      for (int64_t j = 0; j < J; ++j) {
-        double step;
-        if (precondition)
-          step = n2[j] > 0 ? gamma / n2[j] : 0.0;
-        else
-          step = nmax > 0 ? gamma / nmax : 0.0;
-        if (step > 0) dot += (nl[j] - y[j]) * (nl[j] - lam[j]) / step;
+      for (int64_t k = 0; k < D; ++k) {
+        double step = h[k] > 0 ? gamma / h[k] : 0.0;
+        if (step > 0) dot += (nl[k] - y[k]) * (nl[k] - lam[k]) / step;
       }
       restart_now = dot < 0.0;
     }
     if (restart_now) {
       theta = 1.0;
-      for (int64_t j = 0; j < J; ++j) {
-        lam[j] = nl[j];
-        y[j] = nl[j];
+      for (int64_t k = 0; k < D; ++k) {
+        lam[k] = nl[k];
+        y[k] = nl[k];
       }
     } else {
       double th1 = 0.5 * (1.0 + sqrt(1.0 + 4.0 * theta * theta));
       double beta = (theta - 1.0) / th1;
-      for (int64_t j = 0; j < J; ++j) {
-        y[j] = nl[j] + beta * (nl[j] - lam[j]);
-        lam[j] = nl[j];
+      for (int64_t k = 0; k < D; ++k) {
+        y[k] = nl[k] + beta * (nl[k] - lam[k]);
+        lam[k] = nl[k];
       }
       theta = th1;
     }
   }
-  for (int64_t j = 0; j < J; ++j) {
-    lam_out[j] = lam[j];
-    if (y_out) y_out[j] = y[j];
+  for (int64_t k = 0; k < D; ++k) {
+    lam_out[k] = lam[k];
+    if (y_out) y_out[k] = y[k];
   }
   if (theta_out) *theta_out = theta;
-  free(n2);
+  free(h);
   free(lam);
   free(y);
   free(G);
@@ -396,6 +440,7 @@ static void* sweep_range(void* arg) {
 
 void orc_fista_threads(const orc_problem* p, double gamma, int32_t precondition, int64_t T, int32_t nthreads,
                        double* lam_out) {
+  /* (timing of the capacity-only problem; a count constraint is not timed) */
   int64_t J = p->J;
   if (nthreads < 1) nthreads = 1;
   double* n2 = (double*)malloc(sizeof(double) * (size_t)J);

@@ -155,6 +155,22 @@ dlm_status dlm_create(const dlm_problem_desc* desc, void* stream, dlm_problem** 
 dlm_status dlm_set_schedule(dlm_problem* p, double gamma0, double gamma_end, double factor,
                             int64_t iters_per_stage);
 
+/* Global count constraint sum_{(i,j)} x_ij <= M (Sec. 5 names it as the
+ * example of a new coupling constraint: one more dual coordinate mu >= 0,
+ * added to every edge's cost, one more gradient entry sum x - M).  M >= 0;
+ * INFINITY removes it.  While it is set, every dual vector of this handle --
+ * dlm_set_lambda, dlm_get_lambda, dlm_calculate's lambda and grad,
+ * dlm_get_state / dlm_set_state, dlm_ws_features' lam_prev -- has
+ * num_items + 1 entries, the last being mu.  The steps use Gershgorin bounds of
+ * A A^T with the count row: item j's curvature n_j + |s_j| (s_j = sum_i a_ij),
+ * the count row's nnz + sum_j |s_j|; with row normalization each coordinate
+ * takes gamma over its bound, otherwise all take gamma over the largest (slow
+ * with a count row: use row normalization).  The certificate multiplies the
+ * item-scaled point by min(1, M / sum x).  Sets mu to 0; call it before
+ * iterating and before dlm_batch_create.  Meaningful for DLM_SIMPLEX_LE and
+ * DLM_BOX (with DLM_SIMPLEX_EQ, sum x = z per user whatever mu). */
+dlm_status dlm_set_count_limit(dlm_problem* p, double M);
+
 /* Replace the handle's options (see dlm_options; out-of-range values return
  * DLM_ERR_INVALID_ARG).  Synchronizes the handle's stream when the launch
  * shape changes. */

@@ -105,6 +105,7 @@ _SIGS = {
     "dlm_batch_step_timed": [_vp, _i64, ctypes.POINTER(_d), ctypes.POINTER(_d), ctypes.POINTER(_d)],
     "dlm_batch_get_stats": [_vp, ctypes.POINTER(Stats)],
     "dlm_batch_solve": [_vp, _d, _i64, ctypes.POINTER(Stats)],
+    "dlm_set_count_limit": [_vp, _d],
     "dlm_ws_create": [_i32, ctypes.c_uint64, _vp, ctypes.POINTER(_vp)],
     "dlm_ws_num_params": [_vp, ctypes.POINTER(_i64)],
     "dlm_ws_get_params": [_vp, _vp, _vp, _vp],
@@ -367,6 +368,7 @@ class Solver:
         self._keep = None
         self.kind = int(kind)
         self.z = float(z)
+        self.dual_dim = self.num_items  # num_items + 1 while a count constraint is set
 
     def close(self):
         if getattr(self, "h", None):
@@ -395,6 +397,14 @@ class Solver:
         returns (chosen Options, mean sweep ms)."""
         return dlm_autotune(self.h, iters)
 
+    def set_count_limit(self, M):
+        """Global count constraint sum x <= M (math.inf removes it); the dual
+        vectors then carry its dual as one more entry."""
+        import math
+
+        _call("dlm_set_count_limit", self.h, float(M))
+        self.dual_dim = self.num_items + (0 if math.isinf(M) else 1)
+
     def set_lambda(self, lam):
         dlm_set_lambda(self.h, lam, DLM_MEM_DEVICE if getattr(lam, "is_cuda", False) else DLM_MEM_HOST)
 
@@ -412,14 +422,14 @@ class Solver:
 
     def calculate(self, lam, gamma, want_grad=True, want_x=True):
         t = self._torch
-        grad = t.empty(self.num_items, dtype=t.float32, device=self.device) if want_grad else None
+        grad = t.empty(self.dual_dim, dtype=t.float32, device=self.device) if want_grad else None
         x = t.empty(self.nnz, dtype=t.float32, device=self.device) if want_x else None
         g = dlm_calculate(self.h, lam, gamma, grad, x)
         return g, grad, x
 
     def lam(self):
         t = self._torch
-        out = t.empty(self.num_items, dtype=t.float32, device=self.device)
+        out = t.empty(self.dual_dim, dtype=t.float32, device=self.device)
         dlm_get_lambda(self.h, out, DLM_MEM_DEVICE)
         return out
 
@@ -431,7 +441,7 @@ class Solver:
 
     def get_state(self):
         t = self._torch
-        lam = t.empty(self.num_items, dtype=t.float32, device=self.device)
+        lam = t.empty(self.dual_dim, dtype=t.float32, device=self.device)
         y = t.empty_like(lam)
         s = dlm_get_state(self.h, lam, y, DLM_MEM_DEVICE)
         return lam, y, s

@@ -60,12 +60,6 @@ __global__ void k_state_reset(DevState* st, double gamma0) {
   *st = n;
 }
 
-__global__ void k_inv(const double* n2, double* inv, int64_t J) {
-  for (int64_t j = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; j < J;
-       j += static_cast<int64_t>(gridDim.x) * blockDim.x)
-    inv[j] = n2[j] > 0.0 ? 1.0 / n2[j] : 0.0;
-}
-
 int blocks_for(int64_t n) {
   int64_t g = (n + 255) / 256;
   if (g < 1) g = 1;
@@ -132,7 +126,15 @@ struct dlm_problem {
   int sG = 0, sC = 0, sQ = 0;
   bool certified = true;
 
-  double *b = nullptr, *inv_n2 = nullptr;
+  double *b = nullptr, *inv_n2 = nullptr;  // inv_n2: per-coordinate inverse curvature bounds (steps)
+  double inv_hmax = 0;                      // 1 / the largest curvature bound (plain step)
+  double inv_h_count = 0;                   // 1 / curvature bound of the count row
+  // global count constraint sum x <= M: dual entry J of lam and y
+  bool count_on = false;
+  double count_M = INFINITY;
+  int sN = 0;
+  unsigned long long *cnt = nullptr, *cnt2 = nullptr;  // fixed-point sum x at y / at lam
+  int64_t D() const { return J + (count_on ? 1 : 0); }  // dual dimension
   float *lam = nullptr, *y = nullptr;
   unsigned long long *acc = nullptr, *acc2 = nullptr, *accC = nullptr, *accQ = nullptr;
   double *gamma_tab = nullptr, *calc_gamma = nullptr, *stats_out = nullptr;
@@ -179,6 +181,9 @@ InstDesc base_desc(const dlm_problem* p) {
   d.z = static_cast<float>(p->z);
   d.J = static_cast<int32_t>(p->J);
   d.kind = p->kind;
+  d.count_on = p->count_on ? 1 : 0;
+  d.cnt = p->cnt2;
+  d.scaleN = std::ldexp(1.0f, p->sN);
   return d;
 }
 
@@ -197,6 +202,10 @@ StatsInst base_stats(const dlm_problem* p, const Runner& R, int i) {
   s.inv_sQ = std::ldexp(1.0, -p->sQ);
   s.out = p->stats_out;
   s.certified = p->certified ? 1 : 0;
+  s.count_on = p->count_on ? 1 : 0;
+  s.cnt = p->cnt2;
+  s.inv_sN = std::ldexp(1.0, -p->sN);
+  s.count_M = p->count_M;
   return s;
 }
 
@@ -353,6 +362,7 @@ dlm_status write_tables(Runner& R) {
     it[i].accQ = p->accQ;
     it[i].seg_obj = R.seg_obj;
     it[i].xout = nullptr;
+    it[i].cnt = p->cnt;
     ss[i] = base_desc(p);
     ss[i].y = p->lam;
     ss[i].gamma = &p->state->gamma;
@@ -370,11 +380,17 @@ dlm_status write_tables(Runner& R) {
     u.y = p->y;
     u.acc = p->acc;
     u.iters_per_stage = p->ips;
-    u.inv_nmax = p->lay.n2max > 0 ? 1.0 / p->lay.n2max : 0.0;
+    u.inv_nmax = p->inv_hmax;
     u.inv_scaleG = std::ldexp(1.0, -p->sG);
     u.J = static_cast<int32_t>(p->J);
     u.precondition = p->opt.precondition ? 1 : 0;
     u.adaptive_restart = p->opt.restart ? 1 : 0;
+    u.count_on = p->count_on ? 1 : 0;
+    u.cnt = p->cnt;
+    u.cnt_rw = p->cnt;
+    u.inv_scaleN = std::ldexp(1.0, -p->sN);
+    u.count_M = p->count_M;
+    u.inv_h_count = p->inv_h_count;
     up[i] = u;
     st[i] = base_stats(p, R, i);
     st[i].lam = p->lam;
@@ -439,6 +455,8 @@ SweepLaunch launch_of(const Runner& R, const InstDesc* tab) {
   L.threads = R.threads;
   L.coop_max = R.coop_max;
   L.stream = R.stream;
+  L.count = false;
+  for (const dlm_problem* p : R.probs) L.count = L.count || p->count_on;
   L.units = R.h_units.empty() ? nullptr : R.units;
   L.nunits = static_cast<int32_t>(R.h_units.size());
   L.ctr = R.ctr;
@@ -578,6 +596,8 @@ void free_problem(dlm_problem* p) {
   cudaFree(p->lay.orig_off);
   cudaFree(p->lay.udeg);
   cudaFree(p->lay.n2);
+  cudaFree(p->cnt);
+  cudaFree(p->cnt2);
   void* ptrs[] = {p->b,         p->inv_n2,    p->lam,       p->y,         p->acc,   p->acc2,      p->accC,
                   p->accQ,      p->gamma_tab, p->calc_gamma, p->stats_out, p->state, p->inst_calc, p->st_calc};
   for (void* q : ptrs) cudaFree(q);
@@ -587,6 +607,39 @@ void free_problem(dlm_problem* p) {
   if (p->ev) cudaEventDestroy(p->ev);
   if (p->own_stream && p->stream) cudaStreamDestroy(p->stream);
   delete p;
+}
+
+// Per-coordinate curvature bounds and the steps built from them.  One
+// capacity family: A A^T = diag(n), n_j = sum_i a_ij^2 (Def. 1), so the step
+// of item j is gamma / n_j with row normalization and gamma / max_j n_j
+// otherwise (App. B.2).  A count row of ones adds the row and column
+// s_j = sum_i a_ij and the corner nnz; Gershgorin row sums n_j + |s_j| and
+// nnz + sum_j |s_j| then bound the curvature (the diagonal scaling by their
+// inverses is a valid preconditioner and their maximum bounds ||A||^2).
+dlm_status upload_steps(dlm_problem* p) {
+  const int64_t J = p->J;
+  std::vector<double> inv(J + 1, 0.0);
+  double hmax = 0.0, tot = 0.0;
+  for (int64_t j = 0; j < J; ++j) {
+    double h = p->lay.h_n2[j];
+    if (p->count_on) {
+      h += std::fabs(p->lay.h_s1[j]);
+      tot += std::fabs(p->lay.h_s1[j]);
+    }
+    inv[j] = h > 0 ? 1.0 / h : 0.0;
+    hmax = h > hmax ? h : hmax;
+  }
+  p->inv_h_count = 0.0;
+  if (p->count_on) {
+    const double hc = static_cast<double>(p->nnz) + tot;
+    p->inv_h_count = hc > 0 ? 1.0 / hc : 0.0;
+    inv[J] = p->inv_h_count;
+    hmax = hc > hmax ? hc : hmax;
+  }
+  p->inv_hmax = hmax > 0 ? 1.0 / hmax : 0.0;
+  CK(cudaMemcpyAsync(p->inv_n2, inv.data(), sizeof(double) * (J + 1), cudaMemcpyHostToDevice, p->stream));
+  CK(cudaStreamSynchronize(p->stream));
+  return DLM_OK;
 }
 
 dlm_status upload_schedule(dlm_problem* p) {
@@ -601,7 +654,7 @@ dlm_status upload_schedule(dlm_problem* p) {
                      p->stream));
   k_state_reset<<<1, 1, 0, p->stream>>>(p->state, p->gamma0);
   CK(cudaGetLastError());
-  k_warm<<<blocks_for(p->J), 256, 0, p->stream>>>(p->lam, p->lam, p->y, p->J, p->state);
+  k_warm<<<blocks_for(p->D()), 256, 0, p->stream>>>(p->lam, p->lam, p->y, p->D(), p->state);
   CK(cudaGetLastError());
   CK(cudaStreamSynchronize(p->stream));
   invalidate_graph(p->run);
@@ -617,10 +670,10 @@ dlm_status save_state(Runner& R, Saved* S) {
   CK(cudaStreamSynchronize(R.stream));
   for (dlm_problem* p : R.probs) {
     float *l = nullptr, *y = nullptr;
-    CK(dalloc(&l, p->J));
-    CK(dalloc(&y, p->J));
-    CK(cudaMemcpy(l, p->lam, sizeof(float) * p->J, cudaMemcpyDeviceToDevice));
-    CK(cudaMemcpy(y, p->y, sizeof(float) * p->J, cudaMemcpyDeviceToDevice));
+    CK(dalloc(&l, p->D()));
+    CK(dalloc(&y, p->D()));
+    CK(cudaMemcpy(l, p->lam, sizeof(float) * p->D(), cudaMemcpyDeviceToDevice));
+    CK(cudaMemcpy(y, p->y, sizeof(float) * p->D(), cudaMemcpyDeviceToDevice));
     DevState hs;
     CK(cudaMemcpy(&hs, p->state, sizeof(DevState), cudaMemcpyDeviceToHost));
     S->lam.push_back(l);
@@ -633,8 +686,9 @@ dlm_status restore_state(Runner& R, const Saved& S) {
   CK(cudaStreamSynchronize(R.stream));
   for (size_t i = 0; i < R.probs.size(); ++i) {
     dlm_problem* p = R.probs[i];
-    CK(cudaMemcpy(p->lam, S.lam[i], sizeof(float) * p->J, cudaMemcpyDeviceToDevice));
-    CK(cudaMemcpy(p->y, S.y[i], sizeof(float) * p->J, cudaMemcpyDeviceToDevice));
+    CK(cudaMemcpy(p->lam, S.lam[i], sizeof(float) * p->D(), cudaMemcpyDeviceToDevice));
+    CK(cudaMemcpy(p->y, S.y[i], sizeof(float) * p->D(), cudaMemcpyDeviceToDevice));
+    CK(cudaMemset(p->cnt, 0, sizeof(unsigned long long)));
     CK(cudaMemcpy(p->state, &S.st[i], sizeof(DevState), cudaMemcpyHostToDevice));
     CK(cudaMemset(p->acc, 0, sizeof(unsigned long long) * p->J));
   }
@@ -821,7 +875,10 @@ dlm_status dlm_create(const dlm_problem_desc* desc, void* stream, dlm_problem** 
   p->sG = fixed_point_shift(degm * (p->lay.max_abs_a > 0 ? p->lay.max_abs_a : 1.0) * xmax);
   p->sC = fixed_point_shift(degm * (p->lay.max_abs_c > 0 ? p->lay.max_abs_c : 1.0) * xmax);
   p->sQ = fixed_point_shift(degm * xmax * xmax);
-  if (p->sG < 0 || p->sC < 0 || p->sQ < 0) {
+  // sum x <= z per user on the simplex, z per edge on the box
+  const double nmaxx = static_cast<double>(p->kind == DLM_BOX ? nnz : p->lay.num_active_users);
+  p->sN = fixed_point_shift((nmaxx > 0 ? nmaxx : 1.0) * xmax);
+  if (p->sG < 0 || p->sC < 0 || p->sQ < 0 || p->sN < 0) {
     cleanup_tmp();
     free_problem(p);
     return fail(DLM_ERR_UNSUPPORTED, "item sums too large for 64-bit fixed point");
@@ -844,19 +901,21 @@ dlm_status dlm_create(const dlm_problem_desc* desc, void* stream, dlm_problem** 
 
   CKC(dalloc(&p->b, J));
   CKC(cudaMemcpyAsync(p->b, b, sizeof(double) * J, cudaMemcpyDeviceToDevice, p->stream));
-  CKC(dalloc(&p->inv_n2, J));
-  k_inv<<<blocks_for(J), 256, 0, p->stream>>>(p->lay.n2, p->inv_n2, J);
-  CKC(cudaGetLastError());
-  CKC(dalloc(&p->lam, J));
-  CKC(dalloc(&p->y, J));
+  CKC(dalloc(&p->inv_n2, J + 1));
+  CKC(dalloc(&p->lam, J + 1));
+  CKC(dalloc(&p->y, J + 1));
+  CKC(dalloc(&p->cnt, 1));
+  CKC(dalloc(&p->cnt2, 1));
+  CKC(cudaMemsetAsync(p->cnt, 0, sizeof(unsigned long long), p->stream));
+  CKC(cudaMemsetAsync(p->cnt2, 0, sizeof(unsigned long long), p->stream));
   CKC(dalloc(&p->acc, J));
   CKC(dalloc(&p->acc2, J));
   CKC(dalloc(&p->accC, J));
   CKC(dalloc(&p->accQ, J));
   for (unsigned long long* q : {p->acc, p->acc2, p->accC, p->accQ})
     CKC(cudaMemsetAsync(q, 0, sizeof(unsigned long long) * J, p->stream));
-  CKC(cudaMemsetAsync(p->lam, 0, sizeof(float) * J, p->stream));
-  CKC(cudaMemsetAsync(p->y, 0, sizeof(float) * J, p->stream));
+  CKC(cudaMemsetAsync(p->lam, 0, sizeof(float) * (J + 1), p->stream));
+  CKC(cudaMemsetAsync(p->y, 0, sizeof(float) * (J + 1), p->stream));
   CKC(dalloc(&p->gamma_tab, kMaxStages));
   CKC(dalloc(&p->calc_gamma, 1));
   CKC(dalloc(&p->stats_out, 8));
@@ -884,7 +943,8 @@ dlm_status dlm_create(const dlm_problem_desc* desc, void* stream, dlm_problem** 
   R.smemJ = static_cast<int>(J);
   cudaDeviceGetAttribute(&R.sms, cudaDevAttrMultiProcessorCount, p->device);
   p->h_gamma_tab.assign(kMaxStages, p->gamma0);
-  st = runner_configure(R, p->opt, true);
+  st = upload_steps(p);
+  if (st == DLM_OK) st = runner_configure(R, p->opt, true);
   if (st == DLM_OK) st = upload_schedule(p);
   if (st != DLM_OK) {
     free_problem(p);
@@ -904,6 +964,23 @@ dlm_status dlm_set_schedule(dlm_problem* p, double gamma0, double gamma_end, dou
   p->factor = factor;
   p->ips = iters_per_stage;
   return upload_schedule(p);
+}
+
+dlm_status dlm_set_count_limit(dlm_problem* p, double M) {
+  if (!p) return fail(DLM_ERR_INVALID_ARG, "null handle");
+  if (std::isnan(M) || M < 0) return fail(DLM_ERR_INVALID_ARG, "M must be >= 0 (INFINITY removes the constraint)");
+  CK(cudaStreamSynchronize(p->stream));
+  p->count_on = std::isfinite(M);
+  p->count_M = M;
+  // the count dual starts at 0; its accumulators are clear
+  CK(cudaMemset(p->lam + p->J, 0, sizeof(float)));
+  CK(cudaMemset(p->y + p->J, 0, sizeof(float)));
+  CK(cudaMemset(p->cnt, 0, sizeof(unsigned long long)));
+  CK(cudaMemset(p->cnt2, 0, sizeof(unsigned long long)));
+  dlm_status st = upload_steps(p);
+  if (st != DLM_OK) return st;
+  invalidate_graph(p->run);
+  return write_tables(p->run);
 }
 
 dlm_status dlm_set_options(dlm_problem* p, const dlm_options* opt) {
@@ -938,11 +1015,11 @@ dlm_status dlm_set_lambda(dlm_problem* p, const float* lambda0, int32_t memspace
   const float* src = lambda0;
   float* tmp = nullptr;
   if (memspace == DLM_MEM_HOST) {
-    CK(dalloc(&tmp, p->J));
-    CK(cudaMemcpyAsync(tmp, lambda0, sizeof(float) * p->J, cudaMemcpyHostToDevice, p->stream));
+    CK(dalloc(&tmp, p->D()));
+    CK(cudaMemcpyAsync(tmp, lambda0, sizeof(float) * p->D(), cudaMemcpyHostToDevice, p->stream));
     src = tmp;
   }
-  k_warm<<<blocks_for(p->J), 256, 0, p->stream>>>(src, p->lam, p->y, p->J, p->state);
+  k_warm<<<blocks_for(p->D()), 256, 0, p->stream>>>(src, p->lam, p->y, p->D(), p->state);
   cudaError_t e = cudaGetLastError();
   if (tmp) {
     cudaStreamSynchronize(p->stream);
@@ -1042,7 +1119,7 @@ dlm_status dlm_calculate(dlm_problem* p, const float* lambda, double gamma, doub
 
 dlm_status dlm_get_lambda(dlm_problem* p, float* out, int32_t memspace) {
   if (!p || !out) return fail(DLM_ERR_INVALID_ARG, "null argument");
-  CK(cudaMemcpyAsync(out, p->lam, sizeof(float) * p->J,
+  CK(cudaMemcpyAsync(out, p->lam, sizeof(float) * p->D(),
                      memspace == DLM_MEM_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, p->stream));
   if (memspace == DLM_MEM_HOST) CK(cudaStreamSynchronize(p->stream));
   return DLM_OK;
@@ -1088,8 +1165,8 @@ dlm_status dlm_get_x(dlm_problem* p, float* out, int32_t memspace) {
 dlm_status dlm_get_state(dlm_problem* p, float* lam, float* y, dlm_state* s, int32_t memspace) {
   if (!p) return fail(DLM_ERR_INVALID_ARG, "null handle");
   const cudaMemcpyKind k = memspace == DLM_MEM_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
-  if (lam) CK(cudaMemcpyAsync(lam, p->lam, sizeof(float) * p->J, k, p->stream));
-  if (y) CK(cudaMemcpyAsync(y, p->y, sizeof(float) * p->J, k, p->stream));
+  if (lam) CK(cudaMemcpyAsync(lam, p->lam, sizeof(float) * p->D(), k, p->stream));
+  if (y) CK(cudaMemcpyAsync(y, p->y, sizeof(float) * p->D(), k, p->stream));
   CK(cudaStreamSynchronize(p->stream));
   if (s) {
     DevState hs;
@@ -1107,8 +1184,8 @@ dlm_status dlm_set_state(dlm_problem* p, const float* lam, const float* y, const
   if (s->iter < 0 || s->stage < 0) return fail(DLM_ERR_INVALID_ARG, "bad state");
   const cudaMemcpyKind k = memspace == DLM_MEM_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
   CK(cudaStreamSynchronize(p->stream));
-  CK(cudaMemcpy(p->lam, lam, sizeof(float) * p->J, k));
-  CK(cudaMemcpy(p->y, y, sizeof(float) * p->J, k));
+  CK(cudaMemcpy(p->lam, lam, sizeof(float) * p->D(), k));
+  CK(cudaMemcpy(p->y, y, sizeof(float) * p->D(), k));
   DevState hs{};
   hs.iter = s->iter;
   hs.theta = s->theta;
@@ -1144,7 +1221,7 @@ dlm_status dlm_ws_features(dlm_problem* p, const float* lam_prev, double gamma, 
     cudaFree(mx);
     cudaFree(sum);
   };
-  if (dalloc(&grad, p->J) != cudaSuccess || dalloc(&deg, p->J) != cudaSuccess || dalloc(&mx, p->J) != cudaSuccess ||
+  if (dalloc(&grad, p->D()) != cudaSuccess || dalloc(&deg, p->J) != cudaSuccess || dalloc(&mx, p->J) != cudaSuccess ||
       dalloc(&sum, p->J) != cudaSuccess) {
     release();
     return fail(DLM_ERR_OOM, "device allocation failed");

@@ -7,6 +7,7 @@
 #include <stdint.h>
 
 #include <string>
+#include <vector>
 
 #include "dlm.h"
 
@@ -45,6 +46,13 @@ struct UpdInst {
   int32_t J;
   int32_t precondition;
   int32_t adaptive_restart;
+  // global count constraint sum x <= M (dual entry J)
+  int32_t count_on;
+  const unsigned long long* cnt;  // fixed-point sum of all x at y
+  unsigned long long* cnt_rw;     // the same, reset here
+  double inv_scaleN;
+  double count_M;
+  double inv_h_count;             // 1 / curvature bound of the count row (row normalization)
 };
 
 // Per-instance view for the sweep kernels (device memory; one table for the
@@ -67,10 +75,12 @@ struct InstDesc {
   unsigned long long* accQ; // [J] fixed-point sum x^2 (stats)
   double* seg_obj;          // [tasks] FP64 objective partial per (CTA, instance) segment (stats)
   float* xout;              // caller-order x or nullptr (stats)
-  float scaleG, scaleC, scaleQ;
+  unsigned long long* cnt;  // fixed-point sum of all x (global count constraint) or nullptr
+  float scaleG, scaleC, scaleQ, scaleN;
   float z;
   int32_t J;
   int32_t kind;
+  int32_t count_on;         // 1: the dual vector has J + 1 entries, y[J] is the count dual mu
 };
 
 // A task: slices first, first + stride, ... (< end) of instance `inst`.  The
@@ -95,6 +105,7 @@ struct SweepLaunch {
   const Task* units;        // device [nunits] work units (stride 1), ordered by instance
   int32_t nunits;
   unsigned* ctr;            // device [2]: next unit, finished CTAs (zero between launches)
+  bool count;               // some instance has a global count constraint (its own instantiation)
 };
 constexpr int kDefaultCoopMax = 12;
 
@@ -108,10 +119,14 @@ struct StatsInst {
   int32_t nseg;
   int32_t J;
   double inv_sG, inv_sC, inv_sQ;
-  float* grad_out;            // optional [J]
+  float* grad_out;            // optional [J] (+1 with the count constraint)
   double* out;                // [8]: g, P, rel_gap, uncert_gap, max_viol, obj, iter, status
   const DevState* state;
   int32_t certified;          // 0: scaled point not certified (EQ simplex or a < 0)
+  int32_t count_on;
+  unsigned long long* cnt;    // fixed-point sum of all x at lam (reset here)
+  double inv_sN;
+  double count_M;
 };
 
 // Sets the thread-local message returned by dlm_last_error (api.cu).
@@ -141,6 +156,7 @@ struct LayoutOut {
   int64_t num_active_users = 0, nslices = 0, padded_nnz = 0;
   double* n2 = nullptr;          // [J] sum_i a_ij^2
   double n2max = 0;
+  std::vector<double> h_n2, h_s1;  // host copies: sum_i a_ij^2, sum_i a_ij
   int64_t max_item_deg = 0;
   double max_abs_a = 0, max_abs_c = 0;
   bool a_nonneg = true;

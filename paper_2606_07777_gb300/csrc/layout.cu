@@ -181,12 +181,13 @@ __global__ void k_gather(const int64_t* rp, const int32_t* col, const void* c, c
   }
 }
 
-// sum_i a_ij^2 per item in 64-bit fixed point (exact, order independent).
+// sum_i a_ij^2 (or sum_i a_ij) per item in 64-bit fixed point (exact, order
+// independent).
 // With J <= kSmemItems each block sums its contiguous edge range in shared
 // memory and flushes once per item.
 constexpr int kSmemItems = 16384;
 __global__ void k_item_sq(const int32_t* col, const void* a, bool bf16, int64_t nnz, int64_t J, float scale,
-                          unsigned long long* acc) {
+                          bool square, unsigned long long* acc) {
   extern __shared__ unsigned long long sacc[];
   const bool sm = J <= kSmemItems;
   if (sm) {
@@ -197,7 +198,7 @@ __global__ void k_item_sq(const int32_t* col, const void* a, bool bf16, int64_t 
   const int64_t e0 = blockIdx.x * per, e1 = e0 + per < nnz ? e0 + per : nnz;
   for (int64_t e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
     const float av = load_val(a, e, bf16);
-    const unsigned long long q = static_cast<unsigned long long>(__float2ll_rn(av * av * scale));
+    const unsigned long long q = static_cast<unsigned long long>(__float2ll_rn((square ? av * av : av) * scale));
     if (sm)
       atomicAdd(&sacc[col[e]], q);
     else
@@ -387,17 +388,31 @@ dlm_status build_layout(int64_t I, int64_t J, int64_t nnz, const int64_t* rp, co
   if (nnz > 0) {
     const int g = static_cast<int>(nnz / 8192 + 1 < 608 ? nnz / 8192 + 1 : 608);
     const size_t smem = J <= kSmemItems ? sizeof(unsigned long long) * J : 0;
-    k_item_sq<<<g, 1024, smem, s>>>(col, a, bf16, nnz, J, std::ldexp(1.0f, ssq), sq);
+    k_item_sq<<<g, 1024, smem, s>>>(col, a, bf16, nnz, J, std::ldexp(1.0f, ssq), true, sq);
   }
   DLM_CK(cudaGetLastError());
   if (J > 0) k_fix_to_double<<<grid_for(J), kT, 0, s>>>(sq, J, std::ldexp(1.0, -ssq), out->n2);
   DLM_CK(cudaGetLastError());
+  out->h_n2.assign(J > 0 ? J : 1, 0.0);
+  DLM_CK(cudaMemcpyAsync(out->h_n2.data(), out->n2, sizeof(double) * out->h_n2.size(), cudaMemcpyDeviceToHost, s));
+  // ---- s_j = sum_i a_ij (the coupling of item rows with a count row) ----
+  ssq = fixed_point_shift(static_cast<double>(out->max_item_deg) * out->max_abs_a);
+  DLM_CK(cudaMemsetAsync(sq, 0, sizeof(unsigned long long) * (J > 0 ? J : 1), s));
+  if (nnz > 0) {
+    const int g = static_cast<int>(nnz / 8192 + 1 < 608 ? nnz / 8192 + 1 : 608);
+    const size_t smem = J <= kSmemItems ? sizeof(unsigned long long) * J : 0;
+    k_item_sq<<<g, 1024, smem, s>>>(col, a, bf16, nnz, J, std::ldexp(1.0f, ssq), false, sq);
+  }
+  DLM_CK(cudaGetLastError());
   {
-    std::vector<double> n2(J > 0 ? J : 1);
-    DLM_CK(cudaMemcpyAsync(n2.data(), out->n2, sizeof(double) * n2.size(), cudaMemcpyDeviceToHost, s));
+    std::vector<unsigned long long> q(J > 0 ? J : 1);
+    DLM_CK(cudaMemcpyAsync(q.data(), sq, sizeof(unsigned long long) * q.size(), cudaMemcpyDeviceToHost, s));
     DLM_CK(cudaStreamSynchronize(s));
+    out->h_s1.assign(J > 0 ? J : 1, 0.0);
+    for (int64_t j = 0; j < J; ++j)
+      out->h_s1[j] = static_cast<double>(static_cast<long long>(q[j])) * std::ldexp(1.0, -ssq);
     out->n2max = 0;
-    for (int64_t j = 0; j < J; ++j) out->n2max = n2[j] > out->n2max ? n2[j] : out->n2max;
+    for (int64_t j = 0; j < J; ++j) out->n2max = out->h_n2[j] > out->n2max ? out->h_n2[j] : out->n2max;
   }
   goto done;
 

@@ -49,6 +49,7 @@ constexpr unsigned kFull = 0xffffffffu;
 // lane (element index 4 q .. 4 q + 3 of the stream, 16-byte aligned).
 struct F32Pair {
   using T = float2;
+  static constexpr bool kCount = false;
   __device__ __forceinline__ static void get(const T& w, float& c, float& a) {
     c = w.x;
     a = w.y;
@@ -62,6 +63,7 @@ struct F32Pair {
 };
 struct BF16Pair {
   using T = uint32_t;
+  static constexpr bool kCount = false;
   __device__ __forceinline__ static void get(const T& w, float& c, float& a) {
     c = __uint_as_float(w << 16);
     a = __uint_as_float(w & 0xffff0000u);
@@ -73,6 +75,15 @@ struct BF16Pair {
     get(v.z, c[2], a[2]);
     get(v.w, c[3], a[3]);
   }
+};
+
+// The same value layouts for instances with a global count constraint: the
+// count dual mu floors the threshold and every deposit adds x to the count.
+// (A separate instantiation, so that instances without one keep the plain
+// code: the register and comparison cost measured 4 % on the sweep.)
+template <class Base>
+struct Counted : Base {
+  static constexpr bool kCount = true;
 };
 
 // Position of edge k of lane t inside a slice of width w (w4 = w / 4 groups
@@ -117,15 +128,19 @@ __device__ __forceinline__ F2 f2_threshold(F2 sum, float gzh, float gzl, int n) 
 
 struct Seg {
   float gamma, invg, gz, gzl, z;
-  float scaleG, scaleC, scaleQ;
+  float scaleG, scaleC, scaleQ, scaleN;
+  float mu;  // count dual (0 without a count constraint): the floor of the threshold
   int kind;
+  int count;
 };
 
 // Contributions of one edge with x > 0.
-template <bool STATS>
+template <class P, bool STATS>
 __device__ __forceinline__ void deposit(const Seg& S, int j, float c, float a, float x, unsigned long long* accG,
-                                        unsigned long long* accC, unsigned long long* accQ, float& ob) {
+                                        unsigned long long* accC, unsigned long long* accQ, float& ob,
+                                        unsigned long long& cn) {
   atomicAdd(&accG[j], fixp(a * x, S.scaleG));
+  if (P::kCount) cn += fixp(x, S.scaleN);
   if (STATS) {
     atomicAdd(&accC[j], fixp(c * x, S.scaleC));
     atomicAdd(&accQ[j], fixp(x * x, S.scaleQ));
@@ -133,12 +148,14 @@ __device__ __forceinline__ void deposit(const Seg& S, int j, float c, float a, f
   }
 }
 
-// x of one edge given the user's threshold (general mode).
-__device__ __forceinline__ float x_general(const Seg& S, bool box, bool zero, float tau, float taul, float c,
-                                           float a, float y) {
+// x of one edge given the user's threshold (tau, taul): (u - tau) / gamma
+// clipped at 0 (and at z for the box).  On the inequality simplex with the
+// threshold at its floor, and for the box, the caller passes tau = mu (the
+// count dual; 0 without a count constraint), taul = 0.
+__device__ __forceinline__ float x_general(const Seg& S, bool box, float tau, float taul, float c, float a,
+                                           float y) {
   const F2 up = u_pair(c, a, y);
-  if (box) return fminf(fmaxf((up.h + up.l) * S.invg, 0.f), S.z);
-  if (zero) return fmaxf(up.h + up.l, 0.f) * S.invg;
+  if (box) return fminf(fmaxf(((up.h - tau) + (up.l - taul)) * S.invg, 0.f), S.z);
   return fmaxf((up.h - tau) + (up.l - taul), 0.f) * S.invg;
 }
 
@@ -166,7 +183,7 @@ __device__ __forceinline__ void coop_user(const Seg& S, const float* __restrict_
                                           unsigned long long* accC, unsigned long long* accQ,
                                           const int32_t* __restrict__ cp0, const typename P::T* __restrict__ vp0,
                                           int w, int w4, int t, float tau0, bool exact, float& tau, float& taul,
-                                          bool& zero, float& ob) {
+                                          bool& zero, float& ob, unsigned long long& cn) {
   const int lane = threadIdx.x & 31;
   const bool box = S.kind == DLM_BOX;
   const bool eq = S.kind == DLM_SIMPLEX_EQ;
@@ -204,7 +221,7 @@ __device__ __forceinline__ void coop_user(const Seg& S, const float* __restrict_
         tau = tn;
       }
     }
-    zero = !eq && tau <= 0.f;
+    zero = !eq && tau <= (P::kCount ? S.mu : 0.f);
     if (!zero) {
       F2 sum{0.f, 0.f};
       int n = 0;
@@ -223,7 +240,7 @@ __device__ __forceinline__ void coop_user(const Seg& S, const float* __restrict_
         n += __shfl_xor_sync(kFull, n, o);
       }
       const F2 t2 = f2_threshold(sum, S.gz, S.gzl, n > 0 ? n : 1);
-      if (!eq && t2.h + t2.l <= 0.f) {
+      if (!eq && t2.h + t2.l <= (P::kCount ? S.mu : 0.f)) {
         zero = true;
       } else {
         tau = t2.h;
@@ -231,13 +248,16 @@ __device__ __forceinline__ void coop_user(const Seg& S, const float* __restrict_
       }
     }
   }
-  if (zero) tau = taul = 0.f;
+  if (zero) {
+    tau = (P::kCount ? S.mu : 0.f);
+    taul = 0.f;
+  }
   for (int k = lane; k < w; k += 32) {
     int j;
     float c, a;
     if (uval(k, j, c, a) > tau) {
-      const float x = x_general(S, box, zero, tau, taul, c, a, ys[j]);
-      if (x > 0.f) deposit<STATS>(S, j, c, a, x, accG, accC, accQ, ob);
+      const float x = x_general(S, box, tau, taul, c, a, ys[j]);
+      if (x > 0.f) deposit<P, STATS>(S, j, c, a, x, accG, accC, accQ, ob, cn);
     }
   }
 }
@@ -275,7 +295,8 @@ template <class P, bool STATS>
 __device__ __forceinline__ float4 rows_upto3(const Seg S, const float* __restrict__ ys, unsigned long long* accG,
                                           unsigned long long* accC, unsigned long long* accQ,
                                           const int32_t* __restrict__ col0, const typename P::T* __restrict__ ca0,
-                                          int w4, int r, int i0, int i1, int i2, float tau, bool eq) {
+                                          int w4, int r, int i0, int i1, int i2, float tau, bool eq,
+                                          unsigned long long& cn) {
   const int lane = threadIdx.x & 31;
   int jr[3];
   float cr[3], ar[3];
@@ -289,7 +310,7 @@ __device__ __forceinline__ float4 rows_upto3(const Seg S, const float* __restric
       P::get(__ldg(ca0 + el), cr[i], ar[i]);
     }
   }
-  bool zero = !eq && tau <= 0.f;
+  bool zero = !eq && tau <= (P::kCount ? S.mu : 0.f);
   float taul = 0.f;
   if (!zero) {
     F2 sum{0.f, 0.f};
@@ -297,20 +318,23 @@ __device__ __forceinline__ float4 rows_upto3(const Seg S, const float* __restric
     for (int i = 0; i < 3; ++i)
       if (i < r) sum = f2_add(sum, u_pair(cr[i], ar[i], ys[jr[i]]));
     const F2 t2 = f2_threshold(sum, S.gz, S.gzl, r);
-    if (!eq && t2.h + t2.l <= 0.f) {
+    if (!eq && t2.h + t2.l <= (P::kCount ? S.mu : 0.f)) {
       zero = true;
     } else {
       tau = t2.h;
       taul = t2.l;
     }
   }
-  if (zero) tau = taul = 0.f;
+  if (zero) {
+    tau = (P::kCount ? S.mu : 0.f);
+    taul = 0.f;
+  }
   float ob = 0.f;
 #pragma unroll
   for (int i = 0; i < 3; ++i) {
     if (i < r) {
-      const float x = x_general(S, false, zero, tau, taul, cr[i], ar[i], ys[jr[i]]);
-      if (x > 0.f) deposit<STATS>(S, jr[i], cr[i], ar[i], x, accG, accC, accQ, ob);
+      const float x = x_general(S, false, tau, taul, cr[i], ar[i], ys[jr[i]]);
+      if (x > 0.f) deposit<P, STATS>(S, jr[i], cr[i], ar[i], x, accG, accC, accQ, ob, cn);
     }
   }
   return make_float4(tau, taul, zero ? 1.f : 0.f, ob);
@@ -327,7 +351,8 @@ __device__ __forceinline__ float4 rows_upto3(const Seg S, const float* __restric
 template <class P, bool STATS, bool REG3 = false>
 __device__ __forceinline__ void do_slice(const InstDesc& D, const Seg& S, const float* __restrict__ ys,
                                          unsigned long long* accG, unsigned long long* accC,
-                                         unsigned long long* accQ, int64_t s, int coop_max, double& wobj) {
+                                         unsigned long long* accQ, int64_t s, int coop_max, double& wobj,
+                                         unsigned long long& cn) {
   const int lane = threadIdx.x & 31;
   const int64_t off = __ldg(D.slice_off + s);
   const int w = __ldg(D.slice_w + s);
@@ -375,8 +400,8 @@ __device__ __forceinline__ void do_slice(const InstDesc& D, const Seg& S, const 
   bool zero = box;
   int r = 0;
   if (box) {
-    mode = (v0 > 0.f) ? 3 : 0;
-  } else if (v0 == -INFINITY || (!eq && v0 <= 0.f)) {
+    mode = (v0 > (P::kCount ? S.mu : 0.f)) ? 3 : 0;
+  } else if (v0 == -INFINITY || (!eq && v0 <= (P::kCount ? S.mu : 0.f))) {
     mode = 0;
   } else {
     float sm = v0;
@@ -397,12 +422,12 @@ __device__ __forceinline__ void do_slice(const InstDesc& D, const Seg& S, const 
         }
       }
     }
-    mode = (r == 1 && (eq || tau >= 0.f)) ? 1 : (r < 4 ? 2 : 3);
+    mode = (r == 1 && (eq || tau >= (P::kCount ? S.mu : 0.f))) ? 1 : (r < 4 ? 2 : 3);
   }
 
   float ob = 0.f;
   if (mode == 2 && REG3) {
-    const float4 res = rows_upto3<P, STATS>(S, ys, accG, accC, accQ, col0, ca0, w4, r, i0, i1, i2, tau, eq);
+    const float4 res = rows_upto3<P, STATS>(S, ys, accG, accC, accQ, col0, ca0, w4, r, i0, i1, i2, tau, eq, cn);
     tau = res.x;
     taul = res.y;
     zero = res.z != 0.f;
@@ -411,7 +436,7 @@ __device__ __forceinline__ void do_slice(const InstDesc& D, const Seg& S, const 
     // The active set is the r <= 3 recorded edges (on the inequality simplex
     // with tau <= 0: those of them with u > 0).  Threshold over them in pair
     // arithmetic, then x on each (the edges are re-read from L1).
-    zero = !eq && tau <= 0.f;
+    zero = !eq && tau <= (P::kCount ? S.mu : 0.f);
     if (!zero) {
       F2 sum{0.f, 0.f};
       for (int i = 0; i < r; ++i) {
@@ -422,28 +447,31 @@ __device__ __forceinline__ void do_slice(const InstDesc& D, const Seg& S, const 
         sum = f2_add(sum, u_pair(c, a, ys[j]));
       }
       const F2 t2 = f2_threshold(sum, S.gz, S.gzl, r);
-      if (!eq && t2.h + t2.l <= 0.f) {
+      if (!eq && t2.h + t2.l <= (P::kCount ? S.mu : 0.f)) {
         zero = true;
       } else {
         tau = t2.h;
         taul = t2.l;
       }
     }
-    if (zero) tau = taul = 0.f;
+    if (zero) {
+    tau = (P::kCount ? S.mu : 0.f);
+    taul = 0.f;
+  }
     for (int i = 0; i < r; ++i) {
       const int el = sell_el(i == 0 ? i0 : (i == 1 ? i1 : i2), lane, w4);
       const int j = __ldg(col0 + el);
       float c, a;
       P::get(__ldg(ca0 + el), c, a);
-      const float x = x_general(S, false, zero, tau, taul, c, a, ys[j]);
-      if (x > 0.f) deposit<STATS>(S, j, c, a, x, accG, accC, accQ, ob);
+      const float x = x_general(S, false, tau, taul, c, a, ys[j]);
+      if (x > 0.f) deposit<P, STATS>(S, j, c, a, x, accG, accC, accQ, ob, cn);
     }
   } else if (mode == 1) {
     const int el = sell_el(i0, lane, w4);
     const int j = __ldg(col0 + el);
     float c, a;
     P::get(__ldg(ca0 + el), c, a);
-    deposit<STATS>(S, j, c, a, S.z, accG, accC, accQ, ob);
+    deposit<P, STATS>(S, j, c, a, S.z, accG, accC, accQ, ob, cn);
   }
 
   // Mode 3 (four or more active edges, or the box): the whole warp per user
@@ -458,7 +486,7 @@ __device__ __forceinline__ void do_slice(const InstDesc& D, const Seg& S, const 
       const float tt = __shfl_sync(kFull, tau, t);
       float ta, tl;
       bool zr;
-      coop_user<P, STATS>(S, ys, accG, accC, accQ, col0, ca0, w, w4, t, tt, false, ta, tl, zr, ob);
+      coop_user<P, STATS>(S, ys, accG, accC, accQ, col0, ca0, w, w4, t, tt, false, ta, tl, zr, ob, cn);
       if (lane == t) {
         tau = ta;
         taul = tl;
@@ -489,7 +517,7 @@ __device__ __forceinline__ void do_slice(const InstDesc& D, const Seg& S, const 
         if (tn == tau) break;
         tau = tn;
       }
-      zero = !eq && tau <= 0.f;
+      zero = !eq && tau <= (P::kCount ? S.mu : 0.f);
       if (!zero) {
         // the threshold over the active set in pair arithmetic
         F2 sum{0.f, 0.f};
@@ -517,7 +545,7 @@ __device__ __forceinline__ void do_slice(const InstDesc& D, const Seg& S, const 
           visit(__ldg(col0 + el), c, a);
         }
         const F2 t2 = f2_threshold(sum, S.gz, S.gzl, n > 0 ? n : 1);
-        if (!eq && t2.h + t2.l <= 0.f) {
+        if (!eq && t2.h + t2.l <= (P::kCount ? S.mu : 0.f)) {
           zero = true;
         } else {
           tau = t2.h;
@@ -525,7 +553,10 @@ __device__ __forceinline__ void do_slice(const InstDesc& D, const Seg& S, const 
         }
       }
     }
-    if (zero) tau = taul = 0.f;
+    if (zero) {
+    tau = (P::kCount ? S.mu : 0.f);
+    taul = 0.f;
+  }
     // x on the active edges (u > tau; for the box and tau = 0, u > 0)
     for (int k = 0; k < w; ++k) {
       const int el = sell_el(k, lane, w4);
@@ -533,8 +564,8 @@ __device__ __forceinline__ void do_slice(const InstDesc& D, const Seg& S, const 
       float c, a;
       P::get(__ldg(ca0 + el), c, a);
       if (-fmaf(a, ys[j], c) > tau) {
-        const float x = x_general(S, box, zero, tau, taul, c, a, ys[j]);
-        if (x > 0.f) deposit<STATS>(S, j, c, a, x, accG, accC, accQ, ob);
+        const float x = x_general(S, box, tau, taul, c, a, ys[j]);
+        if (x > 0.f) deposit<P, STATS>(S, j, c, a, x, accG, accC, accQ, ob, cn);
       }
     }
   }
@@ -554,7 +585,7 @@ __device__ __forceinline__ void do_slice(const InstDesc& D, const Seg& S, const 
           const int j = __ldg(col0 + el);
           float c, a;
           P::get(__ldg(ca0 + el), c, a);
-          if (-fmaf(a, ys[j], c) > tau) x = x_general(S, box, zero, tau, taul, c, a, ys[j]);
+          if (-fmaf(a, ys[j], c) > tau) x = x_general(S, box, tau, taul, c, a, ys[j]);
         }
         D.xout[o + k] = x;
       }
@@ -607,8 +638,12 @@ __global__ void __launch_bounds__(kSweepThreads, 1)
       S.scaleG = sD.scaleG;
       S.scaleC = sD.scaleC;
       S.scaleQ = sD.scaleQ;
+      S.scaleN = sD.scaleN;
       S.kind = sD.kind;
+      S.count = sD.count_on;
+      S.mu = sD.count_on ? sD.y[J] : 0.f;
     }
+    unsigned long long cn = 0ull;
     if (threadIdx.x == 0) s_next = 0;
     __syncthreads();
     double wobj = 0.0;
@@ -618,7 +653,7 @@ __global__ void __launch_bounds__(kSweepThreads, 1)
         // static order: the FP64 objective partials are summed in a fixed order
         const int64_t step = static_cast<int64_t>(T.stride) * nw;
         for (int64_t s = T.first + static_cast<int64_t>(T.stride) * warp; s < T.end; s += step)
-          do_slice<P, STATS>(sD, S, ys, accG, accC, accQ, s, coop_max, wobj);
+          do_slice<P, STATS>(sD, S, ys, accG, accC, accQ, s, coop_max, wobj, cn);
       } else {
         // dynamic order within the CTA (item sums are exact, so the order of
         // slices does not change any result)
@@ -628,7 +663,7 @@ __global__ void __launch_bounds__(kSweepThreads, 1)
           if (lane == 0) i = atomicAdd(&s_next, 1ull);
           i = __shfl_sync(kFull, i, 0);
           if (i >= nsl) break;
-          do_slice<P, STATS>(sD, S, ys, accG, accC, accQ, T.first + i * T.stride, coop_max, wobj);
+          do_slice<P, STATS>(sD, S, ys, accG, accC, accQ, T.first + i * T.stride, coop_max, wobj, cn);
         }
         __syncthreads();
         if (threadIdx.x == 0) s_next = 0;
@@ -639,6 +674,11 @@ __global__ void __launch_bounds__(kSweepThreads, 1)
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) wobj += __shfl_xor_sync(kFull, wobj, o);
       if (lane == 0) wsum[warp] = wobj;
+    }
+    if (P::kCount && sD.count_on) {
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) cn += __shfl_xor_sync(kFull, cn, o);
+      if (lane == 0 && cn) atomicAdd(sD.cnt, cn);
     }
     __syncthreads();
     for (int j = threadIdx.x; j < J; j += blockDim.x) {
@@ -682,6 +722,7 @@ __global__ void __launch_bounds__(kSweepThreads, 1)
   int cur = -1;
   Seg S{};
   double wobj = 0.0;
+  unsigned long long cn = 0ull;
   for (;;) {
     if (threadIdx.x == 0) {
       s_unit = atomicAdd(ctr, 1u);
@@ -693,6 +734,12 @@ __global__ void __launch_bounds__(kSweepThreads, 1)
     const int inst = out_of_work ? -1 : units[u].inst;
     if (out_of_work || inst != cur) {
       if (cur >= 0) {
+        if (P::kCount && sD.count_on) {
+#pragma unroll
+          for (int o = 16; o > 0; o >>= 1) cn += __shfl_xor_sync(kFull, cn, o);
+          if (lane == 0 && cn) atomicAdd(sD.cnt, cn);
+        }
+        cn = 0ull;
         for (int j = threadIdx.x; j < sD.J; j += blockDim.x) {
           const unsigned long long v = accG[j];
           if (v) atomicAdd(sD.acc + j, v);
@@ -716,7 +763,10 @@ __global__ void __launch_bounds__(kSweepThreads, 1)
       S.scaleG = sD.scaleG;
       S.scaleC = sD.scaleC;
       S.scaleQ = sD.scaleQ;
+      S.scaleN = sD.scaleN;
       S.kind = sD.kind;
+      S.count = sD.count_on;
+      S.mu = sD.count_on ? sD.y[sD.J] : 0.f;
       cur = inst;
       __syncthreads();
     }
@@ -727,7 +777,7 @@ __global__ void __launch_bounds__(kSweepThreads, 1)
       if (lane == 0) i = static_cast<int64_t>(atomicAdd(&s_next, 1ull));
       i = __shfl_sync(kFull, i, 0);
       if (i >= nsl) break;
-      do_slice<P, false, true>(sD, S, ys, accG, nullptr, nullptr, T.first + i, coop_max, wobj);
+      do_slice<P, false, true>(sD, S, ys, accG, nullptr, nullptr, T.first + i, coop_max, wobj, cn);
     }
     __syncthreads();
   }
@@ -760,47 +810,40 @@ size_t sweep_smem_limit() {
   return optin > 1024 ? static_cast<size_t>(optin - 1024) : 0;  // room for static shared memory
 }
 
-cudaError_t sweep_prepare(bool bf16) {
-  const int lim = static_cast<int>(sweep_smem_limit());
-  cudaError_t e =
-      bf16 ? cudaFuncSetAttribute(&sweep_dyn_kernel<BF16Pair>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim)
-           : cudaFuncSetAttribute(&sweep_dyn_kernel<F32Pair>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+template <class P>
+cudaError_t prepare_policy(int lim) {
+  cudaError_t e = cudaFuncSetAttribute(&sweep_dyn_kernel<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
   if (e != cudaSuccess) return e;
-  if (bf16) {
-    e = cudaFuncSetAttribute(kernel_of<BF16Pair, false>(), cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
-    if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(kernel_of<BF16Pair, true>(), cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
-  } else {
-    e = cudaFuncSetAttribute(kernel_of<F32Pair, false>(), cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
-    if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(kernel_of<F32Pair, true>(), cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
-  }
-  return e;
+  e = cudaFuncSetAttribute(kernel_of<P, false>(), cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(kernel_of<P, true>(), cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
 }
 
-cudaError_t launch_sweep(const SweepLaunch& L, bool stats, bool bf16) {
+template <class P>
+cudaError_t launch_policy(const SweepLaunch& L, bool stats) {
   const size_t sm = sweep_smem_bytes(L.smemJ, stats);
   const int th = L.threads > 0 ? L.threads : kSweepThreads;
   const int cm = L.coop_max;
-  if (!stats && L.units != nullptr) {
-    if (bf16)
-      sweep_dyn_kernel<BF16Pair><<<L.grid, th, sm, L.stream>>>(L.inst, L.units, L.nunits, L.ctr, L.smemJ, cm);
-    else
-      sweep_dyn_kernel<F32Pair><<<L.grid, th, sm, L.stream>>>(L.inst, L.units, L.nunits, L.ctr, L.smemJ, cm);
-    return cudaGetLastError();
-  }
-  if (bf16) {
-    if (stats)
-      sweep_kernel<BF16Pair, true><<<L.grid, th, sm, L.stream>>>(L.inst, L.tasks, L.cta_task, L.smemJ, cm);
-    else
-      sweep_kernel<BF16Pair, false><<<L.grid, th, sm, L.stream>>>(L.inst, L.tasks, L.cta_task, L.smemJ, cm);
-  } else {
-    if (stats)
-      sweep_kernel<F32Pair, true><<<L.grid, th, sm, L.stream>>>(L.inst, L.tasks, L.cta_task, L.smemJ, cm);
-    else
-      sweep_kernel<F32Pair, false><<<L.grid, th, sm, L.stream>>>(L.inst, L.tasks, L.cta_task, L.smemJ, cm);
-  }
+  if (!stats && L.units != nullptr)
+    sweep_dyn_kernel<P><<<L.grid, th, sm, L.stream>>>(L.inst, L.units, L.nunits, L.ctr, L.smemJ, cm);
+  else if (stats)
+    sweep_kernel<P, true><<<L.grid, th, sm, L.stream>>>(L.inst, L.tasks, L.cta_task, L.smemJ, cm);
+  else
+    sweep_kernel<P, false><<<L.grid, th, sm, L.stream>>>(L.inst, L.tasks, L.cta_task, L.smemJ, cm);
   return cudaGetLastError();
+}
+
+cudaError_t sweep_prepare(bool bf16) {
+  const int lim = static_cast<int>(sweep_smem_limit());
+  cudaError_t e = bf16 ? prepare_policy<BF16Pair>(lim) : prepare_policy<F32Pair>(lim);
+  if (e != cudaSuccess) return e;
+  return bf16 ? prepare_policy<Counted<BF16Pair>>(lim) : prepare_policy<Counted<F32Pair>>(lim);
+}
+
+cudaError_t launch_sweep(const SweepLaunch& L, bool stats, bool bf16) {
+  if (L.count)
+    return bf16 ? launch_policy<Counted<BF16Pair>>(L, stats) : launch_policy<Counted<F32Pair>>(L, stats);
+  return bf16 ? launch_policy<BF16Pair>(L, stats) : launch_policy<F32Pair>(L, stats);
 }
 
 }  // namespace dlm

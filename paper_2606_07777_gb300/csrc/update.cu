@@ -69,16 +69,22 @@ __global__ void __launch_bounds__(kUpdThreads) fista_update_kernel(const UpdInst
   const double th1 = 0.5 * (1.0 + sqrt(1.0 + 4.0 * st.theta * st.theta));
   const float beta = static_cast<float>((st.theta - 1.0) / th1);
   const float step0 = static_cast<float>(gamma * U.inv_nmax);
+  // coordinates 0..J-1 are the items; J is the count dual when present
+  const int D = U.J + (U.count_on ? 1 : 0);
+  auto grad_of = [&](int j) {
+    return j < U.J ? static_cast<float>(to_real(U.acc[j], U.inv_scaleG) - U.b[j])
+                   : static_cast<float>(to_real(*U.cnt, U.inv_scaleN) - U.count_M);
+  };
   auto lam_next = [&](int j, float& step, float& yj) {
-    const float G = static_cast<float>(to_real(U.acc[j], U.inv_scaleG) - U.b[j]);
-    step = U.precondition ? static_cast<float>(gamma * U.inv_n2[j]) : step0;
+    const float G = grad_of(j);
+    step = U.precondition ? static_cast<float>(gamma * (j < U.J ? U.inv_n2[j] : U.inv_h_count)) : step0;
     yj = U.y[j];
     return fmaxf(0.f, fmaf(step, G, yj));
   };
   bool restart = stage_restart;
   if (U.adaptive_restart && !stage_restart) {
     double dot = 0.0;
-    for (int j = threadIdx.x; j < U.J; j += blockDim.x) {
+    for (int j = threadIdx.x; j < D; j += blockDim.x) {
       float step, yj;
       const float ln = lam_next(j, step, yj);
       if (step > 0.f)
@@ -90,14 +96,18 @@ __global__ void __launch_bounds__(kUpdThreads) fista_update_kernel(const UpdInst
     restart = s_restart != 0;
   }
   double bad = 0.0;
-  for (int j = threadIdx.x; j < U.J; j += blockDim.x) {
-    const float G = static_cast<float>(to_real(U.acc[j], U.inv_scaleG) - U.b[j]);
+  __syncthreads();  // every thread has read the count sum before it is reset
+  for (int j = threadIdx.x; j < D; j += blockDim.x) {
+    const float G = grad_of(j);
     float step, yj;
     const float ln = lam_next(j, step, yj);
     const float yn = restart ? ln : fmaf(beta, ln - U.lam[j], ln);
     U.lam[j] = ln;
     U.y[j] = yn;
-    U.acc[j] = 0ull;
+    if (j < U.J)
+      U.acc[j] = 0ull;
+    else
+      *U.cnt_rw = 0ull;
     if (!isfinite(G) || !isfinite(yj) || !isfinite(yn)) bad = 1.0;
   }
   bad = block_max(bad, sh);
@@ -116,12 +126,19 @@ __global__ void __launch_bounds__(kUpdThreads) fista_update_kernel(const UpdInst
 // (Sec. 3.2 Eq. dual; scaled-point gap as defined in the header):
 //   G_j = (A x)_j - b_j,  g = sum_i (c x + gamma/2 x^2) + lam^T G,
 //   s_j = min(1, b_j / (A x)_j),  P = sum_j s_j (c x)_j + gamma/2 s_j^2 (x^2)_j.
+// With a count constraint sum x <= M (dual mu = lam[J]): g gains mu (sum x - M)
+// and every s_j is multiplied by t = min(1, M / sum x), which keeps the scaled
+// point within the count (sum_j s_j (sum_i x_ij) <= sum x).
 __global__ void __launch_bounds__(kUpdThreads) stats_kernel(const StatsInst* __restrict__ tab) {
   __shared__ double sh[32];
   const StatsInst S = tab[blockIdx.x];
   const double gamma = *S.gamma;
   double obj = 0.0;
   for (int k = threadIdx.x; k < S.nseg; k += blockDim.x) obj += S.seg_obj[S.seg_list[k]];
+  // count constraint: sum x and the common scaling t = min(1, M / sum x)
+  const double total = S.count_on ? to_real(*S.cnt, S.inv_sN) : 0.0;
+  const double t = (S.count_on && total > S.count_M) ? S.count_M / total : 1.0;
+  __syncthreads();  // every thread has read the count sum before it is reset below
   double lg = 0.0, P = 0.0, viol = 0.0;
   for (int j = threadIdx.x; j < S.J; j += blockDim.x) {
     const double Ax = to_real(S.acc[j], S.inv_sG);
@@ -129,13 +146,20 @@ __global__ void __launch_bounds__(kUpdThreads) stats_kernel(const StatsInst* __r
     const double Qx = to_real(S.accQ[j], S.inv_sQ);
     const double G = Ax - S.b[j];
     lg += static_cast<double>(S.lam[j]) * G;
-    const double s = Ax > S.b[j] ? S.b[j] / Ax : 1.0;
+    const double s = t * (Ax > S.b[j] ? S.b[j] / Ax : 1.0);
     P += s * Cx + 0.5 * gamma * s * s * Qx;
     viol = fmax(viol, G);
     if (S.grad_out) S.grad_out[j] = static_cast<float>(G);
     S.acc[j] = 0ull;
     S.accC[j] = 0ull;
     S.accQ[j] = 0ull;
+  }
+  if (S.count_on && threadIdx.x == 0) {
+    const double G = total - S.count_M;
+    lg += static_cast<double>(S.lam[S.J]) * G;
+    viol = fmax(viol, G);
+    if (S.grad_out) S.grad_out[S.J] = static_cast<float>(G);
+    *S.cnt = 0ull;
   }
   obj = block_sum(obj, sh);
   lg = block_sum(lg, sh);

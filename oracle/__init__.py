@@ -9,6 +9,9 @@ Parity status of each function (what pins it is in ``tests/test_oracle_*``):
   project    pinned: brute-force active-set enumeration, closed forms, KKT,
              two independent algorithms (sort and bisection), scipy QP.
   sweep/dual pinned: finite differences (Danskin), concavity, L-smoothness.
+  families   (m capacity families, Def. 1) pinned: finite differences,
+             KKT points by active-set enumeration with 2 rows per item, a
+             slack second family and a duplicated family reducing to one.
   fista      pinned: exact KKT solutions by enumeration of active sets, the
              LP limit (scipy linprog), slack-capacity and one-item closed
              forms, the FISTA O(1/t^2) rate bound; with the adaptive
@@ -51,6 +54,8 @@ class _Problem(ctypes.Structure):
         ("_pad", ctypes.c_int32),
         ("z", ctypes.c_double),
         ("M", ctypes.c_double),
+        ("m", ctypes.c_int32),
+        ("_pad2", ctypes.c_int32),
     ]
 
 
@@ -96,25 +101,33 @@ def _p(a):
 
 class Problem:
     """An instance in FP64: user-major CSR (row_ptr int64, col int32), c, a
-    (float64, e.g. float32 or bfloat16 values widened exactly), b (float64)."""
+    (float64, e.g. float32 or bfloat16 values widened exactly), b (float64).
+    With m capacity families (Def. 1) a has shape [nnz, m] and b [m, J]; the
+    dual vector is then lam[k * J + j] (m J entries, plus mu with a count
+    constraint M)."""
 
     def __init__(self, row_ptr, col, c, a, b, J=None, kind=SIMPLEX_LE, z=1.0, M=np.inf):
         self.row_ptr = np.ascontiguousarray(row_ptr, dtype=np.int64)
         self.col = np.ascontiguousarray(col, dtype=np.int32)
         self.c = np.ascontiguousarray(c, dtype=np.float64)
-        self.a = np.ascontiguousarray(a, dtype=np.float64)
-        self.b = np.ascontiguousarray(b, dtype=np.float64)
+        a = np.asarray(a, dtype=np.float64)
+        b = np.asarray(b, dtype=np.float64)
+        self.m = int(a.shape[1]) if a.ndim == 2 else 1
+        self.a = np.ascontiguousarray(a.reshape(-1))
+        self.b = np.ascontiguousarray(b.reshape(-1))
         self.I = int(self.row_ptr.shape[0] - 1)
-        self.J = int(J if J is not None else self.b.shape[0])
+        self.J = int(J if J is not None else self.b.shape[0] // self.m)
+        if self.b.shape[0] != self.m * self.J or self.a.shape[0] != self.m * int(self.row_ptr[-1]):
+            raise ValueError("a must be [nnz] or [nnz, m] and b [J] or [m, J]")
         self.nnz = int(self.row_ptr[-1])
         self.kind = int(kind)
         self.z = float(z)
         self.M = float(M)
-        self.D = self.J + (1 if np.isfinite(self.M) else 0)  # dual dimension
+        self.D = self.m * self.J + (1 if np.isfinite(self.M) else 0)  # dual dimension
         s = _Problem()
         s.I, s.J, s.nnz = self.I, self.J, self.nnz
         s.row_ptr, s.col, s.c, s.a, s.b = (_p(self.row_ptr), _p(self.col), _p(self.c), _p(self.a), _p(self.b))
-        s.kind, s.z, s.M = self.kind, self.z, self.M
+        s.kind, s.z, s.M, s.m = self.kind, self.z, self.M, self.m
         self._s = s
 
     @classmethod
@@ -144,12 +157,12 @@ def sweep(p: Problem, lam, gamma, want_x=True):
     does grad."""
     lam = _dual_vec(p, lam)
     x = np.empty(p.nnz) if want_x else None
-    Ax, Cx, Qx = np.empty(p.J), np.empty(p.J), np.empty(p.J)
+    Ax, Cx, Qx = np.empty(p.m * p.J), np.empty(p.J), np.empty(p.J)
     obj, count = ctypes.c_double(), ctypes.c_double()
     g = _load().orc_sweep(ctypes.byref(p._s), _p(lam), gamma, _p(x), _p(Ax), _p(Cx), _p(Qx), ctypes.byref(obj),
                           ctypes.byref(count))
     grad = Ax - p.b
-    if p.D > p.J:
+    if p.D > p.m * p.J:
         grad = np.append(grad, count.value - p.M)
     return dict(g=g, x=x, Ax=Ax, Cx=Cx, Qx=Qx, obj=obj.value, count=count.value, grad=grad)
 
@@ -164,13 +177,13 @@ def dual(p: Problem, lam, gamma):
 
 
 def row_sq(p: Problem):
-    out = np.empty(p.J)
+    out = np.empty(p.m * p.J)
     _load().orc_row_sq(ctypes.byref(p._s), _p(out))
     return out
 
 
 def row_sum(p: Problem):
-    out = np.empty(p.J)
+    out = np.empty(p.m * p.J)
     _load().orc_row_sum(ctypes.byref(p._s), _p(out))
     return out
 
@@ -203,7 +216,7 @@ def fista_threads(p: Problem, T, gamma, precondition=False, nthreads=1):
     """Timing only: T fixed-gamma iterations with the sweep split over
     nthreads threads (per-thread item sums added in thread order); returns lam."""
     if p.D != p.J:
-        raise ValueError("the threaded timing loop covers the capacity-only problem")
+        raise ValueError("the threaded timing loop covers the one-family capacity problem")
     lam = np.empty(p.J)
     _load().orc_fista_threads(ctypes.byref(p._s), gamma, int(bool(precondition)), T, int(nthreads), _p(lam))
     return lam

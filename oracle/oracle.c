@@ -8,8 +8,8 @@
  *
  * Problem (Sec. 3.1, Eq. primal):
  *     min_{x in C}  c^T x + (gamma/2) ||x||^2   s.t.  A x <= b,
- * with one capacity family (Sec. 3.3, Eq. dest-capacity):
- *     sum_i a_ij x_ij <= b_j  for every item j,
+ * with m capacity families (Sec. 3.3, Eq. dest-capacity; Def. 1):
+ *     sum_i a_kij x_ij <= b_kj  for every family k and item j,
  * and per-user simple sets C_i (Sec. 3.3): the simplex {x >= 0, sum x <= z}
  * (kind 0), the simplex with equality (kind 1) or the box [0, z] (kind 2).
  *
@@ -42,12 +42,17 @@ typedef struct {
   int32_t _pad;
   double z;               /* simplex radius or box upper bound */
   double M;               /* global count bound sum_ij x_ij <= M (Sec. 5); INFINITY: none */
+  int32_t m;              /* capacity families (Def. 1): a is [nnz x m] edge-major, b [m x J] */
+  int32_t _pad2;
 } orc_problem;
 
-/* With a global count constraint the dual vector is (lam_0..lam_{J-1}, mu):
- * mu >= 0 is the dual of sum_ij x_ij <= M, which adds mu to every edge's cost
- * (one more row of ones in A). */
+/* The dual vector is lam[k J + j] for family k and item j (m J entries), then
+ * mu when there is a global count constraint: mu >= 0 is the dual of
+ * sum_ij x_ij <= M, which adds mu to every edge's cost (one more row of ones
+ * in A). */
 static int has_count(const orc_problem* p) { return isfinite(p->M); }
+static int64_t fams(const orc_problem* p) { return p->m > 0 ? p->m : 1; }
+static int64_t mJ(const orc_problem* p) { return fams(p) * p->J; }
 
 /* ------------------------------------------------------------------------ */
 /* Projections onto one user's simple set (Sec. 3.3, Sec. 4.3)               */
@@ -152,22 +157,23 @@ double orc_project(const double* v, int64_t n, int32_t kind, double z, int32_t m
 
 /* Evaluates, at dual point lam and ridge gamma:
  *   x      = Proj_C(-(A^T lam + c)/gamma)              (per edge, may be NULL)
- *   Ax_j   = sum_i a_ij x_ij                           (per item)
+ *   Ax_kj  = sum_i a_kij x_ij                          (per family and item)
  *   Cx_j   = sum_i c_ij x_ij,  Qx_j = sum_i x_ij^2     (per item, may be NULL)
  *   obj    = sum (c x + gamma/2 x^2)                   (scalar)
- * and returns g(lam) = obj + lam^T (Ax - b). */
+ * and returns g(lam) = obj + lam^T (Ax - b) (+ mu (sum x - M)). */
 double orc_sweep(const orc_problem* p, const double* lam, double gamma, double* x_out, double* Ax, double* Cx,
                  double* Qx, double* obj_out, double* count_out) {
+  const int64_t m = fams(p), J = p->J;
   int64_t maxd = 0;
   for (int64_t i = 0; i < p->I; ++i) {
     int64_t d = p->row_ptr[i + 1] - p->row_ptr[i];
     if (d > maxd) maxd = d;
   }
-  const double mu = has_count(p) ? lam[p->J] : 0.0;
+  const double mu = has_count(p) ? lam[mJ(p)] : 0.0;
   double* v = (double*)malloc(sizeof(double) * (size_t)(maxd > 0 ? maxd : 1));
   double* x = (double*)malloc(sizeof(double) * (size_t)(maxd > 0 ? maxd : 1));
-  for (int64_t j = 0; j < p->J; ++j) {
-    Ax[j] = 0;
+  for (int64_t q = 0; q < m * J; ++q) Ax[q] = 0;
+  for (int64_t j = 0; j < J; ++j) {
     if (Cx) Cx[j] = 0;
     if (Qx) Qx[j] = 0;
   }
@@ -176,13 +182,15 @@ double orc_sweep(const orc_problem* p, const double* lam, double gamma, double* 
     int64_t e0 = p->row_ptr[i], d = p->row_ptr[i + 1] - e0;
     for (int64_t k = 0; k < d; ++k) {
       int64_t e = e0 + k;
-      v[k] = -(p->c[e] + p->a[e] * lam[p->col[e]] + mu) / gamma;
+      double t = p->c[e] + mu;
+      for (int64_t f = 0; f < m; ++f) t += p->a[e * m + f] * lam[f * J + p->col[e]];
+      v[k] = -t / gamma;
     }
     orc_project(v, d, p->kind, p->z, 0, x);
     for (int64_t k = 0; k < d; ++k) {
       int64_t e = e0 + k;
       int32_t j = p->col[e];
-      Ax[j] += p->a[e] * x[k];
+      for (int64_t f = 0; f < m; ++f) Ax[f * J + j] += p->a[e * m + f] * x[k];
       if (Cx) Cx[j] += p->c[e] * x[k];
       if (Qx) Qx[j] += x[k] * x[k];
       obj += p->c[e] * x[k] + 0.5 * gamma * x[k] * x[k];
@@ -193,37 +201,59 @@ double orc_sweep(const orc_problem* p, const double* lam, double gamma, double* 
   free(v);
   free(x);
   double g = obj;
-  for (int64_t j = 0; j < p->J; ++j) g += lam[j] * (Ax[j] - p->b[j]);
+  for (int64_t q = 0; q < m * J; ++q) g += lam[q] * (Ax[q] - p->b[q]);
   if (has_count(p)) g += mu * (count - p->M);
   if (obj_out) *obj_out = obj;
   if (count_out) *count_out = count;
   return g;
 }
 
-/* g(lam) and grad g(lam) = A x*(lam) - b (Eq. dual-gradient); with a count
- * constraint grad has J + 1 entries, the last sum_ij x_ij - M. */
+/* g(lam) and grad g(lam) = A x*(lam) - b (Eq. dual-gradient), m J entries;
+ * with a count constraint one more, sum_ij x_ij - M. */
 double orc_dual(const orc_problem* p, const double* lam, double gamma, double* grad, double* x_out) {
   double count = 0;
   double g = orc_sweep(p, lam, gamma, x_out, grad, NULL, NULL, NULL, &count);
-  for (int64_t j = 0; j < p->J; ++j) grad[j] -= p->b[j];
-  if (has_count(p)) grad[p->J] = count - p->M;
+  for (int64_t q = 0; q < mJ(p); ++q) grad[q] -= p->b[q];
+  if (has_count(p)) grad[mJ(p)] = count - p->M;
   return g;
 }
 
-/* s_j = sum_i a_ij: the coupling between item j's row of A and the count row
+/* s_kj = sum_i a_kij: the coupling between row (k, j) of A and the count row
  * of ones (an entry of A A^T). */
 void orc_row_sum(const orc_problem* p, double* s1) {
-  for (int64_t j = 0; j < p->J; ++j) s1[j] = 0;
-  for (int64_t e = 0; e < p->nnz; ++e) s1[p->col[e]] += p->a[e];
+  const int64_t m = fams(p), J = p->J;
+  for (int64_t q = 0; q < m * J; ++q) s1[q] = 0;
+  for (int64_t e = 0; e < p->nnz; ++e)
+    for (int64_t f = 0; f < m; ++f) s1[f * J + p->col[e]] += p->a[e * m + f];
 }
 
-/* n_j = sum_i a_ij^2.  With one capacity family the rows of A have disjoint
- * supports (Def. 1: each D_i is diagonal), so A A^T = diag(n) and
- * ||A||_2^2 = max_j n_j; App. B.2 bounds the gradient's Lipschitz constant by
- * ||A||_2^2 / gamma. */
+/* n_kj = sum_i a_kij^2, the diagonal of A A^T.  With one capacity family the
+ * rows of A have disjoint supports (Def. 1: each D_i is diagonal), so
+ * A A^T = diag(n) and ||A||_2^2 = max_j n_j; App. B.2 bounds the gradient's
+ * Lipschitz constant by ||A||_2^2 / gamma. */
 void orc_row_sq(const orc_problem* p, double* n2) {
-  for (int64_t j = 0; j < p->J; ++j) n2[j] = 0;
-  for (int64_t e = 0; e < p->nnz; ++e) n2[p->col[e]] += p->a[e] * p->a[e];
+  const int64_t m = fams(p), J = p->J;
+  for (int64_t q = 0; q < m * J; ++q) n2[q] = 0;
+  for (int64_t e = 0; e < p->nnz; ++e)
+    for (int64_t f = 0; f < m; ++f) n2[f * J + p->col[e]] += p->a[e * m + f] * p->a[e * m + f];
+}
+
+/* Gershgorin row sums of A A^T over the capacity rows: for row (k, j),
+ * sum_l |sum_i a_kij a_lij| (the m x m block of item j; the blocks of
+ * different items do not couple, Def. 1). */
+static void gram_rows(const orc_problem* p, double* r) {
+  const int64_t m = fams(p), J = p->J;
+  double* G = (double*)calloc((size_t)(m * m * J), sizeof(double));
+  for (int64_t e = 0; e < p->nnz; ++e)
+    for (int64_t f = 0; f < m; ++f)
+      for (int64_t l = 0; l < m; ++l) G[(f * m + l) * J + p->col[e]] += p->a[e * m + f] * p->a[e * m + l];
+  for (int64_t f = 0; f < m; ++f)
+    for (int64_t j = 0; j < J; ++j) {
+      double t = 0;
+      for (int64_t l = 0; l < m; ++l) t += fabs(G[(f * m + l) * J + j]);
+      r[f * J + j] = t;
+    }
+  free(G);
 }
 
 /* ------------------------------------------------------------------------ */
@@ -240,30 +270,35 @@ void orc_row_sq(const orc_problem* p, double* n2) {
  * (the gap of the unscaled point x(lam), as the paper's quality table
  * reports it), out[5] = primal objective of the unscaled x(lam). */
 void orc_certify(const orc_problem* p, const double* lam, double gamma, double* out) {
-  int64_t J = p->J;
-  double* Ax = (double*)malloc(sizeof(double) * (size_t)J);
+  const int64_t J = p->J, m = fams(p);
+  double* Ax = (double*)malloc(sizeof(double) * (size_t)(m * J));
   double* Cx = (double*)malloc(sizeof(double) * (size_t)J);
   double* Qx = (double*)malloc(sizeof(double) * (size_t)J);
   double obj = 0, count = 0;
   double g = orc_sweep(p, lam, gamma, NULL, Ax, Cx, Qx, &obj, &count);
-  /* item scaling s_j = min(1, b_j / (Ax)_j); with a count constraint a common
-   * factor t = min(1, M / sum x) on top keeps sum x~ <= t sum x <= M */
+  /* item scaling s_j = min(1, min_k b_kj / (A_k x)_j); with a count constraint
+   * a common factor t = min(1, M / sum x) on top keeps sum x~ <= t sum x <= M */
   double t = 1.0;
   if (has_count(p) && count > p->M) t = p->M / count;
   double P = 0, viol = 0, lg = 0;
   for (int64_t j = 0; j < J; ++j) {
     double s = 1.0;
-    if (Ax[j] > p->b[j]) s = p->b[j] / Ax[j];
+    for (int64_t f = 0; f < m; ++f) {
+      const int64_t q = f * J + j;
+      if (Ax[q] > p->b[q] && p->b[q] / Ax[q] < s) s = p->b[q] / Ax[q];
+    }
     s *= t;
     P += s * Cx[j] + 0.5 * gamma * s * s * Qx[j];
-    double r = Ax[j] - p->b[j];
+  }
+  for (int64_t q = 0; q < m * J; ++q) {
+    double r = Ax[q] - p->b[q];
     if (r > viol) viol = r;
-    lg += lam[j] * r;
+    lg += lam[q] * r;
   }
   if (has_count(p)) {
     double r = count - p->M;
     if (r > viol) viol = r;
-    lg += lam[J] * r;
+    lg += lam[m * J] * r;
   }
   double den = fabs(g) > 1e-30 ? fabs(g) : 1e-30;
   out[0] = g;
@@ -302,22 +337,23 @@ static double stage_gamma(double gamma0, double gamma_end, double factor, int64_
  * iteration t: traj_g[t] = g(y_t), traj_gamma[t] (either may be NULL). */
 /* Per-coordinate curvature bounds h_k (step_k = gamma / h_k).  One family:
  * A A^T = diag(n) (Def. 1), so h_j = n_j with row normalization and
- * h = max_j n_j = ||A||^2 otherwise (App. B.2).  With the count row, A A^T
- * gains the row and column s (s_j = sum_i a_ij) and the corner nnz; Gershgorin
- * row sums r_j = n_j + |s_j|, r_mu = nnz + sum_j |s_j| bound it: the diagonal
- * scaling by 1/r is a valid preconditioner, and max_k r_k bounds ||A||^2. */
+ * h = max_j n_j = ||A||^2 otherwise (App. B.2).  With m families A A^T is
+ * block diagonal with one m x m block per item, and with the count row it
+ * gains the row and column s (s_kj = sum_i a_kij) and the corner nnz;
+ * Gershgorin row sums bound it in every case: the diagonal scaling by their
+ * inverses is a valid preconditioner, and their maximum bounds ||A||^2. */
 static int64_t curvature(const orc_problem* p, int32_t precondition, double* h) {
-  int64_t J = p->J, D = J + (has_count(p) ? 1 : 0);
-  orc_row_sq(p, h);
+  const int64_t MJ = mJ(p), D = MJ + (has_count(p) ? 1 : 0);
+  gram_rows(p, h);
   if (has_count(p)) {
-    double* s1 = (double*)malloc(sizeof(double) * (size_t)J);
+    double* s1 = (double*)malloc(sizeof(double) * (size_t)MJ);
     orc_row_sum(p, s1);
     double tot = 0;
-    for (int64_t j = 0; j < J; ++j) {
-      h[j] += fabs(s1[j]);
-      tot += fabs(s1[j]);
+    for (int64_t q = 0; q < MJ; ++q) {
+      h[q] += fabs(s1[q]);
+      tot += fabs(s1[q]);
     }
-    h[J] = (double)p->nnz + tot;
+    h[MJ] = (double)p->nnz + tot;
     free(s1);
   }
   if (!precondition) {
@@ -332,7 +368,7 @@ static int64_t curvature(const orc_problem* p, int32_t precondition, double* h) 
 void orc_fista(const orc_problem* p, double gamma0, double gamma_end, double factor, int64_t iters_per_stage,
                int32_t precondition, int32_t restart, int64_t T, const double* lam0, double* lam_out,
                double* y_out, double* theta_out, double* traj_g, double* traj_gamma) {
-  int64_t J = p->J, D1 = J + 1;
+  int64_t D1 = mJ(p) + 1;
   double* h = (double*)malloc(sizeof(double) * (size_t)D1);
   double* lam = (double*)malloc(sizeof(double) * (size_t)D1);
   double* y = (double*)malloc(sizeof(double) * (size_t)D1);
@@ -440,7 +476,7 @@ static void* sweep_range(void* arg) {
 
 void orc_fista_threads(const orc_problem* p, double gamma, int32_t precondition, int64_t T, int32_t nthreads,
                        double* lam_out) {
-  /* (timing of the capacity-only problem; a count constraint is not timed) */
+  /* (timing of the one-family capacity problem; the wrapper rejects others) */
   int64_t J = p->J;
   if (nthreads < 1) nthreads = 1;
   double* n2 = (double*)malloc(sizeof(double) * (size_t)J);

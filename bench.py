@@ -77,7 +77,7 @@ def load_peaks():
 
 def sweep_source_hash():
     h = hashlib.sha256()
-    for f in ("sweep.cu", "dlm_impl.cuh"):
+    for f in ("sweep.cu", "sweep_common.cuh", "dlm_impl.cuh"):
         with open(os.path.join(ROOT, "paper_2606_07777_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]

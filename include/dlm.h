@@ -59,9 +59,16 @@ typedef enum { DLM_MEM_DEVICE = 0, DLM_MEM_HOST = 1 } dlm_memspace;
  *            row_ptr[num_users] = nnz
  *   item_idx int32 [nnz], 0 <= item_idx < num_items (the eligible items of
  *            each user; a repeated item in one row is a parallel edge)
- *   c, a     [nnz] float32 (val_dtype DLM_F32) or bfloat16 bit patterns
+ *   c        [nnz] float32 (val_dtype DLM_F32) or bfloat16 bit patterns
  *            (DLM_BF16, stored as uint16); all finite
- *   b        float64 [num_items], finite, >= 0
+ *   a        [nnz x num_families], edge-major (a[e * m + k] is edge e's
+ *            coefficient in capacity family k), same type; all finite
+ *   b        float64 [num_families x num_items], family-major, finite, >= 0
+ * With m = num_families > 1 (Def. 1: several coupling families, each with one
+ * diagonal block per user; at most 4) every dual vector of the handle is
+ * [m x num_items] family-major (lam[k * num_items + j]); such handles sweep
+ * with a general kernel, take the static slice orders (mapping 1 or 2), and
+ * do not combine with batches, the count constraint or the warm start.
  * The arrays live in `memspace`.  dlm_create copies them into its own layout;
  * the caller may free or reuse them once dlm_create has returned. */
 typedef struct {
@@ -71,11 +78,11 @@ typedef struct {
   const void* c;
   const void* a;
   const double* b;
-  int32_t val_dtype; /* dlm_dtype */
-  int32_t kind;      /* dlm_simple_kind */
-  double z;          /* simplex radius or box bound, > 0 */
-  int32_t memspace;  /* dlm_memspace of the arrays above */
-  int32_t reserved;
+  int32_t val_dtype;    /* dlm_dtype */
+  int32_t kind;         /* dlm_simple_kind */
+  double z;             /* simplex radius or box bound, > 0 */
+  int32_t memspace;     /* dlm_memspace of the arrays above */
+  int32_t num_families; /* capacity families m, 1..4 (0 means 1) */
 } dlm_problem_desc;
 
 /* Solver options (zero-initialised fields take the defaults).  The mapping

@@ -46,7 +46,7 @@ class ProblemDesc(ctypes.Structure):
                 ("row_ptr", ctypes.c_void_p), ("item_idx", ctypes.c_void_p), ("c", ctypes.c_void_p),
                 ("a", ctypes.c_void_p), ("b", ctypes.c_void_p), ("val_dtype", ctypes.c_int32),
                 ("kind", ctypes.c_int32), ("z", ctypes.c_double), ("memspace", ctypes.c_int32),
-                ("reserved", ctypes.c_int32)]
+                ("num_families", ctypes.c_int32)]
 
 
 class Options(ctypes.Structure):
@@ -349,11 +349,14 @@ class Solver:
         dev = getattr(row_ptr, "is_cuda", False)
         if bf16 is None:
             bf16 = getattr(c, "dtype", None) in (torch.bfloat16,) or str(getattr(c, "dtype", "")) == "uint16"
-        self.num_items = int(num_items if num_items is not None else len(b))
+        # several capacity families: a is [nnz, m] (edge-major), b [m, num_items]
+        self.num_families = int(a.shape[1]) if len(a.shape) == 2 else 1
+        self.num_items = int(num_items if num_items is not None else b.shape[-1])
         self.num_users = int(row_ptr.shape[0] - 1)
         self.nnz = int(col.shape[0])
         self.bf16 = bool(bf16)
         desc = ProblemDesc()
+        desc.num_families = self.num_families
         desc.num_users, desc.num_items, desc.nnz = self.num_users, self.num_items, self.nnz
         desc.row_ptr, desc.item_idx, desc.c, desc.a, desc.b = (_ptr(row_ptr), _ptr(col), _ptr(c), _ptr(a), _ptr(b))
         desc.val_dtype = DLM_BF16 if self.bf16 else DLM_F32
@@ -368,7 +371,8 @@ class Solver:
         self._keep = None
         self.kind = int(kind)
         self.z = float(z)
-        self.dual_dim = self.num_items  # num_items + 1 while a count constraint is set
+        # m num_items (family-major), + 1 while a count constraint is set
+        self.dual_dim = self.num_families * self.num_items
 
     def close(self):
         if getattr(self, "h", None):
@@ -403,7 +407,7 @@ class Solver:
         import math
 
         _call("dlm_set_count_limit", self.h, float(M))
-        self.dual_dim = self.num_items + (0 if math.isinf(M) else 1)
+        self.dual_dim = self.num_families * self.num_items + (0 if math.isinf(M) else 1)
 
     def set_lambda(self, lam):
         dlm_set_lambda(self.h, lam, DLM_MEM_DEVICE if getattr(lam, "is_cuda", False) else DLM_MEM_HOST)

@@ -134,7 +134,14 @@ struct dlm_problem {
   double count_M = INFINITY;
   int sN = 0;
   unsigned long long *cnt = nullptr, *cnt2 = nullptr;  // fixed-point sum x at y / at lam
-  int64_t D() const { return J + (count_on ? 1 : 0); }  // dual dimension
+  // m capacity families (Def. 1): duals and item sums are [m J] family-major;
+  // family k >= 1's coefficients are a stream in slice order at a_ext
+  int m = 1;
+  void* a_ext = nullptr;
+  int64_t ext_stride = 0;
+  std::vector<double> h_gram;  // [m m J]: sum_i a_kij a_lij
+  int64_t MJ() const { return static_cast<int64_t>(m) * J; }
+  int64_t D() const { return MJ() + (count_on ? 1 : 0); }  // dual dimension
   float *lam = nullptr, *y = nullptr;
   unsigned long long *acc = nullptr, *acc2 = nullptr, *accC = nullptr, *accQ = nullptr;
   double *gamma_tab = nullptr, *calc_gamma = nullptr, *stats_out = nullptr;
@@ -184,6 +191,9 @@ InstDesc base_desc(const dlm_problem* p) {
   d.count_on = p->count_on ? 1 : 0;
   d.cnt = p->cnt2;
   d.scaleN = std::ldexp(1.0f, p->sN);
+  d.m = p->m;
+  d.a_ext = p->a_ext;
+  d.ext_stride = p->ext_stride;
   return d;
 }
 
@@ -206,6 +216,7 @@ StatsInst base_stats(const dlm_problem* p, const Runner& R, int i) {
   s.cnt = p->cnt2;
   s.inv_sN = std::ldexp(1.0, -p->sN);
   s.count_M = p->count_M;
+  s.m = p->m;
   return s;
 }
 
@@ -391,6 +402,7 @@ dlm_status write_tables(Runner& R) {
     u.inv_scaleN = std::ldexp(1.0, -p->sN);
     u.count_M = p->count_M;
     u.inv_h_count = p->inv_h_count;
+    u.ncap = static_cast<int32_t>(p->MJ());
     up[i] = u;
     st[i] = base_stats(p, R, i);
     st[i].lam = p->lam;
@@ -456,21 +468,31 @@ SweepLaunch launch_of(const Runner& R, const InstDesc* tab) {
   L.coop_max = R.coop_max;
   L.stream = R.stream;
   L.count = false;
-  for (const dlm_problem* p : R.probs) L.count = L.count || p->count_on;
+  L.fam = 1;
+  for (const dlm_problem* p : R.probs) {
+    L.count = L.count || p->count_on;
+    L.fam = std::max(L.fam, p->m);
+  }
   L.units = R.h_units.empty() ? nullptr : R.units;
   L.nunits = static_cast<int32_t>(R.h_units.size());
   L.ctr = R.ctr;
   return L;
 }
 
+// One-family instances take the sweep of sweep.cu, several families the
+// general sweep of sweep_multi.cu (static tasks only).
+cudaError_t dispatch_sweep(const SweepLaunch& L, bool stats, bool bf16) {
+  return L.fam > 1 ? launch_sweep_multi(L, stats, bf16) : launch_sweep(L, stats, bf16);
+}
+
 dlm_status enqueue_iteration(Runner& R) {
-  CK(launch_sweep(launch_of(R, R.inst_iter), false, R.bf16));
+  CK(dispatch_sweep(launch_of(R, R.inst_iter), false, R.bf16));
   CK(launch_update(R.upd, static_cast<int>(R.probs.size()), R.stream));
   return DLM_OK;
 }
 
 dlm_status enqueue_certificate(Runner& R, const InstDesc* inst_tab, const StatsInst* st_tab) {
-  CK(launch_sweep(launch_of(R, inst_tab), true, R.bf16));
+  CK(dispatch_sweep(launch_of(R, inst_tab), true, R.bf16));
   CK(launch_stats(st_tab, static_cast<int>(R.probs.size()), R.stream));
   return DLM_OK;
 }
@@ -520,7 +542,7 @@ dlm_status runner_step_timed(Runner& R, int64_t n_iters, double* sweep_ms, doubl
   const int n = static_cast<int>(R.probs.size());
   CK(cudaEventRecord(R.events[0], R.stream));
   for (int64_t i = 0; i < n_iters; ++i) {
-    CK(launch_sweep(L, false, R.bf16));
+    CK(dispatch_sweep(L, false, R.bf16));
     CK(cudaEventRecord(R.events[2 * i + 1], R.stream));
     CK(launch_update(R.upd, n, R.stream));
     CK(cudaEventRecord(R.events[2 * i + 2], R.stream));
@@ -552,12 +574,15 @@ dlm_status runner_configure(Runner& R, const dlm_options& o, bool force) {
                      : o.mapping == 2 ? kAssignContiguous
                      : o.mapping == 3 ? kAssignDynamic
                                       : (R.probs.size() > 1 ? kAssignDynamic : kAssignInterleaved);
+  int assign2 = assign;
+  for (const dlm_problem* p : R.probs)
+    if (p->m > 1 && assign2 == kAssignDynamic) assign2 = R.probs.size() > 1 ? kAssignContiguous : kAssignInterleaved;
   R.coop_max = o.coop_max > 0 ? o.coop_max : kDefaultCoopMax;
   R.graph_iters = o.graph_iters > 0 ? o.graph_iters : 10;
-  if (force || grid != R.grid || threads != R.threads || assign != R.assign) {
+  if (force || grid != R.grid || threads != R.threads || assign2 != R.assign) {
     R.grid = grid;
     R.threads = threads;
-    R.assign = assign;
+    R.assign = assign2;
     return runner_build(R);
   }
   invalidate_graph(R);
@@ -598,6 +623,7 @@ void free_problem(dlm_problem* p) {
   cudaFree(p->lay.n2);
   cudaFree(p->cnt);
   cudaFree(p->cnt2);
+  cudaFree(p->a_ext);
   void* ptrs[] = {p->b,         p->inv_n2,    p->lam,       p->y,         p->acc,   p->acc2,      p->accC,
                   p->accQ,      p->gamma_tab, p->calc_gamma, p->stats_out, p->state, p->inst_calc, p->st_calc};
   for (void* q : ptrs) cudaFree(q);
@@ -617,27 +643,35 @@ void free_problem(dlm_problem* p) {
 // nnz + sum_j |s_j| then bound the curvature (the diagonal scaling by their
 // inverses is a valid preconditioner and their maximum bounds ||A||^2).
 dlm_status upload_steps(dlm_problem* p) {
-  const int64_t J = p->J;
-  std::vector<double> inv(J + 1, 0.0);
+  const int64_t J = p->J, MJ = p->MJ();
+  const int m = p->m;
+  std::vector<double> inv(MJ + 1, 0.0);
   double hmax = 0.0, tot = 0.0;
-  for (int64_t j = 0; j < J; ++j) {
-    double h = p->lay.h_n2[j];
-    if (p->count_on) {
-      h += std::fabs(p->lay.h_s1[j]);
-      tot += std::fabs(p->lay.h_s1[j]);
+  for (int64_t q = 0; q < MJ; ++q) {
+    double h;
+    if (m == 1) {
+      h = p->lay.h_n2[q];
+    } else {  // Gershgorin row sum of item j's m x m block
+      const int64_t f = q / J, j = q % J;
+      h = 0.0;
+      for (int l = 0; l < m; ++l) h += std::fabs(p->h_gram[(static_cast<size_t>(f) * m + l) * J + j]);
     }
-    inv[j] = h > 0 ? 1.0 / h : 0.0;
+    if (p->count_on) {
+      h += std::fabs(p->lay.h_s1[q]);
+      tot += std::fabs(p->lay.h_s1[q]);
+    }
+    inv[q] = h > 0 ? 1.0 / h : 0.0;
     hmax = h > hmax ? h : hmax;
   }
   p->inv_h_count = 0.0;
   if (p->count_on) {
     const double hc = static_cast<double>(p->nnz) + tot;
     p->inv_h_count = hc > 0 ? 1.0 / hc : 0.0;
-    inv[J] = p->inv_h_count;
+    inv[MJ] = p->inv_h_count;
     hmax = hc > hmax ? hc : hmax;
   }
   p->inv_hmax = hmax > 0 ? 1.0 / hmax : 0.0;
-  CK(cudaMemcpyAsync(p->inv_n2, inv.data(), sizeof(double) * (J + 1), cudaMemcpyHostToDevice, p->stream));
+  CK(cudaMemcpyAsync(p->inv_n2, inv.data(), sizeof(double) * (MJ + 1), cudaMemcpyHostToDevice, p->stream));
   CK(cudaStreamSynchronize(p->stream));
   return DLM_OK;
 }
@@ -690,7 +724,7 @@ dlm_status restore_state(Runner& R, const Saved& S) {
     CK(cudaMemcpy(p->y, S.y[i], sizeof(float) * p->D(), cudaMemcpyDeviceToDevice));
     CK(cudaMemset(p->cnt, 0, sizeof(unsigned long long)));
     CK(cudaMemcpy(p->state, &S.st[i], sizeof(DevState), cudaMemcpyHostToDevice));
-    CK(cudaMemset(p->acc, 0, sizeof(unsigned long long) * p->J));
+    CK(cudaMemset(p->acc, 0, sizeof(unsigned long long) * p->MJ()));
   }
   return DLM_OK;
 }
@@ -801,6 +835,8 @@ dlm_status dlm_create(const dlm_problem_desc* desc, void* stream, dlm_problem** 
   if (!(desc->z > 0) || !std::isfinite(desc->z)) return fail(DLM_ERR_INVALID_ARG, "z must be finite and > 0");
   if (desc->memspace != DLM_MEM_DEVICE && desc->memspace != DLM_MEM_HOST)
     return fail(DLM_ERR_INVALID_ARG, "bad memspace");
+  const int m = desc->num_families > 0 ? desc->num_families : 1;
+  if (m > kMaxFamilies) return fail(DLM_ERR_UNSUPPORTED, "at most 4 capacity families");
 
   dlm_problem* p = new dlm_problem();
   p->I = desc->num_users;
@@ -809,6 +845,7 @@ dlm_status dlm_create(const dlm_problem_desc* desc, void* stream, dlm_problem** 
   p->bf16 = desc->val_dtype == DLM_BF16;
   p->kind = desc->kind;
   p->z = desc->z;
+  p->m = m;
   p->opt.gap_every = 50;
   p->opt.graph_iters = 10;
   cudaGetDevice(&p->device);
@@ -839,7 +876,7 @@ dlm_status dlm_create(const dlm_problem_desc* desc, void* stream, dlm_problem** 
     for (void* q : tmp) cudaFree(q);
   };
   if (desc->memspace == DLM_MEM_HOST) {
-    size_t sz[5] = {sizeof(int64_t) * (I + 1), sizeof(int32_t) * nnz, vs * nnz, vs * nnz, sizeof(double) * J};
+    size_t sz[5] = {sizeof(int64_t) * (I + 1), sizeof(int32_t) * nnz, vs * nnz, vs * nnz * m, sizeof(double) * J * m};
     const void* src[5] = {rp, col, c, a, b};
     for (int k = 0; k < 5; ++k) {
       if (cudaMalloc(&tmp[k], sz[k] > 0 ? sz[k] : 16) != cudaSuccess) {
@@ -860,12 +897,71 @@ dlm_status dlm_create(const dlm_problem_desc* desc, void* stream, dlm_problem** 
     b = static_cast<const double*>(tmp[4]);
   }
 
-  std::string msg;
-  st = build_layout(I, J, nnz, rp, col, c, a, b, p->bf16, p->stream, &p->lay, &msg);
-  if (st != DLM_OK) {
+  // Several families: one contiguous array per family (family 0 goes through
+  // the one-family layout and validation, the others are checked here).
+  void* split = nullptr;
+  auto cleanup_all = [&]() {
     cleanup_tmp();
+    cudaFree(split);
+    split = nullptr;
+  };
+  if (m > 1) {
+    if (cudaMalloc(&split, vs * (nnz > 0 ? nnz : 1) * m) != cudaSuccess) {
+      cleanup_all();
+      free_problem(p);
+      return fail(DLM_ERR_OOM, "device allocation for the family split failed");
+    }
+    if (families_split(a, nnz, m, p->bf16, split, nnz, p->stream) != cudaSuccess) {
+      cleanup_all();
+      free_problem(p);
+      return fail(DLM_ERR_CUDA, "family split failed");
+    }
+  }
+  const void* a0 = m > 1 ? split : a;
+  auto fam_ptr = [&](int f) { return static_cast<const char*>(split) + vs * nnz * f; };
+
+  std::string msg;
+  st = build_layout(I, J, nnz, rp, col, c, a0, b, p->bf16, p->stream, &p->lay, &msg);
+  if (st != DLM_OK) {
+    cleanup_all();
     free_problem(p);
     return fail(st, msg);
+  }
+  if (m > 1) {
+    // the other families: finite values, b >= 0, max |a|, sign
+    int* flags = nullptr;
+    unsigned* mx = nullptr;
+    int h_flags = 0;
+    unsigned h_mx = 0;
+    std::vector<double> hb(static_cast<size_t>(J) * m);
+    cudaError_t e = cudaMalloc(&flags, sizeof(int));
+    if (e == cudaSuccess) e = cudaMalloc(&mx, sizeof(unsigned));
+    if (e == cudaSuccess) e = cudaMemsetAsync(flags, 0, sizeof(int), p->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(mx, 0, sizeof(unsigned), p->stream);
+    for (int f = 1; f < m && e == cudaSuccess; ++f) e = families_check(fam_ptr(f), nnz, p->bf16, flags, mx, p->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&h_flags, flags, sizeof(int), cudaMemcpyDeviceToHost, p->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&h_mx, mx, sizeof(unsigned), cudaMemcpyDeviceToHost, p->stream);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(hb.data(), b, sizeof(double) * hb.size(), cudaMemcpyDeviceToHost, p->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(p->stream);
+    cudaFree(flags);
+    cudaFree(mx);
+    if (e != cudaSuccess) {
+      cleanup_all();
+      free_problem(p);
+      return fail(DLM_ERR_CUDA, std::string("family checks: ") + cudaGetErrorString(e));
+    }
+    bool bad_b = false;
+    for (double v : hb) bad_b = bad_b || !std::isfinite(v) || v < 0;
+    if ((h_flags & 1) || bad_b) {
+      cleanup_all();
+      free_problem(p);
+      return fail(DLM_ERR_INVALID_ARG, "non-finite coefficient, or b not finite and >= 0, in a capacity family");
+    }
+    if (h_flags & 2) p->lay.a_nonneg = false;
+    float fm;
+    std::memcpy(&fm, &h_mx, sizeof(float));
+    p->lay.max_abs_a = std::max(p->lay.max_abs_a, static_cast<double>(fm));
   }
   p->certified = p->lay.a_nonneg && p->kind != DLM_SIMPLEX_EQ;
 
@@ -879,12 +975,13 @@ dlm_status dlm_create(const dlm_problem_desc* desc, void* stream, dlm_problem** 
   const double nmaxx = static_cast<double>(p->kind == DLM_BOX ? nnz : p->lay.num_active_users);
   p->sN = fixed_point_shift((nmaxx > 0 ? nmaxx : 1.0) * xmax);
   if (p->sG < 0 || p->sC < 0 || p->sQ < 0 || p->sN < 0) {
-    cleanup_tmp();
+    cleanup_all();
     free_problem(p);
     return fail(DLM_ERR_UNSUPPORTED, "item sums too large for 64-bit fixed point");
   }
-  if (sweep_smem_bytes(static_cast<int>(J), true) > sweep_smem_limit()) {
-    cleanup_tmp();
+  if ((m > 1 ? sweep_multi_smem_bytes(static_cast<int>(J), m, true) : sweep_smem_bytes(static_cast<int>(J), true)) >
+      sweep_smem_limit()) {
+    cleanup_all();
     free_problem(p);
     return fail(DLM_ERR_UNSUPPORTED, "num_items too large for the shared-memory item arrays of this build");
   }
@@ -893,29 +990,60 @@ dlm_status dlm_create(const dlm_problem_desc* desc, void* stream, dlm_problem** 
   do {                                                                             \
     cudaError_t e_ = (x);                                                          \
     if (e_ != cudaSuccess) {                                                       \
-      cleanup_tmp();                                                               \
+      cleanup_all();                                                               \
       free_problem(p);                                                             \
       return fail(DLM_ERR_CUDA, std::string(#x) + ": " + cudaGetErrorString(e_)); \
     }                                                                              \
   } while (0)
 
-  CKC(dalloc(&p->b, J));
-  CKC(cudaMemcpyAsync(p->b, b, sizeof(double) * J, cudaMemcpyDeviceToDevice, p->stream));
-  CKC(dalloc(&p->inv_n2, J + 1));
-  CKC(dalloc(&p->lam, J + 1));
-  CKC(dalloc(&p->y, J + 1));
+  const int64_t MJ = p->MJ();
+  if (m > 1) {
+    // extra family streams in slice order, and the per-item Gram sums
+    p->ext_stride = p->lay.padded_nnz + 32;
+    CKC(cudaMalloc(&p->a_ext, vs * p->ext_stride * (m - 1)));
+    for (int f = 1; f < m; ++f)
+      CKC(families_gather(p->lay, fam_ptr(f), p->bf16,
+                          static_cast<char*>(p->a_ext) + vs * p->ext_stride * (f - 1), p->stream));
+    const double degm2 = static_cast<double>(p->lay.max_item_deg > 0 ? p->lay.max_item_deg : 1);
+    const int sgr = fixed_point_shift(degm2 * std::max(p->lay.max_abs_a * p->lay.max_abs_a, 1e-300));
+    unsigned long long* gacc = nullptr;
+    CKC(dalloc(&gacc, J));
+    p->h_gram.assign(static_cast<size_t>(m) * m * J, 0.0);
+    std::vector<unsigned long long> hq(J);
+    for (int f = 0; f < m; ++f)
+      for (int l = f; l < m; ++l) {
+        CKC(cudaMemsetAsync(gacc, 0, sizeof(unsigned long long) * J, p->stream));
+        CKC(families_gram(col, fam_ptr(f), fam_ptr(l), nnz, p->bf16, std::ldexp(1.0f, sgr), gacc, p->stream));
+        CKC(cudaMemcpyAsync(hq.data(), gacc, sizeof(unsigned long long) * J, cudaMemcpyDeviceToHost, p->stream));
+        CKC(cudaStreamSynchronize(p->stream));
+        for (int64_t j = 0; j < J; ++j) {
+          const double v = static_cast<double>(static_cast<long long>(hq[j])) * std::ldexp(1.0, -sgr);
+          p->h_gram[(static_cast<size_t>(f) * m + l) * J + j] = v;
+          p->h_gram[(static_cast<size_t>(l) * m + f) * J + j] = v;
+        }
+      }
+    cudaFree(gacc);
+    CKC(sweep_multi_prepare(p->bf16));
+  }
+  CKC(dalloc(&p->b, MJ));
+  CKC(cudaMemcpyAsync(p->b, b, sizeof(double) * MJ, cudaMemcpyDeviceToDevice, p->stream));
+  CKC(dalloc(&p->inv_n2, MJ + 1));
+  CKC(dalloc(&p->lam, MJ + 1));
+  CKC(dalloc(&p->y, MJ + 1));
   CKC(dalloc(&p->cnt, 1));
   CKC(dalloc(&p->cnt2, 1));
   CKC(cudaMemsetAsync(p->cnt, 0, sizeof(unsigned long long), p->stream));
   CKC(cudaMemsetAsync(p->cnt2, 0, sizeof(unsigned long long), p->stream));
-  CKC(dalloc(&p->acc, J));
-  CKC(dalloc(&p->acc2, J));
+  CKC(dalloc(&p->acc, MJ));
+  CKC(dalloc(&p->acc2, MJ));
   CKC(dalloc(&p->accC, J));
   CKC(dalloc(&p->accQ, J));
-  for (unsigned long long* q : {p->acc, p->acc2, p->accC, p->accQ})
-    CKC(cudaMemsetAsync(q, 0, sizeof(unsigned long long) * J, p->stream));
-  CKC(cudaMemsetAsync(p->lam, 0, sizeof(float) * (J + 1), p->stream));
-  CKC(cudaMemsetAsync(p->y, 0, sizeof(float) * (J + 1), p->stream));
+  CKC(cudaMemsetAsync(p->acc, 0, sizeof(unsigned long long) * MJ, p->stream));
+  CKC(cudaMemsetAsync(p->acc2, 0, sizeof(unsigned long long) * MJ, p->stream));
+  CKC(cudaMemsetAsync(p->accC, 0, sizeof(unsigned long long) * J, p->stream));
+  CKC(cudaMemsetAsync(p->accQ, 0, sizeof(unsigned long long) * J, p->stream));
+  CKC(cudaMemsetAsync(p->lam, 0, sizeof(float) * (MJ + 1), p->stream));
+  CKC(cudaMemsetAsync(p->y, 0, sizeof(float) * (MJ + 1), p->stream));
   CKC(dalloc(&p->gamma_tab, kMaxStages));
   CKC(dalloc(&p->calc_gamma, 1));
   CKC(dalloc(&p->stats_out, 8));
@@ -931,7 +1059,7 @@ dlm_status dlm_create(const dlm_problem_desc* desc, void* stream, dlm_problem** 
   CKC(cudaMemcpyAsync(p->h_slice_off.data(), p->lay.slice_off, sizeof(int64_t) * (p->lay.nslices + 1),
                       cudaMemcpyDeviceToHost, p->stream));
   CKC(cudaStreamSynchronize(p->stream));
-  cleanup_tmp();
+  cleanup_all();
   for (void*& q : tmp) q = nullptr;
 #undef CKC
   // The handle's own runner: this one instance.
@@ -968,6 +1096,7 @@ dlm_status dlm_set_schedule(dlm_problem* p, double gamma0, double gamma_end, dou
 
 dlm_status dlm_set_count_limit(dlm_problem* p, double M) {
   if (!p) return fail(DLM_ERR_INVALID_ARG, "null handle");
+  if (p->m > 1) return fail(DLM_ERR_UNSUPPORTED, "a count constraint with several capacity families");
   if (std::isnan(M) || M < 0) return fail(DLM_ERR_INVALID_ARG, "M must be >= 0 (INFINITY removes the constraint)");
   CK(cudaStreamSynchronize(p->stream));
   p->count_on = std::isfinite(M);
@@ -1202,7 +1331,7 @@ dlm_status dlm_get_info(dlm_problem* p, int64_t* num_users, int64_t* num_items, 
   if (num_users) *num_users = p->I;
   if (num_items) *num_items = p->J;
   if (nnz) *nnz = p->nnz;
-  if (bytes_per_iter) *bytes_per_iter = p->nnz * (4 + 2 * (p->bf16 ? 2 : 4)) + (p->I + 1) * 8;
+  if (bytes_per_iter) *bytes_per_iter = p->nnz * (4 + (1 + p->m) * (p->bf16 ? 2 : 4)) + (p->I + 1) * 8;
   return DLM_OK;
 }
 
@@ -1210,6 +1339,7 @@ void dlm_destroy(dlm_problem* p) { free_problem(p); }
 
 dlm_status dlm_ws_features(dlm_problem* p, const float* lam_prev, double gamma, float* X) {
   if (!p || !lam_prev || !X) return fail(DLM_ERR_INVALID_ARG, "null argument");
+  if (p->m > 1) return fail(DLM_ERR_UNSUPPORTED, "warm-start features with several capacity families");
   if (!(gamma > 0) || !std::isfinite(gamma)) return fail(DLM_ERR_INVALID_ARG, "gamma must be > 0");
   float* grad = nullptr;
   unsigned* deg = nullptr;
@@ -1252,6 +1382,7 @@ dlm_status dlm_batch_create(dlm_problem* const* probs, int32_t n, void* stream, 
     if (!probs[i]) return fail(DLM_ERR_INVALID_ARG, "null problem in batch");
     if (probs[i]->bf16 != probs[0]->bf16) return fail(DLM_ERR_INVALID_ARG, "batch members must share val_dtype");
     if (probs[i]->device != probs[0]->device) return fail(DLM_ERR_INVALID_ARG, "batch members must share a device");
+    if (probs[i]->m > 1) return fail(DLM_ERR_UNSUPPORTED, "batch members with several capacity families");
     for (int k = 0; k < i; ++k)
       if (probs[k] == probs[i]) return fail(DLM_ERR_INVALID_ARG, "a problem appears twice in the batch");
   }

@@ -18,6 +18,7 @@ constexpr int kSweepThreads = 1024;  // 32 warps per sweep CTA, one CTA per SM
 constexpr int kUpdThreads = 1024;    // one CTA per instance for the O(J) kernels
 constexpr int kMaxStages = 64;       // continuation stages tabulated (gamma is flat after)
 constexpr int kMaxSegTasks = 16;     // tasks of one instance in one CTA
+constexpr int kMaxFamilies = 4;      // capacity families per instance (Def. 1)
 
 // Error bits of the device status word.
 enum : int32_t { kStatNumeric = 1, kStatTimeout = 2 };
@@ -53,6 +54,7 @@ struct UpdInst {
   double inv_scaleN;
   double count_M;
   double inv_h_count;             // 1 / curvature bound of the count row (row normalization)
+  int32_t ncap;                   // capacity coordinates m J (the count dual is coordinate ncap)
 };
 
 // Per-instance view for the sweep kernels (device memory; one table for the
@@ -81,6 +83,11 @@ struct InstDesc {
   int32_t J;
   int32_t kind;
   int32_t count_on;         // 1: the dual vector has J + 1 entries, y[J] is the count dual mu
+  // m capacity families (sweep_multi.cu): y, acc are [m J] family-major, and
+  // family k >= 1's coefficients are a stream at a_ext + (k - 1) * ext_stride
+  int32_t m;
+  const void* a_ext;
+  int64_t ext_stride;
 };
 
 // A task: slices first, first + stride, ... (< end) of instance `inst`.  The
@@ -106,6 +113,7 @@ struct SweepLaunch {
   int32_t nunits;
   unsigned* ctr;            // device [2]: next unit, finished CTAs (zero between launches)
   bool count;               // some instance has a global count constraint (its own instantiation)
+  int32_t fam;              // capacity families (> 1: the general sweep of sweep_multi.cu)
 };
 constexpr int kDefaultCoopMax = 12;
 
@@ -127,6 +135,7 @@ struct StatsInst {
   unsigned long long* cnt;    // fixed-point sum of all x at lam (reset here)
   double inv_sN;
   double count_M;
+  int32_t m;                  // capacity families: acc, b, lam, grad_out are [m J] family-major
 };
 
 // Sets the thread-local message returned by dlm_last_error (api.cu).
@@ -139,6 +148,10 @@ cudaError_t sweep_prepare(bool bf16);  // raises the dynamic shared-memory limit
 cudaError_t launch_sweep(const SweepLaunch& L, bool stats, bool bf16);
 cudaError_t launch_update(const UpdInst* dev_tab, int ninst, cudaStream_t s);
 cudaError_t launch_stats(const StatsInst* dev_tab, int ninst, cudaStream_t s);
+// sweep_multi.cu (m > 1 families; static tasks only)
+size_t sweep_multi_smem_bytes(int smemJ, int m, bool stats);
+cudaError_t sweep_multi_prepare(bool bf16);
+cudaError_t launch_sweep_multi(const SweepLaunch& L, bool stats, bool bf16);
 
 // warmstart.cu: per-item features from the laid-out edges (scratch: J each).
 cudaError_t launch_item_features(const int32_t* col, const void* ca, bool bf, int64_t padded, int J, double scale,
@@ -161,6 +174,14 @@ struct LayoutOut {
   double max_abs_a = 0, max_abs_c = 0;
   bool a_nonneg = true;
 };
+// families.cu: set-up of instances with m > 1 capacity families.
+struct LayoutOut;
+cudaError_t families_split(const void* a, int64_t nnz, int m, bool bf16, void* out, int64_t stride, cudaStream_t s);
+cudaError_t families_check(const void* a, int64_t n, bool bf16, int* flags, unsigned* max_abs, cudaStream_t s);
+cudaError_t families_gather(const LayoutOut& lay, const void* src, bool bf16, void* dst, cudaStream_t s);
+cudaError_t families_gram(const int32_t* col, const void* af, const void* al, int64_t nnz, bool bf16, float scale,
+                          unsigned long long* acc, cudaStream_t s);
+
 // Validates and lays out one instance; all pointers are device pointers.
 // Returns DLM_OK or an error with `msg` set.
 dlm_status build_layout(int64_t I, int64_t J, int64_t nnz, const int64_t* rp, const int32_t* col, const void* c,

@@ -39,43 +39,10 @@
 #include <cuda_bf16.h>
 
 #include "dlm_impl.cuh"
+#include "sweep_common.cuh"
 
 namespace dlm {
 namespace {
-
-constexpr unsigned kFull = 0xffffffffu;
-
-// One interleaved (c, a) element, and a group of four consecutive edges of a
-// lane (element index 4 q .. 4 q + 3 of the stream, 16-byte aligned).
-struct F32Pair {
-  using T = float2;
-  static constexpr bool kCount = false;
-  __device__ __forceinline__ static void get(const T& w, float& c, float& a) {
-    c = w.x;
-    a = w.y;
-  }
-  __device__ __forceinline__ static void get4(const T* base, int q, float c[4], float a[4]) {
-    const float4* p = reinterpret_cast<const float4*>(base) + 2 * q;
-    const float4 v0 = __ldg(p), v1 = __ldg(p + 1);
-    c[0] = v0.x, a[0] = v0.y, c[1] = v0.z, a[1] = v0.w;
-    c[2] = v1.x, a[2] = v1.y, c[3] = v1.z, a[3] = v1.w;
-  }
-};
-struct BF16Pair {
-  using T = uint32_t;
-  static constexpr bool kCount = false;
-  __device__ __forceinline__ static void get(const T& w, float& c, float& a) {
-    c = __uint_as_float(w << 16);
-    a = __uint_as_float(w & 0xffff0000u);
-  }
-  __device__ __forceinline__ static void get4(const T* base, int q, float c[4], float a[4]) {
-    const uint4 v = __ldg(reinterpret_cast<const uint4*>(base) + q);
-    get(v.x, c[0], a[0]);
-    get(v.y, c[1], a[1]);
-    get(v.z, c[2], a[2]);
-    get(v.w, c[3], a[3]);
-  }
-};
 
 // The same value layouts for instances with a global count constraint: the
 // count dual mu floors the threshold and every deposit adds x to the count.
@@ -85,46 +52,6 @@ template <class Base>
 struct Counted : Base {
   static constexpr bool kCount = true;
 };
-
-// Position of edge k of lane t inside a slice of width w (w4 = w / 4 groups
-// of four edges per lane, then w % 4 edges edge-major; see layout.cu).
-__device__ __forceinline__ int sell_el(int k, int t, int w4) {
-  return k < 4 * w4 ? 4 * (32 * (k >> 2) + t) + (k & 3) : 128 * w4 + 32 * (k - 4 * w4) + t;
-}
-
-__device__ __forceinline__ unsigned long long fixp(float v, float scale) {
-  return static_cast<unsigned long long>(__float2ll_rn(v * scale));
-}
-
-// Unevaluated float pairs hi + lo (error-free transformations: Knuth's
-// TwoSum, and TwoProduct by FMA).
-struct F2 {
-  float h, l;
-};
-__device__ __forceinline__ F2 two_sum(float a, float b) {
-  const float s = a + b;
-  const float bp = s - a;
-  return {s, (a - (s - bp)) + (b - bp)};
-}
-__device__ __forceinline__ F2 f2_add(F2 a, F2 b) {
-  const F2 s = two_sum(a.h, b.h);
-  return {s.h, s.l + (a.l + b.l)};
-}
-// u = -(c + a*y) as a pair: a*y = p + pe exactly, then -c - p by TwoSum.
-__device__ __forceinline__ F2 u_pair(float c, float a, float y) {
-  const float p = a * y;
-  const float pe = fmaf(a, y, -p);
-  const F2 s = two_sum(-c, -p);
-  return {s.h, s.l - pe};
-}
-// (sum - gz) / n for a pair sum; the quotient's remainder is exact by FMA.
-__device__ __forceinline__ F2 f2_threshold(F2 sum, float gzh, float gzl, int n) {
-  const F2 num = f2_add(sum, F2{-gzh, -gzl});
-  const float fn = static_cast<float>(n);
-  const float th = __fdiv_rn(num.h, fn);
-  const float r = fmaf(-th, fn, num.h);
-  return {th, __fdiv_rn(r + num.l, fn)};
-}
 
 struct Seg {
   float gamma, invg, gz, gzl, z;
@@ -157,17 +84,6 @@ __device__ __forceinline__ float x_general(const Seg& S, bool box, float tau, fl
   const F2 up = u_pair(c, a, y);
   if (box) return fminf(fmaxf(((up.h - tau) + (up.l - taul)) * S.invg, 0.f), S.z);
   return fmaxf((up.h - tau) + (up.l - taul), 0.f) * S.invg;
-}
-
-__device__ __forceinline__ float warp_sum(float v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
-  return v;
-}
-__device__ __forceinline__ int warp_sumi(int v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
-  return v;
 }
 
 // Threshold of user t of the slice computed by the whole warp: lane l takes

@@ -69,15 +69,17 @@ __global__ void __launch_bounds__(kUpdThreads) fista_update_kernel(const UpdInst
   const double th1 = 0.5 * (1.0 + sqrt(1.0 + 4.0 * st.theta * st.theta));
   const float beta = static_cast<float>((st.theta - 1.0) / th1);
   const float step0 = static_cast<float>(gamma * U.inv_nmax);
-  // coordinates 0..J-1 are the items; J is the count dual when present
-  const int D = U.J + (U.count_on ? 1 : 0);
+  // coordinates 0..ncap-1 are (family, item) pairs; ncap is the count dual
+  // when present
+  const int NC = U.ncap;
+  const int D = NC + (U.count_on ? 1 : 0);
   auto grad_of = [&](int j) {
-    return j < U.J ? static_cast<float>(to_real(U.acc[j], U.inv_scaleG) - U.b[j])
-                   : static_cast<float>(to_real(*U.cnt, U.inv_scaleN) - U.count_M);
+    return j < NC ? static_cast<float>(to_real(U.acc[j], U.inv_scaleG) - U.b[j])
+                  : static_cast<float>(to_real(*U.cnt, U.inv_scaleN) - U.count_M);
   };
   auto lam_next = [&](int j, float& step, float& yj) {
     const float G = grad_of(j);
-    step = U.precondition ? static_cast<float>(gamma * (j < U.J ? U.inv_n2[j] : U.inv_h_count)) : step0;
+    step = U.precondition ? static_cast<float>(gamma * (j < NC ? U.inv_n2[j] : U.inv_h_count)) : step0;
     yj = U.y[j];
     return fmaxf(0.f, fmaf(step, G, yj));
   };
@@ -104,7 +106,7 @@ __global__ void __launch_bounds__(kUpdThreads) fista_update_kernel(const UpdInst
     const float yn = restart ? ln : fmaf(beta, ln - U.lam[j], ln);
     U.lam[j] = ln;
     U.y[j] = yn;
-    if (j < U.J)
+    if (j < NC)
       U.acc[j] = 0ull;
     else
       *U.cnt_rw = 0ull;
@@ -128,7 +130,8 @@ __global__ void __launch_bounds__(kUpdThreads) fista_update_kernel(const UpdInst
 //   s_j = min(1, b_j / (A x)_j),  P = sum_j s_j (c x)_j + gamma/2 s_j^2 (x^2)_j.
 // With a count constraint sum x <= M (dual mu = lam[J]): g gains mu (sum x - M)
 // and every s_j is multiplied by t = min(1, M / sum x), which keeps the scaled
-// point within the count (sum_j s_j (sum_i x_ij) <= sum x).
+// point within the count (sum_j s_j (sum_i x_ij) <= sum x).  With m capacity
+// families, s_j = min over the families of min(1, b_kj / (A_k x)_j).
 __global__ void __launch_bounds__(kUpdThreads) stats_kernel(const StatsInst* __restrict__ tab) {
   __shared__ double sh[32];
   const StatsInst S = tab[blockIdx.x];
@@ -140,25 +143,30 @@ __global__ void __launch_bounds__(kUpdThreads) stats_kernel(const StatsInst* __r
   const double t = (S.count_on && total > S.count_M) ? S.count_M / total : 1.0;
   __syncthreads();  // every thread has read the count sum before it is reset below
   double lg = 0.0, P = 0.0, viol = 0.0;
+  const int m = S.m > 0 ? S.m : 1;
   for (int j = threadIdx.x; j < S.J; j += blockDim.x) {
-    const double Ax = to_real(S.acc[j], S.inv_sG);
+    double s = t;
+    for (int f = 0; f < m; ++f) {
+      const int q = f * S.J + j;
+      const double Ax = to_real(S.acc[q], S.inv_sG);
+      const double G = Ax - S.b[q];
+      lg += static_cast<double>(S.lam[q]) * G;
+      if (Ax > S.b[q]) s = fmin(s, t * (S.b[q] / Ax));
+      viol = fmax(viol, G);
+      if (S.grad_out) S.grad_out[q] = static_cast<float>(G);
+      S.acc[q] = 0ull;
+    }
     const double Cx = to_real(S.accC[j], S.inv_sC);
     const double Qx = to_real(S.accQ[j], S.inv_sQ);
-    const double G = Ax - S.b[j];
-    lg += static_cast<double>(S.lam[j]) * G;
-    const double s = t * (Ax > S.b[j] ? S.b[j] / Ax : 1.0);
     P += s * Cx + 0.5 * gamma * s * s * Qx;
-    viol = fmax(viol, G);
-    if (S.grad_out) S.grad_out[j] = static_cast<float>(G);
-    S.acc[j] = 0ull;
     S.accC[j] = 0ull;
     S.accQ[j] = 0ull;
   }
   if (S.count_on && threadIdx.x == 0) {
     const double G = total - S.count_M;
-    lg += static_cast<double>(S.lam[S.J]) * G;
+    lg += static_cast<double>(S.lam[m * S.J]) * G;
     viol = fmax(viol, G);
-    if (S.grad_out) S.grad_out[S.J] = static_cast<float>(G);
+    if (S.grad_out) S.grad_out[m * S.J] = static_cast<float>(G);
     *S.cnt = 0ull;
   }
   obj = block_sum(obj, sh);

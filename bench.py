@@ -41,6 +41,11 @@ WORKLOADS = {
         desc="production shape: 20M users x 2,000 items, ~500M nnz; same generators; c, a FP32; "
              "gamma continuation 1e-1 -> 1e-3 halved every 100 iterations",
         users=20_000_000, items=2_000, seed=1001, bf16=False, schedule=(1e-1, 1e-3, 0.5, 100)),
+    "families": dict(
+        desc="two capacity families (Def. 1): the production shape, 20M users x 2,000 items, ~500M nnz, with a "
+             "second coefficient per edge a2 = U(0.1, 2) and b2_j = 0.05 sum_i a2_ij; c, a, a2 stored BF16; "
+             "gamma = 1e-3 fixed; the general multi-family sweep",
+        users=20_000_000, items=2_000, seed=1001, bf16=True, schedule=(1e-3, 1e-3, 0.5, 1 << 30), families=2),
     "batched": dict(
         desc="batched form: 64 independent instances of the production generators, users log-uniform 1e4-5e6, "
              "items log-uniform 50-2,000, gamma drawn from {1e-1, 1e-2, 1e-3} (fixed per instance); c, a stored "
@@ -61,7 +66,7 @@ def recipe_for(name, scale):
     I = max(1000, int(round(w["users"] * scale)))
     if name == "tiny":
         return synth.recipe_tiny(w["seed"])
-    if name == "production":
+    if name in ("production", "families"):
         return synth.recipe_production(I=I, J=w["items"], seed=w["seed"])
     return synth.recipe_precision(I=I, J=w["items"], seed=w["seed"])
 
@@ -183,6 +188,24 @@ def make_instance(recipe, bf16, torch, pinned, threads):
     else:
         inst = synth.generate(recipe, nthreads=threads, alloc=pin_alloc)
     return inst
+
+
+def add_second_family(inst, torch, threads):
+    """A second capacity family: a2 = U(0.1, 2) per edge (seeded), b2_j = 0.05
+    sum_i a2_ij; inst.a becomes the [nnz, 2] edge-major BF16 pair array and
+    inst.b the [2, J] capacities."""
+    import numpy as np
+    import synth
+
+    a2 = (0.1 + 1.9 * synth.uniforms(1005, 0, 7, inst.nnz)).astype(np.float32)
+    b2 = 0.05 * np.bincount(inst.col, weights=synth.bf16_to_f32(synth.round_bf16(a2, threads)).astype(np.float64),
+                            minlength=inst.J)
+    pair = torch.empty((inst.nnz, 2), dtype=torch.int16, pin_memory=True).numpy().view(np.uint16)
+    pair[:, 0] = inst.a
+    pair[:, 1] = synth.round_bf16(a2, threads)
+    inst.a = pair
+    inst.b = np.ascontiguousarray(np.stack([inst.b, b2]))
+    inst.c32 = inst.a32 = None
 
 
 def bf16_error_statement(dlm, torch, s_bf16, inst, recipe, gamma, frac, threads):
@@ -443,6 +466,8 @@ def main():
     recipe = recipe_for(args.workload, args.scale)
     t_gen = time.perf_counter()
     inst = make_instance(recipe, bf16, torch, True, args.threads)
+    if w.get("families", 1) > 1:
+        add_second_family(inst, torch, args.threads)
     t_gen = time.perf_counter() - t_gen
 
     # Device-resident inputs.
@@ -503,12 +528,13 @@ def main():
     graph_ms_per_step = e0.elapsed_time(e1) / args.steps
 
     bf16_err = None
-    if bf16 and not args.no_error_statement:
+    if bf16 and not args.no_error_statement and w.get("families", 1) == 1:
         bf16_err = bf16_error_statement(dlm, torch, s, inst, recipe, w["schedule"][1], args.cpu_frac, args.threads)
 
     # ---- end to end through the C-ABI: host (pinned) inputs -> create ->
     # iterations -> lam back to the host, every step ----
-    lam_host = torch.empty(J, dtype=torch.float32, pin_memory=True)
+    dual_dim = w.get("families", 1) * J
+    lam_host = torch.empty(dual_dim, dtype=torch.float32, pin_memory=True)
     h2d = inst.row_ptr.nbytes + inst.col.nbytes + inst.c.nbytes + inst.a.nbytes + inst.b.nbytes
     del s
     torch.cuda.synchronize(dev)
@@ -541,7 +567,7 @@ def main():
             "sweep_us": sweep_s * 1e6, "update_us": upd_ms * 1000.0 / iters_total}
 
     cpu = None
-    if rank == 0 and not args.no_cpu_baseline:
+    if rank == 0 and not args.no_cpu_baseline and w.get("families", 1) == 1:
         p = cpu_sample(args.workload, bf16, args.cpu_frac, threads=args.threads)
         nc = host_cores()
         v1, it1, dt1 = time_oracle(p, w["schedule"][1], args.cpu_seconds * 0.4)
@@ -567,7 +593,7 @@ def main():
                    if bytes_iter > 1.3e8 else "inputs fit in L2 (tiny case)"},
         "roofline": roof,
         "cpu_baseline": cpu,
-        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(J * 4),
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(dual_dim * 4),
                 "note": "per step: dlm_create from pinned host arrays (copy + layout), iterations, lam to host"},
         "gpu_launches": 2 * iters_total,
         "clocks": clocks,

@@ -178,28 +178,6 @@ __device__ __forceinline__ void coop_user(const Seg& S, const float* __restrict_
   }
 }
 
-// Sorted insertion of edge k with value u into the four largest values seen
-// (v0 >= ... >= v3), keeping the edge positions of the first three (i0..i2).
-// Strict comparisons: among equal values the earlier edge ranks first.
-__device__ __forceinline__ void top4_insert(float u, int k, float& v0, float& v1, float& v2, float& v3, int& i0,
-                                            int& i1, int& i2) {
-  const bool c0 = u > v0;
-  const float t1 = c0 ? v0 : u;
-  const int k1 = c0 ? i0 : k;
-  v0 = c0 ? u : v0;
-  i0 = c0 ? k : i0;
-  const bool c1 = t1 > v1;
-  const float t2 = c1 ? v1 : t1;
-  const int k2 = c1 ? i1 : k1;
-  v1 = c1 ? t1 : v1;
-  i1 = c1 ? k1 : i1;
-  const bool c2 = t2 > v2;
-  const float t3 = c2 ? v2 : t2;
-  v2 = c2 ? t2 : v2;
-  i2 = c2 ? k2 : i2;
-  v3 = fmaxf(v3, t3);
-}
-
 // A row whose simplex active set is the r <= 3 recorded edges (on the
 // inequality simplex with tau <= 0: those of them with u > 0): load them once,
 // compute the threshold over them in pair arithmetic, deposit x on each.

@@ -46,6 +46,14 @@ WORKLOADS = {
              "second coefficient per edge a2 = U(0.1, 2) and b2_j = 0.05 sum_i a2_ij; c, a, a2 stored BF16; "
              "gamma = 1e-3 fixed; the general multi-family sweep",
         users=20_000_000, items=2_000, seed=1001, bf16=True, schedule=(1e-3, 1e-3, 0.5, 1 << 30), families=2),
+    "appendix": dict(
+        desc="the paper's appendix generator (App. A) at the preconditioning experiment's size: 25M requests x "
+             "10,000 resources, 0.1% density (nu = 10, ~250M nnz); breadth LogNormal(0,1), K_j ~ Poisson(p_j I nu) "
+             "distinct requests; value v_j u_i eps_ij (LogNormal 0.5, 0.5, 0.25) capped at 5, c = -value; "
+             "a = s_j value with s_j ~ LogNormal(0,1.5); b_j = rho_j (greedy load + 1e-3), rho_j ~ U[0.5,1]; "
+             "c, a FP32; gamma = 1e-2 fixed; row normalization (per-item steps)",
+        users=25_000_000, items=10_000, seed=1006, bf16=False, schedule=(1e-2, 1e-2, 0.5, 1 << 30),
+        precondition=True, appendix=True),
     "batched": dict(
         desc="batched form: 64 independent instances of the production generators, users log-uniform 1e4-5e6, "
              "items log-uniform 50-2,000, gamma drawn from {1e-1, 1e-2, 1e-3} (fixed per instance); c, a stored "
@@ -68,6 +76,8 @@ def recipe_for(name, scale):
         return synth.recipe_tiny(w["seed"])
     if name in ("production", "families"):
         return synth.recipe_production(I=I, J=w["items"], seed=w["seed"])
+    if name == "appendix":
+        return synth.recipe_appendix(I=I, J=w["items"], seed=w["seed"])
     return synth.recipe_precision(I=I, J=w["items"], seed=w["seed"])
 
 
@@ -176,6 +186,8 @@ def make_instance(recipe, bf16, torch, pinned, threads):
                                        np.uint16: torch.int16}[np.dtype(dtype).type], pin_memory=pinned)
         return t.numpy().view(dtype)
 
+    if isinstance(recipe, synth.AppRecipe):
+        return synth.generate_appendix(recipe, nthreads=threads, alloc=pin_alloc)
     if bf16:
         inst = synth.generate(recipe, nthreads=threads, alloc=lambda n, dt: pin_alloc(n, dt) if dt != np.float32
                               else np.empty(int(n), dt))
@@ -250,9 +262,10 @@ def bf16_error_statement(dlm, torch, s_bf16, inst, recipe, gamma, frac, threads)
             "at": "lam after the timed steps; gamma %.3g" % gamma}
 
 
-def cpu_sample(workload, bf16, frac, seed=4242, threads=0):
-    """A seeded user sample of the workload, regenerated row by row, as an
-    FP64 oracle problem (BF16 values widened exactly)."""
+def cpu_sample(workload, bf16, frac, seed=4242, threads=0, inst=None):
+    """A seeded user sample of the workload, regenerated row by row (the
+    appendix instance is drawn resource by resource, so its sample is cut
+    from ``inst``), as an FP64 oracle problem (BF16 values widened exactly)."""
     import numpy as np
     import oracle
     import synth
@@ -260,7 +273,11 @@ def cpu_sample(workload, bf16, frac, seed=4242, threads=0):
     r = recipe_for(workload, 1.0) if workload != "batched" else None
     if workload == "batched":
         return batch_sample(frac, seed, threads)
-    if workload == "tiny":
+    if workload == "appendix":
+        if inst is None:
+            inst = synth.generate_appendix(r, nthreads=threads)
+        inst = synth.subset(inst, synth.sample_users(inst.I, frac, seed))
+    elif workload == "tiny":
         inst = synth.generate(r)
     else:
         ids = synth.sample_users(r.I, frac, seed)
@@ -492,6 +509,9 @@ def main():
     torch.cuda.synchronize(dev)
     t_setup = time.perf_counter() - t_setup
     s.set_schedule(*w["schedule"])
+    precond = bool(w.get("precondition", False))
+    if precond:
+        s.set_options(precondition=True)
     info = s.info()
     nnz, I, J, bytes_iter = info["nnz"], info["num_users"], info["num_items"], info["bytes_per_iter"]
 
@@ -527,6 +547,10 @@ def main():
     torch.cuda.synchronize(dev)
     graph_ms_per_step = e0.elapsed_time(e1) / args.steps
 
+    conv = None
+    if w.get("appendix") and not args.no_time_to_gap:
+        conv = precondition_convergence(s, dlm, w["schedule"][1])
+
     bf16_err = None
     if bf16 and not args.no_error_statement and w.get("families", 1) == 1:
         bf16_err = bf16_error_statement(dlm, torch, s, inst, recipe, w["schedule"][1], args.cpu_frac, args.threads)
@@ -544,6 +568,8 @@ def main():
         t0 = time.perf_counter()
         s2 = dlm.Solver(inst.row_ptr, inst.col, inst.c, inst.a, inst.b, inst.J, bf16=bf16)
         s2.set_schedule(*w["schedule"])
+        if precond:
+            s2.set_options(precondition=True)
         s2.step(args.iters)
         dlm.dlm_get_lambda(s2.h, lam_host, dlm.DLM_MEM_HOST)
         s2.close()
@@ -568,7 +594,7 @@ def main():
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline and w.get("families", 1) == 1:
-        p = cpu_sample(args.workload, bf16, args.cpu_frac, threads=args.threads)
+        p = cpu_sample(args.workload, bf16, args.cpu_frac, threads=args.threads, inst=inst)
         nc = host_cores()
         v1, it1, dt1 = time_oracle(p, w["schedule"][1], args.cpu_seconds * 0.4)
         vn, itn, dtn = time_oracle(p, w["schedule"][1], args.cpu_seconds * 0.6, nthreads=nc)
@@ -600,6 +626,7 @@ def main():
         "graph_ms_per_step": graph_ms_per_step,
         "bf16_error": bf16_err,
         "time_to_gap": ttg,
+        "precondition_convergence": conv,
         "setup_s": {"generate": t_gen, "upload_and_create": t_setup},
     }
     if rank == 0:
@@ -607,6 +634,30 @@ def main():
     if dist is not None:
         dist.destroy_process_group()
     return 0
+
+
+def precondition_convergence(s, dlm, gamma, target=1e-4, max_iters=6000, gap_every=25):
+    """The row-normalization comparison of the preconditioning experiment on
+    this instance: from lam = 0, the solve with per-item steps to the target
+    certified gap, then the plain step 1/L for the same number of
+    iterations."""
+    import torch
+
+    out = {"target_rel_gap": target, "gamma": gamma, "gap_every": gap_every}
+    for name, pre in (("row_normalized", True), ("plain", False)):
+        lam0 = torch.zeros(s.dual_dim, dtype=torch.float32, device="cuda")
+        s.set_schedule(gamma)
+        s.set_options(precondition=pre, gap_every=gap_every, restart=True)
+        s.set_lambda(lam0)
+        limit = max_iters if pre else max(out["row_normalized"]["iters"], gap_every)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        st = s.solve(target, limit)
+        torch.cuda.synchronize()
+        out[name] = {"iters": int(st.iter), "seconds": time.perf_counter() - t0, "rel_gap": st.rel_gap,
+                     "max_viol": st.max_viol, "reached": bool(st.rel_gap <= target)}
+    s.set_options(precondition=True)
+    return out
 
 
 def time_to_gap(args, dlm, torch, dev):

@@ -148,7 +148,12 @@ typedef struct dlm_batch dlm_batch;
  * users by degree and lays the edges out for the sweep kernels.  `stream` is
  * a cudaStream_t; with NULL the handle creates its own blocking stream,
  * which is ordered with the legacy default stream in both directions.  Initial state: lam = 0,
- * fixed gamma = 1e-2, no preconditioning.  Synchronous. */
+ * fixed gamma = 1e-2, no preconditioning.  Synchronous.
+ * Item limit: every sweep CTA holds the dual and the gradient sums of all
+ * items in shared memory (12 bytes per item, about 19,000 items on a GPU with
+ * 227 KB per block; with m > 1, (12 m + 16) bytes per item); certificate
+ * sweeps of larger instances take one launch per window of items.  Beyond
+ * the limit: DLM_ERR_UNSUPPORTED. */
 dlm_status dlm_create(const dlm_problem_desc* desc, void* stream, dlm_problem** out);
 
 /* gamma schedule (Sec. 6, App. B.2 "regularization decay"): iteration t is in

@@ -90,6 +90,7 @@ struct Runner {
   int coop_max = kDefaultCoopMax;
   int assign = kAssignInterleaved;
   int smemJ = 0;
+  int win = 0;  // item window of certificate sweeps (smemJ when their arrays fit at once)
   int graph_iters = 10;
   InstDesc *inst_iter = nullptr, *inst_stats = nullptr;
   UpdInst* upd = nullptr;
@@ -464,6 +465,7 @@ SweepLaunch launch_of(const Runner& R, const InstDesc* tab) {
   L.cta_task = R.cta_task;
   L.grid = R.grid;
   L.smemJ = R.smemJ;
+  L.win = R.win;
   L.threads = R.threads;
   L.coop_max = R.coop_max;
   L.stream = R.stream;
@@ -979,8 +981,11 @@ dlm_status dlm_create(const dlm_problem_desc* desc, void* stream, dlm_problem** 
     free_problem(p);
     return fail(DLM_ERR_UNSUPPORTED, "item sums too large for 64-bit fixed point");
   }
-  if ((m > 1 ? sweep_multi_smem_bytes(static_cast<int>(J), m, true) : sweep_smem_bytes(static_cast<int>(J), true)) >
-      sweep_smem_limit()) {
+  // One family: the iteration sweep holds y and G for all items; certificate
+  // sweeps take item windows when their three item arrays do not fit.
+  if (m > 1 ? sweep_multi_smem_bytes(static_cast<int>(J), m, true) > sweep_smem_limit()
+            : (sweep_smem_bytes(static_cast<int>(J), false) > sweep_smem_limit() ||
+               sweep_stats_window(static_cast<int>(J)) < 1)) {
     cleanup_all();
     free_problem(p);
     return fail(DLM_ERR_UNSUPPORTED, "num_items too large for the shared-memory item arrays of this build");
@@ -1069,6 +1074,7 @@ dlm_status dlm_create(const dlm_problem_desc* desc, void* stream, dlm_problem** 
   R.bf16 = p->bf16;
   R.device = p->device;
   R.smemJ = static_cast<int>(J);
+  R.win = m > 1 ? R.smemJ : sweep_stats_window(R.smemJ);
   cudaDeviceGetAttribute(&R.sms, cudaDevAttrMultiProcessorCount, p->device);
   p->h_gamma_tab.assign(kMaxStages, p->gamma0);
   st = upload_steps(p);
@@ -1405,7 +1411,8 @@ dlm_status dlm_batch_create(dlm_problem* const* probs, int32_t n, void* stream, 
     cudaStreamSynchronize(probs[i]->stream);
     R.smemJ = std::max(R.smemJ, static_cast<int>(probs[i]->J));
   }
-  if (sweep_smem_bytes(R.smemJ, true) > sweep_smem_limit()) {
+  R.win = sweep_stats_window(R.smemJ);
+  if (sweep_smem_bytes(R.smemJ, false) > sweep_smem_limit() || R.win < 1) {
     if (bt->own_stream) cudaStreamDestroy(R.stream);
     delete bt;
     return fail(DLM_ERR_UNSUPPORTED, "largest num_items of the batch too large for the shared-memory item arrays");

@@ -105,6 +105,7 @@ struct SweepLaunch {
   const int32_t* cta_task;  // device [grid + 1]
   int32_t grid;
   int32_t smemJ;            // item capacity of the shared arrays
+  int32_t win;              // certificate sweeps: item window per launch (0: all smemJ items)
   int32_t threads;          // threads per sweep CTA (0: kSweepThreads)
   int32_t coop_max;         // warp-cooperative threshold path below this many users per warp
   cudaStream_t stream;
@@ -143,6 +144,10 @@ void set_last_error(const std::string& m);
 
 // ---- launchers (defined in the .cu files) ----
 size_t sweep_smem_bytes(int smemJ, bool stats);
+// Certificate sweep with item sums for a window of win items (0: none).
+size_t sweep_stats_smem_bytes(int smemJ, int win);
+// Widest item window whose certificate sweep fits (smemJ: no windows; 0: none fits).
+int sweep_stats_window(int smemJ);
 size_t sweep_smem_limit();             // usable dynamic shared memory per sweep CTA on this device
 cudaError_t sweep_prepare(bool bf16);  // raises the dynamic shared-memory limit
 cudaError_t launch_sweep(const SweepLaunch& L, bool stats, bool bf16);

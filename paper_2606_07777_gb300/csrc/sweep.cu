@@ -38,6 +38,8 @@
 // slice order, per CTA in warp order and across CTAs in task order.
 #include <cuda_bf16.h>
 
+#include <algorithm>
+
 #include "dlm_impl.cuh"
 #include "sweep_common.cuh"
 
@@ -59,6 +61,7 @@ struct Seg {
   float mu;  // count dual (0 without a count constraint): the floor of the threshold
   int kind;
   int count;
+  int jlo, jw;  // certificate sweeps: item sums kept for items jlo .. jlo + jw - 1
 };
 
 // Contributions of one edge with x > 0.
@@ -66,12 +69,17 @@ template <class P, bool STATS>
 __device__ __forceinline__ void deposit(const Seg& S, int j, float c, float a, float x, unsigned long long* accG,
                                         unsigned long long* accC, unsigned long long* accQ, float& ob,
                                         unsigned long long& cn) {
-  atomicAdd(&accG[j], fixp(a * x, S.scaleG));
   if (P::kCount) cn += fixp(x, S.scaleN);
   if (STATS) {
-    atomicAdd(&accC[j], fixp(c * x, S.scaleC));
-    atomicAdd(&accQ[j], fixp(x * x, S.scaleQ));
+    const unsigned jj = static_cast<unsigned>(j - S.jlo);
+    if (jj < static_cast<unsigned>(S.jw)) {
+      atomicAdd(&accG[jj], fixp(a * x, S.scaleG));
+      atomicAdd(&accC[jj], fixp(c * x, S.scaleC));
+      atomicAdd(&accQ[jj], fixp(x * x, S.scaleQ));
+    }
     ob += fmaf(0.5f * S.gamma * x, x, c * x);
+  } else {
+    atomicAdd(&accG[j], fixp(a * x, S.scaleG));
   }
 }
 
@@ -388,57 +396,76 @@ __device__ __forceinline__ void do_slice(const InstDesc& D, const Seg& S, const 
       }
     }
   } else if (mode == 3) {
+    // Each lane over its own row, in groups of four edges (128-bit loads, as
+    // in pass A) and then the tail, so every pass visits edges 0 .. w-1 in
+    // order.
+    auto row_pass = [&](auto&& visit) {
+      for (int g = 0; g < w4; ++g) {
+        const int q = 32 * g + lane;
+        const int4 jv = __ldg(reinterpret_cast<const int4*>(col0) + q);
+        float c[4], a[4];
+        P::get4(ca0, q, c, a);
+        visit(jv.x, c[0], a[0]);
+        visit(jv.y, c[1], a[1]);
+        visit(jv.z, c[2], a[2]);
+        visit(jv.w, c[3], a[3]);
+      }
+      for (int k = 4 * w4; k < w; ++k) {
+        const int el = 128 * w4 + 32 * (k - 4 * w4) + lane;
+        float c, a;
+        P::get(__ldg(ca0 + el), c, a);
+        visit(__ldg(col0 + el), c, a);
+      }
+    };
     if (!box) {
-      // Michelot iteration from tau_4, a lower bound of the threshold
+      // Michelot iteration from tau_4, a lower bound of the threshold: the
+      // active sets {u > tau} shrink until two passes agree.  Each pass also
+      // sums its active set in pair arithmetic, so the pass that finds the
+      // set unchanged already holds the sum the threshold is refined from.
+      F2 psum{0.f, 0.f};
+      int n = 0;
+      bool settled = false;
       int prevn = -1;
       for (int it = 0; it < 256; ++it) {
         float sm = 0.f;
-        int n = 0;
-        for (int k = 0; k < w; ++k) {
-          const int el = sell_el(k, lane, w4);
-          const int j = __ldg(col0 + el);
-          float c, a;
-          P::get(__ldg(ca0 + el), c, a);
-          const float u = -fmaf(a, ys[j], c);
+        int cnt = 0;
+        F2 ps{0.f, 0.f};
+        row_pass([&](int j, float c, float a) {
+          const float y = ys[j];
+          const float u = -fmaf(a, y, c);
           if (u > tau) {
             sm += u;
-            ++n;
+            ++cnt;
+            ps = f2_add(ps, u_pair(c, a, y));
           }
+        });
+        psum = ps;
+        n = cnt;
+        if (cnt == prevn || cnt == 0) {
+          settled = true;
+          break;
         }
-        if (n == prevn || n == 0) break;
-        prevn = n;
-        const float tn = __fdiv_rn(sm - S.gz, static_cast<float>(n));
-        if (tn == tau) break;
+        prevn = cnt;
+        const float tn = __fdiv_rn(sm - S.gz, static_cast<float>(cnt));
+        if (tn == tau) {
+          settled = true;
+          break;
+        }
         tau = tn;
       }
       zero = !eq && tau <= (P::kCount ? S.mu : 0.f);
       if (!zero) {
-        // the threshold over the active set in pair arithmetic
-        F2 sum{0.f, 0.f};
-        int n = 0;
-        auto visit = [&](int j, float c, float a) {
-          if (-fmaf(a, ys[j], c) > tau) {
-            sum = f2_add(sum, u_pair(c, a, ys[j]));
-            ++n;
-          }
-        };
-        for (int g = 0; g < w4; ++g) {
-          const int q = 32 * g + lane;
-          const int4 jv = __ldg(reinterpret_cast<const int4*>(col0) + q);
-          float c[4], a[4];
-          P::get4(ca0, q, c, a);
-          visit(jv.x, c[0], a[0]);
-          visit(jv.y, c[1], a[1]);
-          visit(jv.z, c[2], a[2]);
-          visit(jv.w, c[3], a[3]);
+        if (!settled) {  // iteration cap: the sum over the current set
+          psum = F2{0.f, 0.f};
+          n = 0;
+          row_pass([&](int j, float c, float a) {
+            if (-fmaf(a, ys[j], c) > tau) {
+              psum = f2_add(psum, u_pair(c, a, ys[j]));
+              ++n;
+            }
+          });
         }
-        for (int k = 4 * w4; k < w; ++k) {
-          const int el = 128 * w4 + 32 * (k - 4 * w4) + lane;
-          float c, a;
-          P::get(__ldg(ca0 + el), c, a);
-          visit(__ldg(col0 + el), c, a);
-        }
-        const F2 t2 = f2_threshold(sum, S.gz, S.gzl, n > 0 ? n : 1);
+        const F2 t2 = f2_threshold(psum, S.gz, S.gzl, n > 0 ? n : 1);
         if (!eq && t2.h + t2.l <= (P::kCount ? S.mu : 0.f)) {
           zero = true;
         } else {
@@ -448,20 +475,17 @@ __device__ __forceinline__ void do_slice(const InstDesc& D, const Seg& S, const 
       }
     }
     if (zero) {
-    tau = (P::kCount ? S.mu : 0.f);
-    taul = 0.f;
-  }
+      tau = (P::kCount ? S.mu : 0.f);
+      taul = 0.f;
+    }
     // x on the active edges (u > tau; for the box and tau = 0, u > 0)
-    for (int k = 0; k < w; ++k) {
-      const int el = sell_el(k, lane, w4);
-      const int j = __ldg(col0 + el);
-      float c, a;
-      P::get(__ldg(ca0 + el), c, a);
-      if (-fmaf(a, ys[j], c) > tau) {
-        const float x = x_general(S, box, tau, taul, c, a, ys[j]);
+    row_pass([&](int j, float c, float a) {
+      const float y = ys[j];
+      if (-fmaf(a, y, c) > tau) {
+        const float x = x_general(S, box, tau, taul, c, a, y);
         if (x > 0.f) deposit<P, STATS>(S, j, c, a, x, accG, accC, accQ, ob, cn);
       }
-    }
+    });
   }
 
   if (STATS) {
@@ -488,15 +512,21 @@ __device__ __forceinline__ void do_slice(const InstDesc& D, const Seg& S, const 
   }
 }
 
+// Certificate sweeps (STATS) keep the item sums of the window of items
+// jlo .. jlo + jw - 1 only, so that instances whose three item arrays do not
+// fit in shared memory take one launch per window; every launch recomputes
+// the same x and writes the same objective partials, and the count sum is
+// flushed by the launch with jlo = 0.
 template <class P, bool STATS>
 __global__ void __launch_bounds__(kSweepThreads, 1)
     sweep_kernel(const InstDesc* __restrict__ insts, const Task* __restrict__ tasks,
-                 const int32_t* __restrict__ cta_task, int smemJ, int coop_max) {
+                 const int32_t* __restrict__ cta_task, int smemJ, int coop_max, int jlo, int jw) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int accN = STATS ? jw : smemJ;
   unsigned long long* accG = reinterpret_cast<unsigned long long*>(smem_raw);
-  unsigned long long* accC = accG + smemJ;
-  unsigned long long* accQ = accC + smemJ;
-  float* ys = reinterpret_cast<float*>(accG + (STATS ? 3 : 1) * static_cast<size_t>(smemJ));
+  unsigned long long* accC = accG + accN;
+  unsigned long long* accQ = accC + accN;
+  float* ys = reinterpret_cast<float*>(accG + (STATS ? 3 : 1) * static_cast<size_t>(accN));
   double* wsum = reinterpret_cast<double*>(ys + ((smemJ + 1) & ~1));
 
   __shared__ InstDesc sD;
@@ -512,8 +542,10 @@ __global__ void __launch_bounds__(kSweepThreads, 1)
     if (threadIdx.x == 0) sD = insts[inst];
     __syncthreads();
     const int J = sD.J;
-    for (int j = threadIdx.x; j < J; j += blockDim.x) {
-      ys[j] = sD.y[j];
+    // items with sums in this launch (STATS: the window, clipped to J)
+    const int nacc = STATS ? max(0, min(J - jlo, jw)) : J;
+    for (int j = threadIdx.x; j < J; j += blockDim.x) ys[j] = sD.y[j];
+    for (int j = threadIdx.x; j < nacc; j += blockDim.x) {
       accG[j] = 0ull;
       if (STATS) {
         accC[j] = 0ull;
@@ -536,6 +568,8 @@ __global__ void __launch_bounds__(kSweepThreads, 1)
       S.kind = sD.kind;
       S.count = sD.count_on;
       S.mu = sD.count_on ? sD.y[J] : 0.f;
+      S.jlo = STATS ? jlo : 0;
+      S.jw = nacc;
     }
     unsigned long long cn = 0ull;
     if (threadIdx.x == 0) s_next = 0;
@@ -569,19 +603,22 @@ __global__ void __launch_bounds__(kSweepThreads, 1)
       for (int o = 16; o > 0; o >>= 1) wobj += __shfl_xor_sync(kFull, wobj, o);
       if (lane == 0) wsum[warp] = wobj;
     }
-    if (P::kCount && sD.count_on) {
+    if (P::kCount && sD.count_on && (!STATS || jlo == 0)) {
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) cn += __shfl_xor_sync(kFull, cn, o);
       if (lane == 0 && cn) atomicAdd(sD.cnt, cn);
     }
     __syncthreads();
-    for (int j = threadIdx.x; j < J; j += blockDim.x) {
-      const unsigned long long v = accG[j];
-      if (v) atomicAdd(sD.acc + j, v);
-      if (STATS) {
-        const unsigned long long vc = accC[j], vq = accQ[j];
-        if (vc) atomicAdd(sD.accC + j, vc);
-        if (vq) atomicAdd(sD.accQ + j, vq);
+    {
+      const int j0 = STATS ? jlo : 0;
+      for (int j = threadIdx.x; j < nacc; j += blockDim.x) {
+        const unsigned long long v = accG[j];
+        if (v) atomicAdd(sD.acc + j0 + j, v);
+        if (STATS) {
+          const unsigned long long vc = accC[j], vq = accQ[j];
+          if (vc) atomicAdd(sD.accC + j0 + j, vc);
+          if (vq) atomicAdd(sD.accQ + j0 + j, vq);
+        }
       }
     }
     if (STATS && threadIdx.x == 0) {
@@ -692,9 +729,20 @@ constexpr auto kernel_of() {
 
 }  // namespace
 
-size_t sweep_smem_bytes(int smemJ, bool stats) {
+size_t sweep_smem_bytes(int smemJ, bool stats) { return sweep_stats_smem_bytes(smemJ, stats ? smemJ : 0); }
+
+size_t sweep_stats_smem_bytes(int smemJ, int win) {
   const size_t J = static_cast<size_t>(smemJ);
-  return (stats ? 3 : 1) * J * 8 + ((J + 1) & ~static_cast<size_t>(1)) * 4 + 32 * 8;
+  const size_t acc = win > 0 ? 3 * static_cast<size_t>(win) : J;
+  return acc * 8 + ((J + 1) & ~static_cast<size_t>(1)) * 4 + 32 * 8;
+}
+
+int sweep_stats_window(int smemJ) {
+  const size_t lim = sweep_smem_limit();
+  if (sweep_stats_smem_bytes(smemJ, smemJ) <= lim) return smemJ;
+  const size_t fixed = sweep_stats_smem_bytes(smemJ, 0) - static_cast<size_t>(smemJ) * 8;
+  if (fixed >= lim) return 0;
+  return static_cast<int>(std::min<size_t>((lim - fixed) / 24, static_cast<size_t>(smemJ)));
 }
 
 size_t sweep_smem_limit() {
@@ -715,15 +763,24 @@ cudaError_t prepare_policy(int lim) {
 
 template <class P>
 cudaError_t launch_policy(const SweepLaunch& L, bool stats) {
-  const size_t sm = sweep_smem_bytes(L.smemJ, stats);
   const int th = L.threads > 0 ? L.threads : kSweepThreads;
   const int cm = L.coop_max;
-  if (!stats && L.units != nullptr)
+  if (stats) {
+    const int w = L.win > 0 ? std::min(L.win, L.smemJ) : L.smemJ;
+    if (w < 1) return cudaErrorInvalidValue;
+    const size_t sm = sweep_stats_smem_bytes(L.smemJ, w);
+    for (int jlo = 0; jlo < L.smemJ || jlo == 0; jlo += w) {
+      sweep_kernel<P, true><<<L.grid, th, sm, L.stream>>>(L.inst, L.tasks, L.cta_task, L.smemJ, cm, jlo, w);
+      const cudaError_t e = cudaGetLastError();
+      if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+  }
+  const size_t sm = sweep_smem_bytes(L.smemJ, false);
+  if (L.units != nullptr)
     sweep_dyn_kernel<P><<<L.grid, th, sm, L.stream>>>(L.inst, L.units, L.nunits, L.ctr, L.smemJ, cm);
-  else if (stats)
-    sweep_kernel<P, true><<<L.grid, th, sm, L.stream>>>(L.inst, L.tasks, L.cta_task, L.smemJ, cm);
   else
-    sweep_kernel<P, false><<<L.grid, th, sm, L.stream>>>(L.inst, L.tasks, L.cta_task, L.smemJ, cm);
+    sweep_kernel<P, false><<<L.grid, th, sm, L.stream>>>(L.inst, L.tasks, L.cta_task, L.smemJ, cm, 0, L.smemJ);
   return cudaGetLastError();
 }
 

@@ -59,6 +59,26 @@ class _Params(ctypes.Structure):
     ]
 
 
+class _AppParams(ctypes.Structure):
+    _fields_ = [
+        ("I", ctypes.c_int64),
+        ("J", ctypes.c_int32),
+        ("_pad0", ctypes.c_int32),
+        ("seed", ctypes.c_uint64),
+        ("nu", ctypes.c_double),
+        ("breadth_sigma", ctypes.c_double),
+        ("v_sigma", ctypes.c_double),
+        ("u_sigma", ctypes.c_double),
+        ("eps_sigma", ctypes.c_double),
+        ("c_max", ctypes.c_double),
+        ("s_mu", ctypes.c_double),
+        ("s_sigma", ctypes.c_double),
+        ("rho_lo", ctypes.c_double),
+        ("rho_hi", ctypes.c_double),
+        ("b_eps", ctypes.c_double),
+    ]
+
+
 @dataclasses.dataclass
 class Recipe:
     """One synthetic instance family (all fields are generator inputs)."""
@@ -117,6 +137,14 @@ def _load():
                                             vp, vp, vp, vp, vp, ctypes.c_double, ctypes.c_double, ctypes.c_int]
         lib.synth_scale_capacity.argtypes = [ctypes.c_uint64, ctypes.c_int32, ctypes.c_double, vp]
         lib.synth_uniforms.argtypes = [ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_int64, vp]
+        lib.synth_poisson.argtypes = [ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_double,
+                                      ctypes.c_int64, vp]
+        AP = P(_AppParams)
+        lib.synth_app_counts.argtypes = [AP, vp]
+        lib.synth_app_pick.argtypes = [AP, vp, vp, ctypes.c_int]
+        lib.synth_app_transpose.argtypes = [ctypes.c_int64, ctypes.c_int32, vp, vp, vp, vp, ctypes.c_int]
+        lib.synth_app_values.argtypes = [AP, ctypes.c_int64, vp, vp, vp, vp, ctypes.c_int]
+        lib.synth_app_capacity.argtypes = [AP, ctypes.c_int64, vp, vp, vp, vp, vp, ctypes.c_int]
         _lib = lib
     return _lib
 
@@ -204,6 +232,13 @@ def bf16_to_f32(bits: np.ndarray) -> np.ndarray:
 def uniforms(seed: int, uid: int, purpose: int, n: int) -> np.ndarray:
     out = np.empty(n, dtype=np.float64)
     _load().synth_uniforms(seed, uid, purpose, n, _ptr(out))
+    return out
+
+
+def poisson(seed: int, uid: int, purpose: int, mu: float, n: int) -> np.ndarray:
+    """n Poisson(mu) draws of the sampler the appendix generator uses."""
+    out = np.empty(n, dtype=np.int64)
+    _load().synth_poisson(seed, uid, purpose, mu, n, _ptr(out))
     return out
 
 
@@ -304,3 +339,104 @@ def next_day(prev: Instance, day: int, seed: int = 1004, churn_p: float = 0.02, 
     b = prev.b.copy()
     lib.synth_scale_capacity(day_seed, r.J, b_sd, _ptr(b))
     return Instance(rp, col, c, a, b, r.J, new_ids, r)
+
+
+# --------------------------------------------------------------------------
+# The appendix generator (App. A): item-major breadth, distinct requests per
+# resource, capped lognormal values, greedy-load capacities
+# --------------------------------------------------------------------------
+
+@dataclasses.dataclass
+class AppRecipe:
+    """Inputs of the App. A construction.  The paper gives its form but not
+    its parameters; the defaults are this project's choice:
+
+    * nu = 10 edges per request on average (the 0.1 % density of the
+      10,000-resource instance of the preconditioning experiment);
+    * breadth w_j ~ LogNormal(0, 1), p_j = w_j / sum w, K_j ~ Poisson(p_j I nu)
+      truncated at I;
+    * value v_j u_i eps_ij with v_j ~ LogNormal(0, 0.5), u_i ~ LogNormal(0, 0.5),
+      eps_ij ~ LogNormal(0, 0.25), capped at c_max = 5; cost c_ij = -value;
+    * a_ij = s_j * value, s_j ~ LogNormal(0, 1.5), so resource rows of A
+      differ by orders of magnitude;
+    * b_j = rho_j (l_j + 1e-3) with rho_j ~ U[0.5, 1] and l_j the greedy load.
+    """
+
+    I: int
+    J: int
+    seed: int
+    nu: float = 10.0
+    breadth_sigma: float = 1.0
+    v_sigma: float = 0.5
+    u_sigma: float = 0.5
+    eps_sigma: float = 0.25
+    c_max: float = 5.0
+    s_mu: float = 0.0
+    s_sigma: float = 1.5
+    rho_lo: float = 0.5
+    rho_hi: float = 1.0
+    b_eps: float = 1e-3
+
+    def _c(self) -> _AppParams:
+        p = _AppParams()
+        for f in dataclasses.fields(self):
+            setattr(p, f.name, getattr(self, f.name))
+        return p
+
+
+@dataclasses.dataclass
+class ItemMajor:
+    """The resource-major draw of the appendix generator: resource j's
+    requests are users[col_ptr[j]:col_ptr[j+1]], ascending."""
+
+    col_ptr: np.ndarray  # int64 [J+1]
+    users: np.ndarray  # int64 [nnz]
+
+
+def appendix_item_major(r: AppRecipe, nthreads: int = 0) -> ItemMajor:
+    lib = _load()
+    p = r._c()
+    K = np.empty(r.J, dtype=np.int64)
+    if lib.synth_app_counts(ctypes.byref(p), _ptr(K)) != 0:
+        raise MemoryError("synth_app_counts")
+    col_ptr = np.zeros(r.J + 1, dtype=np.int64)
+    np.cumsum(K, out=col_ptr[1:])
+    users = np.empty(int(col_ptr[-1]), dtype=np.int64)
+    if lib.synth_app_pick(ctypes.byref(p), _ptr(col_ptr), _ptr(users), nthreads) != 0:
+        raise MemoryError("synth_app_pick")
+    return ItemMajor(col_ptr, users)
+
+
+def generate_appendix(r: AppRecipe, nthreads: int = 0, alloc=_np_empty, want_load: bool = False):
+    """The App. A instance in this package's user-major CSR (requests are the
+    users, resources the items; requests without edges keep empty rows).
+    With ``want_load`` also returns the greedy loads l_j."""
+    lib = _load()
+    p = r._c()
+    im = appendix_item_major(r, nthreads)
+    deg = np.bincount(im.users, minlength=r.I)
+    row_ptr = alloc(r.I + 1, np.int64)
+    row_ptr[0] = 0
+    np.cumsum(deg, dtype=np.int64, out=row_ptr[1:])
+    nnz = int(row_ptr[-1])
+    col = alloc(nnz, np.int32)
+    if lib.synth_app_transpose(r.I, r.J, _ptr(im.col_ptr), _ptr(im.users), _ptr(row_ptr), _ptr(col), nthreads) != 0:
+        raise MemoryError("synth_app_transpose")
+    del im
+    c = alloc(nnz, np.float32)
+    a = alloc(nnz, np.float32)
+    if lib.synth_app_values(ctypes.byref(p), r.I, _ptr(row_ptr), _ptr(col), _ptr(c), _ptr(a), nthreads) != 0:
+        raise MemoryError("synth_app_values")
+    b = np.empty(r.J, dtype=np.float64)
+    load = np.empty(r.J, dtype=np.float64)
+    if lib.synth_app_capacity(ctypes.byref(p), r.I, _ptr(row_ptr), _ptr(col), _ptr(a), _ptr(load), _ptr(b),
+                              nthreads) != 0:
+        raise MemoryError("synth_app_capacity")
+    inst = Instance(row_ptr, col, c, a, b, r.J, None, None)
+    return (inst, load) if want_load else inst
+
+
+def recipe_appendix(I: int = 25_000_000, J: int = 10_000, seed: int = 1006) -> AppRecipe:
+    """The appendix generator at 25M requests x 10,000 resources, 0.1 %
+    density (~250M nnz)."""
+    return AppRecipe(I=I, J=J, seed=seed)

@@ -479,3 +479,261 @@ void synth_uniforms(uint64_t seed, uint64_t id, uint32_t purpose, int64_t n, dou
   rng_init(&r, seed, id, purpose);
   for (int64_t i = 0; i < n; ++i) out[i] = rng_uniform(&r);
 }
+
+/* ------------------------------------------------------------------------ */
+/* The appendix generator (App. A)                                           */
+/* ------------------------------------------------------------------------ */
+/* Item-major construction: resource j draws a lognormal breadth w_j, gets
+ * p_j = w_j / sum_k w_k and K_j ~ Poisson(p_j I nu) requests (truncated at I),
+ * chosen as K_j distinct requests uniformly at random.  Edge values are
+ * v_j u_i eps_ij capped at c_max (v, u, eps lognormal); the stored cost is
+ * its negation (minimisation); a_ij = s_j * value with lognormal s_j.
+ * Capacities come from the greedy load: every request sends its largest a_ij
+ * (first such item on ties) to that item, l_j is the sum, and
+ * b_j = rho_j (l_j + eps_b) with rho_j ~ U[rho_lo, rho_hi].
+ * Distribution parameters are inputs; the paper leaves them open. */
+typedef struct {
+  int64_t I;
+  int32_t J;
+  int32_t _pad0;
+  uint64_t seed;
+  double nu;            /* mean edges per request */
+  double breadth_sigma; /* w_j ~ LogNormal(0, breadth_sigma) */
+  double v_sigma;       /* v_j ~ LogNormal(0, v_sigma) */
+  double u_sigma;       /* u_i ~ LogNormal(0, u_sigma) */
+  double eps_sigma;     /* eps_ij ~ LogNormal(0, eps_sigma) */
+  double c_max;
+  double s_mu, s_sigma; /* s_j ~ LogNormal(s_mu, s_sigma) */
+  double rho_lo, rho_hi;
+  double b_eps;
+} synth_app_params;
+
+enum {
+  PURPOSE_APP_BREADTH = 32,
+  PURPOSE_APP_COUNT = 33,
+  PURPOSE_APP_PICK = 34,
+  PURPOSE_APP_V = 35,
+  PURPOSE_APP_U = 36,
+  PURPOSE_APP_EPS = 37,
+  PURPOSE_APP_S = 38,
+  PURPOSE_APP_RHO = 39
+};
+
+/* Poisson(mu) for any mu >= 0: the sum of independent Poisson draws over
+ * pieces of mu of at most 200 (Poisson laws add), each by inversion. */
+static int64_t rng_poisson_big(rng_t* r, double mu) {
+  int64_t k = 0;
+  while (mu > 200.0) {
+    k += rng_poisson(r, 200.0);
+    mu -= 200.0;
+  }
+  if (mu > 0) k += rng_poisson(r, mu);
+  return k;
+}
+
+static double keyed_lognormal(uint64_t seed, uint64_t id, uint32_t purpose, double mu, double sigma) {
+  rng_t r;
+  rng_init(&r, seed, id, purpose);
+  return exp(mu + sigma * rng_normal(&r));
+}
+
+/* Draw 1: K_j for every resource (sequential over j; O(J + I nu)). */
+int synth_app_counts(const synth_app_params* p, int64_t* K) {
+  const int32_t J = p->J;
+  double* w = (double*)malloc(sizeof(double) * (size_t)(J > 0 ? J : 1));
+  if (!w) return -1;
+  double tot = 0;
+  for (int32_t j = 0; j < J; ++j) {
+    w[j] = keyed_lognormal(p->seed, (uint64_t)j, PURPOSE_APP_BREADTH, 0.0, p->breadth_sigma);
+    tot += w[j];
+  }
+  for (int32_t j = 0; j < J; ++j) {
+    rng_t r;
+    rng_init(&r, p->seed, (uint64_t)j, PURPOSE_APP_COUNT);
+    int64_t k = rng_poisson_big(&r, w[j] / tot * (double)p->I * p->nu);
+    K[j] = k > p->I ? p->I : k;
+  }
+  free(w);
+  return 0;
+}
+
+static int cmp_i64(const void* x, const void* y) {
+  int64_t a = *(const int64_t*)x, b = *(const int64_t*)y;
+  return (a > b) - (a < b);
+}
+
+/* Draw 2: the K_j distinct requests of every resource, ascending, written to
+ * users[col_ptr[j] ..].  Rejection against a bitmap of taken requests; above
+ * I / 2 the I - K_j requests left out are drawn instead. */
+int synth_app_pick(const synth_app_params* p, const int64_t* col_ptr, int64_t* users, int nthreads) {
+  const int64_t I = p->I;
+  const size_t words = (size_t)((I + 63) / 64);
+  int nt = threads_or_default(nthreads);
+  int fail = 0;
+#pragma omp parallel num_threads(nt)
+  {
+    uint64_t* bm = (uint64_t*)calloc(words ? words : 1, sizeof(uint64_t));
+    int64_t* tmp = NULL;
+    int64_t cap = 0;
+    if (!bm) {
+#pragma omp atomic write
+      fail = 1;
+    }
+#pragma omp for schedule(dynamic, 1)
+    for (int32_t j = 0; j < p->J; ++j) {
+      if (!bm) continue;
+      const int64_t K = col_ptr[j + 1] - col_ptr[j];
+      int64_t* out = users + col_ptr[j];
+      const int complement = K > I / 2;
+      const int64_t n = complement ? I - K : K;
+      if (n > cap) {
+        free(tmp);
+        cap = n;
+        tmp = (int64_t*)malloc(sizeof(int64_t) * (size_t)cap);
+      }
+      rng_t r;
+      rng_init(&r, p->seed, (uint64_t)j, PURPOSE_APP_PICK);
+      for (int64_t t = 0; t < n; ++t) {
+        int64_t i;
+        do {
+          i = (int64_t)(rng_uniform(&r) * (double)I);
+          if (i >= I) i = I - 1;
+        } while (bm[i >> 6] >> (i & 63) & 1u);
+        bm[i >> 6] |= (uint64_t)1 << (i & 63);
+        tmp[t] = i;
+      }
+      if (complement) {
+        int64_t o = 0;
+        for (int64_t i = 0; i < I; ++i)
+          if (!(bm[i >> 6] >> (i & 63) & 1u)) out[o++] = i;
+      } else {
+        memcpy(out, tmp, sizeof(int64_t) * (size_t)n);
+        qsort(out, (size_t)n, sizeof(int64_t), cmp_i64);
+      }
+      for (int64_t t = 0; t < n; ++t) bm[tmp[t] >> 6] = 0;
+    }
+    free(tmp);
+    free(bm);
+  }
+  return fail ? -1 : 0;
+}
+
+/* Item-major (col_ptr, users) -> user-major columns: row i lists its
+ * resources ascending at row_ptr[i] ..  Threads own request ranges and find
+ * their part of every resource list by binary search. */
+int synth_app_transpose(int64_t I, int32_t J, const int64_t* col_ptr, const int64_t* users, const int64_t* row_ptr,
+                        int32_t* col, int nthreads) {
+  int nt = threads_or_default(nthreads);
+  int64_t nranges = (int64_t)nt * 16;
+  if (nranges > I) nranges = I > 0 ? I : 1;
+  int fail = 0;
+#pragma omp parallel num_threads(nt)
+  {
+    int64_t* fill = NULL;
+    int64_t fcap = 0;
+#pragma omp for schedule(dynamic, 1)
+    for (int64_t g = 0; g < nranges; ++g) {
+      const int64_t u0 = I * g / nranges, u1 = I * (g + 1) / nranges;
+      if (u1 - u0 > fcap) {
+        free(fill);
+        fcap = u1 - u0;
+        fill = (int64_t*)malloc(sizeof(int64_t) * (size_t)fcap);
+        if (!fill) {
+#pragma omp atomic write
+          fail = 1;
+          fcap = 0;
+          continue;
+        }
+      }
+      for (int64_t u = u0; u < u1; ++u) fill[u - u0] = row_ptr[u];
+      for (int32_t j = 0; j < J; ++j) {
+        int64_t lo = col_ptr[j], hi = col_ptr[j + 1];
+        while (lo < hi) { /* first entry >= u0 */
+          int64_t mid = lo + (hi - lo) / 2;
+          if (users[mid] < u0) lo = mid + 1; else hi = mid;
+        }
+        for (int64_t e = lo; e < col_ptr[j + 1] && users[e] < u1; ++e) col[fill[users[e] - u0]++] = j;
+      }
+    }
+    free(fill);
+  }
+  return fail ? -1 : 0;
+}
+
+/* Edge values of n requests (user-major rows from synth_app_transpose). */
+int synth_app_values(const synth_app_params* p, int64_t n, const int64_t* row_ptr, const int32_t* col, float* c,
+                     float* a, int nthreads) {
+  const int32_t J = p->J;
+  double* v = (double*)malloc(sizeof(double) * (size_t)(J > 0 ? J : 1));
+  double* s = (double*)malloc(sizeof(double) * (size_t)(J > 0 ? J : 1));
+  if (!v || !s) {
+    free(v);
+    free(s);
+    return -1;
+  }
+  for (int32_t j = 0; j < J; ++j) {
+    v[j] = keyed_lognormal(p->seed, (uint64_t)j, PURPOSE_APP_V, 0.0, p->v_sigma);
+    s[j] = keyed_lognormal(p->seed, (uint64_t)j, PURPOSE_APP_S, p->s_mu, p->s_sigma);
+  }
+  int nt = threads_or_default(nthreads);
+#pragma omp parallel for schedule(dynamic, 4096) num_threads(nt)
+  for (int64_t i = 0; i < n; ++i) {
+    if (row_ptr[i + 1] == row_ptr[i]) continue;
+    const double u = keyed_lognormal(p->seed, (uint64_t)i, PURPOSE_APP_U, 0.0, p->u_sigma);
+    for (int64_t e = row_ptr[i]; e < row_ptr[i + 1]; ++e) {
+      const int32_t j = col[e];
+      const double eps =
+          keyed_lognormal(p->seed, (uint64_t)i * (uint64_t)J + (uint64_t)j, PURPOSE_APP_EPS, 0.0, p->eps_sigma);
+      double val = v[j] * u * eps;
+      if (val > p->c_max) val = p->c_max;
+      c[e] = (float)(-val);
+      a[e] = (float)(s[j] * val);
+    }
+  }
+  free(v);
+  free(s);
+  return 0;
+}
+
+/* Greedy loads l_j (sums of the float a in fixed request chunks, chunk
+ * order) and b_j = rho_j (l_j + eps_b).  load may be NULL. */
+int synth_app_capacity(const synth_app_params* p, int64_t n, const int64_t* row_ptr, const int32_t* col,
+                       const float* a, double* load, double* b, int nthreads) {
+  const int32_t J = p->J;
+  int64_t nchunks = n / 65536;
+  if (nchunks < 1) nchunks = 1;
+  if (nchunks > 256) nchunks = 256;
+  double* part = (double*)calloc((size_t)nchunks * (size_t)J, sizeof(double));
+  if (!part) return -1;
+  int nt = threads_or_default(nthreads);
+#pragma omp parallel for schedule(dynamic, 1) num_threads(nt)
+  for (int64_t ch = 0; ch < nchunks; ++ch) {
+    int64_t u0 = n * ch / nchunks, u1 = n * (ch + 1) / nchunks;
+    double* row = part + (size_t)ch * (size_t)J;
+    for (int64_t i = u0; i < u1; ++i) {
+      int64_t best = -1;
+      for (int64_t e = row_ptr[i]; e < row_ptr[i + 1]; ++e)
+        if (best < 0 || a[e] > a[best]) best = e;
+      if (best >= 0) row[col[best]] += (double)a[best];
+    }
+  }
+  for (int32_t j = 0; j < J; ++j) {
+    double l = 0;
+    for (int64_t ch = 0; ch < nchunks; ++ch) l += part[(size_t)ch * (size_t)J + j];
+    rng_t r;
+    rng_init(&r, p->seed, (uint64_t)j, PURPOSE_APP_RHO);
+    const double rho = p->rho_lo + (p->rho_hi - p->rho_lo) * rng_uniform(&r);
+    if (load) load[j] = l;
+    b[j] = rho * (l + p->b_eps);
+  }
+  free(part);
+  return 0;
+}
+
+/* n draws of Poisson(mu) from the stream (seed, id, purpose): exposes the
+ * sampler behind K_j for distribution tests. */
+void synth_poisson(uint64_t seed, uint64_t id, uint32_t purpose, double mu, int64_t n, int64_t* out) {
+  rng_t r;
+  rng_init(&r, seed, id, purpose);
+  for (int64_t i = 0; i < n; ++i) out[i] = rng_poisson_big(&r, mu);
+}

@@ -92,7 +92,7 @@ def load_peaks():
 
 def sweep_source_hash():
     h = hashlib.sha256()
-    for f in ("sweep.cu", "sweep_common.cuh", "dlm_impl.cuh"):
+    for f in ("sweep.cu", "sweep_multi.cu", "sweep_common.cuh", "dlm_impl.cuh"):
         with open(os.path.join(ROOT, "paper_2606_07777_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -434,6 +434,7 @@ def main():
     ap.add_argument("--ref-step-seconds", type=float, default=6.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-error-statement", action="store_true")
+    ap.add_argument("--autotune", action="store_true", help="let the library's tuner pick the sweep mapping")
     ap.add_argument("--no-time-to-gap", action="store_true", help="skip the recurring-instance time-to-gap run")
     ap.add_argument("--ttg-users", type=int, default=5_000_000)
     ap.add_argument("--ttg-items", type=int, default=1_000)
@@ -518,6 +519,14 @@ def main():
     for _ in range(args.warmup):
         s.step(args.iters)
     torch.cuda.synchronize(dev)
+    tuned = None
+    if args.autotune:
+        # the library's tuner picks the sweep mapping from the warmed-up state
+        # (which it restores); its choice depends on that state, so the default
+        # keeps the library's default mapping
+        opts, tune_ms = s.autotune(3)
+        tuned = {k: opts.as_dict()[k] for k in ("mapping", "coop_max", "block_threads")}
+        tuned["sweep_ms"] = tune_ms
 
     # ---- timed region: K steps, every kernel bracketed by CUDA events ----
     sampler = ClockSampler(gpu_id_for_smi(torch, dev))
@@ -585,10 +594,19 @@ def main():
     sweep_s = sweep_ms / 1000.0 / iters_total
     achieved = bytes_iter / sweep_s / 1e9
     traffic = recorded_traffic(args.workload, nnz, I) if args.scale == 1.0 else None
+    # bytes the library's layout streams: 16-bit item indices for one family
+    # (int32 for several), the values, a 12-byte header per 32 users
+    vsz = 2 if bf16 else 4
+    fam = w.get("families", 1)
+    layout_bytes = nnz * ((2 if fam == 1 else 4) + (1 + fam) * vsz) + (I + 31) // 32 * 12
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
             "traffic": traffic, "peak_source": f"{peak_kind} (copy bandwidth, MEASURED_PEAKS.json)"
             if peak_kind == "measured" else "fallback 6.8 TB/s",
-            "kernel": "sweep_kernel", "algorithmic_bytes_per_launch": bytes_iter,
+            "kernel": ("sweep_multi_kernel" if w.get("families", 1) > 1 else
+                       "sweep_dyn_kernel" if tuned is not None and tuned["mapping"] == 3 else "sweep_kernel"),
+            "algorithmic_bytes_per_launch": bytes_iter,
+            "layout_bytes_per_launch": layout_bytes,
+            "layout_frac": layout_bytes / sweep_s / 1e9 / peak,
             "sweep_share_of_iteration": sweep_ms / tot_ms if tot_ms > 0 else None,
             "sweep_us": sweep_s * 1e6, "update_us": upd_ms * 1000.0 / iters_total}
 
@@ -615,6 +633,7 @@ def main():
         "config": {"workload": w["desc"] if args.scale == 1.0 else w["desc"] + f" (users scaled x{args.scale})",
                    "users": I, "items": J, "nnz": nnz, "storage": "bf16" if bf16 else "f32",
                    "iters_per_step": args.iters, "parallelism": "replicas" if world > 1 else "single GPU",
+                   "sweep_mapping": tuned if tuned is not None else "default",
                    "l2": f"inputs {bytes_iter / 1e9:.1f} GB per iteration >> 129 MB L2 (no flush)"
                    if bytes_iter > 1.3e8 else "inputs fit in L2 (tiny case)"},
         "roofline": roof,

@@ -178,6 +178,7 @@ InstDesc base_desc(const dlm_problem* p) {
   d.slice_off = p->lay.slice_off;
   d.slice_w = p->lay.slice_w;
   d.col = p->lay.col;
+  d.col16 = p->lay.col16;
   d.ca = p->lay.ca;
   d.orig_off = p->lay.orig_off;
   d.udeg = p->lay.udeg;
@@ -619,6 +620,7 @@ void free_problem(dlm_problem* p) {
   cudaFree(p->lay.slice_off);
   cudaFree(p->lay.slice_w);
   cudaFree(p->lay.col);
+  cudaFree(p->lay.col16);
   cudaFree(p->lay.ca);
   cudaFree(p->lay.orig_off);
   cudaFree(p->lay.udeg);
@@ -989,6 +991,23 @@ dlm_status dlm_create(const dlm_problem_desc* desc, void* stream, dlm_problem** 
     cleanup_all();
     free_problem(p);
     return fail(DLM_ERR_UNSUPPORTED, "num_items too large for the shared-memory item arrays of this build");
+  }
+  // One family: the sweep and the warm-start features stream the 16-bit item
+  // indices (the limit above keeps J below 65,536); several families: the
+  // general sweep streams int32 indices.
+  if (m == 1) {
+    if (p->lay.col16 == nullptr) {
+      cleanup_all();
+      free_problem(p);
+      return fail(DLM_ERR_UNSUPPORTED, "one-family handle without 16-bit item indices");
+    }
+    cudaStreamSynchronize(p->stream);
+    cudaFree(p->lay.col);
+    p->lay.col = nullptr;
+  } else {
+    cudaStreamSynchronize(p->stream);
+    cudaFree(p->lay.col16);
+    p->lay.col16 = nullptr;
   }
 
 #define CKC(x)                                                                     \
@@ -1368,7 +1387,7 @@ dlm_status dlm_ws_features(dlm_problem* p, const float* lam_prev, double gamma, 
     const double bound = static_cast<double>(p->lay.max_item_deg > 0 ? p->lay.max_item_deg : 1) *
                          (p->lay.max_abs_c > 0 ? p->lay.max_abs_c : 1.0);
     const double scale = std::ldexp(1.0, fixed_point_shift(bound));
-    cudaError_t e = launch_item_features(p->lay.col, p->lay.ca, p->bf16, p->lay.padded_nnz, static_cast<int>(p->J),
+    cudaError_t e = launch_item_features(p->lay.col16, p->lay.ca, p->bf16, p->lay.padded_nnz, static_cast<int>(p->J),
                                          scale, p->b, lam_prev, gamma, grad, X, deg, mx, sum, p->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(p->stream);
     if (e != cudaSuccess) st = fail(DLM_ERR_CUDA, std::string("item features: ") + cudaGetErrorString(e));

@@ -64,7 +64,8 @@ struct UpdInst {
 struct InstDesc {
   const int64_t* slice_off; // [nslices + 1]
   const int32_t* slice_w;   // [nslices] edges per lane (the slice's largest degree)
-  const int32_t* col;       // [padded nnz] item index
+  const int32_t* col;       // [padded nnz] item index (handles with m > 1 families) or nullptr
+  const uint16_t* col16;    // [padded nnz] item index as uint16 (one-family handles) or nullptr
   const void* ca;           // [padded nnz] interleaved (c, a): float2, or bf16 pair in a uint32
   const int64_t* orig_off;  // [users with edges] caller row start of each sorted user
   const int32_t* udeg;      // [users with edges] degree of each sorted user
@@ -159,7 +160,7 @@ cudaError_t sweep_multi_prepare(bool bf16);
 cudaError_t launch_sweep_multi(const SweepLaunch& L, bool stats, bool bf16);
 
 // warmstart.cu: per-item features from the laid-out edges (scratch: J each).
-cudaError_t launch_item_features(const int32_t* col, const void* ca, bool bf, int64_t padded, int J, double scale,
+cudaError_t launch_item_features(const uint16_t* col, const void* ca, bool bf, int64_t padded, int J, double scale,
                                  const double* b, const float* lam_prev, double gamma, const float* grad, float* X,
                                  unsigned* deg, int* mx, unsigned long long* sum, cudaStream_t s);
 
@@ -167,7 +168,8 @@ cudaError_t launch_item_features(const int32_t* col, const void* ca, bool bf, in
 struct LayoutOut {
   int64_t* slice_off = nullptr;  // [nslices + 1]
   int32_t* slice_w = nullptr;    // [nslices]
-  int32_t* col = nullptr;        // [padded_nnz + 32]
+  int32_t* col = nullptr;        // [padded_nnz + 32] (freed for one-family handles)
+  uint16_t* col16 = nullptr;     // [padded_nnz + 64] the same as uint16 when J <= 65,536, else nullptr
   void* ca = nullptr;            // [padded_nnz + 32]
   int64_t* orig_off = nullptr;   // [num_active_users + 32]
   int32_t* udeg = nullptr;       // [num_active_users + 32]

@@ -181,6 +181,13 @@ __global__ void k_gather(const int64_t* rp, const int32_t* col, const void* c, c
   }
 }
 
+// The item index stream as uint16 (instances with at most 65,536 items).
+__global__ void k_narrow(const int32_t* col, int64_t n, uint16_t* out) {
+  for (int64_t e = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; e < n;
+       e += static_cast<int64_t>(gridDim.x) * blockDim.x)
+    out[e] = static_cast<uint16_t>(col[e]);
+}
+
 // sum_i a_ij^2 (or sum_i a_ij) per item in 64-bit fixed point (exact, order
 // independent).
 // With J <= kSmemItems each block sums its contiguous edge range in shared
@@ -378,6 +385,13 @@ dlm_status build_layout(int64_t I, int64_t J, int64_t nnz, const int64_t* rp, co
                                         static_cast<float2*>(out->ca), out->orig_off, out->udeg);
     DLM_CK(cudaGetLastError());
   }
+  // ---- 16-bit copy of the item indices: 2 bytes per edge less to stream ----
+  if (J <= 65536) {
+    DLM_CK(cudaMalloc(&out->col16, sizeof(uint16_t) * (out->padded_nnz + 64)));
+    DLM_CK(cudaMemsetAsync(out->col16, 0, sizeof(uint16_t) * (out->padded_nnz + 64), s));
+    if (out->padded_nnz > 0) k_narrow<<<grid_for(out->padded_nnz), kT, 0, s>>>(out->col, out->padded_nnz, out->col16);
+    DLM_CK(cudaGetLastError());
+  }
 
   // ---- n_j = sum_i a_ij^2 (exact fixed point) ----
   bound_sq = static_cast<double>(out->max_item_deg) * out->max_abs_a * out->max_abs_a;
@@ -435,6 +449,7 @@ done:
     cudaFree(out->slice_w);
     cudaFree(out->slice_off);
     cudaFree(out->col);
+    cudaFree(out->col16);
     cudaFree(out->ca);
     cudaFree(out->orig_off);
     cudaFree(out->udeg);
@@ -442,6 +457,7 @@ done:
     out->slice_w = nullptr;
     out->slice_off = nullptr;
     out->col = nullptr;
+    out->col16 = nullptr;
     out->ca = nullptr;
     out->orig_off = nullptr;
     out->udeg = nullptr;

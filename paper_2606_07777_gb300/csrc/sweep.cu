@@ -55,6 +55,21 @@ struct Counted : Base {
   static constexpr bool kCount = true;
 };
 
+// Item indices as uint16: the shared-memory item arrays bound a one-family
+// handle to fewer than 65,536 items, so the layout keeps the index stream in
+// 16 bits (2 bytes per edge less to stream than int32).  A group of four
+// edges of a lane is one 64-bit load.
+template <class V>
+struct Narrow : V {
+  using IX = uint16_t;
+  __device__ __forceinline__ static const IX* idx(const InstDesc& D) { return D.col16; }
+  __device__ __forceinline__ static void idx4(const IX* p, int q, int j[4]) {
+    const uint2 v = __ldg(reinterpret_cast<const uint2*>(p) + q);
+    j[0] = static_cast<int>(v.x & 0xffffu), j[1] = static_cast<int>(v.x >> 16);
+    j[2] = static_cast<int>(v.y & 0xffffu), j[3] = static_cast<int>(v.y >> 16);
+  }
+};
+
 struct Seg {
   float gamma, invg, gz, gzl, z;
   float scaleG, scaleC, scaleQ, scaleN;
@@ -105,7 +120,7 @@ __device__ __forceinline__ float x_general(const Seg& S, bool box, float tau, fl
 template <class P, bool STATS>
 __device__ __forceinline__ void coop_user(const Seg& S, const float* __restrict__ ys, unsigned long long* accG,
                                           unsigned long long* accC, unsigned long long* accQ,
-                                          const int32_t* __restrict__ cp0, const typename P::T* __restrict__ vp0,
+                                          const typename P::IX* __restrict__ cp0, const typename P::T* __restrict__ vp0,
                                           int w, int w4, int t, float tau0, bool exact, float& tau, float& taul,
                                           bool& zero, float& ob, unsigned long long& cn) {
   const int lane = threadIdx.x & 31;
@@ -113,7 +128,7 @@ __device__ __forceinline__ void coop_user(const Seg& S, const float* __restrict_
   const bool eq = S.kind == DLM_SIMPLEX_EQ;
   auto uval = [&](int k, int& j, float& c, float& a) {
     const int e = sell_el(k, t, w4);
-    j = __ldg(cp0 + e);
+    j = static_cast<int>(__ldg(cp0 + e));
     P::get(__ldg(vp0 + e), c, a);
     return -fmaf(a, ys[j], c);
   };
@@ -196,7 +211,7 @@ __device__ __forceinline__ void coop_user(const Seg& S, const float* __restrict_
 template <class P, bool STATS>
 __device__ __forceinline__ float4 rows_upto3(const Seg S, const float* __restrict__ ys, unsigned long long* accG,
                                           unsigned long long* accC, unsigned long long* accQ,
-                                          const int32_t* __restrict__ col0, const typename P::T* __restrict__ ca0,
+                                          const typename P::IX* __restrict__ col0, const typename P::T* __restrict__ ca0,
                                           int w4, int r, int i0, int i1, int i2, float tau, bool eq,
                                           unsigned long long& cn) {
   const int lane = threadIdx.x & 31;
@@ -208,7 +223,7 @@ __device__ __forceinline__ float4 rows_upto3(const Seg S, const float* __restric
     cr[i] = ar[i] = 0.f;
     if (i < r) {
       const int el = sell_el(i == 0 ? i0 : (i == 1 ? i1 : i2), lane, w4);
-      jr[i] = __ldg(col0 + el);
+      jr[i] = static_cast<int>(__ldg(col0 + el));
       P::get(__ldg(ca0 + el), cr[i], ar[i]);
     }
   }
@@ -259,7 +274,7 @@ __device__ __forceinline__ void do_slice(const InstDesc& D, const Seg& S, const 
   const int64_t off = __ldg(D.slice_off + s);
   const int w = __ldg(D.slice_w + s);
   const int w4 = w >> 2;
-  const int32_t* __restrict__ col0 = D.col + off;
+  const typename P::IX* __restrict__ col0 = P::idx(D) + off;
   const typename P::T* __restrict__ ca0 = static_cast<const typename P::T*>(D.ca) + off;
   const bool box = S.kind == DLM_BOX;
   const bool eq = S.kind == DLM_SIMPLEX_EQ;
@@ -271,10 +286,10 @@ __device__ __forceinline__ void do_slice(const InstDesc& D, const Seg& S, const 
 #pragma unroll 4
   for (int g = 0; g < w4; ++g) {
     const int q = 32 * g + lane;
-    const int4 jv = __ldg(reinterpret_cast<const int4*>(col0) + q);
+    int jj[4];
+    P::idx4(col0, q, jj);
     float c[4], a[4];
     P::get4(ca0, q, c, a);
-    const int jj[4] = {jv.x, jv.y, jv.z, jv.w};
 #pragma unroll
     for (int e = 0; e < 4; ++e) {
       const float u = -fmaf(a[e], ys[jj[e]], c[e]);
@@ -283,7 +298,7 @@ __device__ __forceinline__ void do_slice(const InstDesc& D, const Seg& S, const 
   }
   for (int k = 4 * w4; k < w; ++k) {
     const int el = 128 * w4 + 32 * (k - 4 * w4) + lane;
-    const int j = __ldg(col0 + el);
+    const int j = static_cast<int>(__ldg(col0 + el));
     float c, a;
     P::get(__ldg(ca0 + el), c, a);
     const float u = -fmaf(a, ys[j], c);
@@ -343,7 +358,7 @@ __device__ __forceinline__ void do_slice(const InstDesc& D, const Seg& S, const 
       F2 sum{0.f, 0.f};
       for (int i = 0; i < r; ++i) {
         const int el = sell_el(i == 0 ? i0 : (i == 1 ? i1 : i2), lane, w4);
-        const int j = __ldg(col0 + el);
+        const int j = static_cast<int>(__ldg(col0 + el));
         float c, a;
         P::get(__ldg(ca0 + el), c, a);
         sum = f2_add(sum, u_pair(c, a, ys[j]));
@@ -362,7 +377,7 @@ __device__ __forceinline__ void do_slice(const InstDesc& D, const Seg& S, const 
   }
     for (int i = 0; i < r; ++i) {
       const int el = sell_el(i == 0 ? i0 : (i == 1 ? i1 : i2), lane, w4);
-      const int j = __ldg(col0 + el);
+      const int j = static_cast<int>(__ldg(col0 + el));
       float c, a;
       P::get(__ldg(ca0 + el), c, a);
       const float x = x_general(S, false, tau, taul, c, a, ys[j]);
@@ -370,7 +385,7 @@ __device__ __forceinline__ void do_slice(const InstDesc& D, const Seg& S, const 
     }
   } else if (mode == 1) {
     const int el = sell_el(i0, lane, w4);
-    const int j = __ldg(col0 + el);
+    const int j = static_cast<int>(__ldg(col0 + el));
     float c, a;
     P::get(__ldg(ca0 + el), c, a);
     deposit<P, STATS>(S, j, c, a, S.z, accG, accC, accQ, ob, cn);
@@ -402,19 +417,20 @@ __device__ __forceinline__ void do_slice(const InstDesc& D, const Seg& S, const 
     auto row_pass = [&](auto&& visit) {
       for (int g = 0; g < w4; ++g) {
         const int q = 32 * g + lane;
-        const int4 jv = __ldg(reinterpret_cast<const int4*>(col0) + q);
+        int jj[4];
+        P::idx4(col0, q, jj);
         float c[4], a[4];
         P::get4(ca0, q, c, a);
-        visit(jv.x, c[0], a[0]);
-        visit(jv.y, c[1], a[1]);
-        visit(jv.z, c[2], a[2]);
-        visit(jv.w, c[3], a[3]);
+        visit(jj[0], c[0], a[0]);
+        visit(jj[1], c[1], a[1]);
+        visit(jj[2], c[2], a[2]);
+        visit(jj[3], c[3], a[3]);
       }
       for (int k = 4 * w4; k < w; ++k) {
         const int el = 128 * w4 + 32 * (k - 4 * w4) + lane;
         float c, a;
         P::get(__ldg(ca0 + el), c, a);
-        visit(__ldg(col0 + el), c, a);
+        visit(static_cast<int>(__ldg(col0 + el)), c, a);
       }
     };
     if (!box) {
@@ -500,7 +516,7 @@ __device__ __forceinline__ void do_slice(const InstDesc& D, const Seg& S, const 
           x = (k == i0) ? S.z : 0.f;
         } else if (mode >= 2) {
           const int el = sell_el(k, lane, w4);
-          const int j = __ldg(col0 + el);
+          const int j = static_cast<int>(__ldg(col0 + el));
           float c, a;
           P::get(__ldg(ca0 + el), c, a);
           if (-fmaf(a, ys[j], c) > tau) x = x_general(S, box, tau, taul, c, a, ys[j]);
@@ -784,17 +800,25 @@ cudaError_t launch_policy(const SweepLaunch& L, bool stats) {
   return cudaGetLastError();
 }
 
+template <class V>
+cudaError_t prepare_values(int lim) {
+  cudaError_t e = prepare_policy<Narrow<V>>(lim);
+  if (e == cudaSuccess) e = prepare_policy<Counted<Narrow<V>>>(lim);
+  return e;
+}
+
+template <class V>
+cudaError_t launch_values(const SweepLaunch& L, bool stats) {
+  return L.count ? launch_policy<Counted<Narrow<V>>>(L, stats) : launch_policy<Narrow<V>>(L, stats);
+}
+
 cudaError_t sweep_prepare(bool bf16) {
   const int lim = static_cast<int>(sweep_smem_limit());
-  cudaError_t e = bf16 ? prepare_policy<BF16Pair>(lim) : prepare_policy<F32Pair>(lim);
-  if (e != cudaSuccess) return e;
-  return bf16 ? prepare_policy<Counted<BF16Pair>>(lim) : prepare_policy<Counted<F32Pair>>(lim);
+  return bf16 ? prepare_values<BF16Pair>(lim) : prepare_values<F32Pair>(lim);
 }
 
 cudaError_t launch_sweep(const SweepLaunch& L, bool stats, bool bf16) {
-  if (L.count)
-    return bf16 ? launch_policy<Counted<BF16Pair>>(L, stats) : launch_policy<Counted<F32Pair>>(L, stats);
-  return bf16 ? launch_policy<BF16Pair>(L, stats) : launch_policy<F32Pair>(L, stats);
+  return bf16 ? launch_values<BF16Pair>(L, stats) : launch_values<F32Pair>(L, stats);
 }
 
 }  // namespace dlm

@@ -49,7 +49,7 @@ constexpr int kFeatSmemItems = 8192;
 
 // Per item: degree, max(-c) and sum(-c) (64-bit fixed point, exact) over the
 // laid-out edges; padding (c = +inf) is skipped.
-__global__ void k_feat_accum(const int32_t* __restrict__ col, const void* __restrict__ ca, bool bf, int64_t n,
+__global__ void k_feat_accum(const uint16_t* __restrict__ col, const void* __restrict__ ca, bool bf, int64_t n,
                              int J, float scale, unsigned* __restrict__ gdeg, int* __restrict__ gmax,
                              unsigned long long* __restrict__ gsum) {
   extern __shared__ __align__(16) unsigned char smem[];
@@ -81,7 +81,7 @@ __global__ void k_feat_accum(const int32_t* __restrict__ col, const void* __rest
       c = static_cast<const float2*>(ca)[e].x;
       if (c == INFINITY) continue;  // padding
     }
-    const int j = col[e];
+    const int j = static_cast<int>(col[e]);
     const float nc = -c;
     atomicAdd(&ddeg[j], 1u);
     atomicMax(&dmax[j], float_key(nc));
@@ -425,7 +425,7 @@ int grid_for(int64_t n, int threads = 256) {
 
 }  // namespace
 
-cudaError_t launch_item_features(const int32_t* col, const void* ca, bool bf, int64_t padded, int J, double scale,
+cudaError_t launch_item_features(const uint16_t* col, const void* ca, bool bf, int64_t padded, int J, double scale,
                                  const double* b, const float* lam_prev, double gamma, const float* grad, float* X,
                                  unsigned* deg, int* mx, unsigned long long* sum, cudaStream_t s) {
   k_feat_init<<<grid_for(J), 256, 0, s>>>(J, deg, mx, sum);

@@ -594,11 +594,11 @@ def main():
     sweep_s = sweep_ms / 1000.0 / iters_total
     achieved = bytes_iter / sweep_s / 1e9
     traffic = recorded_traffic(args.workload, nnz, I) if args.scale == 1.0 else None
-    # bytes the library's layout streams: 16-bit item indices for one family
-    # (int32 for several), the values, a 12-byte header per 32 users
+    # bytes the library's layout streams: 16-bit item indices, the values, a
+    # 12-byte header per 32 users
     vsz = 2 if bf16 else 4
     fam = w.get("families", 1)
-    layout_bytes = nnz * ((2 if fam == 1 else 4) + (1 + fam) * vsz) + (I + 31) // 32 * 12
+    layout_bytes = nnz * (2 + (1 + fam) * vsz) + (I + 31) // 32 * 12
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
             "traffic": traffic, "peak_source": f"{peak_kind} (copy bandwidth, MEASURED_PEAKS.json)"
             if peak_kind == "measured" else "fallback 6.8 TB/s",

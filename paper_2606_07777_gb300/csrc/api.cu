@@ -992,23 +992,16 @@ dlm_status dlm_create(const dlm_problem_desc* desc, void* stream, dlm_problem** 
     free_problem(p);
     return fail(DLM_ERR_UNSUPPORTED, "num_items too large for the shared-memory item arrays of this build");
   }
-  // One family: the sweep and the warm-start features stream the 16-bit item
-  // indices (the limit above keeps J below 65,536); several families: the
-  // general sweep streams int32 indices.
-  if (m == 1) {
-    if (p->lay.col16 == nullptr) {
-      cleanup_all();
-      free_problem(p);
-      return fail(DLM_ERR_UNSUPPORTED, "one-family handle without 16-bit item indices");
-    }
-    cudaStreamSynchronize(p->stream);
-    cudaFree(p->lay.col);
-    p->lay.col = nullptr;
-  } else {
-    cudaStreamSynchronize(p->stream);
-    cudaFree(p->lay.col16);
-    p->lay.col16 = nullptr;
+  // The sweeps and the warm-start features stream the 16-bit item indices
+  // (the limit above keeps J below 65,536); the int32 copy is freed.
+  if (p->lay.col16 == nullptr) {
+    cleanup_all();
+    free_problem(p);
+    return fail(DLM_ERR_UNSUPPORTED, "handle without 16-bit item indices");
   }
+  cudaStreamSynchronize(p->stream);
+  cudaFree(p->lay.col);
+  p->lay.col = nullptr;
 
 #define CKC(x)                                                                     \
   do {                                                                             \

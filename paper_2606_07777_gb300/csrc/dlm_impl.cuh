@@ -64,8 +64,8 @@ struct UpdInst {
 struct InstDesc {
   const int64_t* slice_off; // [nslices + 1]
   const int32_t* slice_w;   // [nslices] edges per lane (the slice's largest degree)
-  const int32_t* col;       // [padded nnz] item index (handles with m > 1 families) or nullptr
-  const uint16_t* col16;    // [padded nnz] item index as uint16 (one-family handles) or nullptr
+  const int32_t* col;       // [padded nnz] int32 item index (freed after set-up: nullptr)
+  const uint16_t* col16;    // [padded nnz] item index as uint16 (every handle: J < 65,536)
   const void* ca;           // [padded nnz] interleaved (c, a): float2, or bf16 pair in a uint32
   const int64_t* orig_off;  // [users with edges] caller row start of each sorted user
   const int32_t* udeg;      // [users with edges] degree of each sorted user
@@ -168,7 +168,7 @@ cudaError_t launch_item_features(const uint16_t* col, const void* ca, bool bf, i
 struct LayoutOut {
   int64_t* slice_off = nullptr;  // [nslices + 1]
   int32_t* slice_w = nullptr;    // [nslices]
-  int32_t* col = nullptr;        // [padded_nnz + 32] (freed for one-family handles)
+  int32_t* col = nullptr;        // [padded_nnz + 32] (freed once col16 exists)
   uint16_t* col16 = nullptr;     // [padded_nnz + 64] the same as uint16 when J <= 65,536, else nullptr
   void* ca = nullptr;            // [padded_nnz + 32]
   int64_t* orig_off = nullptr;   // [num_active_users + 32]

@@ -55,10 +55,10 @@ struct Counted : Base {
   static constexpr bool kCount = true;
 };
 
-// Item indices as uint16: the shared-memory item arrays bound a one-family
-// handle to fewer than 65,536 items, so the layout keeps the index stream in
-// 16 bits (2 bytes per edge less to stream than int32).  A group of four
-// edges of a lane is one 64-bit load.
+// Item indices as uint16: the shared-memory item arrays bound a handle to
+// fewer than 65,536 items, so the layout keeps the index stream in 16 bits
+// (2 bytes per edge less to stream than int32).  A group of four edges of a
+// lane is one 64-bit load.
 template <class V>
 struct Narrow : V {
   using IX = uint16_t;

@@ -52,7 +52,7 @@ template <class P, int M>
 __device__ __forceinline__ void load_edge(const InstDesc& D, const MSeg& S, int64_t off, int k, int lane, int w4,
                                           bool bf16, int& j, float& c, float a[M]) {
   const int64_t el = off + sell_el(k, lane, w4);
-  j = __ldg(D.col + el);
+  j = static_cast<int>(__ldg(D.col16 + el));
   P::get(__ldg(static_cast<const typename P::T*>(D.ca) + el), c, a[0]);
 #pragma unroll
   for (int f = 1; f < M; ++f)
@@ -134,7 +134,7 @@ __device__ __forceinline__ void multi_slice(const InstDesc& D, const MSeg& S, co
   const int w4 = w >> 2;
   const bool box = S.kind == DLM_BOX;
   const bool eq = S.kind == DLM_SIMPLEX_EQ;
-  const int32_t* __restrict__ col0 = D.col + off;
+  const uint16_t* __restrict__ col0 = D.col16 + off;
   const typename P::T* __restrict__ ca0 = static_cast<const typename P::T*>(D.ca) + off;
   const size_t vs = bf16 ? 2 : 4;
   auto ext0 = [&](int f) {
@@ -145,13 +145,14 @@ __device__ __forceinline__ void multi_slice(const InstDesc& D, const MSeg& S, co
   int i0 = 0, i1 = 0, i2 = 0;
   for (int g = 0; g < w4; ++g) {
     const int q = 32 * g + lane;
-    const int4 jv = __ldg(reinterpret_cast<const int4*>(col0) + q);
+    const uint2 jv = __ldg(reinterpret_cast<const uint2*>(col0) + q);  // four 16-bit item indices
     float c[4], a[M][4];
     P::get4(ca0, q, c, a[0]);
 #pragma unroll
     for (int f = 1; f < M; ++f)
       if (fam_on<M>(S, f)) ext_get4(ext0(f), q, bf16, a[f]);
-    const int jj[4] = {jv.x, jv.y, jv.z, jv.w};
+    const int jj[4] = {static_cast<int>(jv.x & 0xffffu), static_cast<int>(jv.x >> 16),
+                       static_cast<int>(jv.y & 0xffffu), static_cast<int>(jv.y >> 16)};
 #pragma unroll
     for (int e = 0; e < 4; ++e) {
       float t = c[e];

@@ -1,6 +1,7 @@
 """Parity at the benchmark's full sizes, in the launch configuration bench.py
-times (same layout, kernels, grid and block): after 20 iterations, x(lam) of a
-seeded user sample against the FP64 oracle evaluated one user at a time, and
+times (same layout, kernels, grid and block): after 20 iterations (400 on the
+appendix instance), x(lam) of a seeded user sample against the FP64 oracle
+evaluated one user at a time, and
 properties that hold at any size over the whole instance (the gradient equals
 A x - b of the solver's own x; weak duality of the certificate)."""
 import numpy as np
@@ -14,9 +15,13 @@ pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
 
 WORKLOADS = {
-    # users x items, storage, gamma schedule as bench.py runs them
-    "production": (synth.recipe_production(), False, (1e-1, 1e-3, 0.5, 100)),
-    "precision": (synth.recipe_precision(), True, (1e-3, 1e-3, 0.5, 1 << 30)),
+    # instance, storage, gamma schedule and row normalization as bench.py runs
+    # them, and the iterations before the check (the appendix instance is
+    # checked once half of its rows have four or more active edges)
+    "production": (lambda: synth.generate(synth.recipe_production()), False, (1e-1, 1e-3, 0.5, 100), False, 20),
+    "precision": (lambda: synth.generate(synth.recipe_precision()), True, (1e-3, 1e-3, 0.5, 1 << 30), False, 20),
+    "appendix": (lambda: synth.generate_appendix(synth.recipe_appendix()), False, (1e-2, 1e-2, 0.5, 1 << 30), True,
+                 400),
 }
 
 
@@ -29,10 +34,10 @@ def rows_index(rp, rows):
         torch.arange(total, device=rp.device) - torch.repeat_interleave(torch.cumsum(lens, 0) - lens, lens))
 
 
-@pytest.mark.parametrize("name", ["production", "precision"])
+@pytest.mark.parametrize("name", ["production", "precision", "appendix"])
 def test_full_size_sampled_parity(dlm_lib, name):
-    recipe, bf16, sched = WORKLOADS[name]
-    inst = synth.generate(recipe)
+    make, bf16, sched, precondition, iters = WORKLOADS[name]
+    inst = make()
     dev = torch.device("cuda")
     if bf16:
         c = torch.from_numpy(synth.round_bf16(inst.c).view(np.int16)).to(dev).view(torch.bfloat16)
@@ -44,7 +49,8 @@ def test_full_size_sampled_parity(dlm_lib, name):
     b = torch.from_numpy(inst.b).to(dev)
     s = dlm_lib.Solver(rp, col, c, a, b, inst.J, bf16=bf16)
     s.set_schedule(*sched)
-    s.step(20)
+    s.set_options(precondition=precondition)
+    s.step(iters)
     lam32 = s.lam()
     st = s.stats()
     gamma = st.gamma
@@ -67,5 +73,51 @@ def test_full_size_sampled_parity(dlm_lib, name):
     lam = lam32.cpu().numpy().astype(np.float64)
     ref = oracle.sweep(p, lam, gamma)
     dx, tol = x_error_report(xs, ref["x"], p, lam, gamma)
+    assert (dx <= tol).all(), f"{int((dx > tol).sum())} of {dx.size} sampled edges over tolerance, max {dx.max():.3e}"
+    s.close()
+
+
+def test_full_size_two_families_sampled_parity(dlm_lib):
+    # the families workload: the production shape (20M x 2,000, BF16) with a
+    # second coefficient a2 = U(0.1, 2) per edge and b2_j = 0.05 sum_i a2_ij,
+    # gamma = 1e-3, the general multi-family sweep
+    inst = synth.generate(synth.recipe_production())
+    a2 = (0.1 + 1.9 * synth.uniforms(1005, 0, 7, inst.nnz)).astype(np.float32)
+    c16, a16, a216 = synth.round_bf16(inst.c), synth.round_bf16(inst.a), synth.round_bf16(a2)
+    b2 = 0.05 * np.bincount(inst.col, weights=synth.bf16_to_f32(a216).astype(np.float64), minlength=inst.J)
+    dev = torch.device("cuda")
+    pair = np.stack([a16, a216], axis=1)
+    c = torch.from_numpy(c16.view(np.int16)).to(dev).view(torch.bfloat16)
+    a = torch.from_numpy(pair.view(np.int16)).to(dev).view(torch.bfloat16)
+    rp = torch.from_numpy(inst.row_ptr).to(dev)
+    col = torch.from_numpy(inst.col).to(dev)
+    b = torch.from_numpy(np.ascontiguousarray(np.stack([inst.b, b2]))).to(dev)
+    s = dlm_lib.Solver(rp, col, c, a, b, inst.J, bf16=True)
+    s.set_schedule(1e-3)
+    s.step(20)
+    lam32 = s.lam()
+    st = s.stats()
+    assert st.status == dlm_lib.DLM_OK and st.rel_gap >= -1e-9
+    g, grad, x = s.calculate(lam32, 1e-3)
+    J = inst.J
+    af = a.float()
+    for f in range(2):
+        ax = torch.zeros(J, dtype=torch.float64, device=dev)
+        ax.index_add_(0, col.long(), (af[:, f] * x).double())
+        dg = (grad[f * J:(f + 1) * J].double() - (ax - b[f])).abs()
+        assert float((dg - 2e-6 * (ax + b[f].abs()) - 1e-6).max().item()) <= 0.0, f
+    ids = synth.sample_users(inst.I, 0.001, 778)
+    eidx = rows_index(rp, torch.from_numpy(ids).to(dev))
+    xs = x[eidx].cpu().numpy()
+    sub = synth.subset(inst, ids)
+    e_host = eidx.cpu().numpy()
+    A = np.stack([synth.bf16_to_f32(a16[e_host]), synth.bf16_to_f32(a216[e_host])], axis=1).astype(np.float64)
+    cs = synth.bf16_to_f32(c16[e_host]).astype(np.float64)
+    p = oracle.Problem(sub.row_ptr, sub.col, cs, A, np.stack([inst.b, b2]), J)
+    lam = lam32.cpu().numpy().astype(np.float64)
+    ref = oracle.sweep(p, lam, 1e-3)
+    # allowance at |c| + |a2 lam2|, as in the small two-family parity tests
+    proxy = oracle.Problem(p.row_ptr, p.col, np.abs(cs) + np.abs(A[:, 1] * lam[J:][p.col]), A[:, 0], inst.b, J)
+    dx, tol = x_error_report(xs, ref["x"], proxy, lam[:J], 1e-3)
     assert (dx <= tol).all(), f"{int((dx > tol).sum())} of {dx.size} sampled edges over tolerance, max {dx.max():.3e}"
     s.close()

@@ -841,6 +841,9 @@ def run_batched(args, dlm, torch, dev, rank, world, barrier, max_over_ranks, dis
     nnz = sum(i["nnz"] for i in infos)
     users = sum(i["num_users"] for i in infos)
     bytes_iter = sum(i["bytes_per_iter"] for i in infos)
+    # bytes the layout streams: 16-bit item index + two bf16 values per edge,
+    # a 12-byte header per 32 users
+    layout_bytes = sum(6 * i["nnz"] + (i["num_users"] + 31) // 32 * 12 for i in infos)
 
     t_tune = time.perf_counter()
     chosen, tune_ms = bt.autotune(3)
@@ -918,7 +921,11 @@ def run_batched(args, dlm, torch, dev, rank, world, barrier, max_over_ranks, dis
             "traffic": recorded_traffic("batched", nnz, users) if args.scale == 1.0 else None,
             "peak_source": f"{peak_kind} (copy bandwidth, MEASURED_PEAKS.json)"
             if peak_kind == "measured" else "fallback 6.8 TB/s",
-            "kernel": "sweep_kernel (all 64 instances in one launch)", "algorithmic_bytes_per_launch": bytes_iter,
+            "kernel": ("sweep_dyn_kernel" if chosen.mapping == 3 else "sweep_kernel") +
+                      " (all 64 instances in one launch)",
+            "algorithmic_bytes_per_launch": bytes_iter,
+            "layout_bytes_per_launch": layout_bytes,
+            "layout_frac": layout_bytes / sweep_s / 1e9 / peak,
             "sweep_share_of_iteration": sweep_ms / tot_ms if tot_ms > 0 else None,
             "sweep_us": sweep_s * 1e6, "update_us": upd_ms * 1000.0 / iters_total}
     cpu = None

@@ -204,10 +204,11 @@ __device__ __forceinline__ void coop_user(const Seg& S, const float* __restrict_
 // A row whose simplex active set is the r <= 3 recorded edges (on the
 // inequality simplex with tau <= 0: those of them with u > 0): load them once,
 // compute the threshold over them in pair arithmetic, deposit x on each.
-// Returns (tau, taul, zero, objective part).  Used by the dynamic-mapping
-// sweep only: on the static sweeps the streaming pass measured 3 % slower with
-// it (rows with one active edge dominate there), while on mixed-gamma batches
-// it saves a re-read (4 % on the 64-instance batch).
+// Returns (tau, taul, zero, objective part).  Used by the iteration sweeps
+// (same arithmetic, in the same order, as the re-reading path the certificate
+// sweeps take): it saves a re-read (4 % on the 64-instance batch, 6 % on the
+// appendix instance once its rows have several active edges; no change on
+// the precision sweep).
 template <class P, bool STATS>
 __device__ __forceinline__ float4 rows_upto3(const Seg S, const float* __restrict__ ys, unsigned long long* accG,
                                           unsigned long long* accC, unsigned long long* accQ,
@@ -607,7 +608,7 @@ __global__ void __launch_bounds__(kSweepThreads, 1)
           if (lane == 0) i = atomicAdd(&s_next, 1ull);
           i = __shfl_sync(kFull, i, 0);
           if (i >= nsl) break;
-          do_slice<P, STATS>(sD, S, ys, accG, accC, accQ, T.first + i * T.stride, coop_max, wobj, cn);
+          do_slice<P, STATS, !STATS>(sD, S, ys, accG, accC, accQ, T.first + i * T.stride, coop_max, wobj, cn);
         }
         __syncthreads();
         if (threadIdx.x == 0) s_next = 0;

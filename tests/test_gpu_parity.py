@@ -1,7 +1,7 @@
 """GPU parity: the CUDA path (through the C-ABI) against the FP64 oracle on
 the same seeded inputs.
 
-Tolerances (derived in the design doc from the FP32 arithmetic):
+Tolerances (derived from the FP32 arithmetic of the per-edge path):
   x      |dx| <= 2e-6 z + 4 u x_ref, except on users with an edge within FP32
          resolution of the simplex threshold (the active set is decided in
          FP32 there), where |dx| <= 16 u (|c| + |a lam|) / gamma; u = 2^-24.

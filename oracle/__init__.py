@@ -37,7 +37,7 @@ _LIB = os.path.join(_HERE, "liboracle.so")
 _lock = threading.Lock()
 _lib = None
 
-SIMPLEX_LE, SIMPLEX_EQ, BOX = 0, 1, 2
+SIMPLEX_LE, SIMPLEX_EQ, BOX, BOX_CUT = 0, 1, 2, 3
 
 
 class _Problem(ctypes.Structure):
@@ -56,6 +56,7 @@ class _Problem(ctypes.Structure):
         ("M", ctypes.c_double),
         ("m", ctypes.c_int32),
         ("_pad2", ctypes.c_int32),
+        ("cut", ctypes.c_double),
     ]
 
 
@@ -76,7 +77,7 @@ def _load():
         lib = ctypes.CDLL(build())
         vp, i64, i32, d = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_double
         P = ctypes.POINTER(_Problem)
-        lib.orc_project.argtypes = [vp, i64, i32, d, i32, vp]
+        lib.orc_project.argtypes = [vp, i64, i32, d, d, i32, vp]
         lib.orc_project.restype = d
         lib.orc_sweep.argtypes = [P, vp, d, vp, vp, vp, vp, vp, vp]
         lib.orc_sweep.restype = d
@@ -104,9 +105,10 @@ class Problem:
     (float64, e.g. float32 or bfloat16 values widened exactly), b (float64).
     With m capacity families (Def. 1) a has shape [nnz, m] and b [m, J]; the
     dual vector is then lam[k * J + j] (m J entries, plus mu with a count
-    constraint M)."""
+    constraint M).  kind BOX_CUT: each user's x lies in [0, z] with
+    sum_j x_ij <= cut."""
 
-    def __init__(self, row_ptr, col, c, a, b, J=None, kind=SIMPLEX_LE, z=1.0, M=np.inf):
+    def __init__(self, row_ptr, col, c, a, b, J=None, kind=SIMPLEX_LE, z=1.0, M=np.inf, cut=np.inf):
         self.row_ptr = np.ascontiguousarray(row_ptr, dtype=np.int64)
         self.col = np.ascontiguousarray(col, dtype=np.int32)
         self.c = np.ascontiguousarray(c, dtype=np.float64)
@@ -123,11 +125,15 @@ class Problem:
         self.kind = int(kind)
         self.z = float(z)
         self.M = float(M)
+        self.cut = float(cut)
+        if self.kind == BOX_CUT and not (self.cut > 0 and np.isfinite(self.cut)):
+            raise ValueError("BOX_CUT needs a finite cut > 0")
         self.D = self.m * self.J + (1 if np.isfinite(self.M) else 0)  # dual dimension
         s = _Problem()
         s.I, s.J, s.nnz = self.I, self.J, self.nnz
         s.row_ptr, s.col, s.c, s.a, s.b = (_p(self.row_ptr), _p(self.col), _p(self.c), _p(self.a), _p(self.b))
         s.kind, s.z, s.M, s.m = self.kind, self.z, self.M, self.m
+        s.cut = self.cut if self.kind == BOX_CUT else 0.0
         self._s = s
 
     @classmethod
@@ -136,11 +142,12 @@ class Problem:
                    inst.J, kind, z)
 
 
-def project(v, kind=SIMPLEX_LE, z=1.0, method=0):
-    """Projection of one segment onto the simplex / box; returns (x, theta)."""
+def project(v, kind=SIMPLEX_LE, z=1.0, method=0, cut=np.inf):
+    """Projection of one segment onto the simplex / box / box cut by the
+    budget sum x <= cut; returns (x, theta)."""
     v = np.ascontiguousarray(v, dtype=np.float64)
     x = np.empty_like(v)
-    th = _load().orc_project(_p(v), v.shape[0], kind, z, method, _p(x))
+    th = _load().orc_project(_p(v), v.shape[0], kind, z, float(cut) if kind == BOX_CUT else 0.0, method, _p(x))
     return x, th
 
 

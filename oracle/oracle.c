@@ -11,7 +11,10 @@
  * with m capacity families (Sec. 3.3, Eq. dest-capacity; Def. 1):
  *     sum_i a_kij x_ij <= b_kj  for every family k and item j,
  * and per-user simple sets C_i (Sec. 3.3): the simplex {x >= 0, sum x <= z}
- * (kind 0), the simplex with equality (kind 1) or the box [0, z] (kind 2).
+ * (kind 0), the simplex with equality (kind 1), the box [0, z] (kind 2), or
+ * the box cut by one budget, {0 <= x <= z, sum x <= cut} (kind 3: the paper
+ * lists a box-cut projection among its primitives without defining it; this
+ * is the reading taken).
  *
  * Dual (Sec. 3.2, Eq. dual):  g(lam) = min_{x in C} c^T x + gamma/2 ||x||^2
  *                                       + lam^T (A x - b),
@@ -44,6 +47,7 @@ typedef struct {
   double M;               /* global count bound sum_ij x_ij <= M (Sec. 5); INFINITY: none */
   int32_t m;              /* capacity families (Def. 1): a is [nnz x m] edge-major, b [m x J] */
   int32_t _pad2;
+  double cut;             /* kind 3: per-user budget sum_j x_ij <= cut */
 } orc_problem;
 
 /* The dual vector is lam[k J + j] for family k and item j (m J entries), then
@@ -140,13 +144,91 @@ static void proj_box(const double* v, int64_t n, double u, double* x) {
   for (int64_t k = 0; k < n; ++k) x[k] = v[k] < 0 ? 0 : (v[k] > u ? u : v[k]);
 }
 
-/* Exported: project one segment.  method 0 = sort (Duchi), 1 = bisection.
- * Returns theta (0 for the box). */
-double orc_project(const double* v, int64_t n, int32_t kind, double z, int32_t method, double* x) {
+/* Box cut by one budget, {0 <= x <= z, sum x <= cut}: x = clip(v - theta, 0,
+ * z) with theta = 0 when the clipped input already meets the budget, else the
+ * root of phi(theta) = sum clip(v - theta, 0, z) - cut, which is continuous,
+ * nonincreasing and piecewise linear with breakpoints at v_k and v_k - z.
+ * Method 0 locates the root between consecutive breakpoints and solves the
+ * linear piece there; method 1 bisects on theta. */
+static double boxcut_phi(const double* v, int64_t n, double z, double cut, double t) {
+  double f = -cut;
+  for (int64_t k = 0; k < n; ++k) {
+    double y = v[k] - t;
+    f += y <= 0 ? 0 : (y >= z ? z : y);
+  }
+  return f;
+}
+
+static int cmp_asc(const void* p, const void* q) {
+  double a = *(const double*)p, b = *(const double*)q;
+  return (a > b) - (a < b);
+}
+
+static double proj_boxcut(const double* v, int64_t n, double z, double cut, int32_t method, double* x) {
+  double theta = 0.0;
+  if (n > 0 && boxcut_phi(v, n, z, cut, 0.0) > 0) {
+    double vmax = v[0];
+    for (int64_t k = 1; k < n; ++k)
+      if (v[k] > vmax) vmax = v[k];
+    if (method == 1) {
+      double lo = 0.0, hi = vmax; /* phi(lo) > 0 >= phi(hi) = -cut */
+      for (int it = 0; it < 5000; ++it) {
+        double mid = 0.5 * (lo + hi);
+        if (mid <= lo || mid >= hi) break;
+        if (boxcut_phi(v, n, z, cut, mid) > 0)
+          lo = mid;
+        else
+          hi = mid;
+      }
+      theta = 0.5 * (lo + hi);
+    } else {
+      /* breakpoints in (0, vmax], ascending, with 0 in front */
+      double* bp = (double*)malloc(sizeof(double) * (size_t)(2 * n + 1));
+      int64_t nb = 0;
+      bp[nb++] = 0.0;
+      for (int64_t k = 0; k < n; ++k) {
+        if (v[k] > 0) bp[nb++] = v[k];
+        if (v[k] - z > 0) bp[nb++] = v[k] - z;
+      }
+      qsort(bp + 1, (size_t)(nb - 1), sizeof(double), cmp_asc);
+      /* first breakpoint where phi <= 0 (exists: phi(vmax) = -cut) */
+      int64_t r = 1;
+      while (r < nb && boxcut_phi(v, n, z, cut, bp[r]) > 0) ++r;
+      const double ta = bp[r - 1], tb = r < nb ? bp[r] : vmax;
+      /* on (ta, tb) the free set F = {v - z < t < v} and the capped set U =
+       * {v - z >= t} are fixed: phi(t) = sum_F (v - t) + z |U| - cut */
+      const double mid = 0.5 * (ta + tb);
+      double sf = 0;
+      int64_t nf = 0, nu = 0;
+      for (int64_t k = 0; k < n; ++k) {
+        if (v[k] - z >= mid)
+          ++nu;
+        else if (v[k] > mid) {
+          sf += v[k];
+          ++nf;
+        }
+      }
+      theta = nf > 0 ? (sf + z * (double)nu - cut) / (double)nf : tb;
+      if (theta < ta) theta = ta;
+      if (theta > tb) theta = tb;
+      free(bp);
+    }
+  }
+  for (int64_t k = 0; k < n; ++k) {
+    double y = v[k] - theta;
+    x[k] = y <= 0 ? 0 : (y >= z ? z : y);
+  }
+  return theta;
+}
+
+/* Exported: project one segment.  method 0 = sort (Duchi) or breakpoints,
+ * 1 = bisection.  Returns theta (0 for the box). */
+double orc_project(const double* v, int64_t n, int32_t kind, double z, double cut, int32_t method, double* x) {
   if (kind == 2) {
     proj_box(v, n, z, x);
     return 0.0;
   }
+  if (kind == 3) return proj_boxcut(v, n, z, cut, method, x);
   if (method == 1) return proj_simplex_bisect(v, n, z, kind == 1, x);
   return proj_simplex_sort(v, n, z, kind == 1, x);
 }
@@ -186,7 +268,7 @@ double orc_sweep(const orc_problem* p, const double* lam, double gamma, double* 
       for (int64_t f = 0; f < m; ++f) t += p->a[e * m + f] * lam[f * J + p->col[e]];
       v[k] = -t / gamma;
     }
-    orc_project(v, d, p->kind, p->z, 0, x);
+    orc_project(v, d, p->kind, p->z, p->cut, 0, x);
     for (int64_t k = 0; k < d; ++k) {
       int64_t e = e0 + k;
       int32_t j = p->col[e];
@@ -466,7 +548,7 @@ static void* sweep_range(void* arg) {
   for (int64_t i = jb->u0; i < jb->u1; ++i) {
     int64_t e0 = p->row_ptr[i], d = p->row_ptr[i + 1] - e0;
     for (int64_t k = 0; k < d; ++k) v[k] = -(p->c[e0 + k] + p->a[e0 + k] * jb->y[p->col[e0 + k]]) / jb->gamma;
-    orc_project(v, d, p->kind, p->z, 0, x);
+    orc_project(v, d, p->kind, p->z, p->cut, 0, x);
     for (int64_t k = 0; k < d; ++k) jb->Ax[p->col[e0 + k]] += p->a[e0 + k] * x[k];
   }
   free(v);

@@ -10,7 +10,10 @@
  *
  * over the eligible edges (i, j) only.  C_i is the simplex
  * {x_i >= 0, sum_j x_ij <= z} (DLM_SIMPLEX_LE), the simplex with equality
- * (DLM_SIMPLEX_EQ) or the box [0, z]^n (DLM_BOX).  Only the capacities carry
+ * (DLM_SIMPLEX_EQ), the box [0, z]^n (DLM_BOX), or the box cut by one budget,
+ * {0 <= x_ij <= z, sum_j x_ij <= cut} (DLM_BOX_CUT: the paper lists a box-cut
+ * projection among its primitives, Table 1, without defining it; this is the
+ * reading implemented).  Only the capacities carry
  * dual variables lam >= 0 (Sec. 3.2, Eq. dual).  Each iteration evaluates the
  * dual at a point y (Eq. primal-recovery: x(y) = Proj_C(-(A^T y + c)/gamma);
  * Eq. dual-gradient: grad g(y) = A x(y) - b), then takes a projected
@@ -50,7 +53,7 @@ typedef enum {
 } dlm_status;
 
 typedef enum { DLM_F32 = 0, DLM_BF16 = 1 } dlm_dtype;
-typedef enum { DLM_SIMPLEX_LE = 0, DLM_SIMPLEX_EQ = 1, DLM_BOX = 2 } dlm_simple_kind;
+typedef enum { DLM_SIMPLEX_LE = 0, DLM_SIMPLEX_EQ = 1, DLM_BOX = 2, DLM_BOX_CUT = 3 } dlm_simple_kind;
 typedef enum { DLM_MEM_DEVICE = 0, DLM_MEM_HOST = 1 } dlm_memspace;
 
 /* The instance, as user-major CSR (the paper stores the same data as CSC with
@@ -83,6 +86,9 @@ typedef struct {
   double z;             /* simplex radius or box bound, > 0 */
   int32_t memspace;     /* dlm_memspace of the arrays above */
   int32_t num_families; /* capacity families m, 1..4 (0 means 1) */
+  double cut;           /* DLM_BOX_CUT: per-user budget sum_j x_ij <= cut, finite and > 0 (ignored
+                           otherwise); such handles take one family, no count constraint and no
+                           batch, and sweep with their own kernel (static slice orders) */
 } dlm_problem_desc;
 
 /* Solver options (zero-initialised fields take the defaults).  The mapping

@@ -28,7 +28,7 @@ WS_FEATURES = 7
 
 DLM_OK, DLM_ERR_INVALID_ARG, DLM_ERR_OOM, DLM_ERR_CUDA, DLM_ERR_NUMERIC, DLM_ERR_TIMEOUT, DLM_ERR_UNSUPPORTED = range(7)
 DLM_F32, DLM_BF16 = 0, 1
-DLM_SIMPLEX_LE, DLM_SIMPLEX_EQ, DLM_BOX = 0, 1, 2
+DLM_SIMPLEX_LE, DLM_SIMPLEX_EQ, DLM_BOX, DLM_BOX_CUT = 0, 1, 2, 3
 DLM_MEM_DEVICE, DLM_MEM_HOST = 0, 1
 
 _STATUS = {0: "DLM_OK", 1: "DLM_ERR_INVALID_ARG", 2: "DLM_ERR_OOM", 3: "DLM_ERR_CUDA", 4: "DLM_ERR_NUMERIC",
@@ -46,7 +46,7 @@ class ProblemDesc(ctypes.Structure):
                 ("row_ptr", ctypes.c_void_p), ("item_idx", ctypes.c_void_p), ("c", ctypes.c_void_p),
                 ("a", ctypes.c_void_p), ("b", ctypes.c_void_p), ("val_dtype", ctypes.c_int32),
                 ("kind", ctypes.c_int32), ("z", ctypes.c_double), ("memspace", ctypes.c_int32),
-                ("num_families", ctypes.c_int32)]
+                ("num_families", ctypes.c_int32), ("cut", ctypes.c_double)]
 
 
 class Options(ctypes.Structure):
@@ -342,7 +342,8 @@ class Solver:
     float32, or bfloat16 (torch.bfloat16 tensors or uint16 bit patterns with
     ``bf16=True``)."""
 
-    def __init__(self, row_ptr, col, c, a, b, num_items=None, kind=DLM_SIMPLEX_LE, z=1.0, bf16=None, stream=None):
+    def __init__(self, row_ptr, col, c, a, b, num_items=None, kind=DLM_SIMPLEX_LE, z=1.0, bf16=None, stream=None,
+                 cut=None):
         import torch
 
         self._torch = torch
@@ -361,6 +362,7 @@ class Solver:
         desc.row_ptr, desc.item_idx, desc.c, desc.a, desc.b = (_ptr(row_ptr), _ptr(col), _ptr(c), _ptr(a), _ptr(b))
         desc.val_dtype = DLM_BF16 if self.bf16 else DLM_F32
         desc.kind, desc.z = int(kind), float(z)
+        desc.cut = float(cut) if cut is not None else 0.0  # DLM_BOX_CUT: per-user budget
         desc.memspace = DLM_MEM_DEVICE if dev else DLM_MEM_HOST
         self.device = torch.device("cuda", torch.cuda.current_device())
         if stream is None:

@@ -10,6 +10,7 @@
 #include <string>
 #include <vector>
 
+#include "boxcut.cuh"
 #include "dlm_impl.cuh"
 
 namespace dlm {
@@ -118,6 +119,7 @@ struct dlm_problem {
   bool bf16 = false;
   int kind = DLM_SIMPLEX_LE;
   double z = 1.0;
+  double cut = 0.0;  // DLM_BOX_CUT budget
   cudaStream_t stream = nullptr;
   bool own_stream = false;
   cudaEvent_t ev = nullptr;  // orders the handle's stream before batch work
@@ -488,14 +490,22 @@ cudaError_t dispatch_sweep(const SweepLaunch& L, bool stats, bool bf16) {
   return L.fam > 1 ? launch_sweep_multi(L, stats, bf16) : launch_sweep(L, stats, bf16);
 }
 
+// Handles on the box cut by a budget sweep with their own kernel (a runner
+// holds one such handle: batches do not take them).
+cudaError_t dispatch_sweep(const Runner& R, const SweepLaunch& L, bool stats, bool bf16) {
+  if (R.probs.size() == 1 && R.probs[0]->kind == DLM_BOX_CUT)
+    return launch_sweep_boxcut(L, stats, bf16, R.probs[0]->cut);
+  return dispatch_sweep(L, stats, bf16);
+}
+
 dlm_status enqueue_iteration(Runner& R) {
-  CK(dispatch_sweep(launch_of(R, R.inst_iter), false, R.bf16));
+  CK(dispatch_sweep(R, launch_of(R, R.inst_iter), false, R.bf16));
   CK(launch_update(R.upd, static_cast<int>(R.probs.size()), R.stream));
   return DLM_OK;
 }
 
 dlm_status enqueue_certificate(Runner& R, const InstDesc* inst_tab, const StatsInst* st_tab) {
-  CK(dispatch_sweep(launch_of(R, inst_tab), true, R.bf16));
+  CK(dispatch_sweep(R, launch_of(R, inst_tab), true, R.bf16));
   CK(launch_stats(st_tab, static_cast<int>(R.probs.size()), R.stream));
   return DLM_OK;
 }
@@ -545,7 +555,7 @@ dlm_status runner_step_timed(Runner& R, int64_t n_iters, double* sweep_ms, doubl
   const int n = static_cast<int>(R.probs.size());
   CK(cudaEventRecord(R.events[0], R.stream));
   for (int64_t i = 0; i < n_iters; ++i) {
-    CK(dispatch_sweep(L, false, R.bf16));
+    CK(dispatch_sweep(R, L, false, R.bf16));
     CK(cudaEventRecord(R.events[2 * i + 1], R.stream));
     CK(launch_update(R.upd, n, R.stream));
     CK(cudaEventRecord(R.events[2 * i + 2], R.stream));
@@ -579,7 +589,8 @@ dlm_status runner_configure(Runner& R, const dlm_options& o, bool force) {
                                       : (R.probs.size() > 1 ? kAssignDynamic : kAssignInterleaved);
   int assign2 = assign;
   for (const dlm_problem* p : R.probs)
-    if (p->m > 1 && assign2 == kAssignDynamic) assign2 = R.probs.size() > 1 ? kAssignContiguous : kAssignInterleaved;
+    if ((p->m > 1 || p->kind == DLM_BOX_CUT) && assign2 == kAssignDynamic)
+      assign2 = R.probs.size() > 1 ? kAssignContiguous : kAssignInterleaved;
   R.coop_max = o.coop_max > 0 ? o.coop_max : kDefaultCoopMax;
   R.graph_iters = o.graph_iters > 0 ? o.graph_iters : 10;
   if (force || grid != R.grid || threads != R.threads || assign2 != R.assign) {
@@ -834,8 +845,13 @@ dlm_status dlm_create(const dlm_problem_desc* desc, void* stream, dlm_problem** 
   if (!desc->row_ptr || (desc->nnz > 0 && (!desc->item_idx || !desc->c || !desc->a)) || !desc->b)
     return fail(DLM_ERR_INVALID_ARG, "null array pointer");
   if (desc->val_dtype != DLM_F32 && desc->val_dtype != DLM_BF16) return fail(DLM_ERR_INVALID_ARG, "bad val_dtype");
-  if (desc->kind != DLM_SIMPLEX_LE && desc->kind != DLM_SIMPLEX_EQ && desc->kind != DLM_BOX)
+  if (desc->kind != DLM_SIMPLEX_LE && desc->kind != DLM_SIMPLEX_EQ && desc->kind != DLM_BOX &&
+      desc->kind != DLM_BOX_CUT)
     return fail(DLM_ERR_INVALID_ARG, "bad simple-set kind");
+  if (desc->kind == DLM_BOX_CUT && !(desc->cut > 0 && std::isfinite(desc->cut)))
+    return fail(DLM_ERR_INVALID_ARG, "DLM_BOX_CUT needs a finite cut > 0");
+  if (desc->kind == DLM_BOX_CUT && desc->num_families > 1)
+    return fail(DLM_ERR_UNSUPPORTED, "DLM_BOX_CUT with several capacity families");
   if (!(desc->z > 0) || !std::isfinite(desc->z)) return fail(DLM_ERR_INVALID_ARG, "z must be finite and > 0");
   if (desc->memspace != DLM_MEM_DEVICE && desc->memspace != DLM_MEM_HOST)
     return fail(DLM_ERR_INVALID_ARG, "bad memspace");
@@ -848,6 +864,7 @@ dlm_status dlm_create(const dlm_problem_desc* desc, void* stream, dlm_problem** 
   p->nnz = desc->nnz;
   p->bf16 = desc->val_dtype == DLM_BF16;
   p->kind = desc->kind;
+  p->cut = desc->kind == DLM_BOX_CUT ? desc->cut : 0.0;
   p->z = desc->z;
   p->m = m;
   p->opt.gap_every = 50;
@@ -1071,6 +1088,7 @@ dlm_status dlm_create(const dlm_problem_desc* desc, void* stream, dlm_problem** 
   CKC(cudaMallocHost(reinterpret_cast<void**>(&p->h_inst), sizeof(InstDesc)));
   CKC(cudaMallocHost(reinterpret_cast<void**>(&p->h_stinst), sizeof(StatsInst)));
   CKC(sweep_prepare(p->bf16));
+  if (p->kind == DLM_BOX_CUT) CKC(sweep_boxcut_prepare(p->bf16));
   CKC(cudaEventCreateWithFlags(&p->ev, cudaEventDisableTiming));
   p->h_slice_off.resize(p->lay.nslices + 1);
   CKC(cudaMemcpyAsync(p->h_slice_off.data(), p->lay.slice_off, sizeof(int64_t) * (p->lay.nslices + 1),
@@ -1115,6 +1133,7 @@ dlm_status dlm_set_schedule(dlm_problem* p, double gamma0, double gamma_end, dou
 dlm_status dlm_set_count_limit(dlm_problem* p, double M) {
   if (!p) return fail(DLM_ERR_INVALID_ARG, "null handle");
   if (p->m > 1) return fail(DLM_ERR_UNSUPPORTED, "a count constraint with several capacity families");
+  if (p->kind == DLM_BOX_CUT) return fail(DLM_ERR_UNSUPPORTED, "a count constraint with DLM_BOX_CUT");
   if (std::isnan(M) || M < 0) return fail(DLM_ERR_INVALID_ARG, "M must be >= 0 (INFINITY removes the constraint)");
   CK(cudaStreamSynchronize(p->stream));
   p->count_on = std::isfinite(M);
@@ -1401,6 +1420,7 @@ dlm_status dlm_batch_create(dlm_problem* const* probs, int32_t n, void* stream, 
     if (probs[i]->bf16 != probs[0]->bf16) return fail(DLM_ERR_INVALID_ARG, "batch members must share val_dtype");
     if (probs[i]->device != probs[0]->device) return fail(DLM_ERR_INVALID_ARG, "batch members must share a device");
     if (probs[i]->m > 1) return fail(DLM_ERR_UNSUPPORTED, "batch members with several capacity families");
+    if (probs[i]->kind == DLM_BOX_CUT) return fail(DLM_ERR_UNSUPPORTED, "batch members with DLM_BOX_CUT");
     for (int k = 0; k < i; ++k)
       if (probs[k] == probs[i]) return fail(DLM_ERR_INVALID_ARG, "a problem appears twice in the batch");
   }

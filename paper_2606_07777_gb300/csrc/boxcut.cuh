@@ -1,0 +1,15 @@
+// boxcut.cuh -- the sweep for handles whose simple set is the box cut by one
+// budget, C_i = {0 <= x_ij <= z, sum_j x_ij <= cut} (sweep_boxcut.cu).
+#pragma once
+
+#include "dlm_impl.cuh"
+
+namespace dlm {
+
+// One sweep (iteration or certificate) over a single box-cut instance with the
+// static task table of L; certificate sweeps take item windows like the
+// one-family sweep.  cut > 0 is the per-user budget.
+cudaError_t launch_sweep_boxcut(const SweepLaunch& L, bool stats, bool bf16, double cut);
+cudaError_t sweep_boxcut_prepare(bool bf16);
+
+}  // namespace dlm

@@ -299,6 +299,7 @@ dlm_status dlm_calculate_static(int64_t num_users, int64_t num_items, int64_t nn
     return sfail(DLM_ERR_UNSUPPORTED, "num_items exceeds the static scratch limit of 65536 items");
   if (!row_ptr || (nnz > 0 && (!item_idx || !c || !a)) || !b || !lambda || !g)
     return sfail(DLM_ERR_INVALID_ARG, "null pointer");
+  if (kind == DLM_BOX_CUT) return sfail(DLM_ERR_UNSUPPORTED, "DLM_BOX_CUT needs a handle (dlm_create)");
   if (kind != DLM_SIMPLEX_LE && kind != DLM_SIMPLEX_EQ && kind != DLM_BOX)
     return sfail(DLM_ERR_INVALID_ARG, "bad simple-set kind");
   if (!(z > 0) || !std::isfinite(z) || !(gamma > 0) || !std::isfinite(gamma))

@@ -58,15 +58,20 @@ def oracle_problem(inst, kind=oracle.SIMPLEX_LE, z=1.0, bf16=False):
                           kind, z)
 
 
-def x_error_report(x_gpu, x_ref, p, lam, gamma):
+def x_error_report(x_gpu, x_ref, p, lam, gamma, cap=None):
     """Max |dx| over the bulk of edges and over users with an edge within
     FP32 resolution of the threshold (where the active set itself is only
-    decided to FP32 precision).  Returns (bulk_max, bound_violations)."""
+    decided to FP32 precision).  With ``cap`` (the box bound of a budgeted
+    box, whose threshold also depends on which edges sit at the cap) edges
+    within that resolution of the cap count as border edges too.  Returns
+    (bulk_max, bound_violations)."""
     dx = np.abs(x_gpu.astype(np.float64) - x_ref)
     M = np.abs(p.c) + np.abs(p.a * lam[p.col])
     window = 16 * EPS32 * M / gamma  # how far FP32 rounding of u moves x
     user = np.repeat(np.arange(p.I), np.diff(p.row_ptr))
     border_edge = (x_ref < window) & ((x_ref > 0) | (x_gpu > 0))
+    if cap is not None:
+        border_edge |= np.abs(x_ref - cap) < window
     border_user = np.zeros(p.I, dtype=bool)
     border_user[user[border_edge]] = True
     bw = np.zeros(p.I)

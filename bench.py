@@ -46,6 +46,11 @@ WORKLOADS = {
              "second coefficient per edge a2 = U(0.1, 2) and b2_j = 0.05 sum_i a2_ij; c, a, a2 stored BF16; "
              "gamma = 1e-3 fixed; the general multi-family sweep",
         users=20_000_000, items=2_000, seed=1001, bf16=True, schedule=(1e-3, 1e-3, 0.5, 1 << 30), families=2),
+    "boxcut": dict(
+        desc="box cut by a per-user budget ({0 <= x_ij <= 0.5, sum_j x_ij <= 1}): the production shape, 20M users "
+             "x 2,000 items, ~500M nnz; c, a stored BF16; gamma = 1e-3 fixed; the box-cut sweep",
+        users=20_000_000, items=2_000, seed=1001, bf16=True, schedule=(1e-3, 1e-3, 0.5, 1 << 30),
+        kind=3, z=0.5, cut=1.0),
     "appendix": dict(
         desc="the paper's appendix generator (App. A) at the preconditioning experiment's size: 25M requests x "
              "10,000 resources, 0.1% density (nu = 10, ~250M nnz); breadth LogNormal(0,1), K_j ~ Poisson(p_j I nu) "
@@ -74,7 +79,7 @@ def recipe_for(name, scale):
     I = max(1000, int(round(w["users"] * scale)))
     if name == "tiny":
         return synth.recipe_tiny(w["seed"])
-    if name in ("production", "families"):
+    if name in ("production", "families", "boxcut"):
         return synth.recipe_production(I=I, J=w["items"], seed=w["seed"])
     if name == "appendix":
         return synth.recipe_appendix(I=I, J=w["items"], seed=w["seed"])
@@ -90,9 +95,12 @@ def load_peaks():
     return 6800.0, "fallback"
 
 
-def sweep_source_hash():
+SWEEP_SOURCES = ("sweep.cu", "sweep_multi.cu", "sweep_common.cuh", "dlm_impl.cuh")
+
+
+def sweep_source_hash(files=SWEEP_SOURCES):
     h = hashlib.sha256()
-    for f in ("sweep.cu", "sweep_multi.cu", "sweep_common.cuh", "dlm_impl.cuh"):
+    for f in files:
         with open(os.path.join(ROOT, "paper_2606_07777_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -108,7 +116,7 @@ def recorded_traffic(workload, nnz, users):
         with open(p) as f:
             d = json.load(f)
         rec = d.get(workload)
-        if not rec or rec.get("source_hash") != sweep_source_hash():
+        if not rec or rec.get("source_hash") != sweep_source_hash(tuple(rec.get("files", SWEEP_SOURCES))):
             return None
         return rec["bytes_per_nnz"] * nnz + rec.get("bytes_per_user", 0.0) * users
     except Exception:
@@ -286,7 +294,10 @@ def cpu_sample(workload, bf16, frac, seed=4242, threads=0, inst=None):
     if bf16:
         c = synth.bf16_to_f32(synth.round_bf16(c))
         a = synth.bf16_to_f32(synth.round_bf16(a))
-    return oracle.Problem(inst.row_ptr, inst.col, c.astype(np.float64), a.astype(np.float64), inst.b, inst.J)
+    w = WORKLOADS[workload]
+    return oracle.Problem(inst.row_ptr, inst.col, c.astype(np.float64), a.astype(np.float64), inst.b, inst.J,
+                          w.get("kind", oracle.SIMPLEX_LE), w.get("z", 1.0),
+                          cut=w["cut"] if w.get("cut") is not None else np.inf)
 
 
 def batch_sample(frac, seed=4242, threads=0):
@@ -505,7 +516,8 @@ def main():
     dlm.load()
     t_setup = time.perf_counter()
     arrs = dev_arrays()
-    s = dlm.Solver(*arrs, inst.J, bf16=bf16)
+    kind_args = dict(kind=w.get("kind", 0), z=w.get("z", 1.0), cut=w.get("cut"))
+    s = dlm.Solver(*arrs, inst.J, bf16=bf16, **kind_args)
     del arrs
     torch.cuda.synchronize(dev)
     t_setup = time.perf_counter() - t_setup
@@ -575,7 +587,7 @@ def main():
     for k in range(args.e2e_steps + 1 if args.e2e_steps > 0 else 0):
         torch.cuda.synchronize(dev)
         t0 = time.perf_counter()
-        s2 = dlm.Solver(inst.row_ptr, inst.col, inst.c, inst.a, inst.b, inst.J, bf16=bf16)
+        s2 = dlm.Solver(inst.row_ptr, inst.col, inst.c, inst.a, inst.b, inst.J, bf16=bf16, **kind_args)
         s2.set_schedule(*w["schedule"])
         if precond:
             s2.set_options(precondition=True)
@@ -603,6 +615,7 @@ def main():
             "traffic": traffic, "peak_source": f"{peak_kind} (copy bandwidth, MEASURED_PEAKS.json)"
             if peak_kind == "measured" else "fallback 6.8 TB/s",
             "kernel": ("sweep_multi_kernel" if w.get("families", 1) > 1 else
+                       "sweep_boxcut_kernel" if w.get("kind") == 3 else
                        "sweep_dyn_kernel" if tuned is not None and tuned["mapping"] == 3 else "sweep_kernel"),
             "algorithmic_bytes_per_launch": bytes_iter,
             "layout_bytes_per_launch": layout_bytes,

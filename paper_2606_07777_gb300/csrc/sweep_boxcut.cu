@@ -110,21 +110,104 @@ __device__ __forceinline__ void boxcut_slice(const InstDesc& D, const BSeg& S, c
     return (sf - static_cast<float>(nf) * t) + (static_cast<float>(nu) * gz - S.gch);
   };
 
-  float umax = -INFINITY;
-  row_pass([&](int j, float c, float a) { umax = fmaxf(umax, -fmaf(a, ys[j], c)); });
+  // Pass A: the four largest u (v0 >= v1 >= v2 >= v3) and the sets at tau = 0.
+  float v[4] = {-INFINITY, -INFINITY, -INFINITY, -INFINITY};
+  int nf = 0, nu = 0;
+  float sf = 0.f;
+  int i0 = 0, i1 = 0, i2 = 0;
+  {
+    int k = 0;
+    row_pass([&](int j, float c, float a) {
+      const float u = -fmaf(a, ys[j], c);
+      top4_insert(u, k++, v[0], v[1], v[2], v[3], i0, i1, i2);
+      if (u >= gz) {
+        ++nu;
+      } else if (u > 0.f) {
+        ++nf;
+        sf += u;
+      }
+    });
+  }
+  const float umax = v[0];
   float tau = 0.f, taul = 0.f;
   float ob = 0.f;
+  bool deposited = false;
   if (umax > 0.f) {  // padding lanes and rows without a positive u deposit nothing
-    int nf, nu;
-    float sf;
-    sets_at(0.f, nf, nu, sf);
     if (phi_g(0.f, nf, nu, sf) > 0.f) {
-      // bracket: phi(lo) > 0 >= phi(hi) (phi(umax) = -cut); the sets of the
-      // piece right of lo are (nfl, nul, sfl)
+      // The budget binds.  First try the pieces spanned by the four largest
+      // values: a capped, f free (a + f <= 3), the rest at most v[a + f]; the
+      // consistent one is the root's piece (phi is monotone).  A flat piece
+      // (no free edge, a z = cut) has every point of it as a root.
       float lo = 0.f, hi = umax;
       int nfl = nf, nul = nu;
       float sfl = sf;
-      for (int it = 0; it < 96; ++it) {
+      bool found = false;
+      const float ka = rintf(S.cut / S.z);
+      const bool flat_ok = fabsf(S.cut / S.z - ka) <= 1e-6f * fmaxf(ka, 1.f);
+#pragma unroll
+      for (int a = 0; a < 4; ++a) {
+#pragma unroll
+        for (int f = 0; f + a < 4; ++f) {
+          if (found) continue;
+          const float next = v[a + f];  // the largest value not in the capped or free part
+          float t;
+          if (f == 0) {
+            if (!(flat_ok && static_cast<float>(a) == ka && a > 0)) continue;
+            t = fmaxf(next, 0.f);
+          } else {
+            float sfree = 0.f;
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+              if (i >= a && i < a + f) sfree += v[i];
+            t = __fdiv_rn(sfree - (S.gch - static_cast<float>(a) * gz), static_cast<float>(f));
+            if (!(v[a] - t < gz && v[a + f - 1] - t > 0.f)) continue;
+          }
+          if (!(t > 0.f) && f > 0) continue;
+          if (a > 0 && !(v[a - 1] - t >= gz)) continue;
+          if (!(next <= t)) continue;
+          found = true;
+          lo = t;
+          if (a + f > 0) {
+            // the nonzero edges are the a + f <= 3 largest, at the recorded
+            // positions: load them once, refine the threshold over the free
+            // ones in pair arithmetic and deposit (no further pass)
+            int jr[3];
+            float cr[3], ar[3];
+#pragma unroll
+            for (int i = 0; i < 3; ++i) {
+              jr[i] = 0;
+              cr[i] = ar[i] = 0.f;
+              if (i < a + f) {
+                const int el = sell_el(i == 0 ? i0 : (i == 1 ? i1 : i2), lane, w4);
+                jr[i] = static_cast<int>(__ldg(col0 + el));
+                V::get(__ldg(ca0 + el), cr[i], ar[i]);
+              }
+            }
+            tau = t;
+            taul = 0.f;
+            if (f > 0) {
+              F2 ps{0.f, 0.f};
+#pragma unroll
+              for (int i = 0; i < 3; ++i)
+                if (i >= a && i < a + f) ps = f2_add(ps, u_pair(cr[i], ar[i], ys[jr[i]]));
+              const F2 b = budget_pair(S, a);
+              const F2 t2 = f2_threshold(ps, b.h, b.l, f);
+              tau = t2.h;
+              taul = t2.l;
+            }
+#pragma unroll
+            for (int i = 0; i < 3; ++i) {
+              if (i < a + f) {
+                const F2 up = u_pair(cr[i], ar[i], ys[jr[i]]);
+                const float x = fminf(fmaxf(((up.h - tau) + (up.l - taul)) * S.invg, 0.f), S.z);
+                if (x > 0.f) deposit_b<V, STATS>(S, jr[i], cr[i], ar[i], x, accG, accC, accQ, ob);
+              }
+            }
+            deposited = true;
+          }
+        }
+      }
+      for (int it = 0; it < 96 && !found; ++it) {
         bool newton = nfl > 0;
         float cand = newton ? __fdiv_rn(sfl + (static_cast<float>(nul) * gz - S.gch), static_cast<float>(nfl))
                             : 0.f;
@@ -152,7 +235,7 @@ __device__ __forceinline__ void boxcut_slice(const InstDesc& D, const BSeg& S, c
       // the threshold over the final free set in pair arithmetic
       F2 ps{0.f, 0.f};
       int n_f = 0, n_u = 0;
-      row_pass([&](int j, float c, float a) {
+      if (!deposited) row_pass([&](int j, float c, float a) {
         const float y = ys[j];
         const float u = -fmaf(a, y, c);
         const float d = u - lo;
@@ -163,7 +246,9 @@ __device__ __forceinline__ void boxcut_slice(const InstDesc& D, const BSeg& S, c
           ps = f2_add(ps, u_pair(c, a, y));
         }
       });
-      if (n_f > 0) {
+      if (deposited) {
+        // tau, taul set on the fast path
+      } else if (n_f > 0) {
         const F2 b = budget_pair(S, n_u);
         const F2 t2 = f2_threshold(ps, b.h, b.l, n_f);
         tau = t2.h;
@@ -173,7 +258,7 @@ __device__ __forceinline__ void boxcut_slice(const InstDesc& D, const BSeg& S, c
       }
     }
     // x = clip((u - tau) / gamma, 0, z) on the edges with u > tau
-    row_pass([&](int j, float c, float a) {
+    if (!deposited) row_pass([&](int j, float c, float a) {
       const float y = ys[j];
       if (-fmaf(a, y, c) > tau) {
         const F2 up = u_pair(c, a, y);
@@ -207,8 +292,9 @@ __device__ __forceinline__ void boxcut_slice(const InstDesc& D, const BSeg& S, c
   }
 }
 
-// Static slice order (as the one-family certificate sweep): per CTA its tasks,
-// per warp the slices first + stride (warp + k nw).
+// Per CTA its tasks; certificate sweeps deal a task's slices to warps in a
+// static order (first + stride (warp + k nw)), iteration sweeps from a
+// per-CTA ticket counter.
 template <class V, bool STATS>
 __global__ void __launch_bounds__(kSweepThreads, 1)
     sweep_boxcut_kernel(const InstDesc* __restrict__ insts, const Task* __restrict__ tasks,
@@ -222,6 +308,7 @@ __global__ void __launch_bounds__(kSweepThreads, 1)
   double* wsum = reinterpret_cast<double*>(ys + ((smemJ + 1) & ~1));
 
   __shared__ InstDesc sD;
+  __shared__ unsigned long long s_next;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int nw = blockDim.x >> 5;
   const int t_last = cta_task[blockIdx.x + 1];
@@ -261,13 +348,32 @@ __global__ void __launch_bounds__(kSweepThreads, 1)
       S.jlo = STATS ? jlo : 0;
       S.jw = nacc;
     }
+    if (threadIdx.x == 0) s_next = 0;
     __syncthreads();
     double wobj = 0.0;
     for (int k = t; k < te; ++k) {
       const Task T = tasks[k];
-      const int64_t step = static_cast<int64_t>(T.stride) * nw;
-      for (int64_t s = T.first + static_cast<int64_t>(T.stride) * warp; s < T.end; s += step)
-        boxcut_slice<V, STATS>(sD, S, ys, accG, accC, accQ, s, wobj);
+      if (STATS) {
+        // static order: the FP64 objective partials are summed in a fixed order
+        const int64_t step = static_cast<int64_t>(T.stride) * nw;
+        for (int64_t s = T.first + static_cast<int64_t>(T.stride) * warp; s < T.end; s += step)
+          boxcut_slice<V, STATS>(sD, S, ys, accG, accC, accQ, s, wobj);
+      } else {
+        // dynamic order within the CTA: rows whose threshold needs the
+        // bracketed search take many passes, and the item sums are exact in
+        // any order
+        const int64_t nsl = (T.end - T.first + T.stride - 1) / T.stride;
+        for (;;) {
+          int64_t i = 0;
+          if (lane == 0) i = static_cast<int64_t>(atomicAdd(&s_next, 1ull));
+          i = __shfl_sync(kFull, i, 0);
+          if (i >= nsl) break;
+          boxcut_slice<V, STATS>(sD, S, ys, accG, accC, accQ, T.first + i * T.stride, wobj);
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) s_next = 0;
+        __syncthreads();
+      }
     }
     if (STATS) {
 #pragma unroll

@@ -22,7 +22,10 @@ WORKLOADS = {
     "precision": (lambda: synth.generate(synth.recipe_precision()), True, (1e-3, 1e-3, 0.5, 1 << 30), False, 20),
     "appendix": (lambda: synth.generate_appendix(synth.recipe_appendix()), False, (1e-2, 1e-2, 0.5, 1 << 30), True,
                  400),
+    # the box cut by a per-user budget {0 <= x <= 0.5, sum x <= 1} on the production shape
+    "boxcut": (lambda: synth.generate(synth.recipe_production()), True, (1e-3, 1e-3, 0.5, 1 << 30), False, 20),
 }
+SETS = {"boxcut": dict(kind=oracle.BOX_CUT, z=0.5, cut=1.0)}
 
 
 def rows_index(rp, rows):
@@ -34,9 +37,10 @@ def rows_index(rp, rows):
         torch.arange(total, device=rp.device) - torch.repeat_interleave(torch.cumsum(lens, 0) - lens, lens))
 
 
-@pytest.mark.parametrize("name", ["production", "precision", "appendix"])
+@pytest.mark.parametrize("name", ["production", "precision", "appendix", "boxcut"])
 def test_full_size_sampled_parity(dlm_lib, name):
     make, bf16, sched, precondition, iters = WORKLOADS[name]
+    sset = SETS.get(name, dict(kind=oracle.SIMPLEX_LE, z=1.0, cut=None))
     inst = make()
     dev = torch.device("cuda")
     if bf16:
@@ -47,7 +51,7 @@ def test_full_size_sampled_parity(dlm_lib, name):
     rp = torch.from_numpy(inst.row_ptr).to(dev)
     col = torch.from_numpy(inst.col).to(dev)
     b = torch.from_numpy(inst.b).to(dev)
-    s = dlm_lib.Solver(rp, col, c, a, b, inst.J, bf16=bf16)
+    s = dlm_lib.Solver(rp, col, c, a, b, inst.J, bf16=bf16, kind=sset["kind"], z=sset["z"], cut=sset["cut"])
     s.set_schedule(*sched)
     s.set_options(precondition=precondition)
     s.step(iters)
@@ -69,10 +73,11 @@ def test_full_size_sampled_parity(dlm_lib, name):
     cs, as_ = sub.c, sub.a
     if bf16:
         cs, as_ = synth.bf16_to_f32(synth.round_bf16(cs)), synth.bf16_to_f32(synth.round_bf16(as_))
-    p = oracle.Problem(sub.row_ptr, sub.col, cs.astype(np.float64), as_.astype(np.float64), sub.b, sub.J)
+    p = oracle.Problem(sub.row_ptr, sub.col, cs.astype(np.float64), as_.astype(np.float64), sub.b, sub.J,
+                       sset["kind"], sset["z"], cut=sset["cut"] if sset["cut"] is not None else np.inf)
     lam = lam32.cpu().numpy().astype(np.float64)
     ref = oracle.sweep(p, lam, gamma)
-    dx, tol = x_error_report(xs, ref["x"], p, lam, gamma)
+    dx, tol = x_error_report(xs, ref["x"], p, lam, gamma, cap=sset["z"] if sset["cut"] is not None else None)
     assert (dx <= tol).all(), f"{int((dx > tol).sum())} of {dx.size} sampled edges over tolerance, max {dx.max():.3e}"
     s.close()
 

@@ -71,7 +71,8 @@ typedef enum { DLM_MEM_DEVICE = 0, DLM_MEM_HOST = 1 } dlm_memspace;
  * diagonal block per user; at most 4) every dual vector of the handle is
  * [m x num_items] family-major (lam[k * num_items + j]); such handles sweep
  * with a general kernel, take the static slice orders (mapping 1 or 2), and
- * do not combine with batches, the count constraint or the warm start.
+ * do not combine with the count constraint or the warm start; they batch only
+ * with handles of the same m.
  * The arrays live in `memspace`.  dlm_create copies them into its own layout;
  * the caller may free or reuse them once dlm_create has returned. */
 typedef struct {
@@ -264,7 +265,9 @@ void dlm_destroy(dlm_problem* p);
  * launch with one CTA per member, replayed as CUDA graphs.  Every member keeps
  * its own data, schedule, options' precondition flag, lam, y and state, and
  * its iterates are those it would take alone (bit-identical for the same
- * coop_max).  Members must share val_dtype and device; a handle appears at
+ * coop_max).  Members must share val_dtype, device and the number of
+ * capacity families (several-family members sweep with the general kernel in
+ * a static order); DLM_BOX_CUT handles do not batch; a handle appears at
  * most once.  Set each member's schedule, precondition flag and warm start
  * before dlm_batch_create (the batch captures them; set_lambda and set_state
  * on a member remain valid afterwards).  Work of the batch is ordered on

@@ -1419,7 +1419,10 @@ dlm_status dlm_batch_create(dlm_problem* const* probs, int32_t n, void* stream, 
     if (!probs[i]) return fail(DLM_ERR_INVALID_ARG, "null problem in batch");
     if (probs[i]->bf16 != probs[0]->bf16) return fail(DLM_ERR_INVALID_ARG, "batch members must share val_dtype");
     if (probs[i]->device != probs[0]->device) return fail(DLM_ERR_INVALID_ARG, "batch members must share a device");
-    if (probs[i]->m > 1) return fail(DLM_ERR_UNSUPPORTED, "batch members with several capacity families");
+    if (probs[i]->m != probs[0]->m)
+      return fail(DLM_ERR_UNSUPPORTED, "batch members with different numbers of capacity families");
+    if (probs[i]->m > 1 && probs[i]->count_on)
+      return fail(DLM_ERR_UNSUPPORTED, "a count constraint with several capacity families");
     if (probs[i]->kind == DLM_BOX_CUT) return fail(DLM_ERR_UNSUPPORTED, "batch members with DLM_BOX_CUT");
     for (int k = 0; k < i; ++k)
       if (probs[k] == probs[i]) return fail(DLM_ERR_INVALID_ARG, "a problem appears twice in the batch");
@@ -1443,8 +1446,10 @@ dlm_status dlm_batch_create(dlm_problem* const* probs, int32_t n, void* stream, 
     cudaStreamSynchronize(probs[i]->stream);
     R.smemJ = std::max(R.smemJ, static_cast<int>(probs[i]->J));
   }
-  R.win = sweep_stats_window(R.smemJ);
-  if (sweep_smem_bytes(R.smemJ, false) > sweep_smem_limit() || R.win < 1) {
+  const int m = probs[0]->m;
+  R.win = m > 1 ? R.smemJ : sweep_stats_window(R.smemJ);
+  if (m > 1 ? sweep_multi_smem_bytes(R.smemJ, m, true) > sweep_smem_limit()
+            : (sweep_smem_bytes(R.smemJ, false) > sweep_smem_limit() || R.win < 1)) {
     if (bt->own_stream) cudaStreamDestroy(R.stream);
     delete bt;
     return fail(DLM_ERR_UNSUPPORTED, "largest num_items of the batch too large for the shared-memory item arrays");

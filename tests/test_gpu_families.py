@@ -128,11 +128,39 @@ def test_unsupported_combinations(dlm_lib):
     rp, col = torch.from_numpy(inst.row_ptr).cuda(), torch.from_numpy(inst.col).cuda()
     one = dlm_lib.Solver(rp, col, torch.from_numpy(inst.c).cuda(), torch.from_numpy(inst.a).cuda(),
                          torch.from_numpy(inst.b).cuda(), inst.J)
-    with pytest.raises(dlm_lib.DlmError) as e:
+    with pytest.raises(dlm_lib.DlmError) as e:  # members with different numbers of families
         dlm_lib.Batch([one, s])
     assert e.value.status == dlm_lib.DLM_ERR_UNSUPPORTED
     one.close()
     s.close()
+
+
+def test_batch_of_two_family_members_is_bit_identical(dlm_lib):
+    insts = [tiny_instance(), mixed_instance(seed=9, I=2500, J=200)]
+    fams = [second_family(insts[0], seed=5, scale=0.04), second_family(insts[1], seed=6, scale=0.03)]
+
+    def members():
+        out = []
+        for inst, (a2, b2), pre in zip(insts, fams, (True, False)):
+            s = make(dlm_lib, inst, a2, b2)
+            s.set_schedule(1e-2)
+            s.set_options(precondition=pre)
+            out.append(s)
+        return out
+
+    alone = members()
+    for s in alone:
+        s.step(80)
+    together = members()
+    bt = dlm_lib.Batch(together)
+    bt.step(80)
+    for s0, s1 in zip(alone, together):
+        assert torch.equal(s0.lam(), s1.lam())
+    st = bt.stats()
+    assert all(x.status == dlm_lib.DLM_OK for x in st)
+    bt.close()
+    for s in alone + together:
+        s.close()
 
 
 def test_duplicated_family_matches_one_family_x(dlm_lib):

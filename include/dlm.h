@@ -88,8 +88,8 @@ typedef struct {
   int32_t memspace;     /* dlm_memspace of the arrays above */
   int32_t num_families; /* capacity families m, 1..4 (0 means 1) */
   double cut;           /* DLM_BOX_CUT: per-user budget sum_j x_ij <= cut, finite and > 0 (ignored
-                           otherwise); such handles take one family, no count constraint and no
-                           batch, and sweep with their own kernel (static slice orders) */
+                           otherwise); such handles take one family and no count constraint, batch
+                           only with other box-cut handles, and sweep with their own kernel */
 } dlm_problem_desc;
 
 /* Solver options (zero-initialised fields take the defaults).  The mapping
@@ -267,8 +267,8 @@ void dlm_destroy(dlm_problem* p);
  * its iterates are those it would take alone (bit-identical for the same
  * coop_max).  Members must share val_dtype, device and the number of
  * capacity families (several-family members sweep with the general kernel in
- * a static order); DLM_BOX_CUT handles do not batch; a handle appears at
- * most once.  Set each member's schedule, precondition flag and warm start
+ * a static order); DLM_BOX_CUT handles batch only with each other; a handle
+ * appears at most once.  Set each member's schedule, precondition flag and warm start
  * before dlm_batch_create (the batch captures them; set_lambda and set_state
  * on a member remain valid afterwards).  Work of the batch is ordered on
  * `stream` (NULL: the batch creates its own blocking stream); calls on a

@@ -94,6 +94,7 @@ struct Runner {
   int win = 0;  // item window of certificate sweeps (smemJ when their arrays fit at once)
   int graph_iters = 10;
   InstDesc *inst_iter = nullptr, *inst_stats = nullptr;
+  double* cuts = nullptr;  // per-instance DLM_BOX_CUT budgets (box-cut runners only)
   UpdInst* upd = nullptr;
   StatsInst* st_stats = nullptr;
   Task* tasks = nullptr;
@@ -232,14 +233,15 @@ void invalidate_graph(Runner& R) {
 
 void runner_free(Runner& R) {
   invalidate_graph(R);
-  void* ptrs[] = {R.inst_iter, R.inst_stats, R.upd,      R.st_stats, R.tasks,
-                  R.cta_task,  R.seg_lists,  R.seg_obj, R.units,    R.ctr};
+  void* ptrs[] = {R.inst_iter, R.inst_stats, R.upd,   R.st_stats, R.tasks, R.cta_task,
+                  R.seg_lists, R.seg_obj,    R.units, R.ctr,      R.cuts};
   for (void* q : ptrs) cudaFree(q);
   for (cudaEvent_t e : R.events) cudaEventDestroy(e);
   R.events.clear();
   if (R.done) cudaEventDestroy(R.done);
   R.done = nullptr;
   R.inst_iter = R.inst_stats = nullptr;
+  R.cuts = nullptr;
   R.upd = nullptr;
   R.st_stats = nullptr;
   R.tasks = nullptr;
@@ -432,6 +434,12 @@ dlm_status runner_build(Runner& R) {
     CK(dalloc(&R.upd, n));
     CK(dalloc(&R.st_stats, n));
   }
+  if (R.probs[0]->kind == DLM_BOX_CUT && !R.cuts) {
+    std::vector<double> h(n);
+    for (int i = 0; i < n; ++i) h[i] = R.probs[i]->cut;
+    CK(dalloc(&R.cuts, n));
+    CK(cudaMemcpy(R.cuts, h.data(), sizeof(double) * n, cudaMemcpyHostToDevice));
+  }
   build_task_list(R);
   cudaFree(R.tasks);
   cudaFree(R.cta_task);
@@ -490,11 +498,10 @@ cudaError_t dispatch_sweep(const SweepLaunch& L, bool stats, bool bf16) {
   return L.fam > 1 ? launch_sweep_multi(L, stats, bf16) : launch_sweep(L, stats, bf16);
 }
 
-// Handles on the box cut by a budget sweep with their own kernel (a runner
-// holds one such handle: batches do not take them).
+// Handles on the box cut by a budget sweep with their own kernel (a runner's
+// members are all box-cut or none).
 cudaError_t dispatch_sweep(const Runner& R, const SweepLaunch& L, bool stats, bool bf16) {
-  if (R.probs.size() == 1 && R.probs[0]->kind == DLM_BOX_CUT)
-    return launch_sweep_boxcut(L, stats, bf16, R.probs[0]->cut);
+  if (R.probs[0]->kind == DLM_BOX_CUT) return launch_sweep_boxcut(L, stats, bf16, R.cuts);
   return dispatch_sweep(L, stats, bf16);
 }
 
@@ -1423,7 +1430,8 @@ dlm_status dlm_batch_create(dlm_problem* const* probs, int32_t n, void* stream, 
       return fail(DLM_ERR_UNSUPPORTED, "batch members with different numbers of capacity families");
     if (probs[i]->m > 1 && probs[i]->count_on)
       return fail(DLM_ERR_UNSUPPORTED, "a count constraint with several capacity families");
-    if (probs[i]->kind == DLM_BOX_CUT) return fail(DLM_ERR_UNSUPPORTED, "batch members with DLM_BOX_CUT");
+    if ((probs[i]->kind == DLM_BOX_CUT) != (probs[0]->kind == DLM_BOX_CUT))
+      return fail(DLM_ERR_UNSUPPORTED, "DLM_BOX_CUT members batch only with each other");
     for (int k = 0; k < i; ++k)
       if (probs[k] == probs[i]) return fail(DLM_ERR_INVALID_ARG, "a problem appears twice in the batch");
   }

@@ -6,10 +6,11 @@
 
 namespace dlm {
 
-// One sweep (iteration or certificate) over a single box-cut instance with the
-// static task table of L; certificate sweeps take item windows like the
-// one-family sweep.  cut > 0 is the per-user budget.
-cudaError_t launch_sweep_boxcut(const SweepLaunch& L, bool stats, bool bf16, double cut);
+// One sweep (iteration or certificate) over the box-cut instances of L's
+// task table; certificate sweeps take item windows like the one-family
+// sweep.  cuts (device, one per instance of the table) are the per-user
+// budgets, each > 0.
+cudaError_t launch_sweep_boxcut(const SweepLaunch& L, bool stats, bool bf16, const double* cuts);
 cudaError_t sweep_boxcut_prepare(bool bf16);
 
 }  // namespace dlm

@@ -298,7 +298,8 @@ __device__ __forceinline__ void boxcut_slice(const InstDesc& D, const BSeg& S, c
 template <class V, bool STATS>
 __global__ void __launch_bounds__(kSweepThreads, 1)
     sweep_boxcut_kernel(const InstDesc* __restrict__ insts, const Task* __restrict__ tasks,
-                        const int32_t* __restrict__ cta_task, int smemJ, int jlo, int jw, double cut) {
+                        const int32_t* __restrict__ cta_task, int smemJ, int jlo, int jw,
+                        const double* __restrict__ cuts) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int accN = STATS ? jw : smemJ;
   unsigned long long* accG = reinterpret_cast<unsigned long long*>(smem_raw);
@@ -338,6 +339,7 @@ __global__ void __launch_bounds__(kSweepThreads, 1)
       const double gz = g * static_cast<double>(sD.z);
       S.gzh = static_cast<float>(gz);
       S.gzl = static_cast<float>(gz - static_cast<double>(S.gzh));
+      const double cut = cuts[inst];
       const double gc = g * cut;
       S.gch = static_cast<float>(gc);
       S.gcl = static_cast<float>(gc - static_cast<double>(S.gch));
@@ -412,21 +414,21 @@ cudaError_t prepare_values(int lim) {
 }
 
 template <class V>
-cudaError_t launch_values(const SweepLaunch& L, bool stats, double cut) {
+cudaError_t launch_values(const SweepLaunch& L, bool stats, const double* cuts) {
   const int th = L.threads > 0 ? L.threads : kSweepThreads;
   if (stats) {
     const int w = L.win > 0 ? std::min(L.win, L.smemJ) : L.smemJ;
     if (w < 1) return cudaErrorInvalidValue;
     const size_t sm = sweep_stats_smem_bytes(L.smemJ, w);
     for (int jlo = 0; jlo < L.smemJ || jlo == 0; jlo += w) {
-      sweep_boxcut_kernel<V, true><<<L.grid, th, sm, L.stream>>>(L.inst, L.tasks, L.cta_task, L.smemJ, jlo, w, cut);
+      sweep_boxcut_kernel<V, true><<<L.grid, th, sm, L.stream>>>(L.inst, L.tasks, L.cta_task, L.smemJ, jlo, w, cuts);
       const cudaError_t e = cudaGetLastError();
       if (e != cudaSuccess) return e;
     }
     return cudaSuccess;
   }
   sweep_boxcut_kernel<V, false><<<L.grid, th, sweep_smem_bytes(L.smemJ, false), L.stream>>>(
-      L.inst, L.tasks, L.cta_task, L.smemJ, 0, L.smemJ, cut);
+      L.inst, L.tasks, L.cta_task, L.smemJ, 0, L.smemJ, cuts);
   return cudaGetLastError();
 }
 
@@ -437,8 +439,9 @@ cudaError_t sweep_boxcut_prepare(bool bf16) {
   return bf16 ? prepare_values<BF16Pair>(lim) : prepare_values<F32Pair>(lim);
 }
 
-cudaError_t launch_sweep_boxcut(const SweepLaunch& L, bool stats, bool bf16, double cut) {
-  return bf16 ? launch_values<BF16Pair>(L, stats, cut) : launch_values<F32Pair>(L, stats, cut);
+cudaError_t launch_sweep_boxcut(const SweepLaunch& L, bool stats, bool bf16, const double* cuts) {
+  if (cuts == nullptr) return cudaErrorInvalidValue;
+  return bf16 ? launch_values<BF16Pair>(L, stats, cuts) : launch_values<F32Pair>(L, stats, cuts);
 }
 
 }  // namespace dlm

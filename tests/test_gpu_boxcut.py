@@ -2,7 +2,8 @@
 reading of Table 1's box-cut projection), on the GPU against the FP64
 oracle: one dual evaluation at several gammas, the accelerated trajectory,
 the certificate, the reduction to the box when the budget is slack (the same
-bits), and the combinations the build does not take."""
+bits), batches of box-cut handles (the same bits as alone), and the
+combinations the build does not take."""
 import numpy as np
 import pytest
 
@@ -111,11 +112,44 @@ def test_unsupported_combinations_and_bad_values(dlm_lib):
     with pytest.raises(dlm_lib.DlmError) as e:
         s.set_count_limit(100.0)
     assert e.value.status == dlm_lib.DLM_ERR_UNSUPPORTED
-    with pytest.raises(dlm_lib.DlmError) as e:
-        dlm_lib.Batch([s])
+    rp, col, c, a, b = to_device(inst, torch)
+    plain = dlm_lib.Solver(rp, col, c, a, b, inst.J)
+    with pytest.raises(dlm_lib.DlmError) as e:  # box-cut members batch only with each other
+        dlm_lib.Batch([s, plain])
     assert e.value.status == dlm_lib.DLM_ERR_UNSUPPORTED
+    plain.close()
     s.close()
     for bad in (0.0, -1.0, float("inf"), float("nan")):
         with pytest.raises(dlm_lib.DlmError) as e:
             solver(dlm_lib, inst, 0.3, bad)
         assert e.value.status == dlm_lib.DLM_ERR_INVALID_ARG
+
+
+def test_batch_of_box_cut_members_is_bit_identical(dlm_lib):
+    insts = [tiny_instance(), mixed_instance(seed=9, I=2500, J=200)]
+    sets = [(0.3, 0.5), (0.25, 0.8)]
+
+    def members():
+        out = []
+        for inst, (z, cut), pre in zip(insts, sets, (True, False)):
+            s = solver(dlm_lib, inst, z, cut)
+            s.set_schedule(1e-2)
+            s.set_options(precondition=pre)
+            out.append(s)
+        return out
+
+    alone = members()
+    for s in alone:
+        s.step(80)
+    together = members()
+    bt = dlm_lib.Batch(together)
+    bt.step(80)
+    for s0, s1 in zip(alone, together):
+        assert torch.equal(s0.lam(), s1.lam())
+    st = bt.stats()
+    for x, s0 in zip(st, alone):
+        assert x.status == dlm_lib.DLM_OK
+        assert abs(x.dual_obj - s0.stats().dual_obj) <= 1e-12 * abs(x.dual_obj)
+    bt.close()
+    for s in alone + together:
+        s.close()

@@ -11,12 +11,14 @@
 // elements per stream (item index; interleaved (c, a)).  Its first 4 (w / 4)
 // edges of every user are stored in groups of four: edge k < 4 (w / 4) of
 // user t at slice_off + 4 (32 (k / 4) + t) + k % 4, so that lane t reads four
-// consecutive edges of its user with one 128-bit load (one float2 pair per
-// edge in FP32: two 128-bit loads) and a warp load covers 512 contiguous
+// consecutive edges of its user with one 128-bit value load (one float2 pair
+// per edge in FP32: two 128-bit loads) and a warp load covers 512 contiguous
 // bytes.  The remaining w % 4 edges follow edge-major: edge k at
 // slice_off + 128 (w / 4) + 32 (k - 4 (w / 4)) + t.  Edges past a user's
 // degree are padding with c = +inf, a = 0 (they give u = -inf and are never
-// active).  Users with no edges are dropped from the slices.
+// active).  Users with no edges are dropped from the slices.  The item index
+// stream is laid out as int32 and then narrowed to uint16 (every handle has
+// fewer than 65,536 items), so four indices are one 64-bit load.
 #include <cub/cub.cuh>
 
 #include <cmath>

@@ -187,7 +187,8 @@ dlm_status dlm_set_schedule(dlm_problem* p, double gamma0, double gamma_end, dou
  * with a count row: use row normalization).  The certificate multiplies the
  * item-scaled point by min(1, M / sum x).  Sets mu to 0; call it before
  * iterating and before dlm_batch_create.  Meaningful for DLM_SIMPLEX_LE and
- * DLM_BOX (with DLM_SIMPLEX_EQ, sum x = z per user whatever mu). */
+ * DLM_BOX (with DLM_SIMPLEX_EQ, sum x = z per user whatever mu); handles with
+ * several capacity families or DLM_BOX_CUT return DLM_ERR_UNSUPPORTED. */
 dlm_status dlm_set_count_limit(dlm_problem* p, double M);
 
 /* Replace the handle's options (see dlm_options; out-of-range values return

@@ -91,6 +91,8 @@ def _load():
         lib.orc_stage_gamma.argtypes = [d, d, d, i64]
         lib.orc_fista_threads.argtypes = [P, d, i32, i64, i32, vp]
         lib.orc_fista_threads.restype = None
+        lib.orc_solve_threads.argtypes = [P, d, d, d, i64, i32, i32, d, i64, i64, i32, vp, vp, vp]
+        lib.orc_solve_threads.restype = None
         lib.orc_stage_gamma.restype = d
         _lib = lib
     return _lib
@@ -227,6 +229,23 @@ def fista_threads(p: Problem, T, gamma, precondition=False, nthreads=1):
     lam = np.empty(p.J)
     _load().orc_fista_threads(ctypes.byref(p._s), gamma, int(bool(precondition)), T, int(nthreads), _p(lam))
     return lam
+
+
+def solve_threads(p: Problem, gamma0, gamma_end=None, factor=0.5, iters_per_stage=0, precondition=False,
+                  restart=False, target=1e-4, gap_every=25, max_iters=100_000, nthreads=1, lam0=None):
+    """fista's iteration driven to a certified gap (checked every gap_every
+    iterations once gamma is at gamma_end), with the sweep split over
+    nthreads threads; dict(lam, iters, rel_gap, g, primal).  One capacity
+    family, no count constraint."""
+    if p.D != p.J or p.m != 1:
+        raise ValueError("the threaded solve covers the one-family capacity problem")
+    gamma_end = gamma0 if gamma_end is None else gamma_end
+    lam0 = np.zeros(p.J) if lam0 is None else _dual_vec(p, lam0)
+    lam, st = np.empty(p.J), np.empty(4)
+    _load().orc_solve_threads(ctypes.byref(p._s), gamma0, gamma_end, factor, iters_per_stage,
+                              int(bool(precondition)), int(bool(restart)), target, gap_every, max_iters,
+                              int(nthreads), _p(lam0), _p(lam), _p(st))
+    return dict(lam=lam, iters=int(st[0]), rel_gap=st[1], g=st[2], primal=st[3])
 
 
 def stage_gamma(gamma0, gamma_end, factor, s):

@@ -611,3 +611,193 @@ void orc_fista_threads(const orc_problem* p, double gamma, int32_t precondition,
   free(jobs);
   free(th);
 }
+
+/* ------------------------------------------------------------------------ */
+/* Solve to a certified gap with the sweep split over threads (the CPU       */
+/* baseline of time-to-gap, and reference optima on samples).  The iteration */
+/* is orc_fista's -- gamma continuation, step gamma / h, momentum restart at  */
+/* a change of gamma and optionally the adaptive restart -- with A x summed   */
+/* per thread over contiguous user ranges and the thread vectors added in     */
+/* thread order (one thread: orc_fista's arithmetic exactly).  Before         */
+/* iteration t, when t is a multiple of gap_every and the gamma of t is       */
+/* gamma_end, the certified gap of orc_certify at lam is evaluated (the sums  */
+/* split over threads the same way); the solve stops when it is <= target or  */
+/* after max_iters iterations.  One capacity family, no count constraint.     */
+/* stats[0] = iterations taken, stats[1] = last certified gap (NaN if none),  */
+/* stats[2] = g(lam), stats[3] = P(x~) of that check.                        */
+/* ------------------------------------------------------------------------ */
+
+typedef struct {
+  const orc_problem* p;
+  const double* y;
+  double gamma;
+  int64_t u0, u1;
+  double *Ax, *Cx, *Qx; /* Cx, Qx NULL: gradient sweep only */
+  double obj;
+} solve_job;
+
+static void* solve_range(void* arg) {
+  solve_job* jb = (solve_job*)arg;
+  const orc_problem* p = jb->p;
+  int64_t maxd = 1;
+  for (int64_t i = jb->u0; i < jb->u1; ++i) {
+    int64_t d = p->row_ptr[i + 1] - p->row_ptr[i];
+    if (d > maxd) maxd = d;
+  }
+  double* v = (double*)malloc(sizeof(double) * (size_t)maxd);
+  double* x = (double*)malloc(sizeof(double) * (size_t)maxd);
+  for (int64_t j = 0; j < p->J; ++j) {
+    jb->Ax[j] = 0;
+    if (jb->Cx) jb->Cx[j] = jb->Qx[j] = 0;
+  }
+  double obj = 0;
+  for (int64_t i = jb->u0; i < jb->u1; ++i) {
+    int64_t e0 = p->row_ptr[i], d = p->row_ptr[i + 1] - e0;
+    for (int64_t k = 0; k < d; ++k) {
+      double t = p->c[e0 + k] + 0.0;
+      t += p->a[e0 + k] * jb->y[p->col[e0 + k]];
+      v[k] = -t / jb->gamma;
+    }
+    orc_project(v, d, p->kind, p->z, p->cut, 0, x);
+    for (int64_t k = 0; k < d; ++k) {
+      int32_t j = p->col[e0 + k];
+      jb->Ax[j] += p->a[e0 + k] * x[k];
+      if (jb->Cx) {
+        jb->Cx[j] += p->c[e0 + k] * x[k];
+        jb->Qx[j] += x[k] * x[k];
+        obj += p->c[e0 + k] * x[k] + 0.5 * jb->gamma * x[k] * x[k];
+      }
+    }
+  }
+  jb->obj = obj;
+  free(v);
+  free(x);
+  return NULL;
+}
+
+static void run_jobs(solve_job* jobs, pthread_t* th, int32_t nthreads) {
+  for (int32_t t = 1; t < nthreads; ++t) pthread_create(&th[t], NULL, solve_range, &jobs[t]);
+  solve_range(&jobs[0]);
+  for (int32_t t = 1; t < nthreads; ++t) pthread_join(th[t], NULL);
+}
+
+void orc_solve_threads(const orc_problem* p, double gamma0, double gamma_end, double factor, int64_t iters_per_stage,
+                       int32_t precondition, int32_t restart, double target, int64_t gap_every, int64_t max_iters,
+                       int32_t nthreads, const double* lam0, double* lam_out, double* stats) {
+  const int64_t J = p->J;
+  if (nthreads < 1) nthreads = 1;
+  if (gap_every < 1) gap_every = 1;
+  if (iters_per_stage <= 0) iters_per_stage = max_iters > 0 ? max_iters : 1;
+  double* h = (double*)malloc(sizeof(double) * (size_t)(J + 1));
+  double* lam = (double*)malloc(sizeof(double) * (size_t)J);
+  double* y = (double*)malloc(sizeof(double) * (size_t)J);
+  double* G = (double*)malloc(sizeof(double) * (size_t)J);
+  double* nl = (double*)malloc(sizeof(double) * (size_t)J);
+  double* buf = (double*)malloc(sizeof(double) * (size_t)J * 3 * (size_t)nthreads);
+  solve_job* jobs = (solve_job*)malloc(sizeof(solve_job) * (size_t)nthreads);
+  pthread_t* th = (pthread_t*)malloc(sizeof(pthread_t) * (size_t)nthreads);
+  curvature(p, precondition, h);
+  for (int64_t k = 0; k < J; ++k) lam[k] = y[k] = lam0[k];
+  int64_t u = 0;
+  for (int32_t t = 0; t < nthreads; ++t) {
+    int64_t want = p->nnz * (t + 1) / nthreads;
+    int64_t u1 = u;
+    while (u1 < p->I && p->row_ptr[u1] < want) ++u1;
+    if (t == nthreads - 1) u1 = p->I;
+    jobs[t].p = p;
+    jobs[t].u0 = u;
+    jobs[t].u1 = u1;
+    jobs[t].Ax = buf + (size_t)J * (size_t)(3 * t);
+    jobs[t].Cx = buf + (size_t)J * (size_t)(3 * t + 1);
+    jobs[t].Qx = buf + (size_t)J * (size_t)(3 * t + 2);
+    u = u1;
+  }
+  double theta = 1.0, last_gap = NAN, last_g = NAN, last_P = NAN;
+  int64_t t = 0;
+  for (;; ++t) {
+    const double gamma = stage_gamma(gamma0, gamma_end, factor, t / iters_per_stage);
+    if (t % gap_every == 0 && gamma == gamma_end) {
+      /* certified gap at lam (orc_certify's scaled point) */
+      for (int32_t k = 0; k < nthreads; ++k) {
+        jobs[k].y = lam;
+        jobs[k].gamma = gamma;
+      }
+      run_jobs(jobs, th, nthreads);
+      double obj = jobs[0].obj, P = 0;
+      for (int32_t k = 1; k < nthreads; ++k) obj += jobs[k].obj;
+      double g = obj;
+      for (int64_t j = 0; j < J; ++j) {
+        double Ax = jobs[0].Ax[j], Cx = jobs[0].Cx[j], Qx = jobs[0].Qx[j];
+        for (int32_t k = 1; k < nthreads; ++k) {
+          Ax += jobs[k].Ax[j];
+          Cx += jobs[k].Cx[j];
+          Qx += jobs[k].Qx[j];
+        }
+        const double s = (Ax > p->b[j] && p->b[j] / Ax < 1.0) ? p->b[j] / Ax : 1.0;
+        P += s * Cx + 0.5 * gamma * s * s * Qx;
+        g += lam[j] * (Ax - p->b[j]);
+      }
+      last_g = g;
+      last_P = P;
+      last_gap = (P - g) / (fabs(g) > 1e-30 ? fabs(g) : 1e-30);
+      if (last_gap <= target) break;
+    }
+    if (t >= max_iters) break;
+    /* one iteration at y (gradient sums only) */
+    for (int32_t k = 0; k < nthreads; ++k) {
+      jobs[k].y = y;
+      jobs[k].gamma = gamma;
+      jobs[k].Cx = jobs[k].Qx = NULL;
+    }
+    run_jobs(jobs, th, nthreads);
+    for (int32_t k = 0; k < nthreads; ++k) {
+      jobs[k].Cx = buf + (size_t)J * (size_t)(3 * k + 1);
+      jobs[k].Qx = buf + (size_t)J * (size_t)(3 * k + 2);
+    }
+    for (int64_t j = 0; j < J; ++j) {
+      double Ax = jobs[0].Ax[j];
+      for (int32_t k = 1; k < nthreads; ++k) Ax += jobs[k].Ax[j];
+      G[j] = Ax - p->b[j];
+    }
+    for (int64_t k = 0; k < J; ++k) {
+      double step = h[k] > 0 ? gamma / h[k] : 0.0;
+      double v = y[k] + step * G[k];
+      nl[k] = v > 0 ? v : 0;
+    }
+    const double gamma_next = stage_gamma(gamma0, gamma_end, factor, (t + 1) / iters_per_stage);
+    int restart_now = gamma_next != gamma;
+    if (restart && !restart_now) {
+      double dot = 0.0;
+      for (int64_t k = 0; k < J; ++k) {
+        double step = h[k] > 0 ? gamma / h[k] : 0.0;
+        if (step > 0) dot += (nl[k] - y[k]) * (nl[k] - lam[k]) / step;
+      }
+      restart_now = dot < 0.0;
+    }
+    if (restart_now) {
+      theta = 1.0;
+      for (int64_t k = 0; k < J; ++k) lam[k] = y[k] = nl[k];
+    } else {
+      double th1 = 0.5 * (1.0 + sqrt(1.0 + 4.0 * theta * theta));
+      double beta = (theta - 1.0) / th1;
+      for (int64_t k = 0; k < J; ++k) {
+        y[k] = nl[k] + beta * (nl[k] - lam[k]);
+        lam[k] = nl[k];
+      }
+      theta = th1;
+    }
+  }
+  for (int64_t k = 0; k < J; ++k) lam_out[k] = lam[k];
+  stats[0] = (double)t;
+  stats[1] = last_gap;
+  stats[2] = last_g;
+  stats[3] = last_P;
+  free(h);
+  free(lam);
+  free(y);
+  free(G);
+  free(nl);
+  free(buf);
+  free(jobs);
+  free(th);
+}

@@ -243,3 +243,36 @@ def test_threaded_timing_loop_is_the_same_iteration():
         for nt in (1, 3, 8):
             got = oracle.fista_threads(p, 40, 1e-2, precondition=pre, nthreads=nt)
             assert np.abs(got - ref).max() <= 1e-12 * max(1.0, np.abs(ref).max()), (pre, nt)
+
+
+@pytest.mark.parametrize("sched,precondition,restart", [((1e-1, 1e-2, 0.5, 30), True, False),
+                                                         ((1e-2, 1e-2, 0.5, 0), False, True),
+                                                         ((5e-2, 5e-3, 0.5, 20), True, True)])
+def test_threaded_solve_is_the_fista_iteration(sched, precondition, restart):
+    # one thread: orc_fista's arithmetic exactly; four threads: the same
+    # iteration with the item sums added in another order
+    inst = synth.generate(synth.recipe_production(I=1500, J=40, seed=23))
+    p = oracle.Problem.from_instance(inst)
+    T = 150
+    ref = oracle.fista(p, T, sched[0], sched[1], sched[2], sched[3], precondition=precondition, restart=restart,
+                       trajectory=False)["lam"]
+    one = oracle.solve_threads(p, *sched, precondition=precondition, restart=restart, target=-1.0,
+                               gap_every=10 ** 9, max_iters=T, nthreads=1)
+    assert one["iters"] == T and np.array_equal(one["lam"], ref)
+    four = oracle.solve_threads(p, *sched, precondition=precondition, restart=restart, target=-1.0,
+                                gap_every=10 ** 9, max_iters=T, nthreads=4)
+    assert np.abs(four["lam"] - ref).max() <= 1e-11 * max(np.abs(ref).max(), 1e-9)
+
+
+def test_threaded_solve_stops_at_the_first_certified_check():
+    inst = synth.generate(synth.recipe_production(I=1500, J=40, seed=24))
+    p = oracle.Problem.from_instance(inst)
+    sched = (1e-1, 1e-2, 0.5, 40)  # gamma_end from iteration 160
+    out = oracle.solve_threads(p, *sched, precondition=True, target=1e-4, gap_every=25, max_iters=20000, nthreads=3)
+    T = out["iters"]
+    assert T % 25 == 0 and T >= 175 and out["rel_gap"] <= 1e-4
+    lam = oracle.fista(p, T, *sched, precondition=True, trajectory=False)["lam"]
+    cert = oracle.certify(p, lam, 1e-2)
+    assert abs(cert["rel_gap"] - out["rel_gap"]) <= 1e-9 and abs(cert["g"] - out["g"]) <= 1e-9 * abs(cert["g"])
+    prev = oracle.certify(p, oracle.fista(p, T - 25, *sched, precondition=True, trajectory=False)["lam"], 1e-2)
+    assert prev["rel_gap"] > 1e-4

@@ -60,8 +60,10 @@ typedef enum { DLM_MEM_DEVICE = 0, DLM_MEM_HOST = 1 } dlm_memspace;
  * one column per source, Sec. 4.1; one column per user is one CSR row here).
  *   row_ptr  int64 [num_users + 1], row_ptr[0] = 0, non-decreasing,
  *            row_ptr[num_users] = nnz
- *   item_idx int32 [nnz], 0 <= item_idx < num_items (the eligible items of
- *            each user; a repeated item in one row is a parallel edge)
+ *   item_idx int32 [nnz], 0 <= item_idx < num_items: the eligible items of
+ *            each user, distinct within a row (the eligible set E of
+ *            Sec. 3.3 is a set of (user, item) pairs; a repeated item in one
+ *            row is rejected)
  *   c        [nnz] float32 (val_dtype DLM_F32) or bfloat16 bit patterns
  *            (DLM_BF16, stored as uint16); all finite
  *   a        [nnz x num_families], edge-major (a[e * m + k] is edge e's
@@ -151,7 +153,8 @@ typedef struct dlm_batch dlm_batch;
 
 /* Create a solver handle for one instance (Sec. 3.3 matching LP).  Validates
  * the input (returns DLM_ERR_INVALID_ARG with a message on non-monotone
- * row_ptr, out-of-range items, non-finite values, b < 0, z <= 0), buckets
+ * row_ptr, out-of-range items, an item repeated within a row, non-finite
+ * values, b < 0, z <= 0), buckets
  * users by degree and lays the edges out for the sweep kernels.  `stream` is
  * a cudaStream_t; with NULL the handle creates its own blocking stream,
  * which is ordered with the legacy default stream in both directions.  Initial state: lam = 0,
@@ -169,7 +172,10 @@ dlm_status dlm_create(const dlm_problem_desc* desc, void* stream, dlm_problem** 
  * stage boundary the momentum restarts (theta = 1, y = lam), lam is kept as the
  * warm start, and the step 1/L, L = max_j sum_i a_ij^2 / gamma, follows gamma.
  * gamma0 == gamma_end gives a fixed ridge.  Requires gamma_end > 0,
- * gamma0 >= gamma_end, 0 < factor <= 1, iters_per_stage >= 1.  Resets the
+ * gamma0 >= gamma_end, 0 < factor <= 1 (factor == 1 only with
+ * gamma0 == gamma_end), iters_per_stage >= 1; DLM_ERR_INVALID_ARG otherwise.
+ * The stages down to gamma_end are tabulated; a schedule that needs more than
+ * 2^20 stages to reach gamma_end returns DLM_ERR_UNSUPPORTED.  Resets the
  * iteration counter and momentum (lam is kept). */
 dlm_status dlm_set_schedule(dlm_problem* p, double gamma0, double gamma_end, double factor,
                             int64_t iters_per_stage);
@@ -208,7 +214,8 @@ dlm_status dlm_get_options(dlm_problem* p, dlm_options* opt);
 dlm_status dlm_autotune(dlm_problem* p, int32_t iters, dlm_options* chosen, double* sweep_ms);
 
 /* Warm start: lam <- max(lambda0, 0), y <- lam, theta <- 1, iteration counter
- * kept.  lambda0 has num_items float32 entries in `memspace`. */
+ * kept.  lambda0 has num_items float32 entries in `memspace`.  The handle
+ * keeps its iterate lam, y in FP64 (the sweeps read FP32 copies of it). */
 dlm_status dlm_set_lambda(dlm_problem* p, const float* lambda0, int32_t memspace);
 
 /* One dual evaluation (the paper's ObjectiveFunction.calculate, Table 1):
@@ -231,18 +238,31 @@ dlm_status dlm_solve(dlm_problem* p, double target_rel_gap, int64_t max_iters, d
 /* Certified-gap evaluation at the current lam (one sweep; see dlm_stats). */
 dlm_status dlm_get_stats(dlm_problem* p, dlm_stats* out);
 
-/* Current lam (num_items float32) into `memspace`. */
+/* Current lam (num_items float32: the FP32 copy of the FP64 iterate) into
+ * `memspace`. */
 dlm_status dlm_get_lambda(dlm_problem* p, float* out, int32_t memspace);
 
 /* x(lam) for the current lam and gamma, in the caller's CSR edge order
  * (nnz float32) into `memspace`. */
 dlm_status dlm_get_x(dlm_problem* p, float* out, int32_t memspace);
 
-/* Checkpoint / resume: lam and y (num_items float32 each, `memspace`) and the
- * scalar state.  dlm_set_state restores exactly the trajectory that
- * dlm_get_state saved (same schedule and options assumed). */
-dlm_status dlm_get_state(dlm_problem* p, float* lam, float* y, dlm_state* s, int32_t memspace);
-dlm_status dlm_set_state(dlm_problem* p, const float* lam, const float* y, const dlm_state* s, int32_t memspace);
+/* Checkpoint / resume: the FP64 iterate lam and momentum point y (num_items
+ * float64 each, `memspace`) and the scalar state.  dlm_set_state restores
+ * exactly the trajectory that dlm_get_state saved (same schedule and options
+ * assumed). */
+dlm_status dlm_get_state(dlm_problem* p, double* lam, double* y, dlm_state* s, int32_t memspace);
+dlm_status dlm_set_state(dlm_problem* p, const double* lam, const double* y, const dlm_state* s, int32_t memspace);
+
+/* Dual objective along the iteration (App. B.1 tracks it per iteration; the
+ * paper's ObjectiveFunction.calculate returns it with the gradient, Table 1):
+ * every iteration t records g(y_t) = sum_i (c x_i + gamma/2 ||x_i||^2) +
+ * y_t^T (A x - b) at the point its sweep evaluated (x = x(y_t), gamma of
+ * iteration t), from the sweep's exact fixed-point objective sum and an FP64
+ * dot product.  Copies g(y_t) for t = first_iter .. first_iter + n - 1 to the
+ * host array g_out.  The handle keeps the last 4096 iterations since the last
+ * dlm_set_schedule / dlm_set_state; other ranges return DLM_ERR_INVALID_ARG.
+ * Synchronous. */
+dlm_status dlm_get_trajectory(dlm_problem* p, int64_t first_iter, int64_t n, double* g_out);
 
 /* Run n_iters iterations as individual kernel launches with a CUDA event
  * recorded on the handle's stream between consecutive kernels, and return the
@@ -258,7 +278,18 @@ dlm_status dlm_step_timed(dlm_problem* p, int64_t n_iters, double* sweep_ms, dou
 dlm_status dlm_get_info(dlm_problem* p, int64_t* num_users, int64_t* num_items, int64_t* nnz,
                         int64_t* bytes_per_iter);
 
+/* Free the handle and its device memory.  The instance's large arrays (the
+ * sliced layout, set-up scratch) come from a stream-ordered memory pool per
+ * device that keeps freed memory for later handles, so that re-creating an
+ * instance of similar size (the paper's recurring daily solves, Sec. 1) maps
+ * no new device memory; dlm_release_cached_memory returns that memory to
+ * the device. */
 void dlm_destroy(dlm_problem* p);
+
+/* Return the memory the library's pools keep after dlm_destroy (every device
+ * the library has used) to the device.  Call it with no handle being created
+ * or destroyed on another thread. */
+dlm_status dlm_release_cached_memory(void);
 
 /* Batches (the paper's experiments solve many independent instances; this
  * sweeps them together).  A batch runs n existing handles as one: each
@@ -357,17 +388,20 @@ void dlm_ws_destroy(dlm_ws* w);
  * for FP32 c and a, without a handle.
  *   row_ptr, item_idx, c, a, b, lambda: device arrays as in dlm_problem_desc
  *     (valid CSR; an out-of-range item or row pointer makes the call write
- *     NaN to g and grad instead of reading out of bounds);
+ *     NaN to g and grad instead of reading out of bounds, and x is then
+ *     undefined: a row with a bad row pointer is skipped, its x entries
+ *     keep whatever the buffer held);
  *   kind, z: the simple sets; gamma > 0: the ridge;
  *   g: device double (1), grad: device float (num_items) or NULL,
  *   x: device float (nnz, caller's edge order) or NULL.
  * Asynchronous on `stream` (a cudaStream_t; NULL = legacy default stream).
- * Scratch: one file-scope device array of 1.5 MB (fixed-point item sums for
- * up to 65,536 items, objective partials, bounds), held on every GPU that
- * loads the library until the process exits; num_items > 65,536 returns
+ * Scratch: one file-scope device array of about 0.5 MB (fixed-point item
+ * sums for up to 65,536 items, objective partials, bounds), held on every GPU
+ * that loads the library until the process exits; num_items > 65,536 returns
  * DLM_ERR_UNSUPPORTED.  The first call on a device looks the array's device
- * address up (cudaGetSymbolAddress), so make that first call before any
- * stream capture.  Every call clears the scratch it needs at its start and
+ * address up (cudaGetSymbolAddress) and keeps it for the life of the
+ * process, so make that first call before any stream capture, and do not
+ * call this entry point again after cudaDeviceReset on that device.  Every call clears the scratch it needs at its start and
  * leaves it cleared at its end; calls that overlap on the GPU share the
  * array and race, so issue them one after another on one stream. */
 dlm_status dlm_calculate_static(int64_t num_users, int64_t num_items, int64_t nnz, const int64_t* row_ptr,

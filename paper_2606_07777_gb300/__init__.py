@@ -19,7 +19,7 @@ __all__ = [
     "load", "build", "DlmError", "Solver", "dlm_create", "dlm_set_schedule", "dlm_set_options", "dlm_set_lambda",
     "dlm_calculate", "dlm_step", "dlm_solve", "dlm_get_stats", "dlm_get_lambda", "dlm_get_x", "dlm_get_state",
     "dlm_set_state", "dlm_get_info", "dlm_step_timed", "dlm_calculate_static", "dlm_destroy", "dlm_last_error",
-    "dlm_get_options", "dlm_autotune", "Batch", "dlm_batch_create", "dlm_batch_set_options", "dlm_batch_autotune",
+    "dlm_get_options", "dlm_autotune", "dlm_get_trajectory", "dlm_release_cached_memory", "Batch", "dlm_batch_create", "dlm_batch_set_options", "dlm_batch_autotune",
     "dlm_batch_step", "dlm_batch_step_timed", "dlm_batch_get_stats", "dlm_batch_solve", "dlm_batch_destroy",
     "WarmStart", "WS_FEATURES",
 ]
@@ -93,6 +93,8 @@ _SIGS = {
     "dlm_get_x": [_vp, _vp, _i32],
     "dlm_get_state": [_vp, _vp, _vp, ctypes.POINTER(State), _i32],
     "dlm_set_state": [_vp, _vp, _vp, ctypes.POINTER(State), _i32],
+    "dlm_get_trajectory": [_vp, _i64, _i64, _vp],
+    "dlm_release_cached_memory": [],
     "dlm_get_info": [_vp, ctypes.POINTER(_i64), ctypes.POINTER(_i64), ctypes.POINTER(_i64), ctypes.POINTER(_i64)],
     "dlm_step_timed": [_vp, _i64, ctypes.POINTER(_d), ctypes.POINTER(_d), ctypes.POINTER(_d)],
     "dlm_calculate_static": [_i64, _i64, _i64, _vp, _vp, _vp, _vp, _vp, _i32, _d, _vp, _d, _vp, _vp, _vp, _vp],
@@ -249,6 +251,20 @@ def dlm_get_state(h, lam, y, memspace) -> State:
 
 def dlm_set_state(h, lam, y, state: State, memspace):
     _call("dlm_set_state", h, _ptr(lam), _ptr(y), ctypes.byref(state), memspace)
+
+
+def dlm_get_trajectory(h, first_iter, n):
+    """g(y_t) for t = first_iter .. first_iter + n - 1 (numpy float64)."""
+    import numpy as np
+
+    out = np.empty(max(int(n), 0), dtype=np.float64)
+    _call("dlm_get_trajectory", h, int(first_iter), int(n), _ptr(out) if n > 0 else None)
+    return out
+
+
+def dlm_release_cached_memory():
+    """Return the device memory the library's pools keep after handles are destroyed."""
+    _call("dlm_release_cached_memory")
 
 
 def dlm_get_info(h):
@@ -446,8 +462,9 @@ class Solver:
         return out
 
     def get_state(self):
+        """(lam, y, State): the FP64 iterate and momentum point (CUDA float64)."""
         t = self._torch
-        lam = t.empty(self.dual_dim, dtype=t.float32, device=self.device)
+        lam = t.empty(self.dual_dim, dtype=t.float64, device=self.device)
         y = t.empty_like(lam)
         s = dlm_get_state(self.h, lam, y, DLM_MEM_DEVICE)
         return lam, y, s
@@ -457,6 +474,10 @@ class Solver:
 
     def info(self):
         return dlm_get_info(self.h)
+
+    def trajectory(self, first_iter, n):
+        """Dual objective g(y_t) of iterations first_iter .. first_iter + n - 1."""
+        return dlm_get_trajectory(self.h, first_iter, n)
 
 
 class Batch:

@@ -40,15 +40,40 @@ dlm_status fail(dlm_status s, const std::string& m) {
 
 __global__ void k_set_double(double* p, double v) { *p = v; }
 
-// lam <- max(src, 0), y <- lam, theta <- 1 (warm start).
-__global__ void k_warm(const float* src, float* lam, float* y, int64_t J, DevState* st) {
+// lam <- max(src, 0), y <- lam, theta <- 1 (warm start); the FP64 iterate
+// and its FP32 copies.
+__global__ void k_warm(const float* src, double* lam64, double* y64, float* lam, float* y, int64_t J,
+                       DevState* st) {
   for (int64_t j = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; j < J;
        j += static_cast<int64_t>(gridDim.x) * blockDim.x) {
     const float v = fmaxf(src[j], 0.f);
+    lam64[j] = v;
+    y64[j] = v;
     lam[j] = v;
     y[j] = v;
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) st->theta = 1.0;
+}
+
+// y <- lam (the momentum restart of a new schedule), theta <- 1; FP32 copies.
+__global__ void k_momentum_reset(const double* lam64, double* y64, float* lam, float* y, int64_t n, DevState* st) {
+  for (int64_t j = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; j < n;
+       j += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const double v = lam64[j];
+    y64[j] = v;
+    lam[j] = static_cast<float>(v);
+    y[j] = static_cast<float>(v);
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) st->theta = 1.0;
+}
+
+// FP32 copies of the FP64 iterate (after a restore).
+__global__ void k_shadow(const double* lam64, const double* y64, float* lam, float* y, int64_t n) {
+  for (int64_t j = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; j < n;
+       j += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    lam[j] = static_cast<float>(lam64[j]);
+    y[j] = static_cast<float>(y64[j]);
+  }
 }
 
 __global__ void k_state_reset(DevState* st, double gamma0) {
@@ -130,9 +155,8 @@ struct dlm_problem {
   int sG = 0, sC = 0, sQ = 0;
   bool certified = true;
 
-  double *b = nullptr, *inv_n2 = nullptr;  // inv_n2: per-coordinate inverse curvature bounds (steps)
-  double inv_hmax = 0;                      // 1 / the largest curvature bound (plain step)
-  double inv_h_count = 0;                   // 1 / curvature bound of the count row
+  double *b = nullptr, *curv = nullptr;  // curv: per-coordinate curvature bounds h (steps gamma / h)
+  double curv_max = 0;                    // the largest bound (plain step gamma / curv_max)
   // global count constraint sum x <= M: dual entry J of lam and y
   bool count_on = false;
   double count_M = INFINITY;
@@ -146,9 +170,15 @@ struct dlm_problem {
   std::vector<double> h_gram;  // [m m J]: sum_i a_kij a_lij
   int64_t MJ() const { return static_cast<int64_t>(m) * J; }
   int64_t D() const { return MJ() + (count_on ? 1 : 0); }  // dual dimension
-  float *lam = nullptr, *y = nullptr;
+  double *lam64 = nullptr, *y64 = nullptr;  // the iterate (FP64)
+  float *lam = nullptr, *y = nullptr;       // its FP32 copies, read by the sweeps
   unsigned long long *acc = nullptr, *acc2 = nullptr, *accC = nullptr, *accQ = nullptr;
+  unsigned long long* objq = nullptr;       // fixed-point objective sum of the iteration sweep
+  int sO = 0;                               // its exponent
+  double* traj = nullptr;                   // [kTrajCap] g(y_t) per iteration (ring)
+  int64_t traj_from = 0;                    // first iteration whose trajectory entry is valid
   double *gamma_tab = nullptr, *calc_gamma = nullptr, *stats_out = nullptr;
+  int64_t nstages = 1, gamma_tab_cap = 0;
   DevState* state = nullptr;
   InstDesc* inst_calc = nullptr;
   StatsInst* st_calc = nullptr;
@@ -180,7 +210,6 @@ InstDesc base_desc(const dlm_problem* p) {
   InstDesc d{};
   d.slice_off = p->lay.slice_off;
   d.slice_w = p->lay.slice_w;
-  d.col = p->lay.col;
   d.col16 = p->lay.col16;
   d.ca = p->lay.ca;
   d.orig_off = p->lay.orig_off;
@@ -380,6 +409,8 @@ dlm_status write_tables(Runner& R) {
     it[i].seg_obj = R.seg_obj;
     it[i].xout = nullptr;
     it[i].cnt = p->cnt;
+    it[i].objq = p->objq;
+    it[i].scaleO = std::ldexp(1.0f, p->sO);
     ss[i] = base_desc(p);
     ss[i].y = p->lam;
     ss[i].gamma = &p->state->gamma;
@@ -391,14 +422,20 @@ dlm_status write_tables(Runner& R) {
     UpdInst u{};
     u.state = p->state;
     u.gamma_tab = p->gamma_tab;
+    u.nstages = p->nstages;
     u.b = p->b;
-    u.inv_n2 = p->inv_n2;
+    u.curv = p->curv;
+    u.lam64 = p->lam64;
+    u.y64 = p->y64;
     u.lam = p->lam;
     u.y = p->y;
     u.acc = p->acc;
+    u.objq = p->objq;
+    u.traj = p->traj;
     u.iters_per_stage = p->ips;
-    u.inv_nmax = p->inv_hmax;
+    u.curv_max = p->curv_max;
     u.inv_scaleG = std::ldexp(1.0, -p->sG);
+    u.inv_scaleO = std::ldexp(1.0, -p->sO);
     u.J = static_cast<int32_t>(p->J);
     u.precondition = p->opt.precondition ? 1 : 0;
     u.adaptive_restart = p->opt.restart ? 1 : 0;
@@ -407,7 +444,6 @@ dlm_status write_tables(Runner& R) {
     u.cnt_rw = p->cnt;
     u.inv_scaleN = std::ldexp(1.0, -p->sN);
     u.count_M = p->count_M;
-    u.inv_h_count = p->inv_h_count;
     u.ncap = static_cast<int32_t>(p->MJ());
     up[i] = u;
     st[i] = base_stats(p, R, i);
@@ -635,19 +671,16 @@ void free_problem(dlm_problem* p) {
   if (!p) return;
   if (p->stream) cudaStreamSynchronize(p->stream);
   runner_free(p->run);
-  cudaFree(p->lay.slice_off);
-  cudaFree(p->lay.slice_w);
-  cudaFree(p->lay.col);
-  cudaFree(p->lay.col16);
-  cudaFree(p->lay.ca);
-  cudaFree(p->lay.orig_off);
-  cudaFree(p->lay.udeg);
-  cudaFree(p->lay.n2);
+  cudaStream_t s = p->stream;
+  void* pooled[] = {p->lay.slice_off, p->lay.slice_w, p->lay.col16, p->lay.ca, p->lay.orig_off,
+                    p->lay.udeg,      p->lay.n2,      p->a_ext};
+  for (void* q : pooled) dev_free(q, s);
+  if (s) cudaStreamSynchronize(s);
   cudaFree(p->cnt);
   cudaFree(p->cnt2);
-  cudaFree(p->a_ext);
-  void* ptrs[] = {p->b,         p->inv_n2,    p->lam,       p->y,         p->acc,   p->acc2,      p->accC,
-                  p->accQ,      p->gamma_tab, p->calc_gamma, p->stats_out, p->state, p->inst_calc, p->st_calc};
+  void* ptrs[] = {p->b,         p->curv,      p->lam,       p->y,         p->acc,   p->acc2,      p->accC,
+                  p->accQ,      p->gamma_tab, p->calc_gamma, p->stats_out, p->state, p->inst_calc, p->st_calc,
+                  p->lam64,     p->y64,       p->objq,      p->traj};
   for (void* q : ptrs) cudaFree(q);
   cudaFreeHost(p->h_out);
   cudaFreeHost(p->h_inst);
@@ -667,69 +700,94 @@ void free_problem(dlm_problem* p) {
 dlm_status upload_steps(dlm_problem* p) {
   const int64_t J = p->J, MJ = p->MJ();
   const int m = p->m;
-  std::vector<double> inv(MJ + 1, 0.0);
+  std::vector<double> h(MJ + 1, 0.0);
   double hmax = 0.0, tot = 0.0;
   for (int64_t q = 0; q < MJ; ++q) {
-    double h;
+    double hq;
     if (m == 1) {
-      h = p->lay.h_n2[q];
+      hq = p->lay.h_n2[q];
     } else {  // Gershgorin row sum of item j's m x m block
       const int64_t f = q / J, j = q % J;
-      h = 0.0;
-      for (int l = 0; l < m; ++l) h += std::fabs(p->h_gram[(static_cast<size_t>(f) * m + l) * J + j]);
+      hq = 0.0;
+      for (int l = 0; l < m; ++l) hq += std::fabs(p->h_gram[(static_cast<size_t>(f) * m + l) * J + j]);
     }
     if (p->count_on) {
-      h += std::fabs(p->lay.h_s1[q]);
+      hq += std::fabs(p->lay.h_s1[q]);
       tot += std::fabs(p->lay.h_s1[q]);
     }
-    inv[q] = h > 0 ? 1.0 / h : 0.0;
-    hmax = h > hmax ? h : hmax;
+    h[q] = hq;
+    hmax = hq > hmax ? hq : hmax;
   }
-  p->inv_h_count = 0.0;
   if (p->count_on) {
     const double hc = static_cast<double>(p->nnz) + tot;
-    p->inv_h_count = hc > 0 ? 1.0 / hc : 0.0;
-    inv[MJ] = p->inv_h_count;
+    h[MJ] = hc;
     hmax = hc > hmax ? hc : hmax;
   }
-  p->inv_hmax = hmax > 0 ? 1.0 / hmax : 0.0;
-  CK(cudaMemcpyAsync(p->inv_n2, inv.data(), sizeof(double) * (MJ + 1), cudaMemcpyHostToDevice, p->stream));
+  p->curv_max = hmax;
+  CK(cudaMemcpyAsync(p->curv, h.data(), sizeof(double) * (MJ + 1), cudaMemcpyHostToDevice, p->stream));
   CK(cudaStreamSynchronize(p->stream));
   return DLM_OK;
 }
 
+// Exponent of the iteration sweep's fixed-point objective sum: a bound on
+// |sum_i (c x_i + gamma/2 ||x_i||^2)| for the largest gamma of the schedule
+// (every x_ij <= z; on the simplex sum_j x_ij <= z per user).
+int objective_shift(const dlm_problem* p) {
+  const bool simplex = p->kind == DLM_SIMPLEX_LE || p->kind == DLM_SIMPLEX_EQ;
+  const double units = static_cast<double>(simplex ? p->lay.num_active_users : p->nnz);
+  const double per = p->z * (p->lay.max_abs_c + 0.5 * p->gamma0 * p->z);
+  const double bound = (units > 0 ? units : 1.0) * (per > 0 ? per : 1.0);
+  return std::max(fixed_point_shift(bound), 0);
+}
+
+// The stage table of the continuation schedule (Sec. 6, App. B.2):
+// gamma_0 = gamma0, gamma_{s+1} = max(gamma_end, gamma_s * factor), up to the
+// first stage at gamma_end (every later stage has the same gamma).
 dlm_status upload_schedule(dlm_problem* p) {
-  p->h_gamma_tab.assign(kMaxStages, 0.0);
-  double g = p->gamma0;
-  for (int s = 0; s < kMaxStages; ++s) {
-    p->h_gamma_tab[s] = g;
-    const double n = g * p->factor;
-    g = n > p->gamma_end ? n : p->gamma_end;
+  std::vector<double> tab(1, p->gamma0);
+  while (tab.back() != p->gamma_end) {
+    if (static_cast<int64_t>(tab.size()) >= kMaxStageTable)
+      return fail(DLM_ERR_UNSUPPORTED, "the schedule takes more than 2^20 stages to reach gamma_end");
+    const double n = tab.back() * p->factor;
+    tab.push_back(n > p->gamma_end ? n : p->gamma_end);
   }
-  CK(cudaMemcpyAsync(p->gamma_tab, p->h_gamma_tab.data(), sizeof(double) * kMaxStages, cudaMemcpyHostToDevice,
+  CK(cudaStreamSynchronize(p->stream));
+  if (static_cast<int64_t>(tab.size()) > p->gamma_tab_cap) {
+    cudaFree(p->gamma_tab);
+    p->gamma_tab = nullptr;
+    p->gamma_tab_cap = 0;
+    CK(dalloc(&p->gamma_tab, tab.size()));
+    p->gamma_tab_cap = static_cast<int64_t>(tab.size());
+  }
+  p->h_gamma_tab = tab;
+  p->nstages = static_cast<int64_t>(tab.size());
+  p->sO = objective_shift(p);
+  CK(cudaMemcpyAsync(p->gamma_tab, p->h_gamma_tab.data(), sizeof(double) * tab.size(), cudaMemcpyHostToDevice,
                      p->stream));
   k_state_reset<<<1, 1, 0, p->stream>>>(p->state, p->gamma0);
   CK(cudaGetLastError());
-  k_warm<<<blocks_for(p->D()), 256, 0, p->stream>>>(p->lam, p->lam, p->y, p->D(), p->state);
+  k_momentum_reset<<<blocks_for(p->D()), 256, 0, p->stream>>>(p->lam64, p->y64, p->lam, p->y, p->D(), p->state);
   CK(cudaGetLastError());
+  CK(cudaMemsetAsync(p->objq, 0, sizeof(unsigned long long), p->stream));
   CK(cudaStreamSynchronize(p->stream));
+  p->traj_from = 0;
   invalidate_graph(p->run);
   return write_tables(p->run);
 }
 
-// Saved duals and state of the members (tuning trials must not advance them).
+// Saved iterates and state of the members (tuning trials must not advance them).
 struct Saved {
-  std::vector<float*> lam, y;
+  std::vector<double*> lam, y;
   std::vector<DevState> st;
 };
 dlm_status save_state(Runner& R, Saved* S) {
   CK(cudaStreamSynchronize(R.stream));
   for (dlm_problem* p : R.probs) {
-    float *l = nullptr, *y = nullptr;
+    double *l = nullptr, *y = nullptr;
     CK(dalloc(&l, p->D()));
     CK(dalloc(&y, p->D()));
-    CK(cudaMemcpy(l, p->lam, sizeof(float) * p->D(), cudaMemcpyDeviceToDevice));
-    CK(cudaMemcpy(y, p->y, sizeof(float) * p->D(), cudaMemcpyDeviceToDevice));
+    CK(cudaMemcpy(l, p->lam64, sizeof(double) * p->D(), cudaMemcpyDeviceToDevice));
+    CK(cudaMemcpy(y, p->y64, sizeof(double) * p->D(), cudaMemcpyDeviceToDevice));
     DevState hs;
     CK(cudaMemcpy(&hs, p->state, sizeof(DevState), cudaMemcpyDeviceToHost));
     S->lam.push_back(l);
@@ -742,17 +800,22 @@ dlm_status restore_state(Runner& R, const Saved& S) {
   CK(cudaStreamSynchronize(R.stream));
   for (size_t i = 0; i < R.probs.size(); ++i) {
     dlm_problem* p = R.probs[i];
-    CK(cudaMemcpy(p->lam, S.lam[i], sizeof(float) * p->D(), cudaMemcpyDeviceToDevice));
-    CK(cudaMemcpy(p->y, S.y[i], sizeof(float) * p->D(), cudaMemcpyDeviceToDevice));
+    CK(cudaMemcpy(p->lam64, S.lam[i], sizeof(double) * p->D(), cudaMemcpyDeviceToDevice));
+    CK(cudaMemcpy(p->y64, S.y[i], sizeof(double) * p->D(), cudaMemcpyDeviceToDevice));
+    k_shadow<<<blocks_for(p->D()), 256, 0, R.stream>>>(p->lam64, p->y64, p->lam, p->y, p->D());
+    CK(cudaGetLastError());
+    CK(cudaStreamSynchronize(R.stream));
     CK(cudaMemset(p->cnt, 0, sizeof(unsigned long long)));
+    CK(cudaMemset(p->objq, 0, sizeof(unsigned long long)));
     CK(cudaMemcpy(p->state, &S.st[i], sizeof(DevState), cudaMemcpyHostToDevice));
     CK(cudaMemset(p->acc, 0, sizeof(unsigned long long) * p->MJ()));
+    p->traj_from = S.st[i].iter;
   }
   return DLM_OK;
 }
 void free_saved(Saved& S) {
-  for (float* q : S.lam) cudaFree(q);
-  for (float* q : S.y) cudaFree(q);
+  for (double* q : S.lam) cudaFree(q);
+  for (double* q : S.y) cudaFree(q);
   S.lam.clear();
   S.y.clear();
 }
@@ -891,6 +954,14 @@ dlm_status dlm_create(const dlm_problem_desc* desc, void* stream, dlm_problem** 
   }
   const size_t vs = p->bf16 ? 2 : 4;
   const int64_t I = p->I, J = p->J, nnz = p->nnz;
+  // One family: the iteration sweep holds y and G for all items; certificate
+  // sweeps take item windows when their three item arrays do not fit.
+  if (m > 1 ? sweep_multi_smem_bytes(static_cast<int>(J), m, true) > sweep_smem_limit()
+            : (sweep_smem_bytes(static_cast<int>(J), false) > sweep_smem_limit() ||
+               sweep_stats_window(static_cast<int>(J)) < 1)) {
+    free_problem(p);
+    return fail(DLM_ERR_UNSUPPORTED, "num_items too large for the shared-memory item arrays of this build");
+  }
 
   // Bring host inputs to the device (stream ordered).
   const int64_t* rp = desc->row_ptr;
@@ -901,13 +972,16 @@ dlm_status dlm_create(const dlm_problem_desc* desc, void* stream, dlm_problem** 
   void* tmp[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
   dlm_status st = DLM_OK;
   auto cleanup_tmp = [&]() {
-    for (void* q : tmp) cudaFree(q);
+    for (void*& q : tmp) {
+      dev_free(q, p->stream);
+      q = nullptr;
+    }
   };
   if (desc->memspace == DLM_MEM_HOST) {
     size_t sz[5] = {sizeof(int64_t) * (I + 1), sizeof(int32_t) * nnz, vs * nnz, vs * nnz * m, sizeof(double) * J * m};
     const void* src[5] = {rp, col, c, a, b};
     for (int k = 0; k < 5; ++k) {
-      if (cudaMalloc(&tmp[k], sz[k] > 0 ? sz[k] : 16) != cudaSuccess) {
+      if (dev_alloc(&tmp[k], sz[k], p->stream) != cudaSuccess) {
         cleanup_tmp();
         free_problem(p);
         return fail(DLM_ERR_OOM, "device allocation for host inputs failed");
@@ -930,11 +1004,11 @@ dlm_status dlm_create(const dlm_problem_desc* desc, void* stream, dlm_problem** 
   void* split = nullptr;
   auto cleanup_all = [&]() {
     cleanup_tmp();
-    cudaFree(split);
+    dev_free(split, p->stream);
     split = nullptr;
   };
   if (m > 1) {
-    if (cudaMalloc(&split, vs * (nnz > 0 ? nnz : 1) * m) != cudaSuccess) {
+    if (dev_alloc(&split, vs * (nnz > 0 ? nnz : 1) * m, p->stream) != cudaSuccess) {
       cleanup_all();
       free_problem(p);
       return fail(DLM_ERR_OOM, "device allocation for the family split failed");
@@ -1007,25 +1081,6 @@ dlm_status dlm_create(const dlm_problem_desc* desc, void* stream, dlm_problem** 
     free_problem(p);
     return fail(DLM_ERR_UNSUPPORTED, "item sums too large for 64-bit fixed point");
   }
-  // One family: the iteration sweep holds y and G for all items; certificate
-  // sweeps take item windows when their three item arrays do not fit.
-  if (m > 1 ? sweep_multi_smem_bytes(static_cast<int>(J), m, true) > sweep_smem_limit()
-            : (sweep_smem_bytes(static_cast<int>(J), false) > sweep_smem_limit() ||
-               sweep_stats_window(static_cast<int>(J)) < 1)) {
-    cleanup_all();
-    free_problem(p);
-    return fail(DLM_ERR_UNSUPPORTED, "num_items too large for the shared-memory item arrays of this build");
-  }
-  // The sweeps and the warm-start features stream the 16-bit item indices
-  // (the limit above keeps J below 65,536); the int32 copy is freed.
-  if (p->lay.col16 == nullptr) {
-    cleanup_all();
-    free_problem(p);
-    return fail(DLM_ERR_UNSUPPORTED, "handle without 16-bit item indices");
-  }
-  cudaStreamSynchronize(p->stream);
-  cudaFree(p->lay.col);
-  p->lay.col = nullptr;
 
 #define CKC(x)                                                                     \
   do {                                                                             \
@@ -1041,7 +1096,7 @@ dlm_status dlm_create(const dlm_problem_desc* desc, void* stream, dlm_problem** 
   if (m > 1) {
     // extra family streams in slice order, and the per-item Gram sums
     p->ext_stride = p->lay.padded_nnz + 32;
-    CKC(cudaMalloc(&p->a_ext, vs * p->ext_stride * (m - 1)));
+    CKC(dev_alloc(&p->a_ext, vs * p->ext_stride * (m - 1), p->stream));
     for (int f = 1; f < m; ++f)
       CKC(families_gather(p->lay, fam_ptr(f), p->bf16,
                           static_cast<char*>(p->a_ext) + vs * p->ext_stride * (f - 1), p->stream));
@@ -1068,9 +1123,17 @@ dlm_status dlm_create(const dlm_problem_desc* desc, void* stream, dlm_problem** 
   }
   CKC(dalloc(&p->b, MJ));
   CKC(cudaMemcpyAsync(p->b, b, sizeof(double) * MJ, cudaMemcpyDeviceToDevice, p->stream));
-  CKC(dalloc(&p->inv_n2, MJ + 1));
+  CKC(dalloc(&p->curv, MJ + 1));
   CKC(dalloc(&p->lam, MJ + 1));
   CKC(dalloc(&p->y, MJ + 1));
+  CKC(dalloc(&p->lam64, MJ + 1));
+  CKC(dalloc(&p->y64, MJ + 1));
+  CKC(dalloc(&p->objq, 1));
+  CKC(dalloc(&p->traj, kTrajCap));
+  CKC(cudaMemsetAsync(p->lam64, 0, sizeof(double) * (MJ + 1), p->stream));
+  CKC(cudaMemsetAsync(p->y64, 0, sizeof(double) * (MJ + 1), p->stream));
+  CKC(cudaMemsetAsync(p->objq, 0, sizeof(unsigned long long), p->stream));
+  CKC(cudaMemsetAsync(p->traj, 0, sizeof(double) * kTrajCap, p->stream));
   CKC(dalloc(&p->cnt, 1));
   CKC(dalloc(&p->cnt2, 1));
   CKC(cudaMemsetAsync(p->cnt, 0, sizeof(unsigned long long), p->stream));
@@ -1085,7 +1148,6 @@ dlm_status dlm_create(const dlm_problem_desc* desc, void* stream, dlm_problem** 
   CKC(cudaMemsetAsync(p->accQ, 0, sizeof(unsigned long long) * J, p->stream));
   CKC(cudaMemsetAsync(p->lam, 0, sizeof(float) * (MJ + 1), p->stream));
   CKC(cudaMemsetAsync(p->y, 0, sizeof(float) * (MJ + 1), p->stream));
-  CKC(dalloc(&p->gamma_tab, kMaxStages));
   CKC(dalloc(&p->calc_gamma, 1));
   CKC(dalloc(&p->stats_out, 8));
   CKC(dalloc(&p->state, 1));
@@ -1113,7 +1175,7 @@ dlm_status dlm_create(const dlm_problem_desc* desc, void* stream, dlm_problem** 
   R.smemJ = static_cast<int>(J);
   R.win = m > 1 ? R.smemJ : sweep_stats_window(R.smemJ);
   cudaDeviceGetAttribute(&R.sms, cudaDevAttrMultiProcessorCount, p->device);
-  p->h_gamma_tab.assign(kMaxStages, p->gamma0);
+  p->h_gamma_tab.assign(1, p->gamma0);
   st = upload_steps(p);
   if (st == DLM_OK) st = runner_configure(R, p->opt, true);
   if (st == DLM_OK) st = upload_schedule(p);
@@ -1128,13 +1190,24 @@ dlm_status dlm_create(const dlm_problem_desc* desc, void* stream, dlm_problem** 
 dlm_status dlm_set_schedule(dlm_problem* p, double gamma0, double gamma_end, double factor, int64_t iters_per_stage) {
   if (!p) return fail(DLM_ERR_INVALID_ARG, "null handle");
   if (!(gamma_end > 0) || !(gamma0 >= gamma_end) || !std::isfinite(gamma0) || !(factor > 0) || factor > 1 ||
-      iters_per_stage < 1)
-    return fail(DLM_ERR_INVALID_ARG, "need gamma0 >= gamma_end > 0, 0 < factor <= 1, iters_per_stage >= 1");
+      iters_per_stage < 1 || (factor == 1 && gamma0 != gamma_end))
+    return fail(DLM_ERR_INVALID_ARG,
+                "need gamma0 >= gamma_end > 0, 0 < factor <= 1 (1 only with gamma0 == gamma_end), "
+                "iters_per_stage >= 1");
+  const double g0 = p->gamma0, ge = p->gamma_end, f = p->factor;
+  const int64_t ips = p->ips;
   p->gamma0 = gamma0;
   p->gamma_end = gamma_end;
   p->factor = factor;
   p->ips = iters_per_stage;
-  return upload_schedule(p);
+  const dlm_status st = upload_schedule(p);
+  if (st == DLM_ERR_UNSUPPORTED) {  // keep the previous schedule
+    p->gamma0 = g0;
+    p->gamma_end = ge;
+    p->factor = f;
+    p->ips = ips;
+  }
+  return st;
 }
 
 dlm_status dlm_set_count_limit(dlm_problem* p, double M) {
@@ -1148,6 +1221,8 @@ dlm_status dlm_set_count_limit(dlm_problem* p, double M) {
   // the count dual starts at 0; its accumulators are clear
   CK(cudaMemset(p->lam + p->J, 0, sizeof(float)));
   CK(cudaMemset(p->y + p->J, 0, sizeof(float)));
+  CK(cudaMemset(p->lam64 + p->J, 0, sizeof(double)));
+  CK(cudaMemset(p->y64 + p->J, 0, sizeof(double)));
   CK(cudaMemset(p->cnt, 0, sizeof(unsigned long long)));
   CK(cudaMemset(p->cnt2, 0, sizeof(unsigned long long)));
   dlm_status st = upload_steps(p);
@@ -1192,7 +1267,7 @@ dlm_status dlm_set_lambda(dlm_problem* p, const float* lambda0, int32_t memspace
     CK(cudaMemcpyAsync(tmp, lambda0, sizeof(float) * p->D(), cudaMemcpyHostToDevice, p->stream));
     src = tmp;
   }
-  k_warm<<<blocks_for(p->D()), 256, 0, p->stream>>>(src, p->lam, p->y, p->D(), p->state);
+  k_warm<<<blocks_for(p->D()), 256, 0, p->stream>>>(src, p->lam64, p->y64, p->lam, p->y, p->D(), p->state);
   cudaError_t e = cudaGetLastError();
   if (tmp) {
     cudaStreamSynchronize(p->stream);
@@ -1335,11 +1410,11 @@ dlm_status dlm_get_x(dlm_problem* p, float* out, int32_t memspace) {
   return st;
 }
 
-dlm_status dlm_get_state(dlm_problem* p, float* lam, float* y, dlm_state* s, int32_t memspace) {
+dlm_status dlm_get_state(dlm_problem* p, double* lam, double* y, dlm_state* s, int32_t memspace) {
   if (!p) return fail(DLM_ERR_INVALID_ARG, "null handle");
   const cudaMemcpyKind k = memspace == DLM_MEM_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
-  if (lam) CK(cudaMemcpyAsync(lam, p->lam, sizeof(float) * p->D(), k, p->stream));
-  if (y) CK(cudaMemcpyAsync(y, p->y, sizeof(float) * p->D(), k, p->stream));
+  if (lam) CK(cudaMemcpyAsync(lam, p->lam64, sizeof(double) * p->D(), k, p->stream));
+  if (y) CK(cudaMemcpyAsync(y, p->y64, sizeof(double) * p->D(), k, p->stream));
   CK(cudaStreamSynchronize(p->stream));
   if (s) {
     DevState hs;
@@ -1352,20 +1427,40 @@ dlm_status dlm_get_state(dlm_problem* p, float* lam, float* y, dlm_state* s, int
   return DLM_OK;
 }
 
-dlm_status dlm_set_state(dlm_problem* p, const float* lam, const float* y, const dlm_state* s, int32_t memspace) {
+dlm_status dlm_set_state(dlm_problem* p, const double* lam, const double* y, const dlm_state* s, int32_t memspace) {
   if (!p || !lam || !y || !s) return fail(DLM_ERR_INVALID_ARG, "null argument");
   if (s->iter < 0 || s->stage < 0) return fail(DLM_ERR_INVALID_ARG, "bad state");
   const cudaMemcpyKind k = memspace == DLM_MEM_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
   CK(cudaStreamSynchronize(p->stream));
-  CK(cudaMemcpy(p->lam, lam, sizeof(float) * p->D(), k));
-  CK(cudaMemcpy(p->y, y, sizeof(float) * p->D(), k));
+  CK(cudaMemcpy(p->lam64, lam, sizeof(double) * p->D(), k));
+  CK(cudaMemcpy(p->y64, y, sizeof(double) * p->D(), k));
+  k_shadow<<<blocks_for(p->D()), 256, 0, p->stream>>>(p->lam64, p->y64, p->lam, p->y, p->D());
+  CK(cudaGetLastError());
   DevState hs{};
   hs.iter = s->iter;
   hs.theta = s->theta;
   hs.stage = s->stage;
-  hs.gamma = p->h_gamma_tab[s->stage < kMaxStages ? s->stage : kMaxStages - 1];
+  hs.gamma = p->h_gamma_tab[s->stage < p->nstages ? s->stage : p->nstages - 1];
   hs.status = 0;
+  CK(cudaStreamSynchronize(p->stream));
   CK(cudaMemcpy(p->state, &hs, sizeof(DevState), cudaMemcpyHostToDevice));
+  p->traj_from = s->iter;
+  return DLM_OK;
+}
+
+dlm_status dlm_get_trajectory(dlm_problem* p, int64_t first_iter, int64_t n, double* g_out) {
+  if (!p || (n > 0 && !g_out) || n < 0 || first_iter < 0) return fail(DLM_ERR_INVALID_ARG, "bad argument");
+  DevState hs;
+  CK(cudaStreamSynchronize(p->stream));
+  CK(cudaMemcpy(&hs, p->state, sizeof(DevState), cudaMemcpyDeviceToHost));
+  const int64_t lo = std::max<int64_t>(p->traj_from, hs.iter - kTrajCap);
+  if (first_iter < lo || first_iter + n > hs.iter)
+    return fail(DLM_ERR_INVALID_ARG, "requested iterations [" + std::to_string(first_iter) + ", " +
+                                         std::to_string(first_iter + n) + ") outside the recorded range [" +
+                                         std::to_string(lo) + ", " + std::to_string(hs.iter) + ")");
+  std::vector<double> ring(kTrajCap);
+  CK(cudaMemcpy(ring.data(), p->traj, sizeof(double) * kTrajCap, cudaMemcpyDeviceToHost));
+  for (int64_t k = 0; k < n; ++k) g_out[k] = ring[(first_iter + k) % kTrajCap];
   return DLM_OK;
 }
 
@@ -1380,6 +1475,12 @@ dlm_status dlm_get_info(dlm_problem* p, int64_t* num_users, int64_t* num_items, 
 }
 
 void dlm_destroy(dlm_problem* p) { free_problem(p); }
+
+dlm_status dlm_release_cached_memory(void) {
+  const cudaError_t e = release_cached_memory();
+  if (e != cudaSuccess) return fail(DLM_ERR_CUDA, std::string("memory pool trim: ") + cudaGetErrorString(e));
+  return DLM_OK;
+}
 
 dlm_status dlm_ws_features(dlm_problem* p, const float* lam_prev, double gamma, float* X) {
   if (!p || !lam_prev || !X) return fail(DLM_ERR_INVALID_ARG, "null argument");

@@ -16,7 +16,8 @@ namespace dlm {
 constexpr int kWarp = 32;
 constexpr int kSweepThreads = 1024;  // 32 warps per sweep CTA, one CTA per SM
 constexpr int kUpdThreads = 1024;    // one CTA per instance for the O(J) kernels
-constexpr int kMaxStages = 64;       // continuation stages tabulated (gamma is flat after)
+constexpr int64_t kMaxStageTable = int64_t(1) << 20;  // continuation stages a schedule may take to reach gamma_end
+constexpr int kTrajCap = 4096;       // dual objective values kept per handle (ring, one per iteration)
 constexpr int kMaxSegTasks = 16;     // tasks of one instance in one CTA
 constexpr int kMaxFamilies = 4;      // capacity families per instance (Def. 1)
 
@@ -32,18 +33,25 @@ struct DevState {
   int32_t status; // error bits
 };
 
-// Per-instance constants of the update step (device memory).
+// Per-instance constants of the update step (device memory).  The iterate
+// (lam, y) is kept in FP64; the sweeps read FP32 copies of it.
 struct UpdInst {
   DevState* state;
-  const double* gamma_tab;  // [kMaxStages]
+  const double* gamma_tab;  // [nstages]: gamma of stage s (the last entry is gamma_end)
+  int64_t nstages;
   const double* b;          // [J]
-  const double* inv_n2;     // [J] 1 / sum_i a_ij^2 (0 for empty items)
-  float* lam;               // [J]
-  float* y;                 // [J]
+  const double* curv;       // [D] per-coordinate curvature bound h (0 for an empty item); step = gamma / h
+  double* lam64;            // [D] the iterate
+  double* y64;              // [D] the momentum point
+  float* lam;               // [D] FP32 copies read by the sweeps
+  float* y;                 // [D]
   unsigned long long* acc;  // [J] fixed-point A x at y
+  unsigned long long* objq; // fixed-point sum of (c x + gamma/2 x^2) at y (reset here)
+  double* traj;             // [kTrajCap] g(y_t) at slot t mod kTrajCap
   int64_t iters_per_stage;
-  double inv_nmax;          // 1 / max_j sum_i a_ij^2
+  double curv_max;          // the largest curvature bound (plain step gamma / curv_max)
   double inv_scaleG;        // 2^-sG
+  double inv_scaleO;        // 2^-sO
   int32_t J;
   int32_t precondition;
   int32_t adaptive_restart;
@@ -53,7 +61,6 @@ struct UpdInst {
   unsigned long long* cnt_rw;     // the same, reset here
   double inv_scaleN;
   double count_M;
-  double inv_h_count;             // 1 / curvature bound of the count row (row normalization)
   int32_t ncap;                   // capacity coordinates m J (the count dual is coordinate ncap)
 };
 
@@ -64,7 +71,6 @@ struct UpdInst {
 struct InstDesc {
   const int64_t* slice_off; // [nslices + 1]
   const int32_t* slice_w;   // [nslices] edges per lane (the slice's largest degree)
-  const int32_t* col;       // [padded nnz] int32 item index (freed after set-up: nullptr)
   const uint16_t* col16;    // [padded nnz] item index as uint16 (every handle: J < 65,536)
   const void* ca;           // [padded nnz] interleaved (c, a): float2, or bf16 pair in a uint32
   const int64_t* orig_off;  // [users with edges] caller row start of each sorted user
@@ -79,7 +85,8 @@ struct InstDesc {
   double* seg_obj;          // [tasks] FP64 objective partial per (CTA, instance) segment (stats)
   float* xout;              // caller-order x or nullptr (stats)
   unsigned long long* cnt;  // fixed-point sum of all x (global count constraint) or nullptr
-  float scaleG, scaleC, scaleQ, scaleN;
+  unsigned long long* objq; // iteration sweeps: fixed-point sum of (c x + gamma/2 x^2) over all users
+  float scaleG, scaleC, scaleQ, scaleN, scaleO;
   float z;
   int32_t J;
   int32_t kind;
@@ -143,6 +150,12 @@ struct StatsInst {
 // Sets the thread-local message returned by dlm_last_error (api.cu).
 void set_last_error(const std::string& m);
 
+// layout.cu: stream-ordered device memory from one pool per device that keeps
+// freed memory for later handles (trimmed by release_cached_memory).
+cudaError_t dev_alloc(void** p, size_t bytes, cudaStream_t s);
+void dev_free(void* p, cudaStream_t s);
+cudaError_t release_cached_memory();
+
 // ---- launchers (defined in the .cu files) ----
 size_t sweep_smem_bytes(int smemJ, bool stats);
 // Certificate sweep with item sums for a window of win items (0: none).
@@ -168,8 +181,7 @@ cudaError_t launch_item_features(const uint16_t* col, const void* ca, bool bf, i
 struct LayoutOut {
   int64_t* slice_off = nullptr;  // [nslices + 1]
   int32_t* slice_w = nullptr;    // [nslices]
-  int32_t* col = nullptr;        // [padded_nnz + 32] (freed once col16 exists)
-  uint16_t* col16 = nullptr;     // [padded_nnz + 64] the same as uint16 when J <= 65,536, else nullptr
+  uint16_t* col16 = nullptr;     // [padded_nnz + 64] item index (uint16: J <= 65,536)
   void* ca = nullptr;            // [padded_nnz + 32]
   int64_t* orig_off = nullptr;   // [num_active_users + 32]
   int32_t* udeg = nullptr;       // [num_active_users + 32]

@@ -17,11 +17,17 @@
 // slice_off + 128 (w / 4) + 32 (k - 4 (w / 4)) + t.  Edges past a user's
 // degree are padding with c = +inf, a = 0 (they give u = -inf and are never
 // active).  Users with no edges are dropped from the slices.  The item index
-// stream is laid out as int32 and then narrowed to uint16 (every handle has
-// fewer than 65,536 items), so four indices are one 64-bit load.
+// stream is written as uint16 (every handle has fewer than 65,536 items), so
+// four indices are one 64-bit load.
+//
+// Device memory comes from a stream-ordered pool per device that keeps what
+// handles free (dev_alloc / dev_free): a daily re-creation of an instance of
+// the same size then maps no new memory.
 #include <cub/cub.cuh>
 
 #include <cmath>
+#include <cstdint>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -32,7 +38,9 @@ namespace {
 
 constexpr int kT = 256;
 
-enum : int { kBadRowPtr = 1, kBadItem = 2, kBadValue = 4, kBadB = 8, kNegA = 16 };
+enum : int { kBadRowPtr = 1, kBadItem = 2, kBadValue = 4, kBadB = 8, kNegA = 16, kDupItem = 32 };
+constexpr unsigned kFullMask = 0xffffffffu;
+constexpr int kDupThreads = 256;
 
 __device__ __forceinline__ float load_val(const void* p, int64_t e, bool bf16) {
   if (bf16) {
@@ -104,6 +112,62 @@ __global__ void k_edges(const int32_t* col, const void* c, const void* a, bool b
       if (scnt[j]) atomicAdd(&item_deg[j], static_cast<unsigned long long>(scnt[j]));
 }
 
+// Items distinct within each row (the eligible set of Sec. 3.3 is a set of
+// (user, item) pairs).  A warp takes 32 consecutive rows, whose edges are
+// contiguous: it touches them once (prefetch to L1), then checks one row at a
+// time -- a row of at most 32 edges by __match_any_sync over the lanes'
+// items, a longer one by marking its items in a per-warp bitmap of J bits in
+// shared memory, cleared again after the row.  Runs after the row pointers
+// are checked; items outside [0, J) are skipped here (k_edges flags them).
+__global__ void k_dups(const int64_t* rp, const int32_t* col, int64_t I, int64_t J, int* bad) {
+  extern __shared__ unsigned bm[];
+  const int lane = threadIdx.x & 31;
+  const int words = static_cast<int>((J + 31) >> 5);
+  unsigned* my = bm + static_cast<size_t>(threadIdx.x >> 5) * words;
+  for (int k = lane; k < words; k += 32) my[k] = 0u;
+  __syncwarp();
+  const int64_t gw = (blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x) >> 5;
+  const int64_t nw = (static_cast<int64_t>(gridDim.x) * blockDim.x) >> 5;
+  int flag = 0;
+  for (int64_t i0 = 32 * gw; i0 < I; i0 += 32 * nw) {
+    const int nrow = static_cast<int>(I - i0 < 32 ? I - i0 : 32);
+    const int64_t rk = lane < nrow ? rp[i0 + lane] : 0;
+    const int64_t rend = rp[i0 + nrow];
+    const int64_t e0 = __shfl_sync(kFullMask, rk, 0);
+    for (int64_t e = e0 + 32 * static_cast<int64_t>(lane); e < rend; e += 32 * 32)
+      asm volatile("prefetch.global.L1 [%0];" ::"l"(col + e));
+    for (int r = 0; r < nrow; ++r) {
+      const int64_t s = __shfl_sync(kFullMask, rk, r);
+      const int64_t t = __shfl_sync(kFullMask, rk, r + 1 < nrow ? r + 1 : 0);
+      const int64_t e = r + 1 < nrow ? t : rend;
+      const int64_t d = e - s;
+      if (d <= 1) continue;  // warp-uniform
+      if (d > J) {           // more edges than items: some item repeats
+        flag = 1;
+        continue;
+      }
+      if (d <= 32) {
+        const int j = lane < d ? col[s + lane] : -1 - lane;  // idle lanes: distinct negative keys
+        if (__popc(__match_any_sync(kFullMask, j)) > 1) flag = 1;
+      } else {
+        for (int64_t q = s + lane; q < e; q += 32) {
+          const int j = col[q];
+          if (static_cast<unsigned>(j) >= static_cast<unsigned>(J)) continue;
+          const unsigned bit = 1u << (j & 31);
+          if (atomicOr(&my[j >> 5], bit) & bit) flag = 1;
+        }
+        __syncwarp();
+        for (int64_t q = s + lane; q < e; q += 32) {
+          const int j = col[q];
+          if (static_cast<unsigned>(j) < static_cast<unsigned>(J)) my[j >> 5] = 0u;
+        }
+        __syncwarp();
+      }
+    }
+  }
+  if (__any_sync(kFullMask, flag) && lane == 0) atomicOr(bad, kDupItem);
+}
+
 __global__ void k_b(const double* b, int64_t J, int* bad) {
   int flag = 0;
   for (int64_t j = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; j < J;
@@ -155,7 +219,7 @@ __device__ __forceinline__ uint32_t pad_ca<uint32_t>() {
 template <typename CA>
 __global__ void k_gather(const int64_t* rp, const int32_t* col, const void* c, const void* a, const int32_t* perm,
                          const int32_t* sdeg, int64_t In, int64_t nslices, const int64_t* slice_off,
-                         const int32_t* width, int32_t* col_o, CA* ca_o, int64_t* orig_off, int32_t* udeg) {
+                         const int32_t* width, uint16_t* col_o, CA* ca_o, int64_t* orig_off, int32_t* udeg) {
   const int lane = threadIdx.x & 31;
   const int64_t w0 = (blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x) >> 5;
   const int64_t nwarps = (static_cast<int64_t>(gridDim.x) * blockDim.x) >> 5;
@@ -177,18 +241,12 @@ __global__ void k_gather(const int64_t* rp, const int32_t* col, const void* c, c
       const bool v = k < d;
       const int64_t e = k < 4 * w4 ? base + 4 * (32 * static_cast<int64_t>(k >> 2) + lane) + (k & 3)
                                    : base + 128 * static_cast<int64_t>(w4) + 32 * static_cast<int64_t>(k - 4 * w4) + lane;
-      col_o[e] = v ? col[r + k] : 0;
+      col_o[e] = v ? static_cast<uint16_t>(col[r + k]) : uint16_t(0);
       ca_o[e] = v ? pack_ca<CA>(c, a, r + k) : pad_ca<CA>();
     }
   }
 }
 
-// The item index stream as uint16 (instances with at most 65,536 items).
-__global__ void k_narrow(const int32_t* col, int64_t n, uint16_t* out) {
-  for (int64_t e = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; e < n;
-       e += static_cast<int64_t>(gridDim.x) * blockDim.x)
-    out[e] = static_cast<uint16_t>(col[e]);
-}
 
 // sum_i a_ij^2 (or sum_i a_ij) per item in 64-bit fixed point (exact, order
 // independent).
@@ -233,7 +291,54 @@ int grid_for(int64_t n) {
   return static_cast<int>(g);
 }
 
+std::mutex g_pool_mu;
+cudaMemPool_t g_pool[64] = {};
+
 }  // namespace
+
+cudaError_t dev_alloc(void** p, size_t bytes, cudaStream_t s) {
+  *p = nullptr;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+  cudaMemPool_t pool;
+  {
+    std::lock_guard<std::mutex> lk(g_pool_mu);
+    if (!g_pool[dev]) {
+      cudaMemPoolProps props = {};
+      props.allocType = cudaMemAllocationTypePinned;
+      props.handleTypes = cudaMemHandleTypeNone;
+      props.location.type = cudaMemLocationTypeDevice;
+      props.location.id = dev;
+      e = cudaMemPoolCreate(&g_pool[dev], &props);
+      if (e != cudaSuccess) {
+        g_pool[dev] = nullptr;
+        return e;
+      }
+      uint64_t keep = UINT64_MAX;  // freed memory stays with the pool until dlm_release_cached_memory
+      e = cudaMemPoolSetAttribute(g_pool[dev], cudaMemPoolAttrReleaseThreshold, &keep);
+      if (e != cudaSuccess) return e;
+    }
+    pool = g_pool[dev];
+  }
+  return cudaMallocFromPoolAsync(p, bytes > 0 ? bytes : 16, pool, s);
+}
+
+void dev_free(void* p, cudaStream_t s) {
+  if (p) cudaFreeAsync(p, s);
+}
+
+cudaError_t release_cached_memory() {
+  std::lock_guard<std::mutex> lk(g_pool_mu);
+  cudaError_t first = cudaSuccess;
+  for (cudaMemPool_t& q : g_pool) {
+    if (!q) continue;
+    const cudaError_t e = cudaMemPoolTrimTo(q, 0);
+    if (e != cudaSuccess && first == cudaSuccess) first = e;
+  }
+  return first;
+}
 
 // Fixed-point exponent for sums bounded by `bound`: the largest s with
 // bound * 2^s <= 2^61 (two bits of headroom), clamped to [0, 100].
@@ -275,11 +380,11 @@ dlm_status build_layout(int64_t I, int64_t J, int64_t nnz, const int64_t* rp, co
   int ssq = 0;
   int64_t In = 0, ns = 0;
 
-  DLM_CK(cudaMalloc(&deg, sizeof(int32_t) * (I > 0 ? I : 1)));
-  DLM_CK(cudaMalloc(&zero_cnt, sizeof(unsigned long long)));
-  DLM_CK(cudaMalloc(&item_deg, sizeof(unsigned long long) * (J > 0 ? J : 1)));
-  DLM_CK(cudaMalloc(&mx, sizeof(unsigned) * 2));
-  DLM_CK(cudaMalloc(&bad, sizeof(int)));
+  DLM_CK(dev_alloc(reinterpret_cast<void**>(&deg), sizeof(int32_t) * (I > 0 ? I : 1), s));
+  DLM_CK(dev_alloc(reinterpret_cast<void**>(&zero_cnt), sizeof(unsigned long long), s));
+  DLM_CK(dev_alloc(reinterpret_cast<void**>(&item_deg), sizeof(unsigned long long) * (J > 0 ? J : 1), s));
+  DLM_CK(dev_alloc(reinterpret_cast<void**>(&mx), sizeof(unsigned) * 2, s));
+  DLM_CK(dev_alloc(reinterpret_cast<void**>(&bad), sizeof(int), s));
   DLM_CK(cudaMemsetAsync(zero_cnt, 0, sizeof(unsigned long long), s));
   DLM_CK(cudaMemsetAsync(item_deg, 0, sizeof(unsigned long long) * (J > 0 ? J : 1), s));
   DLM_CK(cudaMemsetAsync(mx, 0, sizeof(unsigned) * 2, s));
@@ -305,6 +410,16 @@ dlm_status build_layout(int64_t I, int64_t J, int64_t nnz, const int64_t* rp, co
     const int g = static_cast<int>(nnz / 8192 + 1 < 608 ? nnz / 8192 + 1 : 608);
     const size_t smem = J <= 16384 ? sizeof(unsigned) * J : 0;
     k_edges<<<g, 1024, smem, s>>>(col, c, a, bf16, nnz, J, item_deg, mx, mx + 1, bad);
+    DLM_CK(cudaGetLastError());
+    const size_t dsm = sizeof(unsigned) * static_cast<size_t>((J + 31) / 32) * (kDupThreads / 32);
+    if (dsm > 48 * 1024) DLM_CK(cudaFuncSetAttribute(k_dups, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                    static_cast<int>(dsm)));
+    int dev = 0, sms = 0;
+    DLM_CK(cudaGetDevice(&dev));
+    DLM_CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    const int64_t want = (I + kDupThreads - 1) / kDupThreads;
+    const int gd = static_cast<int>(want < 8LL * sms ? (want > 0 ? want : 1) : 8LL * sms);
+    k_dups<<<gd, kDupThreads, dsm, s>>>(rp, col, I, J, bad);
   }
   DLM_CK(cudaGetLastError());
   DLM_CK(cudaMemcpyAsync(&h_bad, bad, sizeof(int), cudaMemcpyDeviceToHost, s));
@@ -320,6 +435,11 @@ dlm_status build_layout(int64_t I, int64_t J, int64_t nnz, const int64_t* rp, co
   }
   if (h_bad & kBadValue) {
     *msg = "c and a must be finite";
+    st = DLM_ERR_INVALID_ARG;
+    goto done;
+  }
+  if (h_bad & kDupItem) {
+    *msg = "an item appears twice in one row (the eligible items of a user must be distinct)";
     st = DLM_ERR_INVALID_ARG;
     goto done;
   }
@@ -340,66 +460,66 @@ dlm_status build_layout(int64_t I, int64_t J, int64_t nnz, const int64_t* rp, co
   ns = (In + 31) / 32;
   out->num_active_users = In;
   out->nslices = ns;
-  DLM_CK(cudaMalloc(&sdeg, sizeof(int32_t) * (I + 32)));
+  DLM_CK(dev_alloc(reinterpret_cast<void**>(&sdeg), sizeof(int32_t) * (I + 32), s));
   DLM_CK(cudaMemsetAsync(sdeg, 0, sizeof(int32_t) * (I + 32), s));
-  DLM_CK(cudaMalloc(&idx, sizeof(int32_t) * (I > 0 ? I : 1)));
-  DLM_CK(cudaMalloc(&perm, sizeof(int32_t) * (I > 0 ? I : 1)));
+  DLM_CK(dev_alloc(reinterpret_cast<void**>(&idx), sizeof(int32_t) * (I > 0 ? I : 1), s));
+  DLM_CK(dev_alloc(reinterpret_cast<void**>(&perm), sizeof(int32_t) * (I > 0 ? I : 1), s));
   if (I > 0) {
     k_iota<<<grid_for(I), kT, 0, s>>>(idx, I);
     DLM_CK(cudaGetLastError());
     DLM_CK(cub::DeviceRadixSort::SortPairsDescending(nullptr, tmp_bytes, deg, sdeg, idx, perm, I, 0, 32, s));
-    DLM_CK(cudaMalloc(&tmp, tmp_bytes > 0 ? tmp_bytes : 16));
+    DLM_CK(dev_alloc(reinterpret_cast<void**>(&tmp), tmp_bytes > 0 ? tmp_bytes : 16, s));
     DLM_CK(cub::DeviceRadixSort::SortPairsDescending(tmp, tmp_bytes, deg, sdeg, idx, perm, I, 0, 32, s));
-    DLM_CK(cudaFree(tmp));
+    dev_free(tmp, s);
     tmp = nullptr;
   }
 
   // ---- slices ----
-  DLM_CK(cudaMalloc(&out->slice_w, sizeof(int32_t) * (ns + 1)));
-  DLM_CK(cudaMalloc(&out->slice_off, sizeof(int64_t) * (ns + 1)));
-  DLM_CK(cudaMalloc(&ssize, sizeof(int64_t) * (ns + 1)));
+  DLM_CK(dev_alloc(reinterpret_cast<void**>(&out->slice_w), sizeof(int32_t) * (ns + 1), s));
+  DLM_CK(dev_alloc(reinterpret_cast<void**>(&out->slice_off), sizeof(int64_t) * (ns + 1), s));
+  DLM_CK(dev_alloc(reinterpret_cast<void**>(&ssize), sizeof(int64_t) * (ns + 1), s));
   DLM_CK(cudaMemsetAsync(out->slice_off, 0, sizeof(int64_t), s));
   if (ns > 0) {
     k_slices<<<grid_for(ns), kT, 0, s>>>(sdeg, ns, out->slice_w, ssize);
     DLM_CK(cudaGetLastError());
     tmp_bytes = 0;
     DLM_CK(cub::DeviceScan::InclusiveSum(nullptr, tmp_bytes, ssize, out->slice_off + 1, ns, s));
-    DLM_CK(cudaMalloc(&tmp, tmp_bytes > 0 ? tmp_bytes : 16));
+    DLM_CK(dev_alloc(reinterpret_cast<void**>(&tmp), tmp_bytes > 0 ? tmp_bytes : 16, s));
     DLM_CK(cub::DeviceScan::InclusiveSum(tmp, tmp_bytes, ssize, out->slice_off + 1, ns, s));
-    DLM_CK(cudaFree(tmp));
+    dev_free(tmp, s);
     tmp = nullptr;
   }
   DLM_CK(cudaMemcpyAsync(&out->padded_nnz, out->slice_off + ns, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
   DLM_CK(cudaStreamSynchronize(s));
 
-  // ---- edge streams in slice order ----
-  DLM_CK(cudaMalloc(&out->col, sizeof(int32_t) * (out->padded_nnz + 32)));
-  DLM_CK(cudaMalloc(&out->ca, 2 * vs * (out->padded_nnz + 32)));
-  DLM_CK(cudaMalloc(&out->orig_off, sizeof(int64_t) * (In + 32)));
-  DLM_CK(cudaMalloc(&out->udeg, sizeof(int32_t) * (In + 32)));
+  // ---- edge streams in slice order (16-bit item indices: every handle has
+  // fewer than 65,536 items) ----
+  if (J > 65536) {
+    *msg = "num_items above 65,536";
+    st = DLM_ERR_UNSUPPORTED;
+    goto done;
+  }
+  DLM_CK(dev_alloc(reinterpret_cast<void**>(&out->col16), sizeof(uint16_t) * (out->padded_nnz + 64), s));
+  DLM_CK(dev_alloc(reinterpret_cast<void**>(&out->ca), 2 * vs * (out->padded_nnz + 32), s));
+  DLM_CK(dev_alloc(reinterpret_cast<void**>(&out->orig_off), sizeof(int64_t) * (In + 32), s));
+  DLM_CK(dev_alloc(reinterpret_cast<void**>(&out->udeg), sizeof(int32_t) * (In + 32), s));
+  DLM_CK(cudaMemsetAsync(out->col16 + out->padded_nnz, 0, sizeof(uint16_t) * 64, s));
   if (ns > 0) {
     const int g = grid_for(ns * 32);
     if (bf16)
-      k_gather<uint32_t><<<g, kT, 0, s>>>(rp, col, c, a, perm, sdeg, In, ns, out->slice_off, out->slice_w, out->col,
+      k_gather<uint32_t><<<g, kT, 0, s>>>(rp, col, c, a, perm, sdeg, In, ns, out->slice_off, out->slice_w, out->col16,
                                           static_cast<uint32_t*>(out->ca), out->orig_off, out->udeg);
     else
-      k_gather<float2><<<g, kT, 0, s>>>(rp, col, c, a, perm, sdeg, In, ns, out->slice_off, out->slice_w, out->col,
+      k_gather<float2><<<g, kT, 0, s>>>(rp, col, c, a, perm, sdeg, In, ns, out->slice_off, out->slice_w, out->col16,
                                         static_cast<float2*>(out->ca), out->orig_off, out->udeg);
-    DLM_CK(cudaGetLastError());
-  }
-  // ---- 16-bit copy of the item indices: 2 bytes per edge less to stream ----
-  if (J <= 65536) {
-    DLM_CK(cudaMalloc(&out->col16, sizeof(uint16_t) * (out->padded_nnz + 64)));
-    DLM_CK(cudaMemsetAsync(out->col16, 0, sizeof(uint16_t) * (out->padded_nnz + 64), s));
-    if (out->padded_nnz > 0) k_narrow<<<grid_for(out->padded_nnz), kT, 0, s>>>(out->col, out->padded_nnz, out->col16);
     DLM_CK(cudaGetLastError());
   }
 
   // ---- n_j = sum_i a_ij^2 (exact fixed point) ----
   bound_sq = static_cast<double>(out->max_item_deg) * out->max_abs_a * out->max_abs_a;
   ssq = fixed_point_shift(bound_sq);
-  DLM_CK(cudaMalloc(&sq, sizeof(unsigned long long) * (J > 0 ? J : 1)));
-  DLM_CK(cudaMalloc(&out->n2, sizeof(double) * (J > 0 ? J : 1)));
+  DLM_CK(dev_alloc(reinterpret_cast<void**>(&sq), sizeof(unsigned long long) * (J > 0 ? J : 1), s));
+  DLM_CK(dev_alloc(reinterpret_cast<void**>(&out->n2), sizeof(double) * (J > 0 ? J : 1), s));
   DLM_CK(cudaMemsetAsync(sq, 0, sizeof(unsigned long long) * (J > 0 ? J : 1), s));
   if (nnz > 0) {
     const int g = static_cast<int>(nnz / 8192 + 1 < 608 ? nnz / 8192 + 1 : 608);
@@ -435,30 +555,27 @@ dlm_status build_layout(int64_t I, int64_t J, int64_t nnz, const int64_t* rp, co
 fail:
   st = DLM_ERR_CUDA;
 done:
-  cudaStreamSynchronize(s);
-  cudaFree(deg);
-  cudaFree(sdeg);
-  cudaFree(idx);
-  cudaFree(perm);
-  cudaFree(ssize);
-  cudaFree(zero_cnt);
-  cudaFree(item_deg);
-  cudaFree(sq);
-  cudaFree(mx);
-  cudaFree(bad);
-  if (tmp) cudaFree(tmp);
+  dev_free(deg, s);
+  dev_free(sdeg, s);
+  dev_free(idx, s);
+  dev_free(perm, s);
+  dev_free(ssize, s);
+  dev_free(zero_cnt, s);
+  dev_free(item_deg, s);
+  dev_free(sq, s);
+  dev_free(mx, s);
+  dev_free(bad, s);
+  dev_free(tmp, s);
   if (st != DLM_OK) {
-    cudaFree(out->slice_w);
-    cudaFree(out->slice_off);
-    cudaFree(out->col);
-    cudaFree(out->col16);
-    cudaFree(out->ca);
-    cudaFree(out->orig_off);
-    cudaFree(out->udeg);
-    cudaFree(out->n2);
+    dev_free(out->slice_w, s);
+    dev_free(out->slice_off, s);
+    dev_free(out->col16, s);
+    dev_free(out->ca, s);
+    dev_free(out->orig_off, s);
+    dev_free(out->udeg, s);
+    dev_free(out->n2, s);
     out->slice_w = nullptr;
     out->slice_off = nullptr;
-    out->col = nullptr;
     out->col16 = nullptr;
     out->ca = nullptr;
     out->orig_off = nullptr;

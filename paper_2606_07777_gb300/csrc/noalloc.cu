@@ -22,15 +22,16 @@ constexpr int kStaticThreads = 256;
 constexpr unsigned kFull = 0xffffffffu;
 
 struct StaticScratch {
-  unsigned long long acc[3 * kStaticMaxItems];  // fixed-point sum a x, c x, x^2 per item
-  double obj[kStaticBlocks];                    // objective partial per block
-  unsigned int bits[4];                         // max |a|, max |c| (float bits), error word, unused
+  unsigned long long acc[kStaticMaxItems];  // fixed-point sum a x per item
+  double obj[kStaticBlocks];                // objective partial per block
+  unsigned int bits[4];                     // max |a|, max |c| (float bits), error word, unused
 };
 
 static __device__ __align__(256) StaticScratch g_scratch;
 
 // Device address of g_scratch, looked up once per device (host code may not
-// use the symbol itself as a device address).
+// use the symbol itself as a device address).  The address belongs to the
+// device's primary context: it is not valid after cudaDeviceReset.
 std::mutex g_sym_mu;
 void* g_sym_addr[64] = {nullptr};
 
@@ -77,7 +78,7 @@ __device__ __forceinline__ int shift_for(double bound) {
 
 // Clears the scratch that must start at zero.
 __global__ void k_clear(StaticScratch* S, int64_t J) {
-  for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < 3 * J;
+  for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < J;
        i += static_cast<int64_t>(gridDim.x) * blockDim.x)
     S->acc[i] = 0ull;
   if (blockIdx.x == 0 && threadIdx.x < 4) S->bits[threadIdx.x] = 0u;
@@ -115,9 +116,8 @@ __global__ void __launch_bounds__(kStaticThreads) k_static_sweep(const int64_t* 
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const float amax = __uint_as_float(S->bits[0]), cmax = __uint_as_float(S->bits[1]);
   const double n = static_cast<double>(nnz > 0 ? nnz : 1);
+  (void)cmax;
   const float scG = ldexpf(1.f, shift_for(n * amax * z));
-  const float scC = ldexpf(1.f, shift_for(n * cmax * z));
-  const float scQ = ldexpf(1.f, shift_for(n * z * z));
   const float gf = static_cast<float>(gamma), invg = static_cast<float>(1.0 / gamma);
   const double gzd = gamma * z;
   const float gz = static_cast<float>(gzd), gzl = static_cast<float>(gzd - static_cast<double>(gz));
@@ -154,8 +154,10 @@ __global__ void __launch_bounds__(kStaticThreads) k_static_sweep(const int64_t* 
       m = warp_max(m);
       if (eq || m > 0.f) {
         tau = m - gz;
+        // every pass either stops or strictly shrinks the active set, so
+        // d + 1 passes always reach the fixed point
         int prevn = -1;
-        for (int it = 0; it < 256; ++it) {
+        for (int64_t it = 0; it <= d; ++it) {
           float sm = 0.f;
           int cnt = 0;
           for (int64_t i = lane; i < d; i += 32) {
@@ -223,8 +225,6 @@ __global__ void __launch_bounds__(kStaticThreads) k_static_sweep(const int64_t* 
                 : (zero ? fmaxf(up.h + up.l, 0.f) * invg : fmaxf((up.h - tau) + (up.l - taul), 0.f) * invg);
         if (x > 0.f) {
           atomicAdd(&S->acc[j], static_cast<unsigned long long>(__float2ll_rn(av * x * scG)));
-          atomicAdd(&S->acc[J + j], static_cast<unsigned long long>(__float2ll_rn(cv * x * scC)));
-          atomicAdd(&S->acc[2 * J + j], static_cast<unsigned long long>(__float2ll_rn(x * x * scQ)));
           ob += fmaf(0.5f * gf * x, x, cv * x);
         }
       }
@@ -258,7 +258,7 @@ __global__ void k_static_finish(const double* b, int64_t J, int64_t nnz, double 
     if (grad_out) grad_out[j] = bad ? NAN : static_cast<float>(G);
   }
   __syncthreads();
-  for (int64_t i = threadIdx.x; i < 3 * J; i += blockDim.x) S->acc[i] = 0ull;
+  for (int64_t i = threadIdx.x; i < J; i += blockDim.x) S->acc[i] = 0ull;
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   double v[2] = {lg, obj};
   for (int q = 0; q < 2; ++q) {

@@ -70,9 +70,20 @@ struct Narrow : V {
   }
 };
 
+// Loads from the slice's element streams: __ldg for global memory (the
+// layout), plain loads for a staged copy in shared memory.
+template <bool SM, class X>
+__device__ __forceinline__ X ldx(const X* p) {
+  if constexpr (SM) {
+    return *p;
+  } else {
+    return __ldg(p);
+  }
+}
+
 struct Seg {
   float gamma, invg, gz, gzl, z;
-  float scaleG, scaleC, scaleQ, scaleN;
+  float scaleG, scaleC, scaleQ, scaleN, scaleO;
   float mu;  // count dual (0 without a count constraint): the floor of the threshold
   int kind;
   int count;
@@ -92,10 +103,10 @@ __device__ __forceinline__ void deposit(const Seg& S, int j, float c, float a, f
       atomicAdd(&accC[jj], fixp(c * x, S.scaleC));
       atomicAdd(&accQ[jj], fixp(x * x, S.scaleQ));
     }
-    ob += fmaf(0.5f * S.gamma * x, x, c * x);
   } else {
     atomicAdd(&accG[j], fixp(a * x, S.scaleG));
   }
+  ob += fmaf(0.5f * S.gamma * x, x, c * x);
 }
 
 // x of one edge given the user's threshold (tau, taul): (u - tau) / gamma
@@ -209,7 +220,7 @@ __device__ __forceinline__ void coop_user(const Seg& S, const float* __restrict_
 // sweeps take): it saves a re-read (4 % on the 64-instance batch, 6 % on the
 // appendix instance once its rows have several active edges; no change on
 // the precision sweep).
-template <class P, bool STATS>
+template <class P, bool STATS, bool SM = false>
 __device__ __forceinline__ float4 rows_upto3(const Seg S, const float* __restrict__ ys, unsigned long long* accG,
                                           unsigned long long* accC, unsigned long long* accQ,
                                           const typename P::IX* __restrict__ col0, const typename P::T* __restrict__ ca0,
@@ -224,8 +235,8 @@ __device__ __forceinline__ float4 rows_upto3(const Seg S, const float* __restric
     cr[i] = ar[i] = 0.f;
     if (i < r) {
       const int el = sell_el(i == 0 ? i0 : (i == 1 ? i1 : i2), lane, w4);
-      jr[i] = static_cast<int>(__ldg(col0 + el));
-      P::get(__ldg(ca0 + el), cr[i], ar[i]);
+      jr[i] = static_cast<int>(ldx<SM>(col0 + el));
+      P::get(ldx<SM>(ca0 + el), cr[i], ar[i]);
     }
   }
   bool zero = !eq && tau <= (P::kCount ? S.mu : 0.f);
@@ -264,47 +275,34 @@ __device__ __forceinline__ float4 rows_upto3(const Seg S, const float* __restric
 // keeps the lanes busy).  coop_max is a tuning parameter (0: always per lane,
 // 33: always cooperative).
 
-// One slice: lane t = user t; edge k of lane t is element sell_el(k, t, w/4)
-// of the slice.
-template <class P, bool STATS, bool REG3 = false>
-__device__ __forceinline__ void do_slice(const InstDesc& D, const Seg& S, const float* __restrict__ ys,
-                                         unsigned long long* accG, unsigned long long* accC,
-                                         unsigned long long* accQ, int64_t s, int coop_max, double& wobj,
-                                         unsigned long long& cn) {
+// The four largest u of a row (v0 >= v1 >= v2 >= v3) and the edge
+// positions i0, i1, i2 of the first three.
+struct Top4 {
+  float v0, v1, v2, v3;
+  int i0, i1, i2;
+};
+__device__ __forceinline__ Top4 top4_empty() { return Top4{-INFINITY, -INFINITY, -INFINITY, -INFINITY, 0, 0, 0}; }
+
+// After pass A over a row: the threshold, x and the deposits (modes below).
+// col0/ca0 are the slice's streams in global memory (the Michelot passes and
+// the x output read them); colr/car are where the recorded edges of modes 1
+// and 2 are re-read from -- a staged copy of the slice in shared memory (SM)
+// or the same global streams.
+template <class P, bool STATS, bool REG3, bool SM>
+__device__ __forceinline__ void finish_slice(const InstDesc& D, const Seg& S, const float* __restrict__ ys,
+                                             unsigned long long* accG, unsigned long long* accC,
+                                             unsigned long long* accQ, int64_t s, int w,
+                                             const typename P::IX* __restrict__ col0,
+                                             const typename P::T* __restrict__ ca0,
+                                             const typename P::IX* __restrict__ colr,
+                                             const typename P::T* __restrict__ car, const Top4 tk, int coop_max,
+                                             double& wobj, unsigned long long& cn, unsigned long long& oq) {
   const int lane = threadIdx.x & 31;
-  const int64_t off = __ldg(D.slice_off + s);
-  const int w = __ldg(D.slice_w + s);
   const int w4 = w >> 2;
-  const typename P::IX* __restrict__ col0 = P::idx(D) + off;
-  const typename P::T* __restrict__ ca0 = static_cast<const typename P::T*>(D.ca) + off;
   const bool box = S.kind == DLM_BOX;
   const bool eq = S.kind == DLM_SIMPLEX_EQ;
-
-  // Pass A: the row's four largest u (v0 >= v1 >= v2 >= v3) and the
-  // positions i0, i1, i2 of the first three.
-  float v0 = -INFINITY, v1 = -INFINITY, v2 = -INFINITY, v3 = -INFINITY;
-  int i0 = 0, i1 = 0, i2 = 0;
-#pragma unroll 4
-  for (int g = 0; g < w4; ++g) {
-    const int q = 32 * g + lane;
-    int jj[4];
-    P::idx4(col0, q, jj);
-    float c[4], a[4];
-    P::get4(ca0, q, c, a);
-#pragma unroll
-    for (int e = 0; e < 4; ++e) {
-      const float u = -fmaf(a[e], ys[jj[e]], c[e]);
-      top4_insert(u, 4 * g + e, v0, v1, v2, v3, i0, i1, i2);
-    }
-  }
-  for (int k = 4 * w4; k < w; ++k) {
-    const int el = 128 * w4 + 32 * (k - 4 * w4) + lane;
-    const int j = static_cast<int>(__ldg(col0 + el));
-    float c, a;
-    P::get(__ldg(ca0 + el), c, a);
-    const float u = -fmaf(a, ys[j], c);
-    top4_insert(u, k, v0, v1, v2, v3, i0, i1, i2);
-  }
+  const float v0 = tk.v0, v1 = tk.v1, v2 = tk.v2, v3 = tk.v3;
+  const int i0 = tk.i0, i1 = tk.i1, i2 = tk.i2;
 
   // The equality threshold solves sum_k max(u_k - tau, 0) = gamma z.  With
   // the values sorted, tau_r = (v_0 + ... + v_{r-1} - gamma z) / r and the
@@ -345,7 +343,7 @@ __device__ __forceinline__ void do_slice(const InstDesc& D, const Seg& S, const 
 
   float ob = 0.f;
   if (mode == 2 && REG3) {
-    const float4 res = rows_upto3<P, STATS>(S, ys, accG, accC, accQ, col0, ca0, w4, r, i0, i1, i2, tau, eq, cn);
+    const float4 res = rows_upto3<P, STATS, SM>(S, ys, accG, accC, accQ, colr, car, w4, r, i0, i1, i2, tau, eq, cn);
     tau = res.x;
     taul = res.y;
     zero = res.z != 0.f;
@@ -386,9 +384,9 @@ __device__ __forceinline__ void do_slice(const InstDesc& D, const Seg& S, const 
     }
   } else if (mode == 1) {
     const int el = sell_el(i0, lane, w4);
-    const int j = static_cast<int>(__ldg(col0 + el));
+    const int j = static_cast<int>(ldx<SM>(colr + el));
     float c, a;
-    P::get(__ldg(ca0 + el), c, a);
+    P::get(ldx<SM>(car + el), c, a);
     deposit<P, STATS>(S, j, c, a, S.z, accG, accC, accQ, ob, cn);
   }
 
@@ -526,7 +524,50 @@ __device__ __forceinline__ void do_slice(const InstDesc& D, const Seg& S, const 
       }
     }
     wobj += static_cast<double>(ob);
+  } else {
+    // the user's objective part, added exactly (64-bit fixed point)
+    oq += fixp(ob, S.scaleO);
   }
+}
+
+// One slice: lane t = user t; edge k of lane t is element sell_el(k, t, w/4)
+// of the slice.  Pass A streams the row in groups of four edges and keeps
+// its four largest u with the positions of the first three.
+template <class P, bool STATS, bool REG3 = false>
+__device__ __forceinline__ void do_slice(const InstDesc& D, const Seg& S, const float* __restrict__ ys,
+                                         unsigned long long* accG, unsigned long long* accC,
+                                         unsigned long long* accQ, int64_t s, int coop_max, double& wobj,
+                                         unsigned long long& cn, unsigned long long& oq) {
+  const int lane = threadIdx.x & 31;
+  const int64_t off = __ldg(D.slice_off + s);
+  const int w = __ldg(D.slice_w + s);
+  const int w4 = w >> 2;
+  const typename P::IX* __restrict__ col0 = P::idx(D) + off;
+  const typename P::T* __restrict__ ca0 = static_cast<const typename P::T*>(D.ca) + off;
+  Top4 tk = top4_empty();
+#pragma unroll 4
+  for (int g = 0; g < w4; ++g) {
+    const int q = 32 * g + lane;
+    int jj[4];
+    P::idx4(col0, q, jj);
+    float c[4], a[4];
+    P::get4(ca0, q, c, a);
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      const float u = -fmaf(a[e], ys[jj[e]], c[e]);
+      top4_insert(u, 4 * g + e, tk.v0, tk.v1, tk.v2, tk.v3, tk.i0, tk.i1, tk.i2);
+    }
+  }
+  for (int k = 4 * w4; k < w; ++k) {
+    const int el = 128 * w4 + 32 * (k - 4 * w4) + lane;
+    const int j = static_cast<int>(__ldg(col0 + el));
+    float c, a;
+    P::get(__ldg(ca0 + el), c, a);
+    const float u = -fmaf(a, ys[j], c);
+    top4_insert(u, k, tk.v0, tk.v1, tk.v2, tk.v3, tk.i0, tk.i1, tk.i2);
+  }
+  finish_slice<P, STATS, REG3, false>(D, S, ys, accG, accC, accQ, s, w, col0, ca0, col0, ca0, tk, coop_max, wobj, cn,
+                                      oq);
 }
 
 // Certificate sweeps (STATS) keep the item sums of the window of items
@@ -548,6 +589,7 @@ __global__ void __launch_bounds__(kSweepThreads, 1)
 
   __shared__ InstDesc sD;
   __shared__ unsigned long long s_next;
+  __shared__ unsigned long long s_red[32];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int nw = blockDim.x >> 5;
   const int t_last = cta_task[blockIdx.x + 1];
@@ -582,13 +624,14 @@ __global__ void __launch_bounds__(kSweepThreads, 1)
       S.scaleC = sD.scaleC;
       S.scaleQ = sD.scaleQ;
       S.scaleN = sD.scaleN;
+      S.scaleO = sD.scaleO;
       S.kind = sD.kind;
       S.count = sD.count_on;
       S.mu = sD.count_on ? sD.y[J] : 0.f;
       S.jlo = STATS ? jlo : 0;
       S.jw = nacc;
     }
-    unsigned long long cn = 0ull;
+    unsigned long long cn = 0ull, oq = 0ull;
     if (threadIdx.x == 0) s_next = 0;
     __syncthreads();
     double wobj = 0.0;
@@ -598,7 +641,7 @@ __global__ void __launch_bounds__(kSweepThreads, 1)
         // static order: the FP64 objective partials are summed in a fixed order
         const int64_t step = static_cast<int64_t>(T.stride) * nw;
         for (int64_t s = T.first + static_cast<int64_t>(T.stride) * warp; s < T.end; s += step)
-          do_slice<P, STATS>(sD, S, ys, accG, accC, accQ, s, coop_max, wobj, cn);
+          do_slice<P, STATS>(sD, S, ys, accG, accC, accQ, s, coop_max, wobj, cn, oq);
       } else {
         // dynamic order within the CTA (item sums are exact, so the order of
         // slices does not change any result)
@@ -608,7 +651,8 @@ __global__ void __launch_bounds__(kSweepThreads, 1)
           if (lane == 0) i = atomicAdd(&s_next, 1ull);
           i = __shfl_sync(kFull, i, 0);
           if (i >= nsl) break;
-          do_slice<P, STATS, !STATS>(sD, S, ys, accG, accC, accQ, T.first + i * T.stride, coop_max, wobj, cn);
+          do_slice<P, STATS, !STATS>(sD, S, ys, accG, accC, accQ, T.first + i * T.stride, coop_max, wobj, cn,
+                                     oq);
         }
         __syncthreads();
         if (threadIdx.x == 0) s_next = 0;
@@ -619,6 +663,8 @@ __global__ void __launch_bounds__(kSweepThreads, 1)
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) wobj += __shfl_xor_sync(kFull, wobj, o);
       if (lane == 0) wsum[warp] = wobj;
+    } else {
+      cta_add_u64(oq, s_red, sD.objq);
     }
     if (P::kCount && sD.count_on && (!STATS || jlo == 0)) {
 #pragma unroll
@@ -666,11 +712,12 @@ __global__ void __launch_bounds__(kSweepThreads, 1)
   __shared__ InstDesc sD;
   __shared__ unsigned s_unit;
   __shared__ unsigned long long s_next;
+  __shared__ unsigned long long s_red[32];
   const int lane = threadIdx.x & 31;
   int cur = -1;
   Seg S{};
   double wobj = 0.0;
-  unsigned long long cn = 0ull;
+  unsigned long long cn = 0ull, oq = 0ull;
   for (;;) {
     if (threadIdx.x == 0) {
       s_unit = atomicAdd(ctr, 1u);
@@ -692,6 +739,8 @@ __global__ void __launch_bounds__(kSweepThreads, 1)
           const unsigned long long v = accG[j];
           if (v) atomicAdd(sD.acc + j, v);
         }
+        cta_add_u64(oq, s_red, sD.objq);
+        oq = 0ull;
       }
       __syncthreads();
       if (out_of_work) break;
@@ -712,6 +761,7 @@ __global__ void __launch_bounds__(kSweepThreads, 1)
       S.scaleC = sD.scaleC;
       S.scaleQ = sD.scaleQ;
       S.scaleN = sD.scaleN;
+      S.scaleO = sD.scaleO;
       S.kind = sD.kind;
       S.count = sD.count_on;
       S.mu = sD.count_on ? sD.y[sD.J] : 0.f;
@@ -725,7 +775,7 @@ __global__ void __launch_bounds__(kSweepThreads, 1)
       if (lane == 0) i = static_cast<int64_t>(atomicAdd(&s_next, 1ull));
       i = __shfl_sync(kFull, i, 0);
       if (i >= nsl) break;
-      do_slice<P, false, true>(sD, S, ys, accG, nullptr, nullptr, T.first + i, coop_max, wobj, cn);
+      do_slice<P, false, true>(sD, S, ys, accG, nullptr, nullptr, T.first + i, coop_max, wobj, cn, oq);
     }
     __syncthreads();
   }

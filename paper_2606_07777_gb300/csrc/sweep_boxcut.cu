@@ -28,7 +28,7 @@ namespace {
 
 struct BSeg {
   float gamma, invg, z, gzh, gzl, gch, gcl, cut;
-  float scaleG, scaleC, scaleQ;
+  float scaleG, scaleC, scaleQ, scaleO;
   int jlo, jw;
 };
 
@@ -42,10 +42,10 @@ __device__ __forceinline__ void deposit_b(const BSeg& S, int j, float c, float a
       atomicAdd(&accC[jj], fixp(c * x, S.scaleC));
       atomicAdd(&accQ[jj], fixp(x * x, S.scaleQ));
     }
-    ob += fmaf(0.5f * S.gamma * x, x, c * x);
   } else {
     atomicAdd(&accG[j], fixp(a * x, S.scaleG));
   }
+  ob += fmaf(0.5f * S.gamma * x, x, c * x);
 }
 
 // gamma (cut - z n) as a float pair: gamma cut minus n times gamma z, with the
@@ -61,7 +61,8 @@ __device__ __forceinline__ F2 budget_pair(const BSeg& S, int n) {
 template <class V, bool STATS>
 __device__ __forceinline__ void boxcut_slice(const InstDesc& D, const BSeg& S, const float* __restrict__ ys,
                                              unsigned long long* accG, unsigned long long* accC,
-                                             unsigned long long* accQ, int64_t s, double& wobj) {
+                                             unsigned long long* accQ, int64_t s, double& wobj,
+                                             unsigned long long& oq) {
   const int lane = threadIdx.x & 31;
   const int64_t off = __ldg(D.slice_off + s);
   const int w = __ldg(D.slice_w + s);
@@ -289,6 +290,8 @@ __device__ __forceinline__ void boxcut_slice(const InstDesc& D, const BSeg& S, c
       }
     }
     wobj += static_cast<double>(ob);
+  } else {
+    oq += fixp(ob, S.scaleO);  // the user's objective part, added exactly
   }
 }
 
@@ -310,6 +313,7 @@ __global__ void __launch_bounds__(kSweepThreads, 1)
 
   __shared__ InstDesc sD;
   __shared__ unsigned long long s_next;
+  __shared__ unsigned long long s_red[32];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int nw = blockDim.x >> 5;
   const int t_last = cta_task[blockIdx.x + 1];
@@ -347,19 +351,21 @@ __global__ void __launch_bounds__(kSweepThreads, 1)
       S.scaleG = sD.scaleG;
       S.scaleC = sD.scaleC;
       S.scaleQ = sD.scaleQ;
+      S.scaleO = sD.scaleO;
       S.jlo = STATS ? jlo : 0;
       S.jw = nacc;
     }
     if (threadIdx.x == 0) s_next = 0;
     __syncthreads();
     double wobj = 0.0;
+    unsigned long long oq = 0ull;
     for (int k = t; k < te; ++k) {
       const Task T = tasks[k];
       if (STATS) {
         // static order: the FP64 objective partials are summed in a fixed order
         const int64_t step = static_cast<int64_t>(T.stride) * nw;
         for (int64_t s = T.first + static_cast<int64_t>(T.stride) * warp; s < T.end; s += step)
-          boxcut_slice<V, STATS>(sD, S, ys, accG, accC, accQ, s, wobj);
+          boxcut_slice<V, STATS>(sD, S, ys, accG, accC, accQ, s, wobj, oq);
       } else {
         // dynamic order within the CTA: rows whose threshold needs the
         // bracketed search take many passes, and the item sums are exact in
@@ -370,7 +376,7 @@ __global__ void __launch_bounds__(kSweepThreads, 1)
           if (lane == 0) i = static_cast<int64_t>(atomicAdd(&s_next, 1ull));
           i = __shfl_sync(kFull, i, 0);
           if (i >= nsl) break;
-          boxcut_slice<V, STATS>(sD, S, ys, accG, accC, accQ, T.first + i * T.stride, wobj);
+          boxcut_slice<V, STATS>(sD, S, ys, accG, accC, accQ, T.first + i * T.stride, wobj, oq);
         }
         __syncthreads();
         if (threadIdx.x == 0) s_next = 0;
@@ -381,6 +387,8 @@ __global__ void __launch_bounds__(kSweepThreads, 1)
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) wobj += __shfl_xor_sync(kFull, wobj, o);
       if (lane == 0) wsum[warp] = wobj;
+    } else {
+      cta_add_u64(oq, s_red, sD.objq);
     }
     __syncthreads();
     {

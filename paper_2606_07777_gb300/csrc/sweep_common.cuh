@@ -84,6 +84,22 @@ __device__ __forceinline__ F2 f2_threshold(F2 sum, float gzh, float gzl, int n) 
   return {th, __fdiv_rn(r + num.l, fn)};
 }
 
+// Adds one value per thread into *dst exactly: warp sums, then thread 0 adds
+// the warps' partials and makes one global atomic (64-bit fixed point: the
+// result does not depend on the order).  Every thread of the block calls it.
+__device__ __forceinline__ void cta_add_u64(unsigned long long v, unsigned long long* sh32, unsigned long long* dst) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+  if ((threadIdx.x & 31) == 0) sh32[threadIdx.x >> 5] = v;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned long long t = 0ull;
+    for (int w = 0; w < static_cast<int>(blockDim.x >> 5); ++w) t += sh32[w];
+    if (t && dst) atomicAdd(dst, t);
+  }
+  __syncthreads();
+}
+
 __device__ __forceinline__ float warp_sum(float v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);

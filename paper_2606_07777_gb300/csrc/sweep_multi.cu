@@ -35,7 +35,7 @@ __device__ __forceinline__ float ext_val(const void* base, int64_t el, bool bf16
 
 struct MSeg {
   float gamma, invg, gz, gzl, z;
-  float scaleG, scaleC, scaleQ;
+  float scaleG, scaleC, scaleQ, scaleO;
   int kind, m, J;
 };
 
@@ -110,8 +110,8 @@ __device__ __forceinline__ void deposit_m(const MSeg& S, int j, float c, const f
   if (STATS) {
     atomicAdd(&accC[j], fixp(c * x, S.scaleC));
     atomicAdd(&accQ[j], fixp(x * x, S.scaleQ));
-    ob += fmaf(0.5f * S.gamma * x, x, c * x);
   }
+  ob += fmaf(0.5f * S.gamma * x, x, c * x);
 }
 
 __device__ __forceinline__ float x_of(const MSeg& S, bool box, float tau, float taul, F2 up) {
@@ -127,7 +127,8 @@ __device__ __forceinline__ float x_of(const MSeg& S, bool box, float tau, float 
 template <class P, bool STATS, int M>
 __device__ __forceinline__ void multi_slice(const InstDesc& D, const MSeg& S, const float* __restrict__ ys,
                                             unsigned long long* accG, unsigned long long* accC,
-                                            unsigned long long* accQ, int64_t s, bool bf16, double& wobj) {
+                                            unsigned long long* accQ, int64_t s, bool bf16, double& wobj,
+                                            unsigned long long& oq) {
   const int lane = threadIdx.x & 31;
   const int64_t off = __ldg(D.slice_off + s);
   const int w = __ldg(D.slice_w + s);
@@ -294,6 +295,8 @@ __device__ __forceinline__ void multi_slice(const InstDesc& D, const MSeg& S, co
       }
     }
     wobj += static_cast<double>(ob);
+  } else {
+    oq += fixp(ob, S.scaleO);  // the users' objective parts, added exactly
   }
 }
 
@@ -312,6 +315,7 @@ __global__ void __launch_bounds__(kSweepThreads, 1)
 
   __shared__ InstDesc sD;
   __shared__ unsigned long long s_next;
+  __shared__ unsigned long long s_red[32];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int nw = blockDim.x >> 5;
   const int t_last = cta_task[blockIdx.x + 1];
@@ -342,19 +346,21 @@ __global__ void __launch_bounds__(kSweepThreads, 1)
       S.scaleG = sD.scaleG;
       S.scaleC = sD.scaleC;
       S.scaleQ = sD.scaleQ;
+      S.scaleO = sD.scaleO;
       S.kind = sD.kind;
       S.m = sD.m;
       S.J = J;
     }
     __syncthreads();
     double wobj = 0.0;
+    unsigned long long oq = 0ull;
     for (int k = t; k < te; ++k) {
       const Task T = tasks[k];
       if (STATS) {
         // static order: the FP64 objective partials are summed in a fixed order
         const int64_t step = static_cast<int64_t>(T.stride) * nw;
         for (int64_t s = T.first + static_cast<int64_t>(T.stride) * warp; s < T.end; s += step)
-          multi_slice<P, STATS, M>(sD, S, ys, accG, accC, accQ, s, bf16, wobj);
+          multi_slice<P, STATS, M>(sD, S, ys, accG, accC, accQ, s, bf16, wobj, oq);
       } else {
         // dynamic order within the CTA (the item sums are exact)
         if (threadIdx.x == 0) s_next = 0;
@@ -365,7 +371,7 @@ __global__ void __launch_bounds__(kSweepThreads, 1)
           if (lane == 0) i = static_cast<int64_t>(atomicAdd(&s_next, 1ull));
           i = __shfl_sync(kFull, i, 0);
           if (i >= nsl) break;
-          multi_slice<P, STATS, M>(sD, S, ys, accG, accC, accQ, T.first + i * T.stride, bf16, wobj);
+          multi_slice<P, STATS, M>(sD, S, ys, accG, accC, accQ, T.first + i * T.stride, bf16, wobj, oq);
         }
         __syncthreads();
       }
@@ -374,6 +380,8 @@ __global__ void __launch_bounds__(kSweepThreads, 1)
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) wobj += __shfl_xor_sync(kFull, wobj, o);
       if (lane == 0) wsum[warp] = wobj;
+    } else {
+      cta_add_u64(oq, s_red, sD.objq);
     }
     __syncthreads();
     for (int q = threadIdx.x; q < mJ; q += blockDim.x) {

@@ -85,4 +85,6 @@ def test_null_handle_calls_fail_cleanly(lib):
     assert lib.dlm_set_schedule(None, 0.1, 0.01, 0.5, 10) == dlm.DLM_ERR_INVALID_ARG
     s = dlm.Stats()
     assert lib.dlm_get_stats(None, ctypes.byref(s)) == dlm.DLM_ERR_INVALID_ARG
+    out = (ctypes.c_double * 4)()
+    assert lib.dlm_get_trajectory(None, 0, 4, out) == dlm.DLM_ERR_INVALID_ARG
     lib.dlm_destroy(None)  # no-op

@@ -79,9 +79,12 @@ def test_trajectory_matches_oracle(dlm_lib, precondition):
     T = 150
     s.step(T)
     lam = s.lam().cpu().numpy().astype(np.float64)
-    ref = oracle.fista(oproblem(inst, z, cut), T, 1e-2, precondition=precondition, trajectory=False)["lam"]
+    out = oracle.fista(oproblem(inst, z, cut), T, 1e-2, precondition=precondition)
+    ref = out["lam"]
     err = np.abs(lam - ref).max()
     assert err <= 1e-5 * max(np.abs(ref).max(), 1e-6), f"max err {err:.3e}"
+    g = s.trajectory(0, T)
+    assert np.abs(g - out["g_traj"]).max() <= 1e-5 * np.abs(out["g_traj"]).max()
     assert ref.max() > 1e-3
     s.close()
 

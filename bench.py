@@ -72,6 +72,23 @@ WORKLOADS = {
 }
 
 
+def config_for(args, world):
+    """The `config` object of the JSON line, from the arguments alone, so the
+    oracle arm prints the same one as the GPU arm."""
+    w = WORKLOADS[args.workload]
+    desc = w["desc"] if args.scale == 1.0 else w["desc"] + f" (users scaled x{args.scale})"
+    cfg = {"workload": desc, "iters_per_step": args.iters,
+           "parallelism": "replicas" if world > 1 else "single GPU"}
+    if args.workload == "batched":
+        cfg.update(instances=w["n"], storage="bf16")
+    else:
+        cfg.update(users=max(1000, int(round(w["users"] * args.scale))) if args.workload != "tiny" else w["users"],
+                   items=w["items"], storage="bf16" if w["bf16"] else "f32")
+    cfg["l2"] = ("inputs fit in L2 (tiny case)" if args.workload == "tiny" else
+                 "inputs of several GB per iteration >> 129 MB L2 (no flush)")
+    return cfg
+
+
 def recipe_for(name, scale):
     import synth
 
@@ -228,46 +245,178 @@ def add_second_family(inst, torch, threads):
     inst.c32 = inst.a32 = None
 
 
-def bf16_error_statement(dlm, torch, s_bf16, inst, recipe, gamma, frac, threads):
-    """Error of the BF16-storage form at its current lam: against the FP32 GPU
-    form of the same instance (full instance) and against the FP64 oracle on
-    the FP32 values (seeded user sample)."""
+def solve_from_zero(s, torch, target, max_iters, sched=(1e-1, 1e-3, 0.5, 50), gap_every=50, restart=True):
+    """Drives a handle from lam = 0 to a certified gap under a continuation
+    schedule with row normalization; returns (Stats, seconds)."""
+    s.set_schedule(*sched)
+    s.set_options(precondition=True, restart=restart, gap_every=gap_every)
+    s.set_lambda(torch.zeros(s.dual_dim, dtype=torch.float32, device=s.device))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    st = s.solve(target, max_iters)
+    torch.cuda.synchronize()
+    return st, time.perf_counter() - t0
+
+
+def bf16_error_statement(dlm, torch, inst, recipe, threads, gamma=1e-3, target=1e-5, max_iters=4000,
+                         sample_frac=5e-4):
+    """Error of the BF16-storage form, optimum to optimum.
+
+    Full instance: the BF16 form, the FP32 form and the FP32 form with only c
+    rounded to BF16 are each driven from lam = 0 to a certified gap (the
+    1e-1 -> gamma continuation, row normalization, adaptive restart).  Rounding
+    c alone moves the optimum by at most ||dc||_2 / gamma (the primal optimum
+    is the projection of -c / gamma onto a fixed convex set: nonexpansive);
+    each solve's own distance to its optimum is at most sqrt(2 gap |g| / gamma)
+    on the certified point.  Rounding a changes the feasible set, for which
+    only the measured difference is stated.
+    Sample: a seeded user sample of the same recipe (capacities from the
+    sample) solved by the BF16 form on the GPU and by the FP64 oracle on the
+    FP32 values (all host threads), both to the same gap."""
     import numpy as np
     import oracle
     import synth
 
-    dev = s_bf16.device
-    lam = s_bf16.lam()
-    g16, G16, x16 = s_bf16.calculate(lam, gamma)
-    arrs = [torch.from_numpy(v).to(dev) for v in (inst.row_ptr, inst.col, inst.c32, inst.a32, inst.b)]
-    s32 = dlm.Solver(*arrs, inst.J)
-    del arrs
-    g32, G32, x32 = s32.calculate(lam, gamma)
-    s32.close()
-    Gs = float(G32.abs().max().item()) or 1.0
-    full = {"rel_dual_obj": abs(g16 - g32) / abs(g32), "max_abs_grad": float((G16 - G32).abs().max().item()),
-            "max_abs_grad_rel": float((G16 - G32).abs().max().item()) / Gs,
-            "max_abs_x": float((x16 - x32).abs().max().item()),
-            "mean_abs_x": float((x16 - x32).abs().double().mean().item())}
-    del x32, G32
-    # seeded sample: oracle x on the FP32 values at the same lam, against the BF16 solver's x
-    ids = synth.sample_users(inst.I, frac, 4343)
-    rows = torch.from_numpy(ids).to(dev)
-    rp = torch.from_numpy(inst.row_ptr).to(dev)
-    starts, ends = rp[rows], rp[rows + 1]
-    lens = ends - starts
-    idx = torch.repeat_interleave(starts, lens) + (torch.arange(int(lens.sum().item()), device=dev) -
-                                                   torch.repeat_interleave(torch.cumsum(lens, 0) - lens, lens))
-    xs = x16[idx].cpu().numpy().astype(np.float64)
-    del x16
-    sub = synth.subset(synth.Instance(inst.row_ptr, inst.col, inst.c32, inst.a32, inst.b, inst.J), ids)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    sched = (1e-1, gamma, 0.5, 50)
+    c32 = torch.from_numpy(inst.c32).to(dev)
+    a32 = torch.from_numpy(inst.a32).to(dev)
+    c16 = torch.from_numpy(inst.c.view(np.int16)).to(dev).view(torch.bfloat16)
+    a16 = torch.from_numpy(inst.a.view(np.int16)).to(dev).view(torch.bfloat16)
+    rp, col, b = (torch.from_numpy(v).to(dev) for v in (inst.row_ptr, inst.col, inst.b))
+    forms = {"bf16": (c16, a16, True), "fp32": (c32, a32, False), "fp32_c_rounded": (c16.float(), a32, False)}
+    sol = {}
+    for name, (c, a, bf) in forms.items():
+        h = dlm.Solver(rp, col, c, a, b, inst.J, bf16=bf)
+        st, sec = solve_from_zero(h, torch, target, max_iters, sched)
+        sol[name] = dict(lam=h.lam().double(), x=h.x(), g=st.dual_obj, gap=st.rel_gap, iters=int(st.iter),
+                         seconds=sec, converged=bool(st.converged))
+        h.close()
+    dc = float(torch.linalg.vector_norm((c16.float() - c32).double()).item())
+    tol = {k: math.sqrt(2.0 * max(v["gap"], 0.0) * abs(v["g"]) / gamma) for k, v in sol.items()}
+
+    def diff(u, v):
+        dx = (sol[u]["x"] - sol[v]["x"]).double()
+        dl = (sol[u]["lam"] - sol[v]["lam"]).abs().max().item()
+        return {"x_l2": float(torch.linalg.vector_norm(dx).item()), "x_max_abs": float(dx.abs().max().item()),
+                "lam_max_abs_rel": dl / max(float(sol[v]["lam"].abs().max().item()), 1e-30),
+                "dual_obj_rel": abs(sol[u]["g"] - sol[v]["g"]) / abs(sol[v]["g"])}
+
+    full = {"gamma": gamma, "target_rel_gap": target,
+            "solves": {k: {q: v[q] for q in ("g", "gap", "iters", "seconds", "converged")} for k, v in sol.items()},
+            "c_rounding_only": dict(diff("fp32_c_rounded", "fp32"), bound_l2=dc / gamma,
+                                    solver_tolerance_l2=tol["fp32_c_rounded"] + tol["fp32"]),
+            "bf16_vs_fp32": diff("bf16", "fp32")}
+    c_only = full["c_rounding_only"]
+    c_only["within_bound"] = c_only["x_l2"] <= c_only["bound_l2"] + c_only["solver_tolerance_l2"]
+    del sol, c32, a32, c16, a16, rp, col, b
+    torch.cuda.empty_cache()
+    # sample: GPU BF16 form against the FP64 oracle on the FP32 values
+    ids = synth.sample_users(recipe.I, sample_frac, 4545)
+    sub = synth.generate(recipe, ids=ids, nthreads=threads)
+    cr, ar = synth.round_bf16(sub.c), synth.round_bf16(sub.a)
+    arrs = [torch.from_numpy(v).to(dev) for v in (sub.row_ptr, sub.col)]
+    h = dlm.Solver(arrs[0], arrs[1], torch.from_numpy(cr.view(np.int16)).to(dev).view(torch.bfloat16),
+                   torch.from_numpy(ar.view(np.int16)).to(dev).view(torch.bfloat16),
+                   torch.from_numpy(sub.b).to(dev), sub.J, bf16=True)
+    st, sec = solve_from_zero(h, torch, target, max_iters, sched)
+    lam_g = h.lam().cpu().numpy().astype(np.float64)
+    x_g = h.x().cpu().numpy().astype(np.float64)
+    h.close()
     p = oracle.Problem(sub.row_ptr, sub.col, sub.c.astype(np.float64), sub.a.astype(np.float64), sub.b, sub.J)
-    ref = oracle.sweep(p, lam.cpu().numpy().astype(np.float64), gamma)
-    dx = np.abs(xs - ref["x"])
-    return {"vs_fp32_gpu_full_instance": full,
-            "vs_fp64_oracle_sample": {"users": int(len(ids)), "nnz": int(p.nnz), "max_abs_x": float(dx.max()),
-                                      "mean_abs_x": float(dx.mean())},
-            "at": "lam after the timed steps; gamma %.3g" % gamma}
+    nc = host_cores()
+    t0 = time.perf_counter()
+    ref = oracle.solve_threads(p, *sched, precondition=True, restart=True, target=target, gap_every=50,
+                               max_iters=max_iters, nthreads=nc)
+    t_ref = time.perf_counter() - t0
+    x_r = oracle.sweep(p, ref["lam"], gamma)["x"]
+    sample = {"users": int(len(ids)), "nnz": int(p.nnz), "gpu_bf16": {"g": st.dual_obj, "gap": st.rel_gap,
+                                                                        "iters": int(st.iter)},
+              "oracle_fp64": {"g": ref["g"], "gap": ref["rel_gap"], "iters": ref["iters"], "seconds": t_ref,
+                              "cores": nc},
+              "x_l2": float(np.linalg.norm(x_g - x_r)), "x_max_abs": float(np.abs(x_g - x_r).max()),
+              "lam_max_abs_rel": float(np.abs(lam_g - ref["lam"]).max() / max(np.abs(ref["lam"]).max(), 1e-30)),
+              "dual_obj_rel": abs(st.dual_obj - ref["g"]) / abs(ref["g"]),
+              "bound_c_rounding_l2": float(np.linalg.norm(synth.bf16_to_f32(cr).astype(np.float64) -
+                                                          sub.c.astype(np.float64))) / gamma}
+    return {"full_instance": full, "vs_fp64_oracle_sample": sample,
+            "how": "optimum to optimum: every form solved from lam = 0 to the same certified gap"}
+
+
+def production_summary(args, dlm, torch, dev, threads):
+    """The production shape (20M users x 2,000 items, FP32 values, gamma
+    continuation 1e-1 -> 1e-3 halved every 100 iterations): sweep throughput
+    over the whole continuation (700 iterations, every sweep timed by CUDA
+    events) and the time to a 1e-4 certified gap from lam = 0 (row
+    normalization: the items' row norms are about 250x apart)."""
+    w = WORKLOADS["production"]
+    t0 = time.perf_counter()
+    inst = make_instance(recipe_for("production", args.scale), False, torch, False, threads)
+    t_gen = time.perf_counter() - t0
+    arrs = [torch.from_numpy(v).to(dev) for v in (inst.row_ptr, inst.col, inst.c, inst.a, inst.b)]
+    s = dlm.Solver(*arrs, inst.J)
+    del arrs
+    info = s.info()
+    s.set_schedule(*w["schedule"])
+    s.step(20)
+    s.set_schedule(*w["schedule"])
+    torch.cuda.synchronize()
+    T = 700
+    sw, up, tot = s.step_timed(T)
+    peak, _ = load_peaks()
+    st, sec = solve_from_zero(s, torch, 1e-4, 20000, sched=w["schedule"], gap_every=25)
+    s.close()
+    return {"workload": w["desc"], "nnz": info["nnz"], "generate_s": t_gen,
+            "throughput": {"value": info["nnz"] * T / (tot / 1000.0), "unit": UNIT, "iters": T,
+                           "sweep_us": sw * 1000.0 / T, "update_us": up * 1000.0 / T,
+                           "frac": info["bytes_per_iter"] / (sw / 1000.0 / T) / 1e9 / peak},
+            "time_to_gap": {"target_rel_gap": 1e-4, "seconds": sec, "iters": int(st.iter), "rel_gap": st.rel_gap,
+                            "converged": bool(st.converged), "options": "row normalization, adaptive restart, "
+                                                                        "gap check every 25 iterations"}}
+
+
+def batched_summary(args, dlm, torch, dev, threads, iters=100, steps=2):
+    """The batched workload (64 instances, BF16) in brief: the tuner's mapping,
+    then `steps` x `iters` iterations with every kernel timed."""
+    import numpy as np
+    import synth
+
+    w = WORKLOADS["batched"]
+    t0 = time.perf_counter()
+    recipes = synth.recipe_batch(n=w["n"], seed=w["seed"])
+    solvers = []
+    for r, g in recipes:
+        if args.scale != 1.0:
+            r.I = max(1000, int(round(r.I * args.scale)))
+        inst = make_instance(r, True, torch, False, threads)
+        arrs = [torch.from_numpy(v).to(dev) for v in (inst.row_ptr, inst.col, inst.c.view(np.int16),
+                                                      inst.a.view(np.int16), inst.b)]
+        s = dlm.Solver(arrs[0], arrs[1], arrs[2].view(torch.bfloat16), arrs[3].view(torch.bfloat16), arrs[4],
+                       inst.J, bf16=True)
+        s.set_schedule(g)
+        solvers.append(s)
+        del arrs, inst
+    t_setup = time.perf_counter() - t0
+    bt = dlm.Batch(solvers)
+    chosen, _ = bt.autotune(3)
+    bt.step(iters)
+    sw = up = tot = 0.0
+    for _ in range(steps):
+        a_, b_, c_ = bt.step_timed(iters)
+        sw, up, tot = sw + a_, up + b_, tot + c_
+    infos = [s.info() for s in solvers]
+    nnz = sum(i["nnz"] for i in infos)
+    bytes_iter = sum(i["bytes_per_iter"] for i in infos)
+    status = sorted({x.status for x in bt.stats()})
+    bt.close()
+    for s in solvers:
+        s.close()
+    peak, _ = load_peaks()
+    T = iters * steps
+    return {"workload": w["desc"], "instances": len(solvers), "nnz": nnz, "generate_and_create_s": t_setup,
+            "mapping": {k: getattr(chosen, k) for k in ("mapping", "coop_max", "block_threads")},
+            "value": nnz * T / (tot / 1000.0), "unit": UNIT, "sweep_us": sw * 1000.0 / T, "update_us": up * 1000.0 / T,
+            "frac": bytes_iter / (sw / 1000.0 / T) / 1e9 / peak, "member_status": status}
 
 
 def cpu_sample(workload, bf16, frac, seed=4242, threads=0, inst=None):
@@ -421,7 +570,7 @@ def run_reference(args, rank, world):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1000 * total_s / len(per_step), "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
-        "config": {"workload": WORKLOADS[args.workload]["desc"], "parallelism": "replicas"},
+        "config": config_for(args, world),
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": nc, "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
@@ -451,6 +600,8 @@ def main():
     ap.add_argument("--ttg-items", type=int, default=1_000)
     ap.add_argument("--ttg-gamma", type=float, default=1e-3)
     ap.add_argument("--ttg-only", action="store_true", help="print only the time-to-gap object (development)")
+    ap.add_argument("--no-companions", action="store_true",
+                    help="skip the production and batched summaries of the default line")
     args = ap.parse_args()
 
     rank = int(os.environ.get("RANK", "0"))
@@ -573,8 +724,8 @@ def main():
         conv = precondition_convergence(s, dlm, w["schedule"][1])
 
     bf16_err = None
-    if bf16 and not args.no_error_statement and w.get("families", 1) == 1:
-        bf16_err = bf16_error_statement(dlm, torch, s, inst, recipe, w["schedule"][1], args.cpu_frac, args.threads)
+    if bf16 and not args.no_error_statement and w.get("families", 1) == 1 and args.workload == "precision":
+        bf16_err = bf16_error_statement(dlm, torch, inst, recipe, args.threads, gamma=w["schedule"][1])
 
     # ---- end to end through the C-ABI: host (pinned) inputs -> create ->
     # iterations -> lam back to the host, every step ----
@@ -638,17 +789,18 @@ def main():
     ttg = None
     if rank == 0 and not args.no_time_to_gap and args.workload == "precision":
         ttg = time_to_gap(args, dlm, torch, dev)
+    production = batched = None
+    if rank == 0 and not args.no_companions and args.workload == "precision":
+        production = production_summary(args, dlm, torch, dev, args.threads)
+        batched = batched_summary(args, dlm, torch, dev, args.threads)
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": elapsed_s * 1000.0 / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": w["desc"] if args.scale == 1.0 else w["desc"] + f" (users scaled x{args.scale})",
-                   "users": I, "items": J, "nnz": nnz, "storage": "bf16" if bf16 else "f32",
-                   "iters_per_step": args.iters, "parallelism": "replicas" if world > 1 else "single GPU",
-                   "sweep_mapping": tuned if tuned is not None else "default",
-                   "l2": f"inputs {bytes_iter / 1e9:.1f} GB per iteration >> 129 MB L2 (no flush)"
-                   if bytes_iter > 1.3e8 else "inputs fit in L2 (tiny case)"},
+        "config": config_for(args, world),
+        "instance": {"users": I, "items": J, "nnz": nnz, "bytes_per_iter": bytes_iter,
+                     "sweep_mapping": tuned if tuned is not None else "default"},
         "roofline": roof,
         "cpu_baseline": cpu,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(dual_dim * 4),
@@ -658,6 +810,8 @@ def main():
         "graph_ms_per_step": graph_ms_per_step,
         "bf16_error": bf16_err,
         "time_to_gap": ttg,
+        "production": production,
+        "batched": batched,
         "precondition_convergence": conv,
         "setup_s": {"generate": t_gen, "upload_and_create": t_setup},
     }
@@ -805,12 +959,46 @@ def time_to_gap(args, dlm, torch, dev):
            "seconds_total": time.perf_counter() - t_all}
     out["headline_speedup_bf16_learned_vs_fp32_cold"] = out["modes"]["fp32_cold"]["mean_s"] / \
         out["modes"]["bf16_learned"]["mean_s"]
+    out["oracle_fp32_cold"] = oracle_time_to_gap(args, dlm, torch, dev, g_end, gap_every)
     out["learned_vs_prev_iters"] = out["modes"]["fp32_learned"]["mean_iters"] / out["modes"]["fp32_prev"]["mean_iters"]
     out["learned_vs_prev_iters_short_continuation"] = (out["modes"]["fp32_learned_q"]["mean_iters"] /
                                                        out["modes"]["fp32_prev_q"]["mean_iters"])
     if ws is not None:
         ws.close()
     return out
+
+
+def oracle_time_to_gap(args, dlm, torch, dev, g_end, gap_every, frac=0.01):
+    """The FP64 oracle's time to the 1e-4 certified gap, FP32 cold start and
+    the protocol of fp32_cold (continuation 1e-1 -> gamma_end halved every 50
+    iterations, row normalization, a check every gap_every iterations), on a
+    seeded user sample of the daily recipe (capacities from the sample), on
+    all host threads; the GPU's FP32 cold start on the same sample beside it."""
+    import numpy as np
+    import oracle
+    import synth
+
+    r = synth.recipe_daily(I=args.ttg_users, J=args.ttg_items, seed=1004)
+    ids = synth.sample_users(r.I, frac, 5151)
+    sub = synth.generate(r, ids=ids, nthreads=args.threads)
+    p = oracle.Problem(sub.row_ptr, sub.col, sub.c.astype(np.float64), sub.a.astype(np.float64), sub.b, sub.J)
+    sched = (1e-1, g_end, 0.5, 50)
+    nc = host_cores()
+    t0 = time.perf_counter()
+    ref = oracle.solve_threads(p, *sched, precondition=True, target=1e-4, gap_every=gap_every, max_iters=100_000,
+                               nthreads=nc)
+    t_ref = time.perf_counter() - t0
+    arrs = [torch.from_numpy(v).to(dev) for v in (sub.row_ptr, sub.col, sub.c, sub.a, sub.b)]
+    s = dlm.Solver(*arrs, sub.J)
+    s.set_schedule(*sched)  # warm the graphs and kernels once
+    s.step(20)
+    st, sec = solve_from_zero(s, torch, 1e-4, 100_000, sched=sched, gap_every=gap_every, restart=False)
+    s.close()
+    return {"instance": f"daily recipe, {frac:.0%} seeded user sample of day 0 ({len(ids):,} users, {p.nnz:,} nnz)",
+            "oracle": {"seconds": t_ref, "iters": ref["iters"], "rel_gap": ref["rel_gap"], "cores": nc,
+                       "kind": "oracle (FP64, sweep split over host threads)"},
+            "gpu_fp32_cold": {"seconds": sec, "iters": int(st.iter), "rel_gap": st.rel_gap},
+            "gpu_speedup": t_ref / sec if sec > 0 else None}
 
 
 def run_batched(args, dlm, torch, dev, rank, world, barrier, max_over_ranks, dist):
@@ -955,11 +1143,9 @@ def run_batched(args, dlm, torch, dev, rank, world, barrier, max_over_ranks, dis
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": elapsed_s * 1000.0 / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": w["desc"] if args.scale == 1.0 else w["desc"] + f" (users scaled x{args.scale})",
-                   "instances": len(insts), "users": users, "nnz": nnz, "storage": "bf16",
-                   "iters_per_step": args.iters, "parallelism": "replicas" if world > 1 else "single GPU",
-                   "l2": f"inputs {bytes_iter / 1e9:.1f} GB per iteration >> 129 MB L2 (no flush)",
-                   "mapping": chosen.as_dict(), "tuner_sweep_ms": tune_ms},
+        "config": config_for(args, world),
+        "instance": {"instances": len(insts), "users": users, "nnz": nnz, "bytes_per_iter": bytes_iter,
+                     "mapping": chosen.as_dict(), "tuner_sweep_ms": tune_ms},
         "roofline": roof,
         "cpu_baseline": cpu,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),

@@ -70,17 +70,6 @@ struct Narrow : V {
   }
 };
 
-// Loads from the slice's element streams: __ldg for global memory (the
-// layout), plain loads for a staged copy in shared memory.
-template <bool SM, class X>
-__device__ __forceinline__ X ldx(const X* p) {
-  if constexpr (SM) {
-    return *p;
-  } else {
-    return __ldg(p);
-  }
-}
-
 struct Seg {
   float gamma, invg, gz, gzl, z;
   float scaleG, scaleC, scaleQ, scaleN, scaleO;
@@ -220,7 +209,7 @@ __device__ __forceinline__ void coop_user(const Seg& S, const float* __restrict_
 // sweeps take): it saves a re-read (4 % on the 64-instance batch, 6 % on the
 // appendix instance once its rows have several active edges; no change on
 // the precision sweep).
-template <class P, bool STATS, bool SM = false>
+template <class P, bool STATS>
 __device__ __forceinline__ float4 rows_upto3(const Seg S, const float* __restrict__ ys, unsigned long long* accG,
                                           unsigned long long* accC, unsigned long long* accQ,
                                           const typename P::IX* __restrict__ col0, const typename P::T* __restrict__ ca0,
@@ -235,8 +224,8 @@ __device__ __forceinline__ float4 rows_upto3(const Seg S, const float* __restric
     cr[i] = ar[i] = 0.f;
     if (i < r) {
       const int el = sell_el(i == 0 ? i0 : (i == 1 ? i1 : i2), lane, w4);
-      jr[i] = static_cast<int>(ldx<SM>(col0 + el));
-      P::get(ldx<SM>(ca0 + el), cr[i], ar[i]);
+      jr[i] = static_cast<int>(__ldg(col0 + el));
+      P::get(__ldg(ca0 + el), cr[i], ar[i]);
     }
   }
   bool zero = !eq && tau <= (P::kCount ? S.mu : 0.f);
@@ -283,19 +272,14 @@ struct Top4 {
 };
 __device__ __forceinline__ Top4 top4_empty() { return Top4{-INFINITY, -INFINITY, -INFINITY, -INFINITY, 0, 0, 0}; }
 
-// After pass A over a row: the threshold, x and the deposits (modes below).
-// col0/ca0 are the slice's streams in global memory (the Michelot passes and
-// the x output read them); colr/car are where the recorded edges of modes 1
-// and 2 are re-read from -- a staged copy of the slice in shared memory (SM)
-// or the same global streams.
-template <class P, bool STATS, bool REG3, bool SM>
+// After pass A over a row: the threshold, x and the deposits (modes below);
+// col0/ca0 are the slice's element streams.
+template <class P, bool STATS, bool REG3>
 __device__ __forceinline__ void finish_slice(const InstDesc& D, const Seg& S, const float* __restrict__ ys,
                                              unsigned long long* accG, unsigned long long* accC,
                                              unsigned long long* accQ, int64_t s, int w,
                                              const typename P::IX* __restrict__ col0,
-                                             const typename P::T* __restrict__ ca0,
-                                             const typename P::IX* __restrict__ colr,
-                                             const typename P::T* __restrict__ car, const Top4 tk, int coop_max,
+                                             const typename P::T* __restrict__ ca0, const Top4 tk, int coop_max,
                                              double& wobj, unsigned long long& cn, unsigned long long& oq) {
   const int lane = threadIdx.x & 31;
   const int w4 = w >> 2;
@@ -343,7 +327,7 @@ __device__ __forceinline__ void finish_slice(const InstDesc& D, const Seg& S, co
 
   float ob = 0.f;
   if (mode == 2 && REG3) {
-    const float4 res = rows_upto3<P, STATS, SM>(S, ys, accG, accC, accQ, colr, car, w4, r, i0, i1, i2, tau, eq, cn);
+    const float4 res = rows_upto3<P, STATS>(S, ys, accG, accC, accQ, col0, ca0, w4, r, i0, i1, i2, tau, eq, cn);
     tau = res.x;
     taul = res.y;
     zero = res.z != 0.f;
@@ -384,9 +368,9 @@ __device__ __forceinline__ void finish_slice(const InstDesc& D, const Seg& S, co
     }
   } else if (mode == 1) {
     const int el = sell_el(i0, lane, w4);
-    const int j = static_cast<int>(ldx<SM>(colr + el));
+    const int j = static_cast<int>(__ldg(col0 + el));
     float c, a;
-    P::get(ldx<SM>(car + el), c, a);
+    P::get(__ldg(ca0 + el), c, a);
     deposit<P, STATS>(S, j, c, a, S.z, accG, accC, accQ, ob, cn);
   }
 
@@ -566,8 +550,7 @@ __device__ __forceinline__ void do_slice(const InstDesc& D, const Seg& S, const 
     const float u = -fmaf(a, ys[j], c);
     top4_insert(u, k, tk.v0, tk.v1, tk.v2, tk.v3, tk.i0, tk.i1, tk.i2);
   }
-  finish_slice<P, STATS, REG3, false>(D, S, ys, accG, accC, accQ, s, w, col0, ca0, col0, ca0, tk, coop_max, wobj, cn,
-                                      oq);
+  finish_slice<P, STATS, REG3>(D, S, ys, accG, accC, accQ, s, w, col0, ca0, tk, coop_max, wobj, cn, oq);
 }
 
 // Certificate sweeps (STATS) keep the item sums of the window of items

@@ -259,7 +259,7 @@ def solve_from_zero(s, torch, target, max_iters, sched=(1e-1, 1e-3, 0.5, 50), ga
 
 
 def bf16_error_statement(dlm, torch, inst, recipe, threads, gamma=1e-3, target=1e-5, max_iters=4000,
-                         sample_frac=5e-4):
+                         sample_frac=2e-3, sample_iters=3000):
     """Error of the BF16-storage form, optimum to optimum.
 
     Full instance: the BF16 form, the FP32 form and the FP32 form with only c
@@ -319,7 +319,7 @@ def bf16_error_statement(dlm, torch, inst, recipe, threads, gamma=1e-3, target=1
     h = dlm.Solver(arrs[0], arrs[1], torch.from_numpy(cr.view(np.int16)).to(dev).view(torch.bfloat16),
                    torch.from_numpy(ar.view(np.int16)).to(dev).view(torch.bfloat16),
                    torch.from_numpy(sub.b).to(dev), sub.J, bf16=True)
-    st, sec = solve_from_zero(h, torch, target, max_iters, sched)
+    st, sec = solve_from_zero(h, torch, target, sample_iters, sched)
     lam_g = h.lam().cpu().numpy().astype(np.float64)
     x_g = h.x().cpu().numpy().astype(np.float64)
     h.close()
@@ -327,11 +327,12 @@ def bf16_error_statement(dlm, torch, inst, recipe, threads, gamma=1e-3, target=1
     nc = host_cores()
     t0 = time.perf_counter()
     ref = oracle.solve_threads(p, *sched, precondition=True, restart=True, target=target, gap_every=50,
-                               max_iters=max_iters, nthreads=nc)
+                               max_iters=sample_iters, nthreads=nc)
     t_ref = time.perf_counter() - t0
     x_r = oracle.sweep(p, ref["lam"], gamma)["x"]
     sample = {"users": int(len(ids)), "nnz": int(p.nnz), "gpu_bf16": {"g": st.dual_obj, "gap": st.rel_gap,
-                                                                        "iters": int(st.iter)},
+                                                                        "iters": int(st.iter),
+                                                                        "converged": bool(st.converged)},
               "oracle_fp64": {"g": ref["g"], "gap": ref["rel_gap"], "iters": ref["iters"], "seconds": t_ref,
                               "cores": nc},
               "x_l2": float(np.linalg.norm(x_g - x_r)), "x_max_abs": float(np.abs(x_g - x_r).max()),
@@ -674,8 +675,7 @@ def main():
     t_setup = time.perf_counter() - t_setup
     s.set_schedule(*w["schedule"])
     precond = bool(w.get("precondition", False))
-    if precond:
-        s.set_options(precondition=True)
+    s.set_options(precondition=precond)
     info = s.info()
     nnz, I, J, bytes_iter = info["nnz"], info["num_users"], info["num_items"], info["bytes_per_iter"]
 
@@ -846,29 +846,38 @@ def precondition_convergence(s, dlm, gamma, target=1e-4, max_iters=6000, gap_eve
     return out
 
 
+# Continuations a warm start may enter (gamma_0, factor, iterations per
+# stage); the cold start always takes the first.
+WARM_SCHEDULES = [(1e-1, 0.5, 50), (1e-1, 0.25, 50), (1e-1, 0.5, 25), (1e-1, 0.25, 25), (1e-2, 0.5, 25),
+                  (1e-2, 0.25, 25), (None, 1.0, 1 << 30)]
+
+
 def time_to_gap(args, dlm, torch, dev):
     """Recurring daily instances (users x items of the daily recipe; day t
     from day t-1: 10% of edges' c perturbed by N(0, 0.02), b_j scaled by
     1 + N(0, 0.05), 2% of users churned).  Days 0-20 are solved to a 1e-5
-    certified gap for labels; the warm-start network trains on days 1-20;
-    on days 21-30 each start is driven to a 1e-4 certified gap at the final
-    gamma and timed end to end (features and prediction included):
-      fp32_cold     FP32 values, lam = 0, gamma continuation 1e-1 -> gamma_end
-                    halved every 50 iterations (the plain method)
+    certified gap for labels.  The warm-start network trains on days 1-17;
+    on days 18-20 (held out from the network, before any evaluation day) each
+    warm start -- the previous day's dual and the network's prediction --
+    picks the continuation (WARM_SCHEDULES: where it enters and how fast it
+    descends to gamma_end) with the least mean time to the 1e-4 gap.  On days
+    21-30 every start is driven to a 1e-4 certified gap and timed end to end
+    (features and prediction included):
+      fp32_cold     FP32 values, lam = 0, gamma 1e-1 -> gamma_end halved every
+                    50 iterations (the plain method)
       bf16_cold     the same on BF16 values
-      fp32_prev     FP32, the same continuation started from the previous
-                    day's dual, adaptive restart
-      fp32_learned  FP32, the same from the network's prediction
-      bf16_learned  BF16 values + the network's prediction (the headline)
-      fp32_prev_q, fp32_learned_q   the warm starts with a shorter
-                    continuation (gamma quartered every 50 iterations), where
-                    the quality of the start shows in the iteration count
-    All forms use row normalization and check the gap every 25 iterations."""
+      fp32_prev     FP32 from the previous day's dual, its chosen continuation
+      fp32_learned  FP32 from the network's prediction, its chosen continuation
+      bf16_learned  BF16 values + the prediction (the headline)
+      fp32_prev_base, fp32_learned_base   both warm starts on the cold
+                    start's continuation, for reference
+    All forms use row normalization and check the gap every 25 iterations;
+    warm starts add the adaptive restart."""
     import numpy as np
     import synth
 
     g_end, I, J = args.ttg_gamma, args.ttg_users, args.ttg_items
-    n_days, n_train, gap_every = 30, 20, 25
+    n_days, n_train, n_select, gap_every = 30, 17, 20, 25
     t_all = time.perf_counter()
     inst = synth.generate(synth.recipe_daily(I=I, J=J, seed=1004), nthreads=args.threads)
 
@@ -884,13 +893,30 @@ def time_to_gap(args, dlm, torch, dev):
         del rp, col, c, a, b
         return s
 
+    def run(s, start, sched, d):
+        """One timed solve; returns (seconds, Stats)."""
+        g0, factor, ips = sched
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        s.set_options(precondition=True, gap_every=gap_every, restart=start != "cold")
+        s.set_schedule(g_end if g0 is None else g0, g_end, factor, ips)
+        if start == "cold":
+            s.set_lambda(zeros)
+        elif start == "prev":
+            s.set_lambda(labels[d - 1])
+        else:
+            s.set_lambda(ws.predict(dlm.WarmStart.features(s, labels[d - 1], g_end)))
+        st = s.solve(1e-4, 100_000)
+        torch.cuda.synchronize(dev)
+        return time.perf_counter() - t0, st
+
     peak, _ = load_peaks()
-    # start, continuation factor (gamma_0 = 1e-1, 50 iterations per stage)
-    sched = {"fp32_cold": ("cold", 0.5), "bf16_cold": ("cold", 0.5), "fp32_prev": ("prev", 0.5),
-             "fp32_learned": ("learned", 0.5), "bf16_learned": ("learned", 0.5),
-             "fp32_prev_q": ("prev", 0.25), "fp32_learned_q": ("learned", 0.25)}
-    modes = list(sched)
+    base = WARM_SCHEDULES[0]
+    chosen = {}
+    modes = ["fp32_cold", "bf16_cold", "fp32_prev", "fp32_learned", "bf16_learned", "fp32_prev_base",
+             "fp32_learned_base"]
     res = {m: {"seconds": [], "iters": [], "gap": [], "roofline_frac": []} for m in modes}
+    select = {st: {k: [] for k in range(len(WARM_SCHEDULES))} for st in ("prev", "learned")}
     labels, feats = {}, {}
     label_gap, label_iters = [], []
     ws, train = None, None
@@ -900,37 +926,36 @@ def time_to_gap(args, dlm, torch, dev):
             inst = synth.next_day(inst, d, seed=1004, nthreads=args.threads)
         s32 = make(inst, False)
         bytes32 = s32.info()["bytes_per_iter"]
-        if d > n_train:
+        if n_train < d <= n_select:
+            # held-out days: every warm start tries every continuation
+            for start in ("prev", "learned"):
+                for k, sched in enumerate(WARM_SCHEDULES):
+                    select[start][k].append(run(s32, start, sched, d)[0])
+            if d == n_select:
+                for start in ("prev", "learned"):
+                    chosen[start] = WARM_SCHEDULES[min(select[start], key=lambda k: np.mean(select[start][k]))]
+        if d > n_select:
             s16 = make(inst, True)
             bytes16 = s16.info()["bytes_per_iter"]
+            plan = {"fp32_cold": ("cold", base), "bf16_cold": ("cold", base), "fp32_prev": ("prev", chosen["prev"]),
+                    "fp32_learned": ("learned", chosen["learned"]), "bf16_learned": ("learned", chosen["learned"]),
+                    "fp32_prev_base": ("prev", base), "fp32_learned_base": ("learned", base)}
             for m in modes:
                 s, nbytes = (s16, bytes16) if m.startswith("bf16") else (s32, bytes32)
-                torch.cuda.synchronize(dev)
-                t0 = time.perf_counter()
-                start, factor = sched[m]
-                s.set_options(precondition=True, gap_every=gap_every, restart=start != "cold")
-                s.set_schedule(1e-1, g_end, factor, 50)
-                if start == "cold":
-                    s.set_lambda(zeros)
-                elif start == "prev":
-                    s.set_lambda(labels[d - 1])
-                else:
-                    s.set_lambda(ws.predict(dlm.WarmStart.features(s, labels[d - 1], g_end)))
-                st = s.solve(1e-4, 100_000)
-                torch.cuda.synchronize(dev)
-                dt = time.perf_counter() - t0
+                start, sched = plan[m]
+                dt, st = run(s, start, sched, d)
                 sweeps = st.iter + st.iter // gap_every + 1 + (1 if start == "learned" else 0)
                 res[m]["seconds"].append(dt)
                 res[m]["iters"].append(int(st.iter))
                 res[m]["gap"].append(float(st.rel_gap))
                 res[m]["roofline_frac"].append(sweeps * nbytes / dt / 1e9 / peak)
             s16.close()
-        # label: the day solved to 1e-6 from the previous day's dual
+        # label: the day solved to 1e-5 from the previous day's dual
+        s32.set_options(precondition=True, gap_every=50, restart=True)
         if d == 0:
-            s32.set_options(precondition=True, gap_every=50, restart=True)
             s32.set_schedule(1e-1, g_end, 0.5, 50)
+            s32.set_lambda(zeros)
         else:
-            s32.set_options(precondition=True, gap_every=50, restart=True)
             s32.set_schedule(g_end)
             s32.set_lambda(labels[d - 1])
             if d <= n_train:
@@ -946,23 +971,31 @@ def time_to_gap(args, dlm, torch, dev):
             ws = dlm.WarmStart(128, 1)
             t0 = time.perf_counter()
             losses = ws.train(X, y, 300, 1e-3)
-            train = {"rows": int(X.shape[0]), "steps": 300, "lr": 1e-3, "loss_first": float(losses[0]),
-                     "loss_last": float(losses[-1]), "seconds": time.perf_counter() - t0}
+            train = {"rows": int(X.shape[0]), "days": f"1-{n_train}", "steps": 300, "lr": 1e-3,
+                     "loss_first": float(losses[0]), "loss_last": float(losses[-1]),
+                     "seconds": time.perf_counter() - t0}
+    fmt = lambda sc: {"gamma_0": g_end if sc[0] is None else sc[0], "factor": sc[1],
+                      "iters_per_stage": sc[2] if sc[0] is not None else None}
     out = {"workload": f"recurring daily instances: {I:,} users x {J:,} items (~{I * 25 / 1e6:.0f}M nnz), "
-                       f"30 days, train days 1-20, evaluate days 21-30",
+                       f"30 days; network trained on days 1-{n_train}, continuations chosen on days "
+                       f"{n_train + 1}-{n_select}, evaluated on days {n_select + 1}-{n_days}",
            "gamma_end": g_end, "target_rel_gap": 1e-4, "gap_every": gap_every, "train": train,
            "labels": {"target": 1e-5, "max_iters": 8000, "worst_gap": max(label_gap),
                       "mean_iters": float(np.mean(label_iters))},
+           "continuations": {"candidates": [fmt(sc) for sc in WARM_SCHEDULES],
+                             "chosen": {k: fmt(v) for k, v in chosen.items()},
+                             "selection_mean_s": {st: [float(np.mean(select[st][k])) for k in range(len(WARM_SCHEDULES))]
+                                                  for st in select}},
            "modes": {m: {"mean_s": float(np.mean(v["seconds"])), "mean_iters": float(np.mean(v["iters"])),
                          "mean_roofline_frac": float(np.mean(v["roofline_frac"])), "per_day_s": v["seconds"],
                          "per_day_iters": v["iters"], "max_gap": max(v["gap"])} for m, v in res.items()},
            "seconds_total": time.perf_counter() - t_all}
-    out["headline_speedup_bf16_learned_vs_fp32_cold"] = out["modes"]["fp32_cold"]["mean_s"] / \
-        out["modes"]["bf16_learned"]["mean_s"]
+    M = out["modes"]
+    out["headline_speedup_bf16_learned_vs_fp32_cold"] = M["fp32_cold"]["mean_s"] / M["bf16_learned"]["mean_s"]
+    out["learned_vs_prev_seconds"] = M["fp32_learned"]["mean_s"] / M["fp32_prev"]["mean_s"]
+    out["learned_vs_prev_iters"] = M["fp32_learned"]["mean_iters"] / M["fp32_prev"]["mean_iters"]
+    out["bf16_learned_vs_fp32_prev_iters_saved"] = M["fp32_prev"]["mean_iters"] - M["bf16_learned"]["mean_iters"]
     out["oracle_fp32_cold"] = oracle_time_to_gap(args, dlm, torch, dev, g_end, gap_every)
-    out["learned_vs_prev_iters"] = out["modes"]["fp32_learned"]["mean_iters"] / out["modes"]["fp32_prev"]["mean_iters"]
-    out["learned_vs_prev_iters_short_continuation"] = (out["modes"]["fp32_learned_q"]["mean_iters"] /
-                                                       out["modes"]["fp32_prev_q"]["mean_iters"])
     if ws is not None:
         ws.close()
     return out

@@ -131,13 +131,16 @@ def test_training_is_deterministic_and_learns(dlm_lib):
 
 
 def test_learned_start_gain(dlm_lib):
-    """Recurring daily instances (60,000 users x 200 items, gamma 1e-3): train
-    on days 1-12, evaluate days 13-18.  Every start is driven to the same
-    certified gap (1e-4) by the same solver (row normalization, adaptive
-    restart, fixed gamma); the learned start must need fewer iterations than
-    the previous day's dual, the fallback it replaces.  The cold start with
-    the continuation schedule is reported beside them."""
-    g_end = 1e-3
+    """Recurring daily instances (60,000 users x 200 items, gamma 1e-3): the
+    network trains on days 1-10; on days 11-12 (held out from it) each warm
+    start -- the previous day's dual and the prediction -- picks the
+    continuation it enters (where, and how fast it descends to gamma_end) by
+    its mean iteration count; days 13-18 are evaluated.  Every start is
+    driven to the same certified gap (1e-4, checked every 10 iterations;
+    row normalization; warm starts add the adaptive restart).  The learned
+    start must save more than one gap-check interval over the previous day's
+    dual, the fallback it replaces, and beat the cold start."""
+    g_end, gap_every = 1e-3, 10
     inst = synth.generate(synth.recipe_daily(I=60_000, J=200, seed=77))
     days = [inst]
     for d in range(1, 19):
@@ -145,13 +148,12 @@ def test_learned_start_gain(dlm_lib):
 
     def solver(i):
         rp, col, c, a, b = to_device(days[i], torch)
-        s = dlm_lib.Solver(rp, col, c, a, b, days[i].J)
-        s.set_options(precondition=True, gap_every=10, restart=True)
-        return s
+        return dlm_lib.Solver(rp, col, c, a, b, days[i].J)
 
     labels, feats = [], []
     for i in range(19):
         s = solver(i)
+        s.set_options(precondition=True, gap_every=gap_every, restart=True)
         if i == 0:
             s.set_schedule(1e-1, g_end, 0.5, 50)
         else:
@@ -162,25 +164,33 @@ def test_learned_start_gain(dlm_lib):
         assert st.status in (dlm_lib.DLM_OK, dlm_lib.DLM_ERR_TIMEOUT) and st.rel_gap <= 1e-4
         labels.append(s.lam())
         s.close()
-    Xtr = torch.cat(feats[:12])
-    ytr = torch.cat(labels[1:13])
     ws = dlm_lib.WarmStart(128, 1)
-    losses = ws.train(Xtr, ytr, 300, 1e-3)
+    losses = ws.train(torch.cat(feats[:10]), torch.cat(labels[1:11]), 300, 1e-3)
     assert losses[-1] < 0.5 * losses[0]
-    res = {"cold": [], "prev": [], "learned": []}
-    for i in range(13, 19):
-        for mode in res:
-            s = solver(i)
-            if mode == "cold":
-                s.set_schedule(1e-1, g_end, 0.5, 50)
-            else:
-                s.set_schedule(g_end)
-                s.set_lambda(labels[i - 1] if mode == "prev" else ws.predict(feats[i - 1]))
-            st = s.solve(1e-4, 100_000)
-            assert st.status == dlm_lib.DLM_OK
-            res[mode].append(st.iter)
-            s.close()
+    cold = (1e-1, 0.5, 50)
+    cands = [(1e-1, 0.5, 50), (1e-1, 0.25, 25), (1e-2, 0.5, 25), (1e-2, 0.25, 10), (g_end, 1.0, 1 << 30)]
+
+    def iters(i, mode, sched):
+        s = solver(i)
+        s.set_options(precondition=True, gap_every=gap_every, restart=mode != "cold")
+        s.set_schedule(*sched[:1], g_end, *sched[1:])
+        if mode != "cold":
+            s.set_lambda(labels[i - 1] if mode == "prev" else ws.predict(feats[i - 1]))
+        st = s.solve(1e-4, 100_000)
+        assert st.status == dlm_lib.DLM_OK
+        s.close()
+        return st.iter
+
+    chosen = {}
+    for mode in ("prev", "learned"):
+        trial = [np.mean([iters(i, mode, c) for i in (11, 12)]) for c in cands]
+        chosen[mode] = cands[int(np.argmin(trial))]
+        print(f"{mode}: mean iterations per candidate on days 11-12 {trial}")
+    res = {"cold": [iters(i, "cold", cold) for i in range(13, 19)],
+           "prev": [iters(i, "prev", chosen["prev"]) for i in range(13, 19)],
+           "learned": [iters(i, "learned", chosen["learned"]) for i in range(13, 19)]}
     mean = {k: float(np.mean(v)) for k, v in res.items()}
-    print("iterations to 1e-4:", mean, res)
-    assert mean["learned"] < mean["prev"]
+    print("continuations:", chosen, "iterations to 1e-4:", mean, res)
+    assert mean["learned"] <= mean["prev"] - gap_every
+    assert mean["learned"] < mean["cold"]
     ws.close()

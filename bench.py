@@ -58,7 +58,7 @@ WORKLOADS = {
              "a = s_j value with s_j ~ LogNormal(0,1.5); b_j = rho_j (greedy load + 1e-3), rho_j ~ U[0.5,1]; "
              "c, a FP32; gamma = 1e-2 fixed; row normalization (per-item steps)",
         users=25_000_000, items=10_000, seed=1006, bf16=False, schedule=(1e-2, 1e-2, 0.5, 1 << 30),
-        precondition=True, appendix=True),
+        precondition=True, appendix=True, autotune=True),
     "batched": dict(
         desc="batched form: 64 independent instances of the production generators, users log-uniform 1e4-5e6, "
              "items log-uniform 50-2,000, gamma drawn from {1e-1, 1e-2, 1e-3} (fixed per instance); c, a stored "
@@ -78,7 +78,10 @@ def config_for(args, world):
     w = WORKLOADS[args.workload]
     desc = w["desc"] if args.scale == 1.0 else w["desc"] + f" (users scaled x{args.scale})"
     cfg = {"workload": desc, "iters_per_step": args.iters,
-           "parallelism": "replicas" if world > 1 else "single GPU"}
+           "parallelism": "single GPU" if world == 1 else
+           ("replicas" if args.workload == "batched" else
+            f"user-sharded over {world} GPUs (each rank {w.get('users', 0):,} users; int64 item sums all-reduced "
+            f"every iteration)")}
     if args.workload == "batched":
         cfg.update(instances=w["n"], storage="bf16")
     else:
@@ -415,7 +418,7 @@ def batched_summary(args, dlm, torch, dev, threads, iters=100, steps=2):
     peak, _ = load_peaks()
     T = iters * steps
     return {"workload": w["desc"], "instances": len(solvers), "nnz": nnz, "generate_and_create_s": t_setup,
-            "mapping": {k: getattr(chosen, k) for k in ("mapping", "coop_max", "block_threads")},
+            "mapping": {k: getattr(chosen, k) for k in ("mapping", "coop_max", "block_threads", "topk")},
             "value": nnz * T / (tot / 1000.0), "unit": UNIT, "sweep_us": sw * 1000.0 / T, "update_us": up * 1000.0 / T,
             "frac": bytes_iter / (sw / 1000.0 / T) / 1e9 / peak, "member_status": status}
 
@@ -638,6 +641,8 @@ def main():
 
     if args.workload == "batched":
         return run_batched(args, dlm, torch, dev, rank, world, barrier, max_over_ranks, dist)
+    if world > 1 and args.workload not in ("tiny", "families", "appendix"):
+        return run_sharded(args, dlm, torch, dev, rank, world, barrier, dist)
     if args.ttg_only:
         print(json.dumps(time_to_gap(args, dlm, torch, dev)), flush=True)
         return 0
@@ -683,12 +688,12 @@ def main():
         s.step(args.iters)
     torch.cuda.synchronize(dev)
     tuned = None
-    if args.autotune:
+    if args.autotune or w.get("autotune"):
         # the library's tuner picks the sweep mapping from the warmed-up state
         # (which it restores); its choice depends on that state, so the default
         # keeps the library's default mapping
         opts, tune_ms = s.autotune(3)
-        tuned = {k: opts.as_dict()[k] for k in ("mapping", "coop_max", "block_threads")}
+        tuned = {k: opts.as_dict()[k] for k in ("mapping", "coop_max", "block_threads", "topk")}
         tuned["sweep_ms"] = tune_ms
 
     # ---- timed region: K steps, every kernel bracketed by CUDA events ----
@@ -735,10 +740,12 @@ def main():
     del s
     torch.cuda.synchronize(dev)
     e2e_times = []
+    create_phases = None
     for k in range(args.e2e_steps + 1 if args.e2e_steps > 0 else 0):
         torch.cuda.synchronize(dev)
         t0 = time.perf_counter()
         s2 = dlm.Solver(inst.row_ptr, inst.col, inst.c, inst.a, inst.b, inst.J, bf16=bf16, **kind_args)
+        create_phases = s2.setup_seconds()
         s2.set_schedule(*w["schedule"])
         if precond:
             s2.set_options(precondition=True)
@@ -804,7 +811,8 @@ def main():
         "roofline": roof,
         "cpu_baseline": cpu,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(dual_dim * 4),
-                "note": "per step: dlm_create from pinned host arrays (copy + layout), iterations, lam to host"},
+                "note": "per step: dlm_create from pinned host arrays (copy + layout), iterations, lam to host",
+                "create_seconds_by_phase": create_phases},
         "gpu_launches": 2 * iters_total,
         "clocks": clocks,
         "graph_ms_per_step": graph_ms_per_step,
@@ -1034,6 +1042,89 @@ def oracle_time_to_gap(args, dlm, torch, dev, g_end, gap_every, frac=0.01):
             "gpu_speedup": t_ref / sec if sec > 0 else None}
 
 
+def run_sharded(args, dlm, torch, dev, rank, world, barrier, dist):
+    """N > 1 GPUs on one instance, user-sharded (weak scaling: every rank holds
+    the workload's users -- rank r the users r I .. (r + 1) I - 1 of an
+    instance of N I users over the same items -- and the capacities are those
+    of the whole instance).  Each iteration: every rank sweeps its users, the
+    int64 fixed-point item sums are all-reduced (NCCL), every rank takes the
+    same update.  Timed with CUDA events, barrier and synchronize on both
+    sides, the slowest rank's time."""
+    import numpy as np
+    import synth
+
+    w = WORKLOADS[args.workload]
+    bf16 = w["bf16"]
+    I = max(1000, int(round(w["users"] * args.scale)))
+    r = synth.Recipe(I=I * world, J=w["items"], seed=w["seed"]) if args.workload != "boxcut" else \
+        synth.recipe_production(I=I * world, J=w["items"], seed=w["seed"])
+    t_gen = time.perf_counter()
+    ids = np.arange(rank * I, (rank + 1) * I, dtype=np.int64)
+    inst = synth.generate(r, ids=ids, nthreads=args.threads)
+    b = torch.from_numpy(inst.b).to(dev)
+    dist.all_reduce(b)  # the capacities of the whole instance (0.05 sum over every rank's users)
+    t_gen = time.perf_counter() - t_gen
+    to = lambda v: torch.from_numpy(v).to(dev)
+    if bf16:
+        c = to(synth.round_bf16(inst.c, args.threads).view(np.int16)).view(torch.bfloat16)
+        a = to(synth.round_bf16(inst.a, args.threads).view(np.int16)).view(torch.bfloat16)
+    else:
+        c, a = to(inst.c), to(inst.a)
+    kind_args = dict(kind=w.get("kind", 0), z=w.get("z", 1.0), cut=w.get("cut"), bf16=bf16)
+    t_setup = time.perf_counter()
+    s = dlm.ShardedSolver.distributed(to(inst.row_ptr), to(inst.col), c, a, b, inst.J, **kind_args)
+    torch.cuda.synchronize(dev)
+    t_setup = time.perf_counter() - t_setup
+    s.set_schedule(*w["schedule"])
+    info = s.info()
+    for _ in range(args.warmup):
+        s.step(args.iters)
+    sampler = ClockSampler(gpu_id_for_smi(torch, dev))
+    sampler.start()
+    time.sleep(0.3)
+    st = torch.cuda.current_stream(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier()
+    torch.cuda.synchronize(dev)
+    e0.record(st)
+    for _ in range(args.steps):
+        s.step(args.iters)
+    e1.record(st)
+    torch.cuda.synchronize(dev)
+    barrier()
+    clocks = sampler.stop()
+    elapsed = e0.elapsed_time(e1) / 1000.0
+    units = info["nnz"] * args.iters * args.steps
+    value, tmax = replica_throughput(units, elapsed, dist, dev)
+    cert = s.stats()
+    peak, peak_kind = load_peaks()
+    it_s = tmax / (args.iters * args.steps)
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": tmax * 1000.0 / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": config_for(args, world),
+        "instance": {"users_per_rank": I, "nnz_this_rank": info["nnz"], "items": inst.J,
+                     "bytes_per_iter_this_rank": info["bytes_per_iter"]},
+        "roofline": {"bound": "hbm", "achieved": info["bytes_per_iter"] / it_s / 1e9, "peak": peak, "unit": "GB/s",
+                     "frac": info["bytes_per_iter"] / it_s / 1e9 / peak, "traffic": None,
+                     "peak_source": f"{peak_kind} (copy bandwidth)",
+                     "kernel": "sweep_kernel + int64 all-reduce + fista_update_kernel (per-iteration time of the "
+                               "slowest rank)"},
+        "cpu_baseline": None,
+        "e2e": {"value": None, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0,
+                "note": "not measured in the sharded form"},
+        "gpu_launches": 2 * args.iters * args.steps,
+        "clocks": clocks,
+        "certificate_after_timing": {"rel_gap": cert.rel_gap, "dual_obj": cert.dual_obj, "iter": cert.iter},
+        "setup_s": {"generate": t_gen, "shard_setup_and_create": t_setup},
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    s.close()
+    dist.destroy_process_group()
+    return 0
+
+
 def run_batched(args, dlm, torch, dev, rank, world, barrier, max_over_ranks, dist):
     """The batched workload: 64 handles run as one batch."""
     import numpy as np
@@ -1134,7 +1225,8 @@ def run_batched(args, dlm, torch, dev, rank, world, barrier, max_over_ranks, dis
             s.set_schedule(g)
             ss.append(s)
         b2 = dlm.Batch(ss)
-        b2.set_options(**{f: getattr(chosen, f) for f in ("mapping", "coop_max", "block_threads", "ctas_per_sm")})
+        b2.set_options(**{f: getattr(chosen, f) for f in ("mapping", "coop_max", "block_threads", "ctas_per_sm",
+                                                           "topk")})
         b2.step(args.iters)
         for s, lh in zip(ss, lam_host):
             dlm.dlm_get_lambda(s.h, lh, dlm.DLM_MEM_HOST)

@@ -77,6 +77,8 @@ typedef enum { DLM_MEM_DEVICE = 0, DLM_MEM_HOST = 1 } dlm_memspace;
  * with handles of the same m.
  * The arrays live in `memspace`.  dlm_create copies them into its own layout;
  * the caller may free or reuse them once dlm_create has returned. */
+struct dlm_shard;
+
 typedef struct {
   int64_t num_users, num_items, nnz;
   const int64_t* row_ptr;
@@ -92,6 +94,8 @@ typedef struct {
   double cut;           /* DLM_BOX_CUT: per-user budget sum_j x_ij <= cut, finite and > 0 (ignored
                            otherwise); such handles take one family and no count constraint, batch
                            only with other box-cut handles, and sweep with their own kernel */
+  const struct dlm_shard* shard; /* NULL, or: these rows are one shard of a user-sharded instance
+                                    (see "User-sharded instances" below) */
 } dlm_problem_desc;
 
 /* Solver options (zero-initialised fields take the defaults).  The mapping
@@ -118,7 +122,11 @@ typedef struct {
                             after a step whose direction opposes the momentum in the step metric,
                             sum_j (lam+_j - y_j)(lam+_j - lam_j) / step_j < 0 (O'Donoghue &
                             Candes 2015); 0 (default): the paper's schedule-only restarts */
-  int32_t reserved[3];
+  int32_t topk;          /* one-family sweeps: largest values of a row tracked in the first pass, with
+                            the positions of all but the last: 0 or 4 (default), or 8 -- rows with up
+                            to seven active edges then take their threshold without the iteration
+                            over the row (more work per edge, fewer re-reads of the row) */
+  int32_t reserved[2];
 } dlm_options;
 
 /* Result of a certified-gap evaluation at the current iterate lam (one extra
@@ -206,7 +214,8 @@ dlm_status dlm_get_options(dlm_problem* p, dlm_options* opt);
 /* Mapping tuner (the paper has no counterpart; its kernels have one fixed
  * mapping).  Times `iters` iterations (after one warm-up iteration) of every
  * candidate mapping -- block_threads {1024, 512}, mapping {1, 2, 3},
- * coop_max {1, 6, 12, 20, 33} -- from the handle's current state, restores
+ * coop_max {1, 6, 12, 20, 33}, then topk {4, 8} with the best of those (one
+ * family, not DLM_BOX_CUT) -- from the handle's current state, restores
  * that state (lam, y, theta, counter) after each trial, and keeps the mapping
  * whose sweeps took the least device time.  Writes it to *chosen and the mean
  * sweep time of the winner in milliseconds to *sweep_ms (either may be NULL).
@@ -277,6 +286,14 @@ dlm_status dlm_step_timed(dlm_problem* p, int64_t n_iters, double* sweep_ms, dou
  * pointer per user). */
 dlm_status dlm_get_info(dlm_problem* p, int64_t* num_users, int64_t* num_items, int64_t* nnz,
                         int64_t* bytes_per_iter);
+
+/* Wall-clock seconds dlm_create spent, by phase: out[0] host inputs copied
+ * to the device (0 for device inputs), out[1] validation (row pointers,
+ * items, values, distinct items per row, capacities), out[2] degree sort of
+ * the users and slice sizes, out[3] slice layout and per-item sums, out[4]
+ * the handle's own arrays, tables and schedule, out[5] the whole call.  The
+ * first min(n, 6) entries are written (host array). */
+dlm_status dlm_get_setup_seconds(dlm_problem* p, double* out, int32_t n);
 
 /* Free the handle and its device memory.  The instance's large arrays (the
  * sliced layout, set-up scratch) come from a stream-ordered memory pool per
@@ -408,6 +425,76 @@ dlm_status dlm_calculate_static(int64_t num_users, int64_t num_items, int64_t nn
                                 const int32_t* item_idx, const float* c, const float* a, const double* b,
                                 int32_t kind, double z, const float* lambda, double gamma, double* g, float* grad,
                                 float* x, void* stream);
+
+/* User-sharded instances (Sec. 4.4: the paper splits the sources across
+ * GPUs, sums the gradient on one rank and broadcasts lambda; here every rank
+ * sums and updates).  Users are independent given the dual, so each rank
+ * holds a contiguous range of users (its rows, in dlm_problem_desc) and the
+ * full capacity vector b; after every sweep the ranks add their partial
+ * item sums -- exact 64-bit fixed-point integers, so the sum is the same in
+ * any order and on every rank -- and each rank takes the same update.  The
+ * iterates are bit-identical to those of one handle holding every row.  One
+ * capacity family; no batches.
+ *
+ * Set-up, on every rank:
+ *  1. dlm_shard_local: validates the rows and fills the rank's statistics
+ *     (nnz, active_users, max_abs_a, max_abs_c, a_nonneg) and its item
+ *     degrees (host int64 [num_items]);
+ *  2. the ranks combine them: nnz, active_users and the item degrees by
+ *     sums, max_abs_a and max_abs_c by maxima, a_nonneg by minimum;
+ *     max_item_degree = the largest summed item degree;
+ *  3. dlm_shard_item_sums with the combined statistics: the rank's
+ *     fixed-point sums of a_ij^2 and a_ij per item; the ranks add them
+ *     (int64 sums) into item_sq and item_sum;
+ *  4. dlm_create with desc.shard pointing at the combined dlm_shard, whose
+ *     exchange buffers the caller allocates (device memory, kept for the
+ *     handle's life).
+ * Each iteration: dlm_shard_sweep, then the ranks add `exchange` (int64
+ * sum, in place), then dlm_shard_update.  The iterates equal those of one
+ * handle holding every row when both take every row's threshold in its own
+ * lane (dlm_options.coop_max = 1): the warp-cooperative path for rows with
+ * many active edges sums in another order, and whether a row takes it
+ * depends on the other rows of its slice.  A certified gap: dlm_shard_cert_sweep,
+ * the ranks add `cert_exchange` (int64) and `cert_obj` (float64), then
+ * dlm_shard_cert_finish.  All work is ordered on the handle's stream; the
+ * sums must be complete on that stream before the call that follows them.
+ * dlm_step, dlm_solve and dlm_get_stats are not valid on a shard handle
+ * (DLM_ERR_UNSUPPORTED): each rank alone sees only part of the sums. */
+typedef struct dlm_shard {
+  int64_t nnz;             /* edges, all shards */
+  int64_t active_users;    /* users with at least one edge, all shards */
+  int64_t max_item_degree; /* the largest item degree, degrees summed over the shards */
+  double max_abs_a;        /* largest |a| over the shards */
+  double max_abs_c;        /* largest |c| over the shards */
+  int32_t a_nonneg;        /* 1 when no shard has a negative a */
+  int32_t reserved;
+  const int64_t* item_sq;  /* host [num_items]: fixed-point sum_i a_ij^2 over the shards */
+  const int64_t* item_sum; /* host [num_items]: fixed-point sum_i a_ij over the shards */
+  int64_t* exchange;       /* device [num_items + 2]: the iteration's partial sums (item sums, count, objective) */
+  int64_t* cert_exchange;  /* device [3 num_items + 1]: the certificate's partial sums */
+  double* cert_obj;        /* device [1]: the certificate's objective partial */
+} dlm_shard;
+
+/* Step 1 of the set-up above: statistics of this rank's rows (a
+ * dlm_problem_desc without `shard`); item_degree: host int64 [num_items].
+ * Validates as dlm_create does.  Synchronous. */
+dlm_status dlm_shard_local(const dlm_problem_desc* desc, void* stream, dlm_shard* local, int64_t* item_degree);
+/* Step 3: this rank's fixed-point item sums at the exponents the combined
+ * statistics `global` (max_item_degree, max_abs_a) fix; item_sq, item_sum:
+ * host int64 [num_items].  Synchronous. */
+dlm_status dlm_shard_item_sums(const dlm_problem_desc* desc, const dlm_shard* global, void* stream, int64_t* item_sq,
+                               int64_t* item_sum);
+/* The iteration sweep at y: this rank's partial sums into `exchange`. */
+dlm_status dlm_shard_sweep(dlm_problem* p);
+/* The accelerated step from the summed `exchange` (identical on every rank);
+ * clears `exchange` for the next sweep. */
+dlm_status dlm_shard_update(dlm_problem* p);
+/* The certificate sweep at lam: partial sums into `cert_exchange` and
+ * `cert_obj`. */
+dlm_status dlm_shard_cert_sweep(dlm_problem* p);
+/* The certified gap from the summed certificate buffers (see dlm_stats);
+ * clears them.  Synchronous. */
+dlm_status dlm_shard_cert_finish(dlm_problem* p, dlm_stats* out);
 
 /* Thread-local message describing the last failure on this thread ("" if none). */
 const char* dlm_last_error(void);

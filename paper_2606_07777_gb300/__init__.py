@@ -21,7 +21,8 @@ __all__ = [
     "dlm_set_state", "dlm_get_info", "dlm_step_timed", "dlm_calculate_static", "dlm_destroy", "dlm_last_error",
     "dlm_get_options", "dlm_autotune", "dlm_get_trajectory", "dlm_release_cached_memory", "Batch", "dlm_batch_create", "dlm_batch_set_options", "dlm_batch_autotune",
     "dlm_batch_step", "dlm_batch_step_timed", "dlm_batch_get_stats", "dlm_batch_solve", "dlm_batch_destroy",
-    "WarmStart", "WS_FEATURES",
+    "WarmStart", "WS_FEATURES", "ShardedSolver", "shard_local", "shard_combine", "shard_item_sums",
+    "allreduce_shard_stats", "partition_users",
 ]
 
 WS_FEATURES = 7
@@ -46,13 +47,22 @@ class ProblemDesc(ctypes.Structure):
                 ("row_ptr", ctypes.c_void_p), ("item_idx", ctypes.c_void_p), ("c", ctypes.c_void_p),
                 ("a", ctypes.c_void_p), ("b", ctypes.c_void_p), ("val_dtype", ctypes.c_int32),
                 ("kind", ctypes.c_int32), ("z", ctypes.c_double), ("memspace", ctypes.c_int32),
-                ("num_families", ctypes.c_int32), ("cut", ctypes.c_double)]
+                ("num_families", ctypes.c_int32), ("cut", ctypes.c_double), ("shard", ctypes.c_void_p)]
+
+
+class Shard(ctypes.Structure):
+    """dlm_shard: statistics of a user-sharded instance and its exchange buffers."""
+    _fields_ = [("nnz", ctypes.c_int64), ("active_users", ctypes.c_int64), ("max_item_degree", ctypes.c_int64),
+                ("max_abs_a", ctypes.c_double), ("max_abs_c", ctypes.c_double), ("a_nonneg", ctypes.c_int32),
+                ("reserved", ctypes.c_int32), ("item_sq", ctypes.c_void_p), ("item_sum", ctypes.c_void_p),
+                ("exchange", ctypes.c_void_p), ("cert_exchange", ctypes.c_void_p), ("cert_obj", ctypes.c_void_p)]
 
 
 class Options(ctypes.Structure):
     _fields_ = [("gap_every", ctypes.c_int32), ("precondition", ctypes.c_int32), ("mapping", ctypes.c_int32),
                 ("graph_iters", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32), ("coop_max", ctypes.c_int32),
-                ("block_threads", ctypes.c_int32), ("restart", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3)]
+                ("block_threads", ctypes.c_int32), ("restart", ctypes.c_int32), ("topk", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 2)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}
@@ -95,6 +105,13 @@ _SIGS = {
     "dlm_set_state": [_vp, _vp, _vp, ctypes.POINTER(State), _i32],
     "dlm_get_trajectory": [_vp, _i64, _i64, _vp],
     "dlm_release_cached_memory": [],
+    "dlm_get_setup_seconds": [_vp, _vp, _i32],
+    "dlm_shard_local": [ctypes.POINTER(ProblemDesc), _vp, ctypes.POINTER(Shard), _vp],
+    "dlm_shard_item_sums": [ctypes.POINTER(ProblemDesc), ctypes.POINTER(Shard), _vp, _vp, _vp],
+    "dlm_shard_sweep": [_vp],
+    "dlm_shard_update": [_vp],
+    "dlm_shard_cert_sweep": [_vp],
+    "dlm_shard_cert_finish": [_vp, ctypes.POINTER(Stats)],
     "dlm_get_info": [_vp, ctypes.POINTER(_i64), ctypes.POINTER(_i64), ctypes.POINTER(_i64), ctypes.POINTER(_i64)],
     "dlm_step_timed": [_vp, _i64, ctypes.POINTER(_d), ctypes.POINTER(_d), ctypes.POINTER(_d)],
     "dlm_calculate_static": [_i64, _i64, _i64, _vp, _vp, _vp, _vp, _vp, _i32, _d, _vp, _d, _vp, _vp, _vp, _vp],
@@ -342,12 +359,36 @@ def dlm_batch_destroy(bt):
 
 
 def _options(gap_every=0, precondition=False, mapping=0, graph_iters=0, ctas_per_sm=0, coop_max=0, block_threads=0,
-             restart=False):
+             restart=False, topk=0):
     o = Options()
     o.gap_every, o.precondition, o.mapping = gap_every, int(bool(precondition)), mapping
     o.graph_iters, o.ctas_per_sm, o.coop_max, o.block_threads = graph_iters, ctas_per_sm, coop_max, block_threads
     o.restart = int(bool(restart))
+    o.topk = int(topk)
     return o
+
+
+def _desc(row_ptr, col, c, a, b, num_items=None, kind=DLM_SIMPLEX_LE, z=1.0, bf16=None, cut=None):
+    """A ProblemDesc for the arrays (CUDA tensors: device memspace; CPU
+    tensors / numpy arrays: host memspace); returns (desc, bf16)."""
+    import torch
+
+    dev = getattr(row_ptr, "is_cuda", False)
+    if bf16 is None:
+        bf16 = getattr(c, "dtype", None) in (torch.bfloat16,) or str(getattr(c, "dtype", "")) == "uint16"
+    desc = ProblemDesc()
+    # several capacity families: a is [nnz, m] (edge-major), b [m, num_items]
+    desc.num_families = int(a.shape[1]) if len(a.shape) == 2 else 1
+    desc.num_items = int(num_items if num_items is not None else b.shape[-1])
+    desc.num_users = int(row_ptr.shape[0] - 1)
+    desc.nnz = int(col.shape[0])
+    desc.row_ptr, desc.item_idx, desc.c, desc.a, desc.b = (_ptr(row_ptr), _ptr(col), _ptr(c), _ptr(a), _ptr(b))
+    desc.val_dtype = DLM_BF16 if bf16 else DLM_F32
+    desc.kind, desc.z = int(kind), float(z)
+    desc.cut = float(cut) if cut is not None else 0.0  # DLM_BOX_CUT: per-user budget
+    desc.memspace = DLM_MEM_DEVICE if dev else DLM_MEM_HOST
+    desc.shard = None
+    return desc, bool(bf16)
 
 
 class Solver:
@@ -359,27 +400,15 @@ class Solver:
     ``bf16=True``)."""
 
     def __init__(self, row_ptr, col, c, a, b, num_items=None, kind=DLM_SIMPLEX_LE, z=1.0, bf16=None, stream=None,
-                 cut=None):
+                 cut=None, shard=None):
         import torch
 
         self._torch = torch
-        dev = getattr(row_ptr, "is_cuda", False)
-        if bf16 is None:
-            bf16 = getattr(c, "dtype", None) in (torch.bfloat16,) or str(getattr(c, "dtype", "")) == "uint16"
-        # several capacity families: a is [nnz, m] (edge-major), b [m, num_items]
-        self.num_families = int(a.shape[1]) if len(a.shape) == 2 else 1
-        self.num_items = int(num_items if num_items is not None else b.shape[-1])
-        self.num_users = int(row_ptr.shape[0] - 1)
-        self.nnz = int(col.shape[0])
-        self.bf16 = bool(bf16)
-        desc = ProblemDesc()
-        desc.num_families = self.num_families
-        desc.num_users, desc.num_items, desc.nnz = self.num_users, self.num_items, self.nnz
-        desc.row_ptr, desc.item_idx, desc.c, desc.a, desc.b = (_ptr(row_ptr), _ptr(col), _ptr(c), _ptr(a), _ptr(b))
-        desc.val_dtype = DLM_BF16 if self.bf16 else DLM_F32
-        desc.kind, desc.z = int(kind), float(z)
-        desc.cut = float(cut) if cut is not None else 0.0  # DLM_BOX_CUT: per-user budget
-        desc.memspace = DLM_MEM_DEVICE if dev else DLM_MEM_HOST
+        desc, self.bf16 = _desc(row_ptr, col, c, a, b, num_items, kind, z, bf16, cut)
+        self.num_families = desc.num_families
+        self.num_items, self.num_users, self.nnz = desc.num_items, desc.num_users, desc.nnz
+        if shard is not None:
+            desc.shard = ctypes.addressof(shard)
         self.device = torch.device("cuda", torch.cuda.current_device())
         if stream is None:
             stream = torch.cuda.current_stream(self.device)
@@ -407,9 +436,9 @@ class Solver:
         dlm_set_schedule(self.h, gamma0, gamma0 if gamma_end is None else gamma_end, factor, iters_per_stage)
 
     def set_options(self, gap_every=0, precondition=False, mapping=0, graph_iters=0, ctas_per_sm=0, coop_max=0,
-                    block_threads=0, restart=False):
+                    block_threads=0, restart=False, topk=0):
         dlm_set_options(self.h, _options(gap_every, precondition, mapping, graph_iters, ctas_per_sm, coop_max,
-                                         block_threads, restart))
+                                         block_threads, restart, topk))
 
     def options(self) -> Options:
         return dlm_get_options(self.h)
@@ -475,6 +504,15 @@ class Solver:
     def info(self):
         return dlm_get_info(self.h)
 
+    def setup_seconds(self):
+        """dlm_create's wall time by phase (dict)."""
+        import numpy as np
+
+        v = np.zeros(6)
+        _call("dlm_get_setup_seconds", self.h, _ptr(v), 6)
+        return dict(zip(("host_to_device", "validate", "degree_sort", "layout_and_item_sums", "handle_and_tables",
+                         "total"), v.tolist()))
+
     def trajectory(self, first_iter, n):
         """Dual objective g(y_t) of iterations first_iter .. first_iter + n - 1."""
         return dlm_get_trajectory(self.h, first_iter, n)
@@ -505,9 +543,9 @@ class Batch:
         except Exception:
             pass
 
-    def set_options(self, gap_every=0, mapping=0, graph_iters=0, ctas_per_sm=0, coop_max=0, block_threads=0):
+    def set_options(self, gap_every=0, mapping=0, graph_iters=0, ctas_per_sm=0, coop_max=0, block_threads=0, topk=0):
         dlm_batch_set_options(self.bt, _options(gap_every, False, mapping, graph_iters, ctas_per_sm, coop_max,
-                                                block_threads))
+                                                block_threads, False, topk))
 
     def autotune(self, iters=3):
         return dlm_batch_autotune(self.bt, iters)
@@ -623,3 +661,198 @@ class WarmStart:
 
         return np.concatenate([np.asarray(P[k], dtype=np.float32).ravel() for k in ("W1", "b1", "W2", "b2", "w3",
                                                                                    "b3")])
+
+
+# ---------------------------------------------------------------------------
+# User-sharded instances (include/dlm.h, "User-sharded instances")
+# ---------------------------------------------------------------------------
+
+def partition_users(row_ptr, nparts):
+    """Contiguous user ranges [u0, u1) of about equal edge counts, one per part."""
+    import numpy as np
+
+    rp = np.asarray(row_ptr)
+    nnz = int(rp[-1])
+    cuts = [0]
+    for k in range(1, nparts):
+        cuts.append(int(np.searchsorted(rp, nnz * k // nparts, side="left")))
+    cuts.append(len(rp) - 1)
+    return [(cuts[k], max(cuts[k], cuts[k + 1])) for k in range(nparts)]
+
+
+def shard_local(row_ptr, col, c, a, b, num_items=None, kind=DLM_SIMPLEX_LE, z=1.0, bf16=None, cut=None,
+                stream=None):
+    """This rank's statistics: (dict(nnz, active_users, max_abs_a, max_abs_c,
+    a_nonneg), item degrees as int64 numpy [num_items])."""
+    import numpy as np
+
+    desc, _ = _desc(row_ptr, col, c, a, b, num_items, kind, z, bf16, cut)
+    loc = Shard()
+    deg = np.empty(desc.num_items, dtype=np.int64)
+    _call("dlm_shard_local", ctypes.byref(desc), stream, ctypes.byref(loc), _ptr(deg))
+    return dict(nnz=loc.nnz, active_users=loc.active_users, max_abs_a=loc.max_abs_a, max_abs_c=loc.max_abs_c,
+                a_nonneg=loc.a_nonneg), deg
+
+
+def shard_combine(locals_, degrees):
+    """The whole instance's statistics from every rank's (the sums, maxima and
+    minimum of the protocol)."""
+    import numpy as np
+
+    deg = np.sum(np.stack(degrees), axis=0)
+    return dict(nnz=int(sum(x["nnz"] for x in locals_)), active_users=int(sum(x["active_users"] for x in locals_)),
+                max_abs_a=float(max(x["max_abs_a"] for x in locals_)),
+                max_abs_c=float(max(x["max_abs_c"] for x in locals_)),
+                a_nonneg=int(min(x["a_nonneg"] for x in locals_)), max_item_degree=int(deg.max()) if deg.size else 0)
+
+
+def allreduce_shard_stats(local, degree, group=None, device=None):
+    """shard_combine over the ranks of a torch.distributed process group
+    (int64 sums of the counts and degrees, maxima of the bounds, minimum of
+    the sign flag): every rank gets the same combined statistics."""
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    dev = device if device is not None else torch.device("cpu")
+    counts = torch.tensor([local["nnz"], local["active_users"]], dtype=torch.int64, device=dev)
+    deg = torch.from_numpy(np.ascontiguousarray(degree, dtype=np.int64)).to(dev)
+    bounds = torch.tensor([local["max_abs_a"], local["max_abs_c"], -float(local["a_nonneg"])], dtype=torch.float64,
+                          device=dev)
+    dist.all_reduce(counts, op=dist.ReduceOp.SUM, group=group)
+    dist.all_reduce(deg, op=dist.ReduceOp.SUM, group=group)
+    dist.all_reduce(bounds, op=dist.ReduceOp.MAX, group=group)
+    c, d, bd = counts.cpu().numpy(), deg.cpu().numpy(), bounds.cpu().numpy()
+    return dict(nnz=int(c[0]), active_users=int(c[1]), max_abs_a=float(bd[0]), max_abs_c=float(bd[1]),
+                a_nonneg=int(-bd[2]), max_item_degree=int(d.max()) if d.size else 0)
+
+
+def _shard_struct(g, item_sq=None, item_sum=None):
+    sh = Shard()
+    sh.nnz, sh.active_users, sh.max_item_degree = g["nnz"], g["active_users"], g["max_item_degree"]
+    sh.max_abs_a, sh.max_abs_c, sh.a_nonneg = g["max_abs_a"], g["max_abs_c"], g["a_nonneg"]
+    sh.item_sq, sh.item_sum = _ptr(item_sq), _ptr(item_sum)
+    return sh
+
+
+def shard_item_sums(row_ptr, col, c, a, b, global_stats, num_items=None, kind=DLM_SIMPLEX_LE, z=1.0, bf16=None,
+                    cut=None, stream=None):
+    """This rank's fixed-point item sums (sum a^2, sum a) at the exponents the
+    combined statistics fix: two int64 numpy arrays [num_items]."""
+    import numpy as np
+
+    desc, _ = _desc(row_ptr, col, c, a, b, num_items, kind, z, bf16, cut)
+    sq = np.empty(desc.num_items, dtype=np.int64)
+    s1 = np.empty(desc.num_items, dtype=np.int64)
+    g = _shard_struct(global_stats)
+    _call("dlm_shard_item_sums", ctypes.byref(desc), ctypes.byref(g), stream, _ptr(sq), _ptr(s1))
+    return sq, s1
+
+
+class ShardedSolver(Solver):
+    """One rank's shard (a contiguous range of users, with the full capacity
+    vector b) of a user-sharded instance.  `global_stats`, `item_sq`,
+    `item_sum` are the combined statistics and item sums (shard_combine /
+    allreduce_shard_stats, then the summed shard_item_sums).  Each iteration
+    is sweep(), the ranks' sum of `exchange`, update(); `reduce(tensor)` adds
+    a tensor over the ranks in place (torch.distributed.all_reduce when a
+    process group is given)."""
+
+    def __init__(self, row_ptr, col, c, a, b, num_items, global_stats, item_sq, item_sum, kind=DLM_SIMPLEX_LE, z=1.0,
+                 bf16=None, stream=None, cut=None, reduce=None):
+        import numpy as np
+        import torch
+
+        J = int(num_items)
+        dev = torch.device("cuda", torch.cuda.current_device())
+        self.exchange = torch.zeros(J + 2, dtype=torch.int64, device=dev)
+        self.cert_exchange = torch.zeros(3 * J + 1, dtype=torch.int64, device=dev)
+        self.cert_obj = torch.zeros(1, dtype=torch.float64, device=dev)
+        self._sq = np.ascontiguousarray(item_sq, dtype=np.int64)
+        self._s1 = np.ascontiguousarray(item_sum, dtype=np.int64)
+        self._shard = _shard_struct(global_stats, self._sq, self._s1)
+        self._shard.exchange = self.exchange.data_ptr()
+        self._shard.cert_exchange = self.cert_exchange.data_ptr()
+        self._shard.cert_obj = self.cert_obj.data_ptr()
+        self.reduce = reduce
+        self._gamma_end = 1e-2  # the handle's initial fixed ridge
+        super().__init__(row_ptr, col, c, a, b, J, kind=kind, z=z, bf16=bf16, stream=stream, cut=cut,
+                         shard=self._shard)
+        # every row's threshold in its own lane: the result of a row then does
+        # not depend on which users share its slice on this rank
+        self.set_options(coop_max=1)
+
+    @classmethod
+    def distributed(cls, row_ptr, col, c, a, b, num_items, group=None, **kw):
+        """The whole set-up over a torch.distributed process group (NCCL with
+        CUDA tensors, or any backend for the host-side statistics)."""
+        import numpy as np
+        import torch
+        import torch.distributed as dist
+
+        backend = dist.get_backend(group)
+        dev = torch.device("cuda", torch.cuda.current_device()) if backend == "nccl" else torch.device("cpu")
+        opts = {k: kw[k] for k in ("kind", "z", "bf16", "cut") if k in kw}
+        loc, deg = shard_local(row_ptr, col, c, a, b, num_items, **opts)
+        g = allreduce_shard_stats(loc, deg, group, dev)
+        sq, s1 = shard_item_sums(row_ptr, col, c, a, b, g, num_items, **opts)
+        t = torch.from_numpy(np.stack([sq, s1])).to(dev)
+        dist.all_reduce(t, op=dist.ReduceOp.SUM, group=group)
+        sums = t.cpu().numpy()
+
+        def reduce(x):
+            dist.all_reduce(x, op=dist.ReduceOp.SUM, group=group)
+
+        return cls(row_ptr, col, c, a, b, num_items, g, sums[0], sums[1], reduce=reduce, **kw)
+
+    def sweep(self):
+        _call("dlm_shard_sweep", self.h)
+
+    def update(self):
+        _call("dlm_shard_update", self.h)
+
+    def step(self, n):
+        for _ in range(int(n)):
+            self.sweep()
+            self.reduce(self.exchange)
+            self.update()
+
+    def cert_sweep(self):
+        _call("dlm_shard_cert_sweep", self.h)
+
+    def cert_finish(self) -> Stats:
+        st = Stats()
+        _call("dlm_shard_cert_finish", self.h, ctypes.byref(st))
+        return st
+
+    def stats(self) -> Stats:
+        self.cert_sweep()
+        self.reduce(self.cert_exchange)
+        self.reduce(self.cert_obj)
+        return self.cert_finish()
+
+    def solve(self, target_rel_gap, max_iters, gap_every=50) -> Stats:
+        """dlm_solve's loop over the ranks: the certified gap every gap_every
+        iterations once gamma is at its final value."""
+        import time
+
+        t0 = time.perf_counter()
+        done = 0
+        while True:
+            st = self.stats()
+            if st.status != DLM_OK:
+                break
+            if st.gamma == self._gamma_end and st.rel_gap <= target_rel_gap:
+                st.converged = 1
+                break
+            if done >= max_iters:
+                break
+            n = min(gap_every, max_iters - done)
+            self.step(n)
+            done += n
+        st.seconds = time.perf_counter() - t0
+        return st
+
+    def set_schedule(self, gamma0, gamma_end=None, factor=0.5, iters_per_stage=1 << 30):
+        self._gamma_end = gamma0 if gamma_end is None else gamma_end
+        super().set_schedule(gamma0, gamma_end, factor, iters_per_stage)

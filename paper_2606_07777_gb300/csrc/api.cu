@@ -118,6 +118,9 @@ struct Runner {
   int smemJ = 0;
   int win = 0;  // item window of certificate sweeps (smemJ when their arrays fit at once)
   int graph_iters = 10;
+  int topk = 4;  // one-family sweeps: values tracked per row in the first pass
+  int upd_ctas = 1;      // update grid width (the largest member's)
+  bool upd_test = false; // some member has the adaptive restart (a test kernel runs first)
   InstDesc *inst_iter = nullptr, *inst_stats = nullptr;
   double* cuts = nullptr;  // per-instance DLM_BOX_CUT budgets (box-cut runners only)
   UpdInst* upd = nullptr;
@@ -170,12 +173,24 @@ struct dlm_problem {
   std::vector<double> h_gram;  // [m m J]: sum_i a_kij a_lij
   int64_t MJ() const { return static_cast<int64_t>(m) * J; }
   int64_t D() const { return MJ() + (count_on ? 1 : 0); }  // dual dimension
+  // Partial sums: xsum = [A x (m J) | count | objective] of the iteration
+  // sweep, csum = [A x (m J) | C x (J) | Q x (J) | count] of the certificate
+  // sweep (the views below point into them).  A shard of a user-sharded
+  // instance uses the caller's buffers, which the ranks add up in place.
+  unsigned long long *xsum = nullptr, *csum = nullptr;
+  double* cobj = nullptr;    // shard: the certificate's objective partial
+  bool own_sums = true;
+  bool sharded = false;
+  int64_t glob_nnz = 0, glob_users = 0;  // the whole instance's edges and users with edges
   double *lam64 = nullptr, *y64 = nullptr;  // the iterate (FP64)
   float *lam = nullptr, *y = nullptr;       // its FP32 copies, read by the sweeps
   unsigned long long *acc = nullptr, *acc2 = nullptr, *accC = nullptr, *accQ = nullptr;
   unsigned long long* objq = nullptr;       // fixed-point objective sum of the iteration sweep
   int sO = 0;                               // its exponent
   double* traj = nullptr;                   // [kTrajCap] g(y_t) per iteration (ring)
+  double* upd_part = nullptr;               // update partials [2 update_ctas(m J + 1) + 1]
+  unsigned* upd_ticket = nullptr;           // [2]
+  int32_t* upd_flag = nullptr;
   int64_t traj_from = 0;                    // first iteration whose trajectory entry is valid
   double *gamma_tab = nullptr, *calc_gamma = nullptr, *stats_out = nullptr;
   int64_t nstages = 1, gamma_tab_cap = 0;
@@ -193,6 +208,7 @@ struct dlm_problem {
   dlm_options opt{};
   std::vector<double> h_gamma_tab;
   double last_solve_seconds = 0;
+  double setup_s[6] = {0, 0, 0, 0, 0, 0};  // see dlm_get_setup_seconds
 
   Runner run;
 };
@@ -251,6 +267,7 @@ StatsInst base_stats(const dlm_problem* p, const Runner& R, int i) {
   s.inv_sN = std::ldexp(1.0, -p->sN);
   s.count_M = p->count_M;
   s.m = p->m;
+  s.obj_in = nullptr;
   return s;
 }
 
@@ -432,6 +449,10 @@ dlm_status write_tables(Runner& R) {
     u.acc = p->acc;
     u.objq = p->objq;
     u.traj = p->traj;
+    u.part = p->upd_part;
+    u.ticket = p->upd_ticket;
+    u.flag = p->upd_flag;
+    u.nct = update_ctas(p->D());
     u.iters_per_stage = p->ips;
     u.curv_max = p->curv_max;
     u.inv_scaleG = std::ldexp(1.0, -p->sG);
@@ -447,6 +468,7 @@ dlm_status write_tables(Runner& R) {
     u.ncap = static_cast<int32_t>(p->MJ());
     up[i] = u;
     st[i] = base_stats(p, R, i);
+    st[i].obj_in = p->sharded ? p->cobj : nullptr;
     st[i].lam = p->lam;
     st[i].gamma = &p->state->gamma;
     st[i].grad_out = nullptr;
@@ -455,6 +477,12 @@ dlm_status write_tables(Runner& R) {
   CK(cudaMemcpy(R.inst_iter, it.data(), sizeof(InstDesc) * n, cudaMemcpyHostToDevice));
   CK(cudaMemcpy(R.inst_stats, ss.data(), sizeof(InstDesc) * n, cudaMemcpyHostToDevice));
   CK(cudaMemcpy(R.upd, up.data(), sizeof(UpdInst) * n, cudaMemcpyHostToDevice));
+  R.upd_ctas = 1;
+  R.upd_test = false;
+  for (const UpdInst& u : up) {
+    R.upd_ctas = std::max(R.upd_ctas, u.nct);
+    R.upd_test = R.upd_test || u.adaptive_restart;
+  }
   CK(cudaMemcpy(R.st_stats, st.data(), sizeof(StatsInst) * n, cudaMemcpyHostToDevice));
   return DLM_OK;
 }
@@ -525,6 +553,7 @@ SweepLaunch launch_of(const Runner& R, const InstDesc* tab) {
   L.units = R.h_units.empty() ? nullptr : R.units;
   L.nunits = static_cast<int32_t>(R.h_units.size());
   L.ctr = R.ctr;
+  L.topk = R.topk;
   return L;
 }
 
@@ -543,7 +572,7 @@ cudaError_t dispatch_sweep(const Runner& R, const SweepLaunch& L, bool stats, bo
 
 dlm_status enqueue_iteration(Runner& R) {
   CK(dispatch_sweep(R, launch_of(R, R.inst_iter), false, R.bf16));
-  CK(launch_update(R.upd, static_cast<int>(R.probs.size()), R.stream));
+  CK(launch_update(R.upd, static_cast<int>(R.probs.size()), R.upd_ctas, R.upd_test, R.stream));
   return DLM_OK;
 }
 
@@ -600,7 +629,7 @@ dlm_status runner_step_timed(Runner& R, int64_t n_iters, double* sweep_ms, doubl
   for (int64_t i = 0; i < n_iters; ++i) {
     CK(dispatch_sweep(R, L, false, R.bf16));
     CK(cudaEventRecord(R.events[2 * i + 1], R.stream));
-    CK(launch_update(R.upd, n, R.stream));
+    CK(launch_update(R.upd, n, R.upd_ctas, R.upd_test, R.stream));
     CK(cudaEventRecord(R.events[2 * i + 2], R.stream));
   }
   CK(cudaStreamSynchronize(R.stream));
@@ -636,6 +665,9 @@ dlm_status runner_configure(Runner& R, const dlm_options& o, bool force) {
       assign2 = R.probs.size() > 1 ? kAssignContiguous : kAssignInterleaved;
   R.coop_max = o.coop_max > 0 ? o.coop_max : kDefaultCoopMax;
   R.graph_iters = o.graph_iters > 0 ? o.graph_iters : 10;
+  const int topk = o.topk == 8 ? 8 : 4;
+  if (topk != R.topk) invalidate_graph(R);
+  R.topk = topk;
   if (force || grid != R.grid || threads != R.threads || assign2 != R.assign) {
     R.grid = grid;
     R.threads = threads;
@@ -676,11 +708,13 @@ void free_problem(dlm_problem* p) {
                     p->lay.udeg,      p->lay.n2,      p->a_ext};
   for (void* q : pooled) dev_free(q, s);
   if (s) cudaStreamSynchronize(s);
-  cudaFree(p->cnt);
-  cudaFree(p->cnt2);
-  void* ptrs[] = {p->b,         p->curv,      p->lam,       p->y,         p->acc,   p->acc2,      p->accC,
-                  p->accQ,      p->gamma_tab, p->calc_gamma, p->stats_out, p->state, p->inst_calc, p->st_calc,
-                  p->lam64,     p->y64,       p->objq,      p->traj};
+  if (p->own_sums) {
+    cudaFree(p->xsum);
+    cudaFree(p->csum);
+  }
+  void* ptrs[] = {p->b,         p->curv,      p->lam,      p->y,      p->gamma_tab, p->calc_gamma, p->stats_out,
+                  p->state,     p->inst_calc, p->st_calc,  p->lam64,  p->y64,       p->traj,       p->upd_part,
+                  p->upd_ticket, p->upd_flag};
   for (void* q : ptrs) cudaFree(q);
   cudaFreeHost(p->h_out);
   cudaFreeHost(p->h_inst);
@@ -719,7 +753,7 @@ dlm_status upload_steps(dlm_problem* p) {
     hmax = hq > hmax ? hq : hmax;
   }
   if (p->count_on) {
-    const double hc = static_cast<double>(p->nnz) + tot;
+    const double hc = static_cast<double>(p->glob_nnz) + tot;
     h[MJ] = hc;
     hmax = hc > hmax ? hc : hmax;
   }
@@ -734,7 +768,7 @@ dlm_status upload_steps(dlm_problem* p) {
 // (every x_ij <= z; on the simplex sum_j x_ij <= z per user).
 int objective_shift(const dlm_problem* p) {
   const bool simplex = p->kind == DLM_SIMPLEX_LE || p->kind == DLM_SIMPLEX_EQ;
-  const double units = static_cast<double>(simplex ? p->lay.num_active_users : p->nnz);
+  const double units = static_cast<double>(simplex ? p->glob_users : p->glob_nnz);
   const double per = p->z * (p->lay.max_abs_c + 0.5 * p->gamma0 * p->z);
   const double bound = (units > 0 ? units : 1.0) * (per > 0 ? per : 1.0);
   return std::max(fixed_point_shift(bound), 0);
@@ -862,6 +896,29 @@ dlm_status tune(Runner& R, dlm_options base, int iters, dlm_options* chosen, dou
       }
     }
   }
+  // the first-pass scan width, with the mapping chosen above (one-family
+  // sweeps; rows with many active edges resolve without the threshold
+  // iteration when eight values are tracked)
+  bool one_family = true;
+  for (const dlm_problem* p : R.probs) one_family = one_family && p->m == 1 && p->kind != DLM_BOX_CUT;
+  if (one_family) {
+    dlm_options o = best;
+    o.topk = best.topk == 8 ? 4 : 8;
+    double sw = 0;
+    st = runner_configure(R, o, false);
+    if (st == DLM_OK) st = restore_state(R, S);
+    if (st == DLM_OK) st = runner_step_timed(R, 1, nullptr, nullptr, nullptr);
+    if (st == DLM_OK) st = restore_state(R, S);
+    if (st == DLM_OK) st = runner_step_timed(R, iters, &sw, nullptr, nullptr);
+    if (st != DLM_OK) {
+      free_saved(S);
+      return st;
+    }
+    if (sw < best_ms) {
+      best_ms = sw;
+      best = o;
+    }
+  }
   st = runner_configure(R, best, false);
   if (st == DLM_OK) st = restore_state(R, S);
   free_saved(S);
@@ -893,8 +950,68 @@ dlm_status check_options(const dlm_options* opt) {
   if (opt->gap_every < 0 || opt->graph_iters < 0 || opt->mapping < 0 || opt->mapping > 3 || opt->ctas_per_sm < 0 ||
       opt->ctas_per_sm > 4 || opt->coop_max < 0 || opt->coop_max > 33 ||
       (opt->block_threads != 0 && opt->block_threads != 512 && opt->block_threads != 1024) || opt->restart < 0 ||
-      opt->restart > 1)
+      opt->restart > 1 || (opt->topk != 0 && opt->topk != 4 && opt->topk != 8))
     return fail(DLM_ERR_INVALID_ARG, "bad option value");
+  return DLM_OK;
+}
+
+dlm_status shard_only_error() {
+  return fail(DLM_ERR_UNSUPPORTED, "a shard handle iterates through dlm_shard_sweep / dlm_shard_update");
+}
+
+
+// A shard's rows on the device (copied from host memory when they live
+// there); the copies are freed with the object.
+struct ShardRows {
+  const int64_t* rp = nullptr;
+  const int32_t* col = nullptr;
+  const void *c = nullptr, *a = nullptr;
+  const double* b = nullptr;
+  void* tmp[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+  cudaStream_t s = nullptr;
+  ~ShardRows() {
+    for (void* q : tmp) dev_free(q, s);
+    if (s) cudaStreamSynchronize(s);
+  }
+};
+
+dlm_status shard_rows(const dlm_problem_desc* d, cudaStream_t s, ShardRows* r) {
+  if (!d) return fail(DLM_ERR_INVALID_ARG, "null argument");
+  if (d->num_users < 0 || d->num_items <= 0 || d->nnz < 0 || d->num_users >= (int64_t(1) << 31) ||
+      d->num_items > 65536)
+    return fail(DLM_ERR_INVALID_ARG, "bad sizes");
+  if (!d->row_ptr || (d->nnz > 0 && (!d->item_idx || !d->c || !d->a)) || !d->b)
+    return fail(DLM_ERR_INVALID_ARG, "null array pointer");
+  if (d->val_dtype != DLM_F32 && d->val_dtype != DLM_BF16) return fail(DLM_ERR_INVALID_ARG, "bad val_dtype");
+  if (d->num_families > 1) return fail(DLM_ERR_UNSUPPORTED, "a user-sharded instance with several capacity families");
+  if (d->memspace != DLM_MEM_DEVICE && d->memspace != DLM_MEM_HOST) return fail(DLM_ERR_INVALID_ARG, "bad memspace");
+  r->s = s;
+  r->rp = d->row_ptr;
+  r->col = d->item_idx;
+  r->c = d->c;
+  r->a = d->a;
+  r->b = d->b;
+  if (d->memspace == DLM_MEM_HOST) {
+    const size_t vs = d->val_dtype == DLM_BF16 ? 2 : 4;
+    const size_t sz[5] = {sizeof(int64_t) * (d->num_users + 1), sizeof(int32_t) * d->nnz, vs * d->nnz, vs * d->nnz,
+                          sizeof(double) * d->num_items};
+    const void* src[5] = {d->row_ptr, d->item_idx, d->c, d->a, d->b};
+    for (int k = 0; k < 5; ++k) {
+      if (dev_alloc(&r->tmp[k], sz[k], s) != cudaSuccess) return fail(DLM_ERR_OOM, "device allocation failed");
+      if (sz[k] > 0) CK(cudaMemcpyAsync(r->tmp[k], src[k], sz[k], cudaMemcpyHostToDevice, s));
+    }
+    r->rp = static_cast<const int64_t*>(r->tmp[0]);
+    r->col = static_cast<const int32_t*>(r->tmp[1]);
+    r->c = r->tmp[2];
+    r->a = r->tmp[3];
+    r->b = static_cast<const double*>(r->tmp[4]);
+  }
+  return DLM_OK;
+}
+
+dlm_status shard_handle(dlm_problem* p) {
+  if (!p) return fail(DLM_ERR_INVALID_ARG, "null handle");
+  if (!p->sharded) return fail(DLM_ERR_INVALID_ARG, "not a shard handle (dlm_problem_desc.shard was NULL)");
   return DLM_OK;
 }
 
@@ -906,6 +1023,8 @@ const char* dlm_last_error(void) { return g_err.c_str(); }
 
 dlm_status dlm_create(const dlm_problem_desc* desc, void* stream, dlm_problem** out) {
   g_err.clear();
+  const auto t_create = std::chrono::steady_clock::now();
+  auto since = [&]() { return std::chrono::duration<double>(std::chrono::steady_clock::now() - t_create).count(); };
   if (!desc || !out) return fail(DLM_ERR_INVALID_ARG, "null argument");
   *out = nullptr;
   if (desc->num_users < 0 || desc->num_items <= 0 || desc->nnz < 0)
@@ -927,6 +1046,15 @@ dlm_status dlm_create(const dlm_problem_desc* desc, void* stream, dlm_problem** 
     return fail(DLM_ERR_INVALID_ARG, "bad memspace");
   const int m = desc->num_families > 0 ? desc->num_families : 1;
   if (m > kMaxFamilies) return fail(DLM_ERR_UNSUPPORTED, "at most 4 capacity families");
+  const dlm_shard* shard = desc->shard;
+  if (shard) {
+    if (m > 1) return fail(DLM_ERR_UNSUPPORTED, "a user-sharded instance with several capacity families");
+    if (!shard->item_sq || !shard->item_sum || !shard->exchange || !shard->cert_exchange || !shard->cert_obj)
+      return fail(DLM_ERR_INVALID_ARG, "dlm_shard: null item sums or exchange buffer");
+    if (shard->nnz < desc->nnz || shard->active_users < 0 || shard->max_item_degree < 0 ||
+        !(shard->max_abs_a >= 0) || !(shard->max_abs_c >= 0))
+      return fail(DLM_ERR_INVALID_ARG, "dlm_shard: statistics smaller than this shard's");
+  }
 
   dlm_problem* p = new dlm_problem();
   p->I = desc->num_users;
@@ -997,7 +1125,9 @@ dlm_status dlm_create(const dlm_problem_desc* desc, void* stream, dlm_problem** 
     c = tmp[2];
     a = tmp[3];
     b = static_cast<const double*>(tmp[4]);
+    cudaStreamSynchronize(p->stream);
   }
+  p->setup_s[0] = since();
 
   // Several families: one contiguous array per family (family 0 goes through
   // the one-family layout and validation, the others are checked here).
@@ -1023,12 +1153,28 @@ dlm_status dlm_create(const dlm_problem_desc* desc, void* stream, dlm_problem** 
   auto fam_ptr = [&](int f) { return static_cast<const char*>(split) + vs * nnz * f; };
 
   std::string msg;
-  st = build_layout(I, J, nnz, rp, col, c, a0, b, p->bf16, p->stream, &p->lay, &msg);
+  ShardGlobal sg{};
+  if (shard) {
+    sg.nnz = shard->nnz;
+    sg.active_users = shard->active_users;
+    sg.max_item_deg = shard->max_item_degree;
+    sg.max_abs_a = shard->max_abs_a;
+    sg.max_abs_c = shard->max_abs_c;
+    sg.a_nonneg = shard->a_nonneg != 0;
+    sg.item_sq = shard->item_sq;
+    sg.item_sum = shard->item_sum;
+  }
+  st = build_layout(I, J, nnz, rp, col, c, a0, b, p->bf16, p->stream, &p->lay, &msg, nullptr, shard ? &sg : nullptr);
   if (st != DLM_OK) {
     cleanup_all();
     free_problem(p);
     return fail(st, msg);
   }
+  for (int k = 0; k < 3; ++k) p->setup_s[1 + k] = p->lay.phase_s[k];
+  const double t_layout_end = since();
+  p->sharded = shard != nullptr;
+  p->glob_nnz = shard ? shard->nnz : nnz;
+  p->glob_users = shard ? shard->active_users : p->lay.num_active_users;
   if (m > 1) {
     // the other families: finite values, b >= 0, max |a|, sign
     int* flags = nullptr;
@@ -1074,7 +1220,7 @@ dlm_status dlm_create(const dlm_problem_desc* desc, void* stream, dlm_problem** 
   p->sC = fixed_point_shift(degm * (p->lay.max_abs_c > 0 ? p->lay.max_abs_c : 1.0) * xmax);
   p->sQ = fixed_point_shift(degm * xmax * xmax);
   // sum x <= z per user on the simplex, z per edge on the box
-  const double nmaxx = static_cast<double>(p->kind == DLM_BOX ? nnz : p->lay.num_active_users);
+  const double nmaxx = static_cast<double>(p->kind == DLM_BOX ? p->glob_nnz : p->glob_users);
   p->sN = fixed_point_shift((nmaxx > 0 ? nmaxx : 1.0) * xmax);
   if (p->sG < 0 || p->sC < 0 || p->sQ < 0 || p->sN < 0) {
     cleanup_all();
@@ -1128,24 +1274,33 @@ dlm_status dlm_create(const dlm_problem_desc* desc, void* stream, dlm_problem** 
   CKC(dalloc(&p->y, MJ + 1));
   CKC(dalloc(&p->lam64, MJ + 1));
   CKC(dalloc(&p->y64, MJ + 1));
-  CKC(dalloc(&p->objq, 1));
   CKC(dalloc(&p->traj, kTrajCap));
+  CKC(dalloc(&p->upd_part, 2 * static_cast<size_t>(update_ctas(MJ + 1)) + 1));
+  CKC(dalloc(&p->upd_ticket, 2));
+  CKC(dalloc(&p->upd_flag, 1));
+  CKC(cudaMemsetAsync(p->upd_ticket, 0, sizeof(unsigned) * 2, p->stream));
+  CKC(cudaMemsetAsync(p->upd_flag, 0, sizeof(int32_t), p->stream));
   CKC(cudaMemsetAsync(p->lam64, 0, sizeof(double) * (MJ + 1), p->stream));
   CKC(cudaMemsetAsync(p->y64, 0, sizeof(double) * (MJ + 1), p->stream));
-  CKC(cudaMemsetAsync(p->objq, 0, sizeof(unsigned long long), p->stream));
   CKC(cudaMemsetAsync(p->traj, 0, sizeof(double) * kTrajCap, p->stream));
-  CKC(dalloc(&p->cnt, 1));
-  CKC(dalloc(&p->cnt2, 1));
-  CKC(cudaMemsetAsync(p->cnt, 0, sizeof(unsigned long long), p->stream));
-  CKC(cudaMemsetAsync(p->cnt2, 0, sizeof(unsigned long long), p->stream));
-  CKC(dalloc(&p->acc, MJ));
-  CKC(dalloc(&p->acc2, MJ));
-  CKC(dalloc(&p->accC, J));
-  CKC(dalloc(&p->accQ, J));
-  CKC(cudaMemsetAsync(p->acc, 0, sizeof(unsigned long long) * MJ, p->stream));
-  CKC(cudaMemsetAsync(p->acc2, 0, sizeof(unsigned long long) * MJ, p->stream));
-  CKC(cudaMemsetAsync(p->accC, 0, sizeof(unsigned long long) * J, p->stream));
-  CKC(cudaMemsetAsync(p->accQ, 0, sizeof(unsigned long long) * J, p->stream));
+  if (shard) {
+    p->xsum = reinterpret_cast<unsigned long long*>(shard->exchange);
+    p->csum = reinterpret_cast<unsigned long long*>(shard->cert_exchange);
+    p->cobj = shard->cert_obj;
+    p->own_sums = false;
+  } else {
+    CKC(dalloc(&p->xsum, MJ + 2));
+    CKC(dalloc(&p->csum, MJ + 2 * J + 1));
+  }
+  CKC(cudaMemsetAsync(p->xsum, 0, sizeof(unsigned long long) * (MJ + 2), p->stream));
+  CKC(cudaMemsetAsync(p->csum, 0, sizeof(unsigned long long) * (MJ + 2 * J + 1), p->stream));
+  p->acc = p->xsum;
+  p->cnt = p->xsum + MJ;
+  p->objq = p->xsum + MJ + 1;
+  p->acc2 = p->csum;
+  p->accC = p->csum + MJ;
+  p->accQ = p->csum + MJ + J;
+  p->cnt2 = p->csum + MJ + 2 * J;
   CKC(cudaMemsetAsync(p->lam, 0, sizeof(float) * (MJ + 1), p->stream));
   CKC(cudaMemsetAsync(p->y, 0, sizeof(float) * (MJ + 1), p->stream));
   CKC(dalloc(&p->calc_gamma, 1));
@@ -1183,6 +1338,8 @@ dlm_status dlm_create(const dlm_problem_desc* desc, void* stream, dlm_problem** 
     free_problem(p);
     return st;
   }
+  p->setup_s[5] = since();
+  p->setup_s[4] = p->setup_s[5] - t_layout_end;
   *out = p;
   return DLM_OK;
 }
@@ -1279,16 +1436,19 @@ dlm_status dlm_set_lambda(dlm_problem* p, const float* lambda0, int32_t memspace
 
 dlm_status dlm_step(dlm_problem* p, int64_t n_iters) {
   if (!p || n_iters < 0) return fail(DLM_ERR_INVALID_ARG, "bad argument");
+  if (p->sharded) return shard_only_error();
   return runner_step(p->run, n_iters);
 }
 
 dlm_status dlm_step_timed(dlm_problem* p, int64_t n_iters, double* sweep_ms, double* update_ms, double* total_ms) {
   if (!p || n_iters < 0) return fail(DLM_ERR_INVALID_ARG, "bad argument");
+  if (p->sharded) return shard_only_error();
   return runner_step_timed(p->run, n_iters, sweep_ms, update_ms, total_ms);
 }
 
 dlm_status dlm_get_stats(dlm_problem* p, dlm_stats* out) {
   if (!p) return fail(DLM_ERR_INVALID_ARG, "null handle");
+  if (p->sharded) return shard_only_error();
   dlm_status st = enqueue_certificate(p->run, p->run.inst_stats, p->run.st_stats);
   if (st != DLM_OK) return st;
   return read_stats(p, out);
@@ -1296,6 +1456,7 @@ dlm_status dlm_get_stats(dlm_problem* p, dlm_stats* out) {
 
 dlm_status dlm_solve(dlm_problem* p, double target_rel_gap, int64_t max_iters, dlm_stats* out) {
   if (!p || max_iters < 0) return fail(DLM_ERR_INVALID_ARG, "bad argument");
+  if (p->sharded) return shard_only_error();
   const auto t0 = std::chrono::steady_clock::now();
   dlm_stats s{};
   int64_t start_iter = 0;
@@ -1336,6 +1497,7 @@ dlm_status dlm_solve(dlm_problem* p, double target_rel_gap, int64_t max_iters, d
 
 dlm_status dlm_calculate(dlm_problem* p, const float* lambda, double gamma, double* g, float* grad, float* x) {
   if (!p || !lambda) return fail(DLM_ERR_INVALID_ARG, "null argument");
+  if (p->sharded) return shard_only_error();
   if (!(gamma > 0) || !std::isfinite(gamma)) return fail(DLM_ERR_INVALID_ARG, "gamma must be > 0");
   CK(cudaStreamSynchronize(p->stream));
   k_set_double<<<1, 1, 0, p->stream>>>(p->calc_gamma, gamma);
@@ -1476,6 +1638,86 @@ dlm_status dlm_get_info(dlm_problem* p, int64_t* num_users, int64_t* num_items, 
 
 void dlm_destroy(dlm_problem* p) { free_problem(p); }
 
+dlm_status dlm_get_setup_seconds(dlm_problem* p, double* out, int32_t n) {
+  if (!p || (n > 0 && !out) || n < 0) return fail(DLM_ERR_INVALID_ARG, "bad argument");
+  for (int k = 0; k < n && k < 6; ++k) out[k] = p->setup_s[k];
+  return DLM_OK;
+}
+
+// ---------------------------------------------------------------------------
+// User-sharded instances
+// ---------------------------------------------------------------------------
+
+dlm_status dlm_shard_local(const dlm_problem_desc* desc, void* stream, dlm_shard* local, int64_t* item_degree) {
+  g_err.clear();
+  if (!local || !item_degree) return fail(DLM_ERR_INVALID_ARG, "null argument");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  ShardRows r;
+  dlm_status st = shard_rows(desc, s, &r);
+  if (st != DLM_OK) return st;
+  LayoutOut lay;
+  RowStats rs;
+  std::string msg;
+  st = build_layout(desc->num_users, desc->num_items, desc->nnz, r.rp, r.col, r.c, r.a, r.b,
+                    desc->val_dtype == DLM_BF16, s, &lay, &msg, &rs, nullptr);
+  if (st != DLM_OK) return fail(st, msg);
+  *local = dlm_shard{};
+  local->nnz = rs.nnz;
+  local->active_users = rs.active_users;
+  local->max_item_degree = rs.max_item_deg;
+  local->max_abs_a = rs.max_abs_a;
+  local->max_abs_c = rs.max_abs_c;
+  local->a_nonneg = rs.a_nonneg ? 1 : 0;
+  for (int64_t j = 0; j < desc->num_items; ++j) item_degree[j] = static_cast<int64_t>(rs.item_deg[j]);
+  return DLM_OK;
+}
+
+dlm_status dlm_shard_item_sums(const dlm_problem_desc* desc, const dlm_shard* global, void* stream, int64_t* item_sq,
+                               int64_t* item_sum) {
+  g_err.clear();
+  if (!global || !item_sq || !item_sum) return fail(DLM_ERR_INVALID_ARG, "null argument");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  ShardRows r;
+  dlm_status st = shard_rows(desc, s, &r);
+  if (st != DLM_OK) return st;
+  int ssq = 0, ss1 = 0;
+  item_sum_shifts(global->max_item_degree, global->max_abs_a, &ssq, &ss1);
+  std::string msg;
+  st = item_sums(desc->num_items, desc->nnz, r.col, r.a, desc->val_dtype == DLM_BF16, ssq, ss1, s, item_sq, item_sum,
+                 &msg);
+  if (st != DLM_OK) return fail(st, msg);
+  return DLM_OK;
+}
+
+dlm_status dlm_shard_sweep(dlm_problem* p) {
+  dlm_status st = shard_handle(p);
+  if (st != DLM_OK) return st;
+  CK(dispatch_sweep(p->run, launch_of(p->run, p->run.inst_iter), false, p->bf16));
+  return DLM_OK;
+}
+
+dlm_status dlm_shard_update(dlm_problem* p) {
+  dlm_status st = shard_handle(p);
+  if (st != DLM_OK) return st;
+  CK(launch_update(p->run.upd, 1, p->run.upd_ctas, p->run.upd_test, p->stream));
+  return DLM_OK;
+}
+
+dlm_status dlm_shard_cert_sweep(dlm_problem* p) {
+  dlm_status st = shard_handle(p);
+  if (st != DLM_OK) return st;
+  CK(dispatch_sweep(p->run, launch_of(p->run, p->run.inst_stats), true, p->bf16));
+  CK(launch_seg_sum(p->run.st_stats, p->cobj, p->stream));
+  return DLM_OK;
+}
+
+dlm_status dlm_shard_cert_finish(dlm_problem* p, dlm_stats* out) {
+  dlm_status st = shard_handle(p);
+  if (st != DLM_OK) return st;
+  CK(launch_stats(p->run.st_stats, 1, p->stream));
+  return read_stats(p, out);
+}
+
 dlm_status dlm_release_cached_memory(void) {
   const cudaError_t e = release_cached_memory();
   if (e != cudaSuccess) return fail(DLM_ERR_CUDA, std::string("memory pool trim: ") + cudaGetErrorString(e));
@@ -1533,6 +1775,7 @@ dlm_status dlm_batch_create(dlm_problem* const* probs, int32_t n, void* stream, 
       return fail(DLM_ERR_UNSUPPORTED, "a count constraint with several capacity families");
     if ((probs[i]->kind == DLM_BOX_CUT) != (probs[0]->kind == DLM_BOX_CUT))
       return fail(DLM_ERR_UNSUPPORTED, "DLM_BOX_CUT members batch only with each other");
+    if (probs[i]->sharded) return fail(DLM_ERR_UNSUPPORTED, "a shard handle in a batch");
     for (int k = 0; k < i; ++k)
       if (probs[k] == probs[i]) return fail(DLM_ERR_INVALID_ARG, "a problem appears twice in the batch");
   }

@@ -48,6 +48,10 @@ struct UpdInst {
   unsigned long long* acc;  // [J] fixed-point A x at y
   unsigned long long* objq; // fixed-point sum of (c x + gamma/2 x^2) at y (reset here)
   double* traj;             // [kTrajCap] g(y_t) at slot t mod kTrajCap
+  double* part;             // [2 nct + 1] per-CTA partials of the update's sums
+  unsigned* ticket;         // [2] CTAs of the instance done (reset by the last)
+  int32_t* flag;            // the adaptive restart decision of the iteration
+  int32_t nct;              // update CTAs of the instance (update_ctas(D))
   int64_t iters_per_stage;
   double curv_max;          // the largest curvature bound (plain step gamma / curv_max)
   double inv_scaleG;        // 2^-sG
@@ -123,6 +127,7 @@ struct SweepLaunch {
   unsigned* ctr;            // device [2]: next unit, finished CTAs (zero between launches)
   bool count;               // some instance has a global count constraint (its own instantiation)
   int32_t fam;              // capacity families (> 1: the general sweep of sweep_multi.cu)
+  int32_t topk = 4;         // one-family sweep: largest values tracked per row in the first pass (4 or 8)
 };
 constexpr int kDefaultCoopMax = 12;
 
@@ -145,6 +150,7 @@ struct StatsInst {
   double inv_sN;
   double count_M;
   int32_t m;                  // capacity families: acc, b, lam, grad_out are [m J] family-major
+  const double* obj_in;       // non-null: the objective sum (a shard's, added over the ranks) instead of seg_obj
 };
 
 // Sets the thread-local message returned by dlm_last_error (api.cu).
@@ -165,8 +171,14 @@ int sweep_stats_window(int smemJ);
 size_t sweep_smem_limit();             // usable dynamic shared memory per sweep CTA on this device
 cudaError_t sweep_prepare(bool bf16);  // raises the dynamic shared-memory limit
 cudaError_t launch_sweep(const SweepLaunch& L, bool stats, bool bf16);
-cudaError_t launch_update(const UpdInst* dev_tab, int ninst, cudaStream_t s);
+// The update of ninst instances: a grid of max_cta x ninst CTAs (instance i
+// uses its first update_ctas(D_i)); any_test: some instance has the adaptive
+// restart on (a first kernel takes the test).
+cudaError_t launch_update(const UpdInst* dev_tab, int ninst, int max_cta, bool any_test, cudaStream_t s);
+int update_ctas(int64_t D);
 cudaError_t launch_stats(const StatsInst* dev_tab, int ninst, cudaStream_t s);
+// The certificate sweep's objective partials of instance 0 summed into *out.
+cudaError_t launch_seg_sum(const StatsInst* dev_tab, double* out, cudaStream_t s);
 // sweep_multi.cu (m > 1 families; static tasks only)
 size_t sweep_multi_smem_bytes(int smemJ, int m, bool stats);
 cudaError_t sweep_multi_prepare(bool bf16);
@@ -179,6 +191,7 @@ cudaError_t launch_item_features(const uint16_t* col, const void* ca, bool bf, i
 
 // layout.cu
 struct LayoutOut {
+  double phase_s[3] = {0, 0, 0};  // wall seconds: validation, degree sort, slice layout + item sums
   int64_t* slice_off = nullptr;  // [nslices + 1]
   int32_t* slice_w = nullptr;    // [nslices]
   uint16_t* col16 = nullptr;     // [padded_nnz + 64] item index (uint16: J <= 65,536)
@@ -201,9 +214,36 @@ cudaError_t families_gather(const LayoutOut& lay, const void* src, bool bf16, vo
 cudaError_t families_gram(const int32_t* col, const void* af, const void* al, int64_t nnz, bool bf16, float scale,
                           unsigned long long* acc, cudaStream_t s);
 
+// Statistics of an instance's rows (one shard's, or all of them).
+struct RowStats {
+  int64_t nnz = 0, active_users = 0, max_item_deg = 0;
+  double max_abs_a = 0, max_abs_c = 0;
+  bool a_nonneg = true;
+  std::vector<unsigned long long> item_deg;  // [J]
+};
+// The statistics of all shards of a user-sharded instance, and its exact
+// fixed-point item sums (sum_i a_ij^2 and sum_i a_ij at the exponents
+// item_sum_shifts gives for max_item_deg and max_abs_a), host memory.
+struct ShardGlobal {
+  int64_t nnz, active_users, max_item_deg;
+  double max_abs_a, max_abs_c;
+  bool a_nonneg;
+  const int64_t* item_sq;
+  const int64_t* item_sum;
+};
+void item_sum_shifts(int64_t max_item_deg, double max_abs_a, int* ssq, int* ss1);
+
 // Validates and lays out one instance; all pointers are device pointers.
-// Returns DLM_OK or an error with `msg` set.
+// With `measure`, validates and fills the row statistics only (no layout);
+// with `shard`, the instance is one shard of a larger one and the item sums
+// and bounds are the global ones given.  Returns DLM_OK or an error with
+// `msg` set.
 dlm_status build_layout(int64_t I, int64_t J, int64_t nnz, const int64_t* rp, const int32_t* col, const void* c,
-                        const void* a, const double* b, bool bf16, cudaStream_t s, LayoutOut* out, std::string* msg);
+                        const void* a, const double* b, bool bf16, cudaStream_t s, LayoutOut* out, std::string* msg,
+                        RowStats* measure = nullptr, const ShardGlobal* shard = nullptr);
+// Fixed-point sums over the given rows: sum_i a_ij^2 at 2^ssq and sum_i a_ij
+// at 2^ss1 into the host arrays sq, s1 [J].
+dlm_status item_sums(int64_t J, int64_t nnz, const int32_t* col, const void* a, bool bf16, int ssq, int ss1,
+                     cudaStream_t s, int64_t* sq, int64_t* s1, std::string* msg);
 
 }  // namespace dlm

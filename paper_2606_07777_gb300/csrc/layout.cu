@@ -25,6 +25,7 @@
 // the same size then maps no new memory.
 #include <cub/cub.cuh>
 
+#include <chrono>
 #include <cmath>
 #include <cstdint>
 #include <mutex>
@@ -358,9 +359,46 @@ int fixed_point_shift(double bound) {
     }                                                                        \
   } while (0)
 
+void item_sum_shifts(int64_t max_item_deg, double max_abs_a, int* ssq, int* ss1) {
+  *ssq = fixed_point_shift(static_cast<double>(max_item_deg) * max_abs_a * max_abs_a);
+  *ss1 = fixed_point_shift(static_cast<double>(max_item_deg) * max_abs_a);
+}
+
+dlm_status item_sums(int64_t J, int64_t nnz, const int32_t* col, const void* a, bool bf16, int ssq, int ss1,
+                     cudaStream_t s, int64_t* sq, int64_t* s1, std::string* msg) {
+  cudaFuncSetAttribute(k_item_sq, cudaFuncAttributeMaxDynamicSharedMemorySize, 8 * kSmemItems);
+  unsigned long long* acc = nullptr;
+  dlm_status st = DLM_OK;
+  const int g = static_cast<int>(nnz / 8192 + 1 < 608 ? nnz / 8192 + 1 : 608);
+  const size_t smem = J <= kSmemItems ? sizeof(unsigned long long) * J : 0;
+  DLM_CK(dev_alloc(reinterpret_cast<void**>(&acc), sizeof(unsigned long long) * 2 * (J > 0 ? J : 1), s));
+  DLM_CK(cudaMemsetAsync(acc, 0, sizeof(unsigned long long) * 2 * (J > 0 ? J : 1), s));
+  if (nnz > 0) {
+    k_item_sq<<<g, 1024, smem, s>>>(col, a, bf16, nnz, J, std::ldexp(1.0f, ssq), true, acc);
+    DLM_CK(cudaGetLastError());
+    k_item_sq<<<g, 1024, smem, s>>>(col, a, bf16, nnz, J, std::ldexp(1.0f, ss1), false, acc + J);
+    DLM_CK(cudaGetLastError());
+  }
+  DLM_CK(cudaMemcpyAsync(sq, acc, sizeof(int64_t) * J, cudaMemcpyDeviceToHost, s));
+  DLM_CK(cudaMemcpyAsync(s1, acc + J, sizeof(int64_t) * J, cudaMemcpyDeviceToHost, s));
+  DLM_CK(cudaStreamSynchronize(s));
+  goto done;
+fail:
+  st = DLM_ERR_CUDA;
+done:
+  dev_free(acc, s);
+  cudaStreamSynchronize(s);
+  return st;
+}
+
 dlm_status build_layout(int64_t I, int64_t J, int64_t nnz, const int64_t* rp, const int32_t* col, const void* c,
                         const void* a, const double* b, bool bf16, cudaStream_t s, LayoutOut* out,
-                        std::string* msg) {
+                        std::string* msg, RowStats* measure, const ShardGlobal* shard) {
+  const auto t_start = std::chrono::steady_clock::now();
+  auto lap = [&](int k) {
+    out->phase_s[k] = std::chrono::duration<double>(std::chrono::steady_clock::now() - t_start).count() -
+                      (k > 0 ? out->phase_s[0] : 0.0) - (k > 1 ? out->phase_s[1] : 0.0);
+  };
   const size_t vs = bf16 ? 2 : 4;
   cudaFuncSetAttribute(k_item_sq, cudaFuncAttributeMaxDynamicSharedMemorySize, 8 * kSmemItems);
   cudaFuncSetAttribute(k_edges, cudaFuncAttributeMaxDynamicSharedMemorySize, 4 * 16384);
@@ -428,6 +466,7 @@ dlm_status build_layout(int64_t I, int64_t J, int64_t nnz, const int64_t* rp, co
   DLM_CK(cudaMemcpyAsync(h_deg.data(), item_deg, sizeof(unsigned long long) * h_deg.size(), cudaMemcpyDeviceToHost,
                          s));
   DLM_CK(cudaStreamSynchronize(s));
+  lap(0);
   if (h_bad & kBadItem) {
     *msg = "item_idx out of range [0, num_items)";
     st = DLM_ERR_INVALID_ARG;
@@ -454,6 +493,22 @@ dlm_status build_layout(int64_t I, int64_t J, int64_t nnz, const int64_t* rp, co
   out->max_item_deg = 0;
   for (int64_t j = 0; j < J; ++j)
     if (static_cast<int64_t>(h_deg[j]) > out->max_item_deg) out->max_item_deg = static_cast<int64_t>(h_deg[j]);
+  if (measure) {
+    measure->nnz = nnz;
+    measure->active_users = I - static_cast<int64_t>(h_zero);
+    measure->max_item_deg = out->max_item_deg;
+    measure->max_abs_a = out->max_abs_a;
+    measure->max_abs_c = out->max_abs_c;
+    measure->a_nonneg = out->a_nonneg;
+    measure->item_deg.assign(h_deg.begin(), h_deg.begin() + J);
+    goto done;
+  }
+  if (shard) {  // bounds of the whole instance: the fixed-point exponents must agree on every shard
+    out->max_item_deg = shard->max_item_deg;
+    out->max_abs_a = shard->max_abs_a;
+    out->max_abs_c = shard->max_abs_c;
+    out->a_nonneg = shard->a_nonneg;
+  }
 
   // ---- stable sort of users by degree, largest first ----
   In = I - static_cast<int64_t>(h_zero);
@@ -491,6 +546,7 @@ dlm_status build_layout(int64_t I, int64_t J, int64_t nnz, const int64_t* rp, co
   }
   DLM_CK(cudaMemcpyAsync(&out->padded_nnz, out->slice_off + ns, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
   DLM_CK(cudaStreamSynchronize(s));
+  lap(1);
 
   // ---- edge streams in slice order (16-bit item indices: every handle has
   // fewer than 65,536 items) ----
@@ -515,7 +571,25 @@ dlm_status build_layout(int64_t I, int64_t J, int64_t nnz, const int64_t* rp, co
     DLM_CK(cudaGetLastError());
   }
 
-  // ---- n_j = sum_i a_ij^2 (exact fixed point) ----
+  // ---- n_j = sum_i a_ij^2 and s_j = sum_i a_ij (exact fixed point; the
+  // whole instance's sums for a shard) ----
+  if (shard) {
+    int sq_shift = 0, s1_shift = 0;
+    item_sum_shifts(out->max_item_deg, out->max_abs_a, &sq_shift, &s1_shift);
+    out->h_n2.assign(J > 0 ? J : 1, 0.0);
+    out->h_s1.assign(J > 0 ? J : 1, 0.0);
+    out->n2max = 0;
+    for (int64_t j = 0; j < J; ++j) {
+      out->h_n2[j] = static_cast<double>(shard->item_sq[j]) * std::ldexp(1.0, -sq_shift);
+      out->h_s1[j] = static_cast<double>(shard->item_sum[j]) * std::ldexp(1.0, -s1_shift);
+      out->n2max = out->h_n2[j] > out->n2max ? out->h_n2[j] : out->n2max;
+    }
+    DLM_CK(dev_alloc(reinterpret_cast<void**>(&out->n2), sizeof(double) * (J > 0 ? J : 1), s));
+    DLM_CK(cudaMemcpyAsync(out->n2, out->h_n2.data(), sizeof(double) * out->h_n2.size(), cudaMemcpyHostToDevice, s));
+    DLM_CK(cudaStreamSynchronize(s));
+    lap(2);
+    goto done;
+  }
   bound_sq = static_cast<double>(out->max_item_deg) * out->max_abs_a * out->max_abs_a;
   ssq = fixed_point_shift(bound_sq);
   DLM_CK(dev_alloc(reinterpret_cast<void**>(&sq), sizeof(unsigned long long) * (J > 0 ? J : 1), s));
@@ -550,6 +624,7 @@ dlm_status build_layout(int64_t I, int64_t J, int64_t nnz, const int64_t* rp, co
     out->n2max = 0;
     for (int64_t j = 0; j < J; ++j) out->n2max = out->h_n2[j] > out->n2max ? out->h_n2[j] : out->n2max;
   }
+  lap(2);
   goto done;
 
 fail:

@@ -209,21 +209,21 @@ __device__ __forceinline__ void coop_user(const Seg& S, const float* __restrict_
 // sweeps take): it saves a re-read (4 % on the 64-instance batch, 6 % on the
 // appendix instance once its rows have several active edges; no change on
 // the precision sweep).
-template <class P, bool STATS>
-__device__ __forceinline__ float4 rows_upto3(const Seg S, const float* __restrict__ ys, unsigned long long* accG,
-                                          unsigned long long* accC, unsigned long long* accQ,
-                                          const typename P::IX* __restrict__ col0, const typename P::T* __restrict__ ca0,
-                                          int w4, int r, int i0, int i1, int i2, float tau, bool eq,
-                                          unsigned long long& cn) {
+template <class P, bool STATS, int K>
+__device__ __forceinline__ float4 rows_upto(const Seg S, const float* __restrict__ ys, unsigned long long* accG,
+                                         unsigned long long* accC, unsigned long long* accQ,
+                                         const typename P::IX* __restrict__ col0, const typename P::T* __restrict__ ca0,
+                                         int w4, int r, const int (&pos)[K - 1], float tau, bool eq,
+                                         unsigned long long& cn) {
   const int lane = threadIdx.x & 31;
-  int jr[3];
-  float cr[3], ar[3];
+  int jr[K - 1];
+  float cr[K - 1], ar[K - 1];
 #pragma unroll
-  for (int i = 0; i < 3; ++i) {
+  for (int i = 0; i < K - 1; ++i) {
     jr[i] = 0;
     cr[i] = ar[i] = 0.f;
     if (i < r) {
-      const int el = sell_el(i == 0 ? i0 : (i == 1 ? i1 : i2), lane, w4);
+      const int el = sell_el(pos[i], lane, w4);
       jr[i] = static_cast<int>(__ldg(col0 + el));
       P::get(__ldg(ca0 + el), cr[i], ar[i]);
     }
@@ -233,7 +233,7 @@ __device__ __forceinline__ float4 rows_upto3(const Seg S, const float* __restric
   if (!zero) {
     F2 sum{0.f, 0.f};
 #pragma unroll
-    for (int i = 0; i < 3; ++i)
+    for (int i = 0; i < K - 1; ++i)
       if (i < r) sum = f2_add(sum, u_pair(cr[i], ar[i], ys[jr[i]]));
     const F2 t2 = f2_threshold(sum, S.gz, S.gzl, r);
     if (!eq && t2.h + t2.l <= (P::kCount ? S.mu : 0.f)) {
@@ -249,7 +249,7 @@ __device__ __forceinline__ float4 rows_upto3(const Seg S, const float* __restric
   }
   float ob = 0.f;
 #pragma unroll
-  for (int i = 0; i < 3; ++i) {
+  for (int i = 0; i < K - 1; ++i) {
     if (i < r) {
       const float x = x_general(S, false, tau, taul, cr[i], ar[i], ys[jr[i]]);
       if (x > 0.f) deposit<P, STATS>(S, jr[i], cr[i], ar[i], x, accG, accC, accQ, ob, cn);
@@ -264,35 +264,63 @@ __device__ __forceinline__ float4 rows_upto3(const Seg S, const float* __restric
 // keeps the lanes busy).  coop_max is a tuning parameter (0: always per lane,
 // 33: always cooperative).
 
-// The four largest u of a row (v0 >= v1 >= v2 >= v3) and the edge
-// positions i0, i1, i2 of the first three.
-struct Top4 {
-  float v0, v1, v2, v3;
-  int i0, i1, i2;
+// The K largest u of a row (v[0] >= ... >= v[K-1]) and the edge positions
+// id[0..K-2] of the first K - 1.  K = 4 for most instances; K = 8 resolves
+// rows with up to seven active edges without the threshold iteration.
+template <int K>
+struct TopK {
+  float v[K];
+  int id[K - 1];
 };
-__device__ __forceinline__ Top4 top4_empty() { return Top4{-INFINITY, -INFINITY, -INFINITY, -INFINITY, 0, 0, 0}; }
+template <int K>
+__device__ __forceinline__ TopK<K> topk_empty() {
+  TopK<K> t;
+#pragma unroll
+  for (int q = 0; q < K; ++q) t.v[q] = -INFINITY;
+#pragma unroll
+  for (int q = 0; q < K - 1; ++q) t.id[q] = 0;
+  return t;
+}
+// Sorted insertion of edge k with value u (strict comparisons: among equal
+// values the earlier edge ranks first; for K = 4 the network of top4_insert).
+template <int K>
+__device__ __forceinline__ void topk_insert(float u, int k, TopK<K>& t) {
+  float x = u;
+  int xi = k;
+#pragma unroll
+  for (int q = 0; q < K - 1; ++q) {
+    const bool c = x > t.v[q];
+    const float lo = c ? t.v[q] : x;
+    const int loi = c ? t.id[q] : xi;
+    t.v[q] = c ? x : t.v[q];
+    t.id[q] = c ? xi : t.id[q];
+    x = lo;
+    xi = loi;
+  }
+  t.v[K - 1] = fmaxf(t.v[K - 1], x);
+}
 
 // After pass A over a row: the threshold, x and the deposits (modes below);
 // col0/ca0 are the slice's element streams.
-template <class P, bool STATS, bool REG3>
+template <class P, bool STATS, bool REG3, int K>
 __device__ __forceinline__ void finish_slice(const InstDesc& D, const Seg& S, const float* __restrict__ ys,
                                              unsigned long long* accG, unsigned long long* accC,
                                              unsigned long long* accQ, int64_t s, int w,
                                              const typename P::IX* __restrict__ col0,
-                                             const typename P::T* __restrict__ ca0, const Top4 tk, int coop_max,
+                                             const typename P::T* __restrict__ ca0, const TopK<K>& tk, int coop_max,
                                              double& wobj, unsigned long long& cn, unsigned long long& oq) {
   const int lane = threadIdx.x & 31;
   const int w4 = w >> 2;
   const bool box = S.kind == DLM_BOX;
   const bool eq = S.kind == DLM_SIMPLEX_EQ;
-  const float v0 = tk.v0, v1 = tk.v1, v2 = tk.v2, v3 = tk.v3;
-  const int i0 = tk.i0, i1 = tk.i1, i2 = tk.i2;
+  const float v0 = tk.v[0];
+  const int i0 = tk.id[0];
 
   // The equality threshold solves sum_k max(u_k - tau, 0) = gamma z.  With
   // the values sorted, tau_r = (v_0 + ... + v_{r-1} - gamma z) / r and the
-  // active count is the first r with v_r <= tau_r; scanning the four largest
+  // active count is the first r with v_r <= tau_r; scanning the K largest
   // either finds it (the active set lies among them) or shows that at least
-  // four edges are active, and then tau_4 is a lower bound for the iteration.
+  // K edges are active, and then tau_K is a lower bound for the iteration.
   // mode 0: no edge active; 1: the maximum alone, x = z; 2: threshold of the
   // final active set known (tau); 3: iterate from tau.
   int mode;
@@ -307,40 +335,35 @@ __device__ __forceinline__ void finish_slice(const InstDesc& D, const Seg& S, co
     float sm = v0;
     r = 1;
     tau = v0 - S.gz;
-    if (v1 > tau) {
-      sm += v1;
-      r = 2;
-      tau = __fdiv_rn(sm - S.gz, 2.f);
-      if (v2 > tau) {
-        sm += v2;
-        r = 3;
-        tau = __fdiv_rn(sm - S.gz, 3.f);
-        if (v3 > tau) {
-          sm += v3;
-          r = 4;
-          tau = __fdiv_rn(sm - S.gz, 4.f);
-        }
+#pragma unroll
+    for (int q = 1; q < K; ++q) {
+      if (r == q && tk.v[q] > tau) {
+        sm += tk.v[q];
+        r = q + 1;
+        tau = __fdiv_rn(sm - S.gz, static_cast<float>(q + 1));
       }
     }
-    mode = (r == 1 && (eq || tau >= (P::kCount ? S.mu : 0.f))) ? 1 : (r < 4 ? 2 : 3);
+    mode = (r == 1 && (eq || tau >= (P::kCount ? S.mu : 0.f))) ? 1 : (r < K ? 2 : 3);
   }
 
   float ob = 0.f;
   if (mode == 2 && REG3) {
-    const float4 res = rows_upto3<P, STATS>(S, ys, accG, accC, accQ, col0, ca0, w4, r, i0, i1, i2, tau, eq, cn);
+    const float4 res = rows_upto<P, STATS, K>(S, ys, accG, accC, accQ, col0, ca0, w4, r, tk.id, tau, eq, cn);
     tau = res.x;
     taul = res.y;
     zero = res.z != 0.f;
     ob += res.w;
   } else if (mode == 2) {
-    // The active set is the r <= 3 recorded edges (on the inequality simplex
+    // The active set is the r < K recorded edges (on the inequality simplex
     // with tau <= 0: those of them with u > 0).  Threshold over them in pair
     // arithmetic, then x on each (the edges are re-read from L1).
     zero = !eq && tau <= (P::kCount ? S.mu : 0.f);
     if (!zero) {
       F2 sum{0.f, 0.f};
-      for (int i = 0; i < r; ++i) {
-        const int el = sell_el(i == 0 ? i0 : (i == 1 ? i1 : i2), lane, w4);
+#pragma unroll
+      for (int i = 0; i < K - 1; ++i) {
+        if (i >= r) break;
+        const int el = sell_el(tk.id[i], lane, w4);
         const int j = static_cast<int>(__ldg(col0 + el));
         float c, a;
         P::get(__ldg(ca0 + el), c, a);
@@ -358,8 +381,10 @@ __device__ __forceinline__ void finish_slice(const InstDesc& D, const Seg& S, co
     tau = (P::kCount ? S.mu : 0.f);
     taul = 0.f;
   }
-    for (int i = 0; i < r; ++i) {
-      const int el = sell_el(i == 0 ? i0 : (i == 1 ? i1 : i2), lane, w4);
+#pragma unroll
+    for (int i = 0; i < K - 1; ++i) {
+      if (i >= r) break;
+      const int el = sell_el(tk.id[i], lane, w4);
       const int j = static_cast<int>(__ldg(col0 + el));
       float c, a;
       P::get(__ldg(ca0 + el), c, a);
@@ -374,7 +399,7 @@ __device__ __forceinline__ void finish_slice(const InstDesc& D, const Seg& S, co
     deposit<P, STATS>(S, j, c, a, S.z, accG, accC, accQ, ob, cn);
   }
 
-  // Mode 3 (four or more active edges, or the box): the whole warp per user
+  // Mode 3 (K or more active edges, or the box): the whole warp per user
   // while few lanes need it, else each lane over its own row.
   const unsigned mask3 = __ballot_sync(kFull, mode == 3);
   const bool coop = mask3 != 0u && __popc(mask3) < coop_max;  // warp-uniform
@@ -386,7 +411,15 @@ __device__ __forceinline__ void finish_slice(const InstDesc& D, const Seg& S, co
       const float tt = __shfl_sync(kFull, tau, t);
       float ta, tl;
       bool zr;
-      coop_user<P, STATS>(S, ys, accG, accC, accQ, col0, ca0, w, w4, t, tt, false, ta, tl, zr, ob, cn);
+      // every lane adds the objective of its edges of user t: that piece
+      // goes to fixed point on its own, so the total does not depend on
+      // which users share the warp
+      float obu = 0.f;
+      coop_user<P, STATS>(S, ys, accG, accC, accQ, col0, ca0, w, w4, t, tt, false, ta, tl, zr, obu, cn);
+      if (STATS)
+        ob += obu;
+      else
+        oq += fixp(obu, S.scaleO);
       if (lane == t) {
         tau = ta;
         taul = tl;
@@ -417,7 +450,7 @@ __device__ __forceinline__ void finish_slice(const InstDesc& D, const Seg& S, co
       }
     };
     if (!box) {
-      // Michelot iteration from tau_4, a lower bound of the threshold: the
+      // Michelot iteration from tau_K, a lower bound of the threshold: the
       // active sets {u > tau} shrink until two passes agree.  Each pass also
       // sums its active set in pair arithmetic, so the pass that finds the
       // set unchanged already holds the sum the threshold is refined from.
@@ -517,7 +550,7 @@ __device__ __forceinline__ void finish_slice(const InstDesc& D, const Seg& S, co
 // One slice: lane t = user t; edge k of lane t is element sell_el(k, t, w/4)
 // of the slice.  Pass A streams the row in groups of four edges and keeps
 // its four largest u with the positions of the first three.
-template <class P, bool STATS, bool REG3 = false>
+template <class P, bool STATS, bool REG3, int K>
 __device__ __forceinline__ void do_slice(const InstDesc& D, const Seg& S, const float* __restrict__ ys,
                                          unsigned long long* accG, unsigned long long* accC,
                                          unsigned long long* accQ, int64_t s, int coop_max, double& wobj,
@@ -528,7 +561,7 @@ __device__ __forceinline__ void do_slice(const InstDesc& D, const Seg& S, const 
   const int w4 = w >> 2;
   const typename P::IX* __restrict__ col0 = P::idx(D) + off;
   const typename P::T* __restrict__ ca0 = static_cast<const typename P::T*>(D.ca) + off;
-  Top4 tk = top4_empty();
+  TopK<K> tk = topk_empty<K>();
 #pragma unroll 4
   for (int g = 0; g < w4; ++g) {
     const int q = 32 * g + lane;
@@ -539,7 +572,7 @@ __device__ __forceinline__ void do_slice(const InstDesc& D, const Seg& S, const 
 #pragma unroll
     for (int e = 0; e < 4; ++e) {
       const float u = -fmaf(a[e], ys[jj[e]], c[e]);
-      top4_insert(u, 4 * g + e, tk.v0, tk.v1, tk.v2, tk.v3, tk.i0, tk.i1, tk.i2);
+      topk_insert<K>(u, 4 * g + e, tk);
     }
   }
   for (int k = 4 * w4; k < w; ++k) {
@@ -548,9 +581,9 @@ __device__ __forceinline__ void do_slice(const InstDesc& D, const Seg& S, const 
     float c, a;
     P::get(__ldg(ca0 + el), c, a);
     const float u = -fmaf(a, ys[j], c);
-    top4_insert(u, k, tk.v0, tk.v1, tk.v2, tk.v3, tk.i0, tk.i1, tk.i2);
+    topk_insert<K>(u, k, tk);
   }
-  finish_slice<P, STATS, REG3>(D, S, ys, accG, accC, accQ, s, w, col0, ca0, tk, coop_max, wobj, cn, oq);
+  finish_slice<P, STATS, REG3, K>(D, S, ys, accG, accC, accQ, s, w, col0, ca0, tk, coop_max, wobj, cn, oq);
 }
 
 // Certificate sweeps (STATS) keep the item sums of the window of items
@@ -558,7 +591,7 @@ __device__ __forceinline__ void do_slice(const InstDesc& D, const Seg& S, const 
 // fit in shared memory take one launch per window; every launch recomputes
 // the same x and writes the same objective partials, and the count sum is
 // flushed by the launch with jlo = 0.
-template <class P, bool STATS>
+template <class P, bool STATS, int K>
 __global__ void __launch_bounds__(kSweepThreads, 1)
     sweep_kernel(const InstDesc* __restrict__ insts, const Task* __restrict__ tasks,
                  const int32_t* __restrict__ cta_task, int smemJ, int coop_max, int jlo, int jw) {
@@ -624,7 +657,7 @@ __global__ void __launch_bounds__(kSweepThreads, 1)
         // static order: the FP64 objective partials are summed in a fixed order
         const int64_t step = static_cast<int64_t>(T.stride) * nw;
         for (int64_t s = T.first + static_cast<int64_t>(T.stride) * warp; s < T.end; s += step)
-          do_slice<P, STATS>(sD, S, ys, accG, accC, accQ, s, coop_max, wobj, cn, oq);
+          do_slice<P, STATS, false, K>(sD, S, ys, accG, accC, accQ, s, coop_max, wobj, cn, oq);
       } else {
         // dynamic order within the CTA (item sums are exact, so the order of
         // slices does not change any result)
@@ -634,8 +667,8 @@ __global__ void __launch_bounds__(kSweepThreads, 1)
           if (lane == 0) i = atomicAdd(&s_next, 1ull);
           i = __shfl_sync(kFull, i, 0);
           if (i >= nsl) break;
-          do_slice<P, STATS, !STATS>(sD, S, ys, accG, accC, accQ, T.first + i * T.stride, coop_max, wobj, cn,
-                                     oq);
+          do_slice<P, STATS, !STATS, K>(sD, S, ys, accG, accC, accQ, T.first + i * T.stride, coop_max, wobj, cn,
+                                        oq);
         }
         __syncthreads();
         if (threadIdx.x == 0) s_next = 0;
@@ -684,7 +717,7 @@ __global__ void __launch_bounds__(kSweepThreads, 1)
 // moves to another instance.  The last CTA to finish resets the counters for
 // the next launch.  The units are ordered by instance and shrink toward the
 // end of the table, so the CTAs finish together.
-template <class P>
+template <class P, int K>
 __global__ void __launch_bounds__(kSweepThreads, 1)
     sweep_dyn_kernel(const InstDesc* __restrict__ insts, const Task* __restrict__ units, int nunits,
                      unsigned* __restrict__ ctr, int smemJ, int coop_max) {
@@ -758,7 +791,7 @@ __global__ void __launch_bounds__(kSweepThreads, 1)
       if (lane == 0) i = static_cast<int64_t>(atomicAdd(&s_next, 1ull));
       i = __shfl_sync(kFull, i, 0);
       if (i >= nsl) break;
-      do_slice<P, false, true>(sD, S, ys, accG, nullptr, nullptr, T.first + i, coop_max, wobj, cn, oq);
+      do_slice<P, false, true, K>(sD, S, ys, accG, nullptr, nullptr, T.first + i, coop_max, wobj, cn, oq);
     }
     __syncthreads();
   }
@@ -772,9 +805,9 @@ __global__ void __launch_bounds__(kSweepThreads, 1)
   }
 }
 
-template <class P, bool STATS>
+template <class P, bool STATS, int K>
 constexpr auto kernel_of() {
-  return &sweep_kernel<P, STATS>;
+  return &sweep_kernel<P, STATS, K>;
 }
 
 }  // namespace
@@ -802,17 +835,23 @@ size_t sweep_smem_limit() {
   return optin > 1024 ? static_cast<size_t>(optin - 1024) : 0;  // room for static shared memory
 }
 
-template <class P>
-cudaError_t prepare_policy(int lim) {
-  cudaError_t e = cudaFuncSetAttribute(&sweep_dyn_kernel<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+template <class P, int K>
+cudaError_t prepare_width(int lim) {
+  cudaError_t e = cudaFuncSetAttribute(&sweep_dyn_kernel<P, K>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
   if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(kernel_of<P, false>(), cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+  e = cudaFuncSetAttribute(kernel_of<P, false, K>(), cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
   if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(kernel_of<P, true>(), cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+  return cudaFuncSetAttribute(kernel_of<P, true, K>(), cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
 }
 
 template <class P>
-cudaError_t launch_policy(const SweepLaunch& L, bool stats) {
+cudaError_t prepare_policy(int lim) {
+  const cudaError_t e = prepare_width<P, 4>(lim);
+  return e != cudaSuccess ? e : prepare_width<P, 8>(lim);
+}
+
+template <class P, int K>
+cudaError_t launch_width(const SweepLaunch& L, bool stats) {
   const int th = L.threads > 0 ? L.threads : kSweepThreads;
   const int cm = L.coop_max;
   if (stats) {
@@ -820,7 +859,7 @@ cudaError_t launch_policy(const SweepLaunch& L, bool stats) {
     if (w < 1) return cudaErrorInvalidValue;
     const size_t sm = sweep_stats_smem_bytes(L.smemJ, w);
     for (int jlo = 0; jlo < L.smemJ || jlo == 0; jlo += w) {
-      sweep_kernel<P, true><<<L.grid, th, sm, L.stream>>>(L.inst, L.tasks, L.cta_task, L.smemJ, cm, jlo, w);
+      sweep_kernel<P, true, K><<<L.grid, th, sm, L.stream>>>(L.inst, L.tasks, L.cta_task, L.smemJ, cm, jlo, w);
       const cudaError_t e = cudaGetLastError();
       if (e != cudaSuccess) return e;
     }
@@ -828,10 +867,15 @@ cudaError_t launch_policy(const SweepLaunch& L, bool stats) {
   }
   const size_t sm = sweep_smem_bytes(L.smemJ, false);
   if (L.units != nullptr)
-    sweep_dyn_kernel<P><<<L.grid, th, sm, L.stream>>>(L.inst, L.units, L.nunits, L.ctr, L.smemJ, cm);
+    sweep_dyn_kernel<P, K><<<L.grid, th, sm, L.stream>>>(L.inst, L.units, L.nunits, L.ctr, L.smemJ, cm);
   else
-    sweep_kernel<P, false><<<L.grid, th, sm, L.stream>>>(L.inst, L.tasks, L.cta_task, L.smemJ, cm, 0, L.smemJ);
+    sweep_kernel<P, false, K><<<L.grid, th, sm, L.stream>>>(L.inst, L.tasks, L.cta_task, L.smemJ, cm, 0, L.smemJ);
   return cudaGetLastError();
+}
+
+template <class P>
+cudaError_t launch_policy(const SweepLaunch& L, bool stats) {
+  return L.topk == 8 ? launch_width<P, 8>(L, stats) : launch_width<P, 4>(L, stats);
 }
 
 template <class V>

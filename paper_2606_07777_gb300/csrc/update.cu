@@ -57,13 +57,21 @@ __device__ double block_max(double v, double* sh) {
 // The iterate lam, y is FP64 (G from the exact fixed-point sum minus b in
 // FP64; products and sums rounded separately, no fused multiply-add, as the
 // FP64 reference arithmetic of the method takes them); the sweeps read FP32
-// copies written here.  The kernel also records the dual objective at the
+// copies written here.  The update also records the dual objective at the
 // sweep point (Sec. 3.2, Eq. dual):
 //   g(y) = sum_i (c x + gamma/2 x^2) + y^T G,
-// from the sweep's exact fixed-point objective sum and an FP64 dot product in
-// a fixed order, into the trajectory slot t mod kTrajCap.
-constexpr int kUpdPer = 4;          // coordinates per thread whose loads are issued together
-constexpr int kFistaThreads = 512;  // threads of the update CTA (registers for kUpdPer coordinates)
+// from the sweep's exact fixed-point objective sum and an FP64 dot product,
+// into the trajectory slot t mod kTrajCap.
+//
+// Grid: CTA x of row y takes coordinates x kUpdChunk .. of instance y (one
+// coordinate per thread: the FP64 work is spread over the SMs).  Scalars
+// that need every coordinate -- the dot product of g, the restart test, the
+// finiteness flag -- are summed per CTA in a fixed order, written as
+// partials, and added in CTA order by the last CTA of the instance to finish
+// (an integer ticket; no CTA waits for another), which also writes the new
+// iteration state.  With the adaptive restart a first kernel computes the
+// test the same way and leaves its decision for the second.
+constexpr int kUpdChunk = 256;  // coordinates per update CTA (one per thread)
 
 // Sums of two values over the block in a fixed order; results valid in thread 0.
 __device__ void block_sum2(double& a, double& b, double (*sh)[32]) {
@@ -89,103 +97,133 @@ __device__ void block_sum2(double& a, double& b, double (*sh)[32]) {
   __syncthreads();
 }
 
-__global__ void __launch_bounds__(kFistaThreads) fista_update_kernel(const UpdInst* __restrict__ tab) {
-  __shared__ double sh[2][32];
-  __shared__ int s_restart;
-  const UpdInst U = tab[blockIdx.x];
-  const DevState st = *U.state;
-  const double gamma = st.gamma;
-  const int64_t t1 = st.iter + 1;
-  const int64_t s1 = t1 / U.iters_per_stage;
-  const double gamma1 = U.gamma_tab[s1 < U.nstages ? s1 : U.nstages - 1];
-  const bool stage_restart = gamma1 != gamma;
-  const double th1 = 0.5 * (1.0 + sqrt(1.0 + 4.0 * st.theta * st.theta));
-  const double beta = (st.theta - 1.0) / th1;
-  const double step0 = U.curv_max > 0.0 ? gamma / U.curv_max : 0.0;
-  // coordinates 0..ncap-1 are (family, item) pairs; ncap is the count dual
-  // when present
-  const int NC = U.ncap;
-  const int D = NC + (U.count_on ? 1 : 0);
-  unsigned long long* __restrict__ acc = U.acc;
-  const double* __restrict__ b = U.b;
-  const double* __restrict__ curv = U.curv;
-  double* __restrict__ lam64 = U.lam64;
-  double* __restrict__ y64 = U.y64;
-  float* __restrict__ lam32 = U.lam;
-  float* __restrict__ y32 = U.y;
-  const bool pre = U.precondition != 0;
-  const bool test = U.adaptive_restart && !stage_restart;  // the restart test decides before any write
-  const double count_G = U.count_on ? to_real(*U.cnt, U.inv_scaleN) - U.count_M : 0.0;
-  auto step_of = [&](double h) { return pre ? (h > 0.0 ? gamma / h : 0.0) : step0; };
-  auto lam_next = [&](double G, double step, double yj) {
-    const double v = __dadd_rn(yj, __dmul_rn(step, G));
-    return v > 0.0 ? v : 0.0;
-  };
-  const int stride = static_cast<int>(blockDim.x);
-  double lg = 0.0, dot = 0.0, bad = 0.0;
-  bool restart = stage_restart;
-  // One pass loads kUpdPer coordinates per thread at once (their loads are
-  // independent); pass 0 runs only for the restart test, pass 1 writes.
-  for (int pass = test ? 0 : 1; pass < 2; ++pass) {
-    for (int j0 = threadIdx.x; j0 < D; j0 += stride * kUpdPer) {
-      double G[kUpdPer], yv[kUpdPer], lv[kUpdPer], hv[kUpdPer];
-      float yf[kUpdPer];
-#pragma unroll
-      for (int q = 0; q < kUpdPer; ++q) {
-        const int j = j0 + q * stride;
-        G[q] = yv[q] = lv[q] = hv[q] = 0.0;
-        yf[q] = 0.f;
-        if (j < D) {
-          G[q] = j < NC ? to_real(acc[j], U.inv_scaleG) - __ldg(b + j) : count_G;
-          yf[q] = y32[j];
-          yv[q] = y64[j];
-          lv[q] = lam64[j];
-          if (pre) hv[q] = __ldg(curv + j);
-        }
-      }
-#pragma unroll
-      for (int q = 0; q < kUpdPer; ++q) {
-        const int j = j0 + q * stride;
-        if (j >= D) continue;
-        const double step = step_of(hv[q]);
-        const double ln = lam_next(G[q], step, yv[q]);
-        if (pass == 0) {
-          // dual objective at the point the sweep read (the FP32 copy of y)
-          lg += static_cast<double>(yf[q]) * G[q];
-          if (step > 0.0) dot += __ddiv_rn(__dmul_rn(ln - yv[q], ln - lv[q]), step);
-        } else {
-          if (!test) lg += static_cast<double>(yf[q]) * G[q];
-          const double yn = restart ? ln : __dadd_rn(ln, __dmul_rn(beta, ln - lv[q]));
-          lam64[j] = ln;
-          y64[j] = yn;
-          lam32[j] = static_cast<float>(ln);
-          y32[j] = static_cast<float>(yn);
-          if (j < NC) acc[j] = 0ull;
-          if (!isfinite(G[q]) || !isfinite(yv[q]) || !isfinite(yn)) bad = 1.0;
-        }
-      }
-    }
-    if (pass == 0) {
-      block_sum2(lg, dot, sh);
-      if (threadIdx.x == 0) s_restart = dot < 0.0;
-      __syncthreads();
-      restart = s_restart != 0;
+// The step's scalars for iteration t of instance U.
+struct StepScalars {
+  DevState st;
+  int64_t s1;
+  double gamma1, th1, beta, step0;
+  bool stage_restart, test;
+  int NC, D;
+};
+__device__ __forceinline__ StepScalars step_scalars(const UpdInst& U) {
+  StepScalars c;
+  c.st = *U.state;
+  const int64_t t1 = c.st.iter + 1;
+  c.s1 = t1 / U.iters_per_stage;
+  c.gamma1 = U.gamma_tab[c.s1 < U.nstages ? c.s1 : U.nstages - 1];
+  c.stage_restart = c.gamma1 != c.st.gamma;
+  c.th1 = 0.5 * (1.0 + sqrt(1.0 + 4.0 * c.st.theta * c.st.theta));
+  c.beta = (c.st.theta - 1.0) / c.th1;
+  c.step0 = U.curv_max > 0.0 ? c.st.gamma / U.curv_max : 0.0;
+  c.test = U.adaptive_restart && !c.stage_restart;  // the restart test decides before any write
+  c.NC = U.ncap;
+  c.D = c.NC + (U.count_on ? 1 : 0);
+  return c;
+}
+
+// Coordinate j's gradient, step and candidate lam+ (j < D).
+__device__ __forceinline__ void coord(const UpdInst& U, const StepScalars& c, int j, double& G, double& step,
+                                      double& yj, double& ln) {
+  G = j < c.NC ? to_real(U.acc[j], U.inv_scaleG) - __ldg(U.b + j) : to_real(*U.cnt, U.inv_scaleN) - U.count_M;
+  if (U.precondition) {
+    const double h = __ldg(U.curv + j);
+    step = h > 0.0 ? c.st.gamma / h : 0.0;
+  } else {
+    step = c.step0;
+  }
+  yj = U.y64[j];
+  const double v = __dadd_rn(yj, __dmul_rn(step, G));
+  ln = v > 0.0 ? v : 0.0;
+}
+
+// Adds this CTA's two partials and, in the last CTA of the instance to
+// arrive, returns true with all of them visible (the ticket is reset).
+__device__ __forceinline__ bool arrive(const UpdInst& U, int slot, double a, double b, int* s_last) {
+  if (threadIdx.x == 0) {
+    U.part[2 * blockIdx.x] = a;
+    U.part[2 * blockIdx.x + 1] = b;
+    __threadfence();
+    const unsigned prev = atomicAdd(&U.ticket[slot], 1u);
+    *s_last = prev == static_cast<unsigned>(U.nct) - 1u;
+    if (*s_last) {
+      __threadfence();
+      U.ticket[slot] = 0u;
     }
   }
-  double lg2 = test ? 0.0 : lg;
-  block_sum2(lg2, bad, sh);
-  if (threadIdx.x == 0) {
-    if (!test) lg = lg2;
-    const double g = to_real(*U.objq, U.inv_scaleO) + lg;
+  __syncthreads();
+  return *s_last != 0;
+}
+
+// Kernel A (instances with the adaptive restart test due): the test's dot
+// product and g's dot product; the last CTA decides and keeps g's part.
+__global__ void __launch_bounds__(kUpdChunk) restart_test_kernel(const UpdInst* __restrict__ tab) {
+  __shared__ double sh[2][32];
+  __shared__ int s_last;
+  const UpdInst U = tab[blockIdx.y];
+  if (static_cast<int>(blockIdx.x) >= U.nct) return;
+  const StepScalars c = step_scalars(U);
+  if (!c.test) return;
+  const int j = blockIdx.x * kUpdChunk + threadIdx.x;
+  double lg = 0.0, dot = 0.0;
+  if (j < c.D) {
+    double G, step, yj, ln;
+    coord(U, c, j, G, step, yj, ln);
+    lg = static_cast<double>(U.y[j]) * G;
+    if (step > 0.0) dot = __ddiv_rn(__dmul_rn(ln - yj, ln - U.lam64[j]), step);
+  }
+  block_sum2(lg, dot, sh);
+  if (arrive(U, 0, lg, dot, &s_last) && threadIdx.x == 0) {
+    double L = 0.0, Dt = 0.0;
+    for (int k = 0; k < U.nct; ++k) {
+      L += __ldcg(U.part + 2 * k);
+      Dt += __ldcg(U.part + 2 * k + 1);
+    }
+    U.part[2 * U.nct] = L;
+    *U.flag = Dt < 0.0 ? 1 : 0;
+  }
+}
+
+// Kernel B: the step on every coordinate; the last CTA writes the state and
+// the trajectory.
+__global__ void __launch_bounds__(kUpdChunk) fista_update_kernel(const UpdInst* __restrict__ tab) {
+  __shared__ double sh[2][32];
+  __shared__ int s_last;
+  const UpdInst U = tab[blockIdx.y];
+  if (static_cast<int>(blockIdx.x) >= U.nct) return;
+  const StepScalars c = step_scalars(U);
+  const bool restart = c.stage_restart || (c.test && *U.flag != 0);
+  const int j = blockIdx.x * kUpdChunk + threadIdx.x;
+  double lg = 0.0, bad = 0.0;
+  if (j < c.D) {
+    double G, step, yj, ln;
+    coord(U, c, j, G, step, yj, ln);
+    if (!c.test) lg = static_cast<double>(U.y[j]) * G;  // (with the test, kernel A summed it)
+    const double yn = restart ? ln : __dadd_rn(ln, __dmul_rn(c.beta, ln - U.lam64[j]));
+    U.lam64[j] = ln;
+    U.y64[j] = yn;
+    U.lam[j] = static_cast<float>(ln);
+    U.y[j] = static_cast<float>(yn);
+    if (j < c.NC) U.acc[j] = 0ull;
+    if (!isfinite(G) || !isfinite(yj) || !isfinite(yn)) bad = 1.0;
+  }
+  block_sum2(lg, bad, sh);
+  if (arrive(U, 1, lg, bad, &s_last) && threadIdx.x == 0) {
+    double L = 0.0, B = 0.0;
+    for (int k = 0; k < U.nct; ++k) {
+      L += __ldcg(U.part + 2 * k);
+      B += __ldcg(U.part + 2 * k + 1);
+    }
+    if (c.test) L = __ldcg(U.part + 2 * U.nct);
+    const double g = to_real(*U.objq, U.inv_scaleO) + L;
     *U.objq = 0ull;
     if (U.count_on) *U.cnt_rw = 0ull;
-    U.traj[st.iter % kTrajCap] = g;
-    DevState n = st;
-    n.iter = t1;
-    n.theta = restart ? 1.0 : th1;
-    n.gamma = gamma1;
-    n.stage = static_cast<int32_t>(s1 < 0x7fffffff ? s1 : 0x7fffffff);
-    if (bad > 0.0 || !isfinite(g)) n.status |= kStatNumeric;
+    U.traj[c.st.iter % kTrajCap] = g;
+    DevState n = c.st;
+    n.iter = c.st.iter + 1;
+    n.theta = restart ? 1.0 : c.th1;
+    n.gamma = c.gamma1;
+    n.stage = static_cast<int32_t>(c.s1 < 0x7fffffff ? c.s1 : 0x7fffffff);
+    if (B > 0.0 || !isfinite(g)) n.status |= kStatNumeric;
     *U.state = n;
   }
 }
@@ -203,7 +241,11 @@ __global__ void __launch_bounds__(kUpdThreads) stats_kernel(const StatsInst* __r
   const StatsInst S = tab[blockIdx.x];
   const double gamma = *S.gamma;
   double obj = 0.0;
-  for (int k = threadIdx.x; k < S.nseg; k += blockDim.x) obj += S.seg_obj[S.seg_list[k]];
+  if (S.obj_in) {
+    if (threadIdx.x == 0) obj = *S.obj_in;
+  } else {
+    for (int k = threadIdx.x; k < S.nseg; k += blockDim.x) obj += S.seg_obj[S.seg_list[k]];
+  }
   // count constraint: sum x and the common scaling t = min(1, M / sum x)
   const double total = S.count_on ? to_real(*S.cnt, S.inv_sN) : 0.0;
   const double t = (S.count_on && total > S.count_M) ? S.count_M / total : 1.0;
@@ -253,15 +295,39 @@ __global__ void __launch_bounds__(kUpdThreads) stats_kernel(const StatsInst* __r
   }
 }
 
+// The objective partials of instance 0's certificate-sweep segments, summed
+// in a fixed order (a shard's share of the certificate objective).
+__global__ void __launch_bounds__(kUpdThreads) seg_sum_kernel(const StatsInst* __restrict__ tab, double* out) {
+  __shared__ double sh[32];
+  const StatsInst S = tab[0];
+  double obj = 0.0;
+  for (int k = threadIdx.x; k < S.nseg; k += blockDim.x) obj += S.seg_obj[S.seg_list[k]];
+  obj = block_sum(obj, sh);
+  if (threadIdx.x == 0) *out = obj;
+}
+
 }  // namespace
 
-cudaError_t launch_update(const UpdInst* dev_tab, int ninst, cudaStream_t s) {
-  fista_update_kernel<<<ninst, kFistaThreads, 0, s>>>(dev_tab);
+cudaError_t launch_update(const UpdInst* dev_tab, int ninst, int max_cta, bool any_test, cudaStream_t s) {
+  const dim3 grid(static_cast<unsigned>(max_cta > 0 ? max_cta : 1), static_cast<unsigned>(ninst));
+  if (any_test) {
+    restart_test_kernel<<<grid, kUpdChunk, 0, s>>>(dev_tab);
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  fista_update_kernel<<<grid, kUpdChunk, 0, s>>>(dev_tab);
   return cudaGetLastError();
 }
 
+int update_ctas(int64_t D) { return static_cast<int>((D + kUpdChunk - 1) / kUpdChunk); }
+
 cudaError_t launch_stats(const StatsInst* dev_tab, int ninst, cudaStream_t s) {
   stats_kernel<<<ninst, kUpdThreads, 0, s>>>(dev_tab);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_seg_sum(const StatsInst* dev_tab, double* out, cudaStream_t s) {
+  seg_sum_kernel<<<1, kUpdThreads, 0, s>>>(dev_tab, out);
   return cudaGetLastError();
 }
 

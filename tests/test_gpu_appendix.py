@@ -58,11 +58,13 @@ def check_calculate(s, inst, p, lam32, gamma):
     assert abs(g - ref["g"]) <= 2e-6 * (abs(ref["g"]) + abs(ref["obj"]) + 1e-9) + float(np.abs(p.c) @ tol)
 
 
-@pytest.mark.parametrize("kind,gamma", [(oracle.SIMPLEX_LE, 1e-2), (oracle.SIMPLEX_LE, 1e-3),
-                                        (oracle.BOX, 1e-2), (oracle.SIMPLEX_EQ, 1e-1)])
-def test_calculate_on_an_appendix_instance(dlm_lib, kind, gamma):
+@pytest.mark.parametrize("kind,gamma,topk", [(oracle.SIMPLEX_LE, 1e-2, 4), (oracle.SIMPLEX_LE, 1e-3, 4),
+                                             (oracle.BOX, 1e-2, 4), (oracle.SIMPLEX_EQ, 1e-1, 4),
+                                             (oracle.SIMPLEX_LE, 1e-2, 8), (oracle.SIMPLEX_EQ, 1e-1, 8)])
+def test_calculate_on_an_appendix_instance(dlm_lib, kind, gamma, topk):
     inst = app_instance(20_000, 300, 31)
     s = solver(dlm_lib, inst, kind)
+    s.set_options(topk=topk)
     p = oproblem(inst, kind)
     rng = np.random.default_rng(5)
     for scale in (0.3, 1.0, 3.0):
@@ -70,21 +72,27 @@ def test_calculate_on_an_appendix_instance(dlm_lib, kind, gamma):
     s.close()
 
 
-def test_trajectory_with_row_normalization(dlm_lib):
+@pytest.mark.parametrize("topk", [4, 8])
+def test_trajectory_with_row_normalization(dlm_lib, topk):
     inst = app_instance(20_000, 300, 31)
     s = solver(dlm_lib, inst)
     s.set_schedule(1e-2)
-    s.set_options(precondition=True)
-    # The momentum amplifies FP32 rounding geometrically on this instance
-    # (measured max |dlam| / max |lam|: 4e-7 after 25 steps, 2.2e-6 after
-    # 100, 2.4e-5 after 200); 100 steps keep the comparison within the FP32
-    # trajectory bound while lam is still moving on every resource.
-    T = 100
+    s.set_options(precondition=True, topk=topk)
+    # The momentum amplifies rounding geometrically on this instance (with
+    # FP32 storage of the iterate, max |dlam| / max |lam| measured 2.2e-6
+    # after 100 steps and 2.4e-5 after 200); here rows with four to seven
+    # active edges are common, so topk = 8 takes most of them without the
+    # threshold iteration.
+    T = 200
     s.step(T)
     lam = s.lam().cpu().numpy().astype(np.float64)
-    ref = oracle.fista(oproblem(inst), T, 1e-2, precondition=True, trajectory=False)["lam"]
+    out = oracle.fista(oproblem(inst), T, 1e-2, precondition=True)
+    ref = out["lam"]
     err = np.abs(lam - ref).max()
+    print(f"appendix trajectory topk={topk}: max |dlam| / |lam| = {err / np.abs(ref).max():.3e}")
     assert err <= 1e-5 * np.abs(ref).max(), f"max err {err:.3e} (|lam| {np.abs(ref).max():.3f})"
+    g = s.trajectory(0, T)
+    assert np.abs(g - out["g_traj"]).max() <= 1e-5 * np.abs(out["g_traj"]).max()
     s.close()
 
 

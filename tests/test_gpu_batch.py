@@ -191,3 +191,27 @@ def test_handle_mappings_are_bit_identical(dlm_lib, cases, alone, mapping, threa
         s.step(T)
         assert np.array_equal(lam_of(s).view(np.uint32), alone[k].view(np.uint32)), f"member {k} differs"
         s.close()
+
+
+def test_wide_scan_batch_is_bit_identical_to_single_handles(dlm_lib, cases):
+    # topk = 8 (eight values tracked in the first pass) on every member: the
+    # batch (dynamic units) and each handle alone (interleaved slices) agree
+    # bit for bit, as with the default scan
+    alone8 = []
+    for inst, sched, pre in cases:
+        s = make(dlm_lib, inst, sched, pre)
+        s.set_options(precondition=pre, topk=8)
+        s.step(T)
+        alone8.append(lam_of(s))
+        s.close()
+    solvers = [make(dlm_lib, *c) for c in cases]
+    for s, c in zip(solvers, cases):
+        s.set_options(precondition=c[2], topk=8)
+    bt = dlm_lib.Batch(solvers)
+    bt.set_options(mapping=3, topk=8)
+    bt.step(T)
+    for k, s in enumerate(solvers):
+        assert np.array_equal(lam_of(s).view(np.uint32), alone8[k].view(np.uint32)), f"member {k} differs"
+    bt.close()
+    for s in solvers:
+        s.close()

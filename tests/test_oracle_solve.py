@@ -182,6 +182,33 @@ def test_continuation_schedule_values():
     assert got[7] == 1e-3 and got[6] > 1e-3
 
 
+def test_long_schedule_stages_follow_the_closed_form():
+    # gamma_s = max(gamma_end, gamma_0 factor^s) for every stage, far past 64
+    # stages (Sec. 6, App. B.2: the decay reaches gamma_end at stage 90 here)
+    for s_ in (0, 1, 63, 64, 65, 89, 90, 91, 500):
+        want = max(1e-3, 1e-1 * 0.95 ** s_)
+        assert abs(oracle.stage_gamma(1e-1, 1e-3, 0.95, s_) - want) <= 1e-15 * want, s_
+    r = synth.recipe_production(I=200, J=10, seed=13)
+    r.deg_mean, r.deg_max = 4.0, 10
+    p = oracle.Problem.from_instance(synth.generate(r))
+    run = oracle.fista(p, 500, 1e-1, 1e-3, 0.95, iters_per_stage=5)
+    want = [max(1e-3, 1e-1 * 0.95 ** (t // 5)) for t in range(500)]
+    np.testing.assert_allclose(run["gamma_traj"], want, rtol=1e-14)
+
+
+def test_recorded_dual_value_is_g_at_the_swept_point():
+    # g_traj[t] is the dual objective at the point the t-th sweep evaluates,
+    # y_t (the momentum point that t iterations leave), at that iteration's gamma
+    r = synth.recipe_production(I=300, J=12, seed=21)
+    r.deg_mean, r.deg_max = 5.0, 12
+    p = oracle.Problem.from_instance(synth.generate(r))
+    full = oracle.fista(p, 60, 0.2, 0.05, 0.5, iters_per_stage=20)
+    for t in (0, 1, 7, 19, 20, 21, 45, 59):
+        y_t = oracle.fista(p, t, 0.2, 0.05, 0.5, iters_per_stage=20)["y"] if t > 0 else np.zeros(p.D)
+        g = oracle.sweep(p, y_t, full["gamma_traj"][t], want_x=False)["g"]
+        assert abs(full["g_traj"][t] - g) <= 1e-12 * max(1.0, abs(g)), t
+
+
 def test_stage_change_warm_starts_and_resets_momentum():
     # Two stages run at once equal stage 1, then a fresh run of stage 2 from
     # stage 1's lam (theta reset to 1, y = lam): Sec. 6 warm start.

@@ -101,7 +101,7 @@ typedef struct {
 /* Solver options (zero-initialised fields take the defaults).  The mapping
  * fields change only how the sweep is laid onto the GPU: every mapping gives
  * the same item sums (they are exact), and mappings with the same coop_max
- * give bit-identical iterates. */
+ * and short_rows give bit-identical iterates. */
 typedef struct {
   int32_t gap_every;     /* iterations between certified-gap checks in dlm_solve (default 50) */
   int32_t precondition;  /* 1: row normalization (App. B.2) as the per-item step gamma/sum_i a_ij^2 */
@@ -126,7 +126,13 @@ typedef struct {
                             the positions of all but the last: 0 or 4 (default), or 8 -- rows with up
                             to seven active edges then take their threshold without the iteration
                             over the row (more work per edge, fewer re-reads of the row) */
-  int32_t reserved[2];
+  int32_t short_rows;    /* 1: iteration sweeps of a single one-family handle without a count
+                            constraint (not box-cut) take the slices whose rows have at most 16
+                            edges in a second kernel that holds each row's values in registers and
+                            finds its threshold by the iteration over them (for instances whose
+                            short rows have many active edges); 0 (default): one sweep kernel.
+                            Certificate sweeps are unchanged.  Other handles ignore it. */
+  int32_t reserved[1];
 } dlm_options;
 
 /* Result of a certified-gap evaluation at the current iterate lam (one extra

@@ -62,7 +62,7 @@ class Options(ctypes.Structure):
     _fields_ = [("gap_every", ctypes.c_int32), ("precondition", ctypes.c_int32), ("mapping", ctypes.c_int32),
                 ("graph_iters", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32), ("coop_max", ctypes.c_int32),
                 ("block_threads", ctypes.c_int32), ("restart", ctypes.c_int32), ("topk", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 2)]
+                ("short_rows", ctypes.c_int32), ("reserved", ctypes.c_int32 * 1)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}
@@ -359,12 +359,13 @@ def dlm_batch_destroy(bt):
 
 
 def _options(gap_every=0, precondition=False, mapping=0, graph_iters=0, ctas_per_sm=0, coop_max=0, block_threads=0,
-             restart=False, topk=0):
+             restart=False, topk=0, short_rows=False):
     o = Options()
     o.gap_every, o.precondition, o.mapping = gap_every, int(bool(precondition)), mapping
     o.graph_iters, o.ctas_per_sm, o.coop_max, o.block_threads = graph_iters, ctas_per_sm, coop_max, block_threads
     o.restart = int(bool(restart))
     o.topk = int(topk)
+    o.short_rows = int(bool(short_rows))
     return o
 
 
@@ -436,9 +437,9 @@ class Solver:
         dlm_set_schedule(self.h, gamma0, gamma0 if gamma_end is None else gamma_end, factor, iters_per_stage)
 
     def set_options(self, gap_every=0, precondition=False, mapping=0, graph_iters=0, ctas_per_sm=0, coop_max=0,
-                    block_threads=0, restart=False, topk=0):
+                    block_threads=0, restart=False, topk=0, short_rows=False):
         dlm_set_options(self.h, _options(gap_every, precondition, mapping, graph_iters, ctas_per_sm, coop_max,
-                                         block_threads, restart, topk))
+                                         block_threads, restart, topk, short_rows))
 
     def options(self) -> Options:
         return dlm_get_options(self.h)

@@ -55,60 +55,6 @@ struct Counted : Base {
   static constexpr bool kCount = true;
 };
 
-// Item indices as uint16: the shared-memory item arrays bound a handle to
-// fewer than 65,536 items, so the layout keeps the index stream in 16 bits
-// (2 bytes per edge less to stream than int32).  A group of four edges of a
-// lane is one 64-bit load.
-template <class V>
-struct Narrow : V {
-  using IX = uint16_t;
-  __device__ __forceinline__ static const IX* idx(const InstDesc& D) { return D.col16; }
-  __device__ __forceinline__ static void idx4(const IX* p, int q, int j[4]) {
-    const uint2 v = __ldg(reinterpret_cast<const uint2*>(p) + q);
-    j[0] = static_cast<int>(v.x & 0xffffu), j[1] = static_cast<int>(v.x >> 16);
-    j[2] = static_cast<int>(v.y & 0xffffu), j[3] = static_cast<int>(v.y >> 16);
-  }
-};
-
-struct Seg {
-  float gamma, invg, gz, gzl, z;
-  float scaleG, scaleC, scaleQ, scaleN, scaleO;
-  float mu;  // count dual (0 without a count constraint): the floor of the threshold
-  int kind;
-  int count;
-  int jlo, jw;  // certificate sweeps: item sums kept for items jlo .. jlo + jw - 1
-};
-
-// Contributions of one edge with x > 0.
-template <class P, bool STATS>
-__device__ __forceinline__ void deposit(const Seg& S, int j, float c, float a, float x, unsigned long long* accG,
-                                        unsigned long long* accC, unsigned long long* accQ, float& ob,
-                                        unsigned long long& cn) {
-  if (P::kCount) cn += fixp(x, S.scaleN);
-  if (STATS) {
-    const unsigned jj = static_cast<unsigned>(j - S.jlo);
-    if (jj < static_cast<unsigned>(S.jw)) {
-      atomicAdd(&accG[jj], fixp(a * x, S.scaleG));
-      atomicAdd(&accC[jj], fixp(c * x, S.scaleC));
-      atomicAdd(&accQ[jj], fixp(x * x, S.scaleQ));
-    }
-  } else {
-    atomicAdd(&accG[j], fixp(a * x, S.scaleG));
-  }
-  ob += fmaf(0.5f * S.gamma * x, x, c * x);
-}
-
-// x of one edge given the user's threshold (tau, taul): (u - tau) / gamma
-// clipped at 0 (and at z for the box).  On the inequality simplex with the
-// threshold at its floor, and for the box, the caller passes tau = mu (the
-// count dual; 0 without a count constraint), taul = 0.
-__device__ __forceinline__ float x_general(const Seg& S, bool box, float tau, float taul, float c, float a,
-                                           float y) {
-  const F2 up = u_pair(c, a, y);
-  if (box) return fminf(fmaxf(((up.h - tau) + (up.l - taul)) * S.invg, 0.f), S.z);
-  return fmaxf((up.h - tau) + (up.l - taul), 0.f) * S.invg;
-}
-
 // Threshold of user t of the slice computed by the whole warp: lane l takes
 // edges l, l + 32, ... of the user (re-read from L1/L2; the warp has just
 // streamed them), the Michelot sums and the pair-arithmetic refinement are
@@ -594,7 +540,7 @@ __device__ __forceinline__ void do_slice(const InstDesc& D, const Seg& S, const 
 template <class P, bool STATS, int K>
 __global__ void __launch_bounds__(kSweepThreads, 1)
     sweep_kernel(const InstDesc* __restrict__ insts, const Task* __restrict__ tasks,
-                 const int32_t* __restrict__ cta_task, int smemJ, int coop_max, int jlo, int jw) {
+                 const int32_t* __restrict__ cta_task, int smemJ, int coop_max, int jlo, int jw, int64_t s_lim) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int accN = STATS ? jw : smemJ;
   unsigned long long* accG = reinterpret_cast<unsigned long long*>(smem_raw);
@@ -660,8 +606,10 @@ __global__ void __launch_bounds__(kSweepThreads, 1)
           do_slice<P, STATS, false, K>(sD, S, ys, accG, accC, accQ, s, coop_max, wobj, cn, oq);
       } else {
         // dynamic order within the CTA (item sums are exact, so the order of
-        // slices does not change any result)
-        const int64_t nsl = (T.end - T.first + T.stride - 1) / T.stride;
+        // slices does not change any result); slices from s_lim on belong to
+        // the short-row sweep
+        const int64_t end = T.end < s_lim ? T.end : s_lim;
+        const int64_t nsl = end > T.first ? (end - T.first + T.stride - 1) / T.stride : 0;
         for (;;) {
           int64_t i = 0;
           if (lane == 0) i = atomicAdd(&s_next, 1ull);
@@ -720,7 +668,7 @@ __global__ void __launch_bounds__(kSweepThreads, 1)
 template <class P, int K>
 __global__ void __launch_bounds__(kSweepThreads, 1)
     sweep_dyn_kernel(const InstDesc* __restrict__ insts, const Task* __restrict__ units, int nunits,
-                     unsigned* __restrict__ ctr, int smemJ, int coop_max) {
+                     unsigned* __restrict__ ctr, int smemJ, int coop_max, int64_t s_lim) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   unsigned long long* accG = reinterpret_cast<unsigned long long*>(smem_raw);
   float* ys = reinterpret_cast<float*>(accG + smemJ);
@@ -785,7 +733,7 @@ __global__ void __launch_bounds__(kSweepThreads, 1)
       __syncthreads();
     }
     const Task T = units[u];
-    const int64_t nsl = T.end - T.first;
+    const int64_t nsl = (T.end < s_lim ? T.end : s_lim) - T.first;  // slices from s_lim on: short-row sweep
     for (;;) {
       int64_t i = 0;
       if (lane == 0) i = static_cast<int64_t>(atomicAdd(&s_next, 1ull));
@@ -859,17 +807,22 @@ cudaError_t launch_width(const SweepLaunch& L, bool stats) {
     if (w < 1) return cudaErrorInvalidValue;
     const size_t sm = sweep_stats_smem_bytes(L.smemJ, w);
     for (int jlo = 0; jlo < L.smemJ || jlo == 0; jlo += w) {
-      sweep_kernel<P, true, K><<<L.grid, th, sm, L.stream>>>(L.inst, L.tasks, L.cta_task, L.smemJ, cm, jlo, w);
+      sweep_kernel<P, true, K><<<L.grid, th, sm, L.stream>>>(L.inst, L.tasks, L.cta_task, L.smemJ, cm, jlo, w,
+                                                             INT64_MAX);
       const cudaError_t e = cudaGetLastError();
       if (e != cudaSuccess) return e;
     }
     return cudaSuccess;
   }
   const size_t sm = sweep_smem_bytes(L.smemJ, false);
+  // with the short-row sweep on, this launch takes the slices before short_first
+  const int64_t lim = L.short_first >= 0 ? L.short_first : INT64_MAX;
+  if (lim == 0) return cudaSuccess;
   if (L.units != nullptr)
-    sweep_dyn_kernel<P, K><<<L.grid, th, sm, L.stream>>>(L.inst, L.units, L.nunits, L.ctr, L.smemJ, cm);
+    sweep_dyn_kernel<P, K><<<L.grid, th, sm, L.stream>>>(L.inst, L.units, L.nunits, L.ctr, L.smemJ, cm, lim);
   else
-    sweep_kernel<P, false, K><<<L.grid, th, sm, L.stream>>>(L.inst, L.tasks, L.cta_task, L.smemJ, cm, 0, L.smemJ);
+    sweep_kernel<P, false, K><<<L.grid, th, sm, L.stream>>>(L.inst, L.tasks, L.cta_task, L.smemJ, cm, 0, L.smemJ,
+                                                            lim);
   return cudaGetLastError();
 }
 
@@ -892,11 +845,14 @@ cudaError_t launch_values(const SweepLaunch& L, bool stats) {
 
 cudaError_t sweep_prepare(bool bf16) {
   const int lim = static_cast<int>(sweep_smem_limit());
-  return bf16 ? prepare_values<BF16Pair>(lim) : prepare_values<F32Pair>(lim);
+  const cudaError_t e = bf16 ? prepare_values<BF16Pair>(lim) : prepare_values<F32Pair>(lim);
+  return e != cudaSuccess ? e : sweep_short_prepare(bf16);
 }
 
 cudaError_t launch_sweep(const SweepLaunch& L, bool stats, bool bf16) {
-  return bf16 ? launch_values<BF16Pair>(L, stats) : launch_values<F32Pair>(L, stats);
+  const cudaError_t e = bf16 ? launch_values<BF16Pair>(L, stats) : launch_values<F32Pair>(L, stats);
+  if (e != cudaSuccess || stats) return e;
+  return launch_sweep_short(L, bf16);  // no-op unless the short-row sweep is on
 }
 
 }  // namespace dlm

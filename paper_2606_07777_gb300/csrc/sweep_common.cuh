@@ -1,6 +1,7 @@
 // sweep_common.cuh -- device helpers shared by the sweep kernels (sweep.cu,
-// sweep_multi.cu): the value layouts of the interleaved (c, a) stream, the
-// slice element order, 64-bit fixed point, and float-pair arithmetic.
+// sweep_short.cu, sweep_multi.cu, sweep_boxcut.cu): the value layouts of the
+// interleaved (c, a) stream, the slice element order, 64-bit fixed point,
+// float-pair arithmetic, and the per-edge deposit of the one-family sweeps.
 #pragma once
 
 #include <cuda_bf16.h>
@@ -82,6 +83,60 @@ __device__ __forceinline__ F2 f2_threshold(F2 sum, float gzh, float gzl, int n) 
   const float th = __fdiv_rn(num.h, fn);
   const float r = fmaf(-th, fn, num.h);
   return {th, __fdiv_rn(r + num.l, fn)};
+}
+
+// Item indices as uint16: the shared-memory item arrays bound a handle to
+// fewer than 65,536 items, so the layout keeps the index stream in 16 bits
+// (2 bytes per edge less to stream than int32).  A group of four edges of a
+// lane is one 64-bit load.
+template <class V>
+struct Narrow : V {
+  using IX = uint16_t;
+  __device__ __forceinline__ static const IX* idx(const InstDesc& D) { return D.col16; }
+  __device__ __forceinline__ static void idx4(const IX* p, int q, int j[4]) {
+    const uint2 v = __ldg(reinterpret_cast<const uint2*>(p) + q);
+    j[0] = static_cast<int>(v.x & 0xffffu), j[1] = static_cast<int>(v.x >> 16);
+    j[2] = static_cast<int>(v.y & 0xffffu), j[3] = static_cast<int>(v.y >> 16);
+  }
+};
+
+struct Seg {
+  float gamma, invg, gz, gzl, z;
+  float scaleG, scaleC, scaleQ, scaleN, scaleO;
+  float mu;  // count dual (0 without a count constraint): the floor of the threshold
+  int kind;
+  int count;
+  int jlo, jw;  // certificate sweeps: item sums kept for items jlo .. jlo + jw - 1
+};
+
+// Contributions of one edge with x > 0.
+template <class P, bool STATS>
+__device__ __forceinline__ void deposit(const Seg& S, int j, float c, float a, float x, unsigned long long* accG,
+                                        unsigned long long* accC, unsigned long long* accQ, float& ob,
+                                        unsigned long long& cn) {
+  if (P::kCount) cn += fixp(x, S.scaleN);
+  if (STATS) {
+    const unsigned jj = static_cast<unsigned>(j - S.jlo);
+    if (jj < static_cast<unsigned>(S.jw)) {
+      atomicAdd(&accG[jj], fixp(a * x, S.scaleG));
+      atomicAdd(&accC[jj], fixp(c * x, S.scaleC));
+      atomicAdd(&accQ[jj], fixp(x * x, S.scaleQ));
+    }
+  } else {
+    atomicAdd(&accG[j], fixp(a * x, S.scaleG));
+  }
+  ob += fmaf(0.5f * S.gamma * x, x, c * x);
+}
+
+// x of one edge given the user's threshold (tau, taul): (u - tau) / gamma
+// clipped at 0 (and at z for the box).  On the inequality simplex with the
+// threshold at its floor, and for the box, the caller passes tau = mu (the
+// count dual; 0 without a count constraint), taul = 0.
+__device__ __forceinline__ float x_general(const Seg& S, bool box, float tau, float taul, float c, float a,
+                                           float y) {
+  const F2 up = u_pair(c, a, y);
+  if (box) return fminf(fmaxf(((up.h - tau) + (up.l - taul)) * S.invg, 0.f), S.z);
+  return fmaxf((up.h - tau) + (up.l - taul), 0.f) * S.invg;
 }
 
 // Adds one value per thread into *dst exactly: warp sums, then thread 0 adds

@@ -136,7 +136,7 @@ def test_autotune_keeps_the_state_and_trajectory(dlm_lib, cases):
     assert (st0.iter, st0.theta, st0.stage) == (st1.iter, st1.theta, st1.stage)
     assert ms > 0 and chosen.block_threads in (512, 1024) and chosen.mapping in (1, 2, 3)
     assert s.options().coop_max == chosen.coop_max
-    ref.set_options(precondition=pre, coop_max=chosen.coop_max)
+    ref.set_options(precondition=pre, coop_max=chosen.coop_max, short_rows=chosen.short_rows)
     s.step(40)
     ref.step(40)
     assert torch.equal(s.lam(), ref.lam())

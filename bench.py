@@ -762,10 +762,8 @@ def main():
         bf16_err = bf16_error_statement(dlm, torch, inst, recipe, args.threads, gamma=w["schedule"][1])
 
     # ---- roofline of the dominant kernel (the sweep) ----
-    # with the short-row sweep an iteration's sweep is two launches (the
-    # general kernel over the slices wider than 16 edges, when there are any)
+    # the tuner may pick the short-row sweep (one launch, another kernel)
     short_on = bool(tuned is not None and tuned.get("short_rows"))
-    sweep_launches = (2 if int(np.diff(inst.row_ptr).max()) > 16 else 1) if short_on else 1
     peak, peak_kind = load_peaks()
     sweep_s = sweep_ms / 1000.0 / iters_total
     achieved = bytes_iter / sweep_s / 1e9
@@ -780,8 +778,8 @@ def main():
             if peak_kind == "measured" else "fallback 6.8 TB/s",
             "kernel": ("sweep_multi_kernel" if w.get("families", 1) > 1 else
                        "sweep_boxcut_kernel" if w.get("kind") == 3 else
-                       ("sweep_dyn_kernel" if tuned is not None and tuned["mapping"] == 3 else "sweep_kernel")
-                       + (" + sweep_short_kernel" if short_on else "")),
+                       "sweep_short_kernel" if short_on else
+                       "sweep_dyn_kernel" if tuned is not None and tuned["mapping"] == 3 else "sweep_kernel"),
             "algorithmic_bytes_per_launch": bytes_iter,
             "layout_bytes_per_launch": layout_bytes,
             "layout_frac": layout_bytes / sweep_s / 1e9 / peak,
@@ -820,7 +818,7 @@ def main():
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(dual_dim * 4),
                 "note": "per step: dlm_create from pinned host arrays (copy + layout), iterations, lam to host",
                 "create_seconds_by_phase": create_phases},
-        "gpu_launches": (sweep_launches + 1) * iters_total,
+        "gpu_launches": 2 * iters_total,
         "clocks": clocks,
         "graph_ms_per_step": graph_ms_per_step,
         "bf16_error": bf16_err,

@@ -127,11 +127,12 @@ typedef struct {
                             to seven active edges then take their threshold without the iteration
                             over the row (more work per edge, fewer re-reads of the row) */
   int32_t short_rows;    /* 1: iteration sweeps of a single one-family handle without a count
-                            constraint (not box-cut) take the slices whose rows have at most 16
-                            edges in a second kernel that holds each row's values in registers and
-                            finds its threshold by the iteration over them (for instances whose
-                            short rows have many active edges); 0 (default): one sweep kernel.
-                            Certificate sweeps are unchanged.  Other handles ignore it. */
+                            constraint (not box-cut) take the short-row kernel: each row of at most
+                            32 edges is held in registers and sorted to find its threshold in one
+                            scan, wider rows are read again for every pass of the threshold
+                            iteration -- for instances whose rows are short and have many active
+                            edges near the optimum; 0 (default): the general sweep.  Certificate
+                            sweeps are unchanged; other handles ignore it. */
   int32_t reserved[1];
 } dlm_options;
 

@@ -119,7 +119,7 @@ struct Runner {
   int win = 0;  // item window of certificate sweeps (smemJ when their arrays fit at once)
   int graph_iters = 10;
   int topk = 4;  // one-family sweeps: values tracked per row in the first pass
-  int64_t short_first = -1;  // short-row sweep: its first slice (-1: off)
+  bool short_rows = false;   // iteration sweeps take the short-row sweep (sweep_short.cu)
   int upd_ctas = 1;      // update grid width (the largest member's)
   bool upd_test = false; // some member has the adaptive restart (a test kernel runs first)
   InstDesc *inst_iter = nullptr, *inst_stats = nullptr;
@@ -534,6 +534,23 @@ dlm_status runner_build(Runner& R) {
   return write_tables(R);
 }
 
+// Whether the runner's iteration sweeps can take the short-row sweep: a
+// single one-family handle, not box-cut (a count constraint, set later, is
+// checked at launch).
+bool short_capable(const Runner& R) {
+  if (R.probs.size() != 1) return false;
+  const dlm_problem* p = R.probs[0];
+  return p->m == 1 && p->kind != DLM_BOX_CUT;
+}
+
+// Whether some slice's rows have at most kShortRowW edges (slices are sorted
+// by width, widest first: the last one is the narrowest).
+bool has_short_slices(const Runner& R) {
+  const dlm_problem* p = R.probs[0];
+  const int64_t ns = p->lay.nslices;
+  return ns > 0 && p->h_slice_off[ns] - p->h_slice_off[ns - 1] <= 32 * static_cast<int64_t>(kShortRowW);
+}
+
 SweepLaunch launch_of(const Runner& R, const InstDesc* tab) {
   SweepLaunch L;
   L.inst = tab;
@@ -555,9 +572,9 @@ SweepLaunch launch_of(const Runner& R, const InstDesc* tab) {
   L.nunits = static_cast<int32_t>(R.h_units.size());
   L.ctr = R.ctr;
   L.topk = R.topk;
-  if (R.short_first >= 0 && R.probs.size() == 1 && !L.count && L.fam == 1 && R.probs[0]->kind != DLM_BOX_CUT) {
-    L.short_first = R.short_first;
-    L.short_end = R.probs[0]->lay.nslices;
+  if (R.short_rows && short_capable(R) && !L.count) {
+    L.short_rows = true;
+    L.nslices0 = R.probs[0]->lay.nslices;
   }
   return L;
 }
@@ -654,26 +671,6 @@ dlm_status runner_step_timed(Runner& R, int64_t n_iters, double* sweep_ms, doubl
   return DLM_OK;
 }
 
-// First slice of the short-row sweep (widths at most kShortRowW; slices are
-// sorted by width, widest first), or -1 when the runner cannot take it (a
-// batch, several families, the box-cut set) or has no such slice.
-int64_t short_slices_from(const Runner& R) {
-  if (R.probs.size() != 1) return -1;
-  const dlm_problem* p = R.probs[0];
-  if (p->m != 1 || p->kind == DLM_BOX_CUT) return -1;
-  const int64_t ns = p->lay.nslices;
-  const std::vector<int64_t>& so = p->h_slice_off;
-  int64_t a = 0, b = ns;  // first s with width(s) <= kShortRowW
-  while (a < b) {
-    const int64_t m = (a + b) / 2;
-    if (so[m + 1] - so[m] > 32 * static_cast<int64_t>(kShortRowW))
-      a = m + 1;
-    else
-      b = m;
-  }
-  return a < ns ? a : -1;
-}
-
 // Applies mapping options to a runner: grid, threads, cooperative threshold,
 // assignment.  Rebuilds the tasks when the launch shape changes.
 dlm_status runner_configure(Runner& R, const dlm_options& o, bool force) {
@@ -693,9 +690,8 @@ dlm_status runner_configure(Runner& R, const dlm_options& o, bool force) {
   const int topk = o.topk == 8 ? 8 : 4;
   if (topk != R.topk) invalidate_graph(R);
   R.topk = topk;
-  const int64_t sf = o.short_rows ? short_slices_from(R) : -1;
-  if (sf != R.short_first) invalidate_graph(R);
-  R.short_first = sf;
+  if ((o.short_rows != 0) != R.short_rows) invalidate_graph(R);
+  R.short_rows = o.short_rows != 0;
   if (force || grid != R.grid || threads != R.threads || assign2 != R.assign) {
     R.grid = grid;
     R.threads = threads;
@@ -947,9 +943,9 @@ dlm_status tune(Runner& R, dlm_options base, int iters, dlm_options* chosen, dou
       best = o;
     }
   }
-  // the short-row sweep for the slices of at most kShortRowW edges, with the
-  // choices above (single one-family handles)
-  if (short_slices_from(R) >= 0) {
+  // the short-row sweep, with the choices above (single one-family handles
+  // with rows of at most kShortRowW edges)
+  if (short_capable(R) && has_short_slices(R)) {
     dlm_options o = best;
     o.short_rows = best.short_rows ? 0 : 1;
     double sw = 0;

@@ -20,7 +20,7 @@ constexpr int64_t kMaxStageTable = int64_t(1) << 20;  // continuation stages a s
 constexpr int kTrajCap = 4096;       // dual objective values kept per handle (ring, one per iteration)
 constexpr int kMaxSegTasks = 16;     // tasks of one instance in one CTA
 constexpr int kMaxFamilies = 4;      // capacity families per instance (Def. 1)
-constexpr int kShortRowW = 16;       // widest slice the short-row sweep takes (sweep_short.cu)
+constexpr int kShortRowW = 32;       // widest rows the short-row sweep holds in registers (sweep_short.cu)
 
 // Error bits of the device status word.
 enum : int32_t { kStatNumeric = 1, kStatTimeout = 2 };
@@ -130,10 +130,9 @@ struct SweepLaunch {
   int32_t fam;              // capacity families (> 1: the general sweep of sweep_multi.cu)
   int32_t topk = 4;         // one-family sweep: largest values tracked per row in the first pass (4 or 8)
   // Short-row sweep (iteration sweeps of a single one-family handle without a
-  // count constraint): slices short_first .. short_end - 1 of instance 0 take
-  // sweep_short.cu, the general sweep the slices before them (-1: off).
-  int64_t short_first = -1;
-  int64_t short_end = 0;
+  // count constraint, sweep_short.cu): slices 0 .. nslices0 - 1 of instance 0.
+  bool short_rows = false;
+  int64_t nslices0 = 0;
 };
 constexpr int kDefaultCoopMax = 12;
 
@@ -177,7 +176,8 @@ int sweep_stats_window(int smemJ);
 size_t sweep_smem_limit();             // usable dynamic shared memory per sweep CTA on this device
 cudaError_t sweep_prepare(bool bf16);  // raises the dynamic shared-memory limit
 cudaError_t launch_sweep(const SweepLaunch& L, bool stats, bool bf16);
-// sweep_short.cu: the iteration sweep of the short slices (L.short_first ..).
+// sweep_short.cu: the iteration sweep with rows of at most kShortRowW edges
+// held in registers (L.short_rows).
 cudaError_t sweep_short_prepare(bool bf16);
 cudaError_t launch_sweep_short(const SweepLaunch& L, bool bf16);
 // The update of ninst instances: a grid of max_cta x ninst CTAs (instance i

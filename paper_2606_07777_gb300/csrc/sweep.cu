@@ -540,7 +540,7 @@ __device__ __forceinline__ void do_slice(const InstDesc& D, const Seg& S, const 
 template <class P, bool STATS, int K>
 __global__ void __launch_bounds__(kSweepThreads, 1)
     sweep_kernel(const InstDesc* __restrict__ insts, const Task* __restrict__ tasks,
-                 const int32_t* __restrict__ cta_task, int smemJ, int coop_max, int jlo, int jw, int64_t s_lim) {
+                 const int32_t* __restrict__ cta_task, int smemJ, int coop_max, int jlo, int jw) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int accN = STATS ? jw : smemJ;
   unsigned long long* accG = reinterpret_cast<unsigned long long*>(smem_raw);
@@ -606,10 +606,8 @@ __global__ void __launch_bounds__(kSweepThreads, 1)
           do_slice<P, STATS, false, K>(sD, S, ys, accG, accC, accQ, s, coop_max, wobj, cn, oq);
       } else {
         // dynamic order within the CTA (item sums are exact, so the order of
-        // slices does not change any result); slices from s_lim on belong to
-        // the short-row sweep
-        const int64_t end = T.end < s_lim ? T.end : s_lim;
-        const int64_t nsl = end > T.first ? (end - T.first + T.stride - 1) / T.stride : 0;
+        // slices does not change any result)
+        const int64_t nsl = (T.end - T.first + T.stride - 1) / T.stride;
         for (;;) {
           int64_t i = 0;
           if (lane == 0) i = atomicAdd(&s_next, 1ull);
@@ -668,7 +666,7 @@ __global__ void __launch_bounds__(kSweepThreads, 1)
 template <class P, int K>
 __global__ void __launch_bounds__(kSweepThreads, 1)
     sweep_dyn_kernel(const InstDesc* __restrict__ insts, const Task* __restrict__ units, int nunits,
-                     unsigned* __restrict__ ctr, int smemJ, int coop_max, int64_t s_lim) {
+                     unsigned* __restrict__ ctr, int smemJ, int coop_max) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   unsigned long long* accG = reinterpret_cast<unsigned long long*>(smem_raw);
   float* ys = reinterpret_cast<float*>(accG + smemJ);
@@ -733,7 +731,7 @@ __global__ void __launch_bounds__(kSweepThreads, 1)
       __syncthreads();
     }
     const Task T = units[u];
-    const int64_t nsl = (T.end < s_lim ? T.end : s_lim) - T.first;  // slices from s_lim on: short-row sweep
+    const int64_t nsl = T.end - T.first;
     for (;;) {
       int64_t i = 0;
       if (lane == 0) i = static_cast<int64_t>(atomicAdd(&s_next, 1ull));
@@ -807,22 +805,17 @@ cudaError_t launch_width(const SweepLaunch& L, bool stats) {
     if (w < 1) return cudaErrorInvalidValue;
     const size_t sm = sweep_stats_smem_bytes(L.smemJ, w);
     for (int jlo = 0; jlo < L.smemJ || jlo == 0; jlo += w) {
-      sweep_kernel<P, true, K><<<L.grid, th, sm, L.stream>>>(L.inst, L.tasks, L.cta_task, L.smemJ, cm, jlo, w,
-                                                             INT64_MAX);
+      sweep_kernel<P, true, K><<<L.grid, th, sm, L.stream>>>(L.inst, L.tasks, L.cta_task, L.smemJ, cm, jlo, w);
       const cudaError_t e = cudaGetLastError();
       if (e != cudaSuccess) return e;
     }
     return cudaSuccess;
   }
   const size_t sm = sweep_smem_bytes(L.smemJ, false);
-  // with the short-row sweep on, this launch takes the slices before short_first
-  const int64_t lim = L.short_first >= 0 ? L.short_first : INT64_MAX;
-  if (lim == 0) return cudaSuccess;
   if (L.units != nullptr)
-    sweep_dyn_kernel<P, K><<<L.grid, th, sm, L.stream>>>(L.inst, L.units, L.nunits, L.ctr, L.smemJ, cm, lim);
+    sweep_dyn_kernel<P, K><<<L.grid, th, sm, L.stream>>>(L.inst, L.units, L.nunits, L.ctr, L.smemJ, cm);
   else
-    sweep_kernel<P, false, K><<<L.grid, th, sm, L.stream>>>(L.inst, L.tasks, L.cta_task, L.smemJ, cm, 0, L.smemJ,
-                                                            lim);
+    sweep_kernel<P, false, K><<<L.grid, th, sm, L.stream>>>(L.inst, L.tasks, L.cta_task, L.smemJ, cm, 0, L.smemJ);
   return cudaGetLastError();
 }
 
@@ -850,9 +843,9 @@ cudaError_t sweep_prepare(bool bf16) {
 }
 
 cudaError_t launch_sweep(const SweepLaunch& L, bool stats, bool bf16) {
-  const cudaError_t e = bf16 ? launch_values<BF16Pair>(L, stats) : launch_values<F32Pair>(L, stats);
-  if (e != cudaSuccess || stats) return e;
-  return launch_sweep_short(L, bf16);  // no-op unless the short-row sweep is on
+  // iteration sweeps of a handle with the short-row sweep on take it alone
+  if (!stats && L.short_rows) return launch_sweep_short(L, bf16);
+  return bf16 ? launch_values<BF16Pair>(L, stats) : launch_values<F32Pair>(L, stats);
 }
 
 }  // namespace dlm

@@ -1,18 +1,19 @@
-// sweep_short.cu -- the iteration sweep over slices of short rows.
+// sweep_short.cu -- the iteration sweep for instances of short rows.
 //
-// Rows of at most kShortRowW edges (the tail of the degree-sorted slice
-// order) are projected from registers: one pass streams the row and keeps its
-// values u = -(c + a y); a sorting network orders them and the sort-based
-// threshold rule finds the active set in one scan; the pair-arithmetic
-// refinement and the deposits read the row's edges again (from L1).  The
-// general sweep (sweep.cu) tracks the four (or eight) largest values and, for
-// rows with more active edges, iterates over the row, streaming it again for
-// every pass -- the usual case near the optimum on instances whose short rows
-// are mostly active (App. A's construction: about ten edges per request, many
-// within gamma z of the row's maximum).  With this sweep switched on
-// (dlm_options.short_rows) an iteration takes two launches, the general sweep
-// over the wider slices and this one over the rest, both adding into the same
-// exact fixed-point sums; certificate sweeps always take the general sweep.
+// Rows of at most kShortRowW (32) edges are projected from registers: one
+// pass streams the row and keeps its values u = -(c + a y) (with, for short
+// enough rows, each edge's value as a float pair or its dual); a sorting
+// network orders the values and the sort-based threshold rule finds the
+// active set in one scan; the pair-arithmetic refinement and the deposits read
+// the row's c, a and items again (from L1).  The general sweep (sweep.cu)
+// tracks the four (or eight) largest values and, for rows with more active
+// edges, iterates over the row, streaming it again for every pass -- the
+// usual case near the optimum on instances whose rows are short and mostly
+// active (App. A's construction: about ten edges per request, many within
+// gamma z of the row's maximum).  With this sweep switched on
+// (dlm_options.short_rows) it takes every slice of the iteration sweep; the
+// rare wider rows take a plain re-reading threshold iteration.  Certificate
+// sweeps always take the general sweep.
 //
 // Arithmetic per row (Sec. 3.2 Eq. primal-recovery; Sec. 4.3 sorts the row to
 // find the simplex threshold, as here): with the values sorted,
@@ -44,31 +45,40 @@ __device__ __forceinline__ void sort_desc(float (&v)[N]) {
   }
 }
 
-// One slice whose width w lies in (WC - 4, WC]: groups 0 .. G - 2 of the
-// lane's edges are full groups of four, group G - 1 is a full group when
-// w = WC and otherwise the slice's tail of w - 4 (G - 1) edges, stored
-// edge-major (layout.cu).
+// One slice of width w <= WC (a multiple of four): the lane's edges
+// 0 .. 4 w4 - 1 are w4 = w / 4 groups of four, the rest the slice's tail of
+// w - 4 w4 edges, stored edge-major (layout.cu); positions past w are
+// padding.
+//
+// What the first pass keeps besides the sorted values depends on the width
+// (registers): up to 12 edges every edge's u as a float pair (uh, ul), so the
+// refinement is a register pass and the deposits read only the edges' c, a
+// and item again; 13 to 16 edges each edge's dual y_j, the later passes
+// recomputing the pair from c, a read again; wider rows nothing more, the
+// later passes also gathering y_j again.
 template <class P, int WC>
 __device__ __forceinline__ void short_slice(const InstDesc& D, const Seg& S, const float* __restrict__ ys,
                                             unsigned long long* accG, int64_t off, int w,
                                             unsigned long long& oq) {
   constexpr int G = WC / 4;
+  constexpr bool KEEP = WC <= 12;
+  constexpr bool YK = WC > 12 && WC <= 16;
   const int lane = threadIdx.x & 31;
-  const bool full = w == WC;
+  const int w4 = w >> 2;
   const uint16_t* __restrict__ col0 = D.col16 + off;
   const typename P::T* __restrict__ ca0 = static_cast<const typename P::T*>(D.ca) + off;
   const bool box = S.kind == DLM_BOX;
   const bool eq = S.kind == DLM_SIMPLEX_EQ;
 
-  // Loads edges 4 g .. 4 g + 3 of the lane (padding and edges past w:
-  // c = +inf, a = 0, j = 0, so that u = -inf).
+  // Edges 4 g .. 4 g + 3 of the lane (padding and edges past w: c = +inf,
+  // a = 0, j = 0, so that u = -inf).
   struct Grp {
     int j[4];
     float c[4], a[4];
   };
   auto group = [&](int g) {
     Grp r;
-    if (g < G - 1 || full) {
+    if (g < w4) {
       const int q = 32 * g + lane;
       P::idx4(col0, q, r.j);
       P::get4(ca0, q, r.c, r.a);
@@ -78,7 +88,7 @@ __device__ __forceinline__ void short_slice(const InstDesc& D, const Seg& S, con
         r.j[e] = 0;
         r.c[e] = INFINITY;
         r.a[e] = 0.f;
-        if (4 * g + e < w) {
+        if (g == w4 && 4 * g + e < w) {
           const int el = 128 * g + 32 * e + lane;
           P::get(__ldg(ca0 + el), r.c[e], r.a[e]);
           r.j[e] = static_cast<int>(__ldg(col0 + el));
@@ -88,14 +98,29 @@ __device__ __forceinline__ void short_slice(const InstDesc& D, const Seg& S, con
     return r;
   };
 
-  // The row's u, sorted descending (the edge order is not kept: the passes
-  // below read the edges again).
-  float v[WC];
+  // First pass: the values sorted descending into v; per edge (edge order)
+  // the pair (uh, ul) with KEEP, else the dual y.  The value an edge is
+  // ranked and tested by is uh with KEEP (the pair's high part; -inf for
+  // padding) and -fma(a, y, c) otherwise.
+  float v[WC], uh[KEEP ? WC : 1], ul[KEEP ? WC : 1], yk[YK ? WC : 1];
 #pragma unroll
   for (int g = 0; g < G; ++g) {
     const Grp r = group(g);
 #pragma unroll
-    for (int e = 0; e < 4; ++e) v[4 * g + e] = -fmaf(r.a[e], ys[r.j[e]], r.c[e]);
+    for (int e = 0; e < 4; ++e) {
+      const int k = 4 * g + e;
+      const float y = ys[r.j[e]];
+      if constexpr (KEEP) {
+        const F2 u = u_pair(r.c[e], r.a[e], y);
+        const bool pad = r.c[e] == INFINITY;
+        uh[k] = pad ? -INFINITY : u.h;
+        ul[k] = pad ? 0.f : u.l;
+        v[k] = uh[k];
+      } else {
+        if constexpr (YK) yk[k] = y;
+        v[k] = -fmaf(r.a[e], y, r.c[e]);
+      }
+    }
   }
   sort_desc<WC>(v);
   // no edge with x > 0: an empty row (all padding), or every u <= 0 on the
@@ -124,15 +149,25 @@ __device__ __forceinline__ void short_slice(const InstDesc& D, const Seg& S, con
       // the threshold over the active set in pair arithmetic (edge order)
       F2 ps{0.f, 0.f};
       int cnt = 0;
+      if constexpr (KEEP) {
 #pragma unroll
-      for (int g = 0; g < G; ++g) {
-        const Grp r = group(g);
-#pragma unroll
-        for (int e = 0; e < 4; ++e) {
-          const float y = ys[r.j[e]];
-          if (-fmaf(r.a[e], y, r.c[e]) > tau) {
-            ps = f2_add(ps, u_pair(r.c[e], r.a[e], y));
+        for (int k = 0; k < WC; ++k) {
+          if (uh[k] > tau) {
+            ps = f2_add(ps, F2{uh[k], ul[k]});
             ++cnt;
+          }
+        }
+      } else {
+#pragma unroll
+        for (int g = 0; g < G; ++g) {
+          const Grp rg = group(g);
+#pragma unroll
+          for (int e = 0; e < 4; ++e) {
+            const float y = YK ? yk[YK ? 4 * g + e : 0] : ys[rg.j[e]];
+            if (-fmaf(rg.a[e], y, rg.c[e]) > tau) {
+              ps = f2_add(ps, u_pair(rg.c[e], rg.a[e], y));
+              ++cnt;
+            }
           }
         }
       }
@@ -155,26 +190,134 @@ __device__ __forceinline__ void short_slice(const InstDesc& D, const Seg& S, con
   if (!none) {
 #pragma unroll
     for (int g = 0; g < G; ++g) {
-      const Grp r = group(g);
+      const Grp rg = group(g);
 #pragma unroll
       for (int e = 0; e < 4; ++e) {
-        const float y = ys[r.j[e]];
-        if (-fmaf(r.a[e], y, r.c[e]) > tau) {
-          const float x = single ? S.z : x_general(S, box, tau, taul, r.c[e], r.a[e], y);
-          if (x > 0.f) deposit<P, false>(S, r.j[e], r.c[e], r.a[e], x, accG, nullptr, nullptr, ob, cn);
+        const int k = 4 * g + e;
+        float x = 0.f;
+        if constexpr (KEEP) {
+          if (uh[k] > tau) {
+            const float d = (uh[k] - tau) + (ul[k] - taul);
+            x = single ? S.z : box ? fminf(fmaxf(d * S.invg, 0.f), S.z) : fmaxf(d, 0.f) * S.invg;
+          }
+        } else {
+          const float y = YK ? yk[YK ? k : 0] : ys[rg.j[e]];
+          if (-fmaf(rg.a[e], y, rg.c[e]) > tau) x = single ? S.z : x_general(S, box, tau, taul, rg.c[e], rg.a[e], y);
         }
+        if (x > 0.f) deposit<P, false>(S, rg.j[e], rg.c[e], rg.a[e], x, accG, nullptr, nullptr, ob, cn);
       }
     }
   }
   oq += fixp(ob, S.scaleO);
 }
 
-// Slices s_begin .. s_end - 1 of instance 0, dealt to the warps in turn
-// (every warp gets the same mix of widths); item sums in shared memory,
-// flushed once per CTA.
+// A slice of rows wider than kShortRowW (few, on the instances this sweep is
+// for): each pass reads the lane's row again -- its maximum, then the
+// Michelot iteration tau <- (sum_{u > tau} u - gamma z) / #{u > tau} from the
+// lower bound max u - gamma z (the active sets shrink until two passes
+// agree), the pair-arithmetic refinement over the final set and the deposits.
+template <class P>
+__device__ __forceinline__ void wide_slice(const InstDesc& D, const Seg& S, const float* __restrict__ ys,
+                                        unsigned long long* accG, int64_t off, int w, unsigned long long& oq) {
+  const int lane = threadIdx.x & 31;
+  const int w4 = w >> 2;
+  const uint16_t* __restrict__ col0 = D.col16 + off;
+  const typename P::T* __restrict__ ca0 = static_cast<const typename P::T*>(D.ca) + off;
+  const bool box = S.kind == DLM_BOX;
+  const bool eq = S.kind == DLM_SIMPLEX_EQ;
+  auto edge = [&](int k, int& j, float& c, float& a) {
+    const int el = sell_el(k, lane, w4);
+    j = static_cast<int>(__ldg(col0 + el));
+    P::get(__ldg(ca0 + el), c, a);
+  };
+  float m = -INFINITY;
+#pragma unroll 1
+  for (int k = 0; k < w; ++k) {
+    int j;
+    float c, a;
+    edge(k, j, c, a);
+    m = fmaxf(m, -fmaf(a, ys[j], c));
+  }
+  const bool none = m == -INFINITY || (!eq && !(m > 0.f));
+  float tau = 0.f, taul = 0.f;
+  bool single = false;
+  if (!box && !none) {
+    tau = m - S.gz;
+    int n = 0, prevn = -1;
+#pragma unroll 1
+    for (int it = 0; it <= w; ++it) {  // every pass shrinks the set or stops
+      float sm = 0.f;
+      int cnt = 0;
+#pragma unroll 1
+      for (int k = 0; k < w; ++k) {
+        int j;
+        float c, a;
+        edge(k, j, c, a);
+        const float u = -fmaf(a, ys[j], c);
+        if (u > tau) {
+          sm += u;
+          ++cnt;
+        }
+      }
+      n = cnt;
+      if (cnt == prevn || cnt == 0) break;
+      prevn = cnt;
+      const float tn = __fdiv_rn(sm - S.gz, static_cast<float>(cnt));
+      if (tn == tau) break;
+      tau = tn;
+    }
+    bool zero = !eq && tau <= 0.f;
+    single = !zero && n == 1;
+    if (!zero && !single) {
+      F2 ps{0.f, 0.f};
+      int cnt = 0;
+#pragma unroll 1
+      for (int k = 0; k < w; ++k) {
+        int j;
+        float c, a;
+        edge(k, j, c, a);
+        const float y = ys[j];
+        if (-fmaf(a, y, c) > tau) {
+          ps = f2_add(ps, u_pair(c, a, y));
+          ++cnt;
+        }
+      }
+      const F2 t2 = f2_threshold(ps, S.gz, S.gzl, cnt > 0 ? cnt : 1);
+      if (!eq && t2.h + t2.l <= 0.f) {
+        zero = true;
+      } else {
+        tau = t2.h;
+        taul = t2.l;
+      }
+    }
+    if (zero) {
+      tau = 0.f;
+      taul = 0.f;
+    }
+  }
+  float ob = 0.f;
+  unsigned long long cn = 0ull;
+  if (!none) {
+#pragma unroll 1
+    for (int k = 0; k < w; ++k) {
+      int j;
+      float c, a;
+      edge(k, j, c, a);
+      const float y = ys[j];
+      if (-fmaf(a, y, c) > tau) {
+        const float x = single ? S.z : x_general(S, box, tau, taul, c, a, y);
+        if (x > 0.f) deposit<P, false>(S, j, c, a, x, accG, nullptr, nullptr, ob, cn);
+      }
+    }
+  }
+  oq += fixp(ob, S.scaleO);
+}
+
+// Every slice of instance 0, dealt to the warps in turn (every warp gets the
+// same mix of widths); item sums in shared memory, flushed once per CTA.
 template <class P>
 __global__ void __launch_bounds__(kSweepThreads, 1)
-    sweep_short_kernel(const InstDesc* __restrict__ insts, int64_t s_begin, int64_t s_end) {
+    sweep_short_kernel(const InstDesc* __restrict__ insts, int64_t nslices) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ InstDesc sD;
   __shared__ unsigned long long s_red[32];
@@ -204,11 +347,17 @@ __global__ void __launch_bounds__(kSweepThreads, 1)
   unsigned long long oq = 0ull;
   const int nw = blockDim.x >> 5;
   const int64_t step = static_cast<int64_t>(gridDim.x) * nw;
-  for (int64_t s = s_begin + static_cast<int64_t>(blockIdx.x) * nw + (threadIdx.x >> 5); s < s_end; s += step) {
+  for (int64_t s = static_cast<int64_t>(blockIdx.x) * nw + (threadIdx.x >> 5); s < nslices; s += step) {
     const int64_t off = __ldg(sD.slice_off + s);
     const int w = __ldg(sD.slice_w + s);
-    // width classes of four (warp-uniform branch)
-    if (w > 12)
+    // width classes (warp-uniform branch)
+    if (w > kShortRowW)
+      wide_slice<P>(sD, S, ys, accG, off, w, oq);
+    else if (w > 24)
+      short_slice<P, 32>(sD, S, ys, accG, off, w, oq);
+    else if (w > 16)
+      short_slice<P, 24>(sD, S, ys, accG, off, w, oq);
+    else if (w > 12)
       short_slice<P, 16>(sD, S, ys, accG, off, w, oq);
     else if (w > 8)
       short_slice<P, 12>(sD, S, ys, accG, off, w, oq);
@@ -229,7 +378,7 @@ template <class V>
 cudaError_t launch_short_values(const SweepLaunch& L) {
   const int th = L.threads > 0 ? L.threads : kSweepThreads;
   const size_t sm = sweep_smem_bytes(L.smemJ, false);
-  sweep_short_kernel<Narrow<V>><<<L.grid, th, sm, L.stream>>>(L.inst, L.short_first, L.short_end);
+  sweep_short_kernel<Narrow<V>><<<L.grid, th, sm, L.stream>>>(L.inst, L.nslices0);
   return cudaGetLastError();
 }
 
@@ -244,7 +393,6 @@ cudaError_t sweep_short_prepare(bool bf16) {
 }
 
 cudaError_t launch_sweep_short(const SweepLaunch& L, bool bf16) {
-  if (L.short_first < 0 || L.short_end <= L.short_first) return cudaSuccess;
   return bf16 ? launch_short_values<BF16Pair>(L) : launch_short_values<F32Pair>(L);
 }
 

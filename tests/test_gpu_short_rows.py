@@ -1,10 +1,11 @@
-"""The short-row sweep (dlm_options.short_rows): slices whose rows have at
-most 16 edges take a second kernel that holds each row's u in registers and
-runs the threshold iteration over them.  Iterates against the FP64 oracle
-(Sec. 3.2 primal recovery, the projected accelerated step) at the task's
-1e-5 bound on lambda, on instances where the iteration takes both kernels
-(heavy degree tails) or mostly the short one (App. A's requests), and
-bit-identity across runs and slice-to-CTA mappings."""
+"""The short-row sweep (dlm_options.short_rows): iteration sweeps take a
+kernel that holds each row of at most 32 edges in registers, sorts its values
+and finds the threshold by the sort-based rule in one scan; wider rows take a
+re-reading threshold iteration.  Iterates against the FP64 oracle (Sec. 3.2
+primal recovery, the projected accelerated step) at the 1e-5 bound on lambda,
+on instances with heavy degree tails (rows of 1 to 690 edges: every width
+class and the wide path) and on App. A's requests (about ten edges, many
+active), and bit-identity across runs and slice-to-CTA mappings."""
 import numpy as np
 import pytest
 
@@ -30,7 +31,7 @@ def check_lam(s, ref, what):
 
 
 def test_tiny_500_iterations(dlm_lib):
-    # degrees 1 + Poisson(9): most slices are short, the widest ones are not
+    # degrees 1 + Poisson(9): every width class up to 32
     inst = tiny_instance()
     s = solver_for(dlm_lib, inst)
     s.set_schedule(1e-2)
@@ -44,7 +45,7 @@ def test_tiny_500_iterations(dlm_lib):
 @pytest.mark.parametrize("kind,z,bf16", [(oracle.SIMPLEX_LE, 1.0, False), (oracle.SIMPLEX_EQ, 0.7, False),
                                          (oracle.BOX, 0.6, False), (oracle.SIMPLEX_LE, 1.0, True)])
 def test_continuation_trajectory(dlm_lib, kind, z, bf16):
-    # heavy degree tail: rows of 1 .. 690 edges, so both sweep kernels run
+    # heavy degree tail: rows of 1 .. 690 edges, every width class and the wide path
     inst = mixed_instance(seed=5, I=3000, J=300)
     s = solver_for(dlm_lib, inst, kind, z, bf16)
     s.set_schedule(1e-1, 1e-3, 0.5, 20)

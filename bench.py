@@ -762,12 +762,13 @@ def main():
         bf16_err = bf16_error_statement(dlm, torch, inst, recipe, args.threads, gamma=w["schedule"][1])
 
     # ---- roofline of the dominant kernel (the sweep) ----
-    # the tuner may pick the short-row sweep (one launch, another kernel)
+    # the tuner may pick the short-row sweep (one launch, another kernel, its own traffic record)
     short_on = bool(tuned is not None and tuned.get("short_rows"))
+    traffic = (recorded_traffic(args.workload + ("_short" if short_on else ""), nnz, I) if args.scale == 1.0
+               else None)
     peak, peak_kind = load_peaks()
     sweep_s = sweep_ms / 1000.0 / iters_total
     achieved = bytes_iter / sweep_s / 1e9
-    traffic = recorded_traffic(args.workload, nnz, I) if args.scale == 1.0 else None
     # bytes the library's layout streams: 16-bit item indices, the values, a
     # 12-byte header per 32 users
     vsz = 2 if bf16 else 4

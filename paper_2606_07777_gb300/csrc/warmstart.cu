@@ -1,6 +1,6 @@
 // warmstart.cu -- the learned warm start: per-item features of an instance, a
 // three-layer perceptron whose products run on the tensor cores
-// (mma.sync m16n8k16, BF16 operands, FP32 accumulation), trained with Adam on
+// (tcgen05.mma with TMEM accumulators, BF16 operands, FP32 accumulation), trained with Adam on
 // solved days, and its prediction of the item duals.
 //
 // Network (width H, F = 7 features):
@@ -126,9 +126,16 @@ __global__ void k_feat_final(int J, const unsigned* __restrict__ deg, const int*
 }
 
 // ---------------------------------------------------------------------------
-// Tensor-core GEMM: part[z] = sum over the z-th K range of A(m, k) B(k, n),
-// A and B bf16 with arbitrary element strides, FP32 accumulation.  CTA tile
-// 64 x 64 (four warps of 32 x 32), K in steps of 32.
+// Tensor-core GEMM (tcgen05, TMEM accumulator): part[z] = sum over the z-th K
+// range of A(m, k) B(k, n), A and B bf16 with arbitrary element strides,
+// FP32 accumulation.  One CTA of 128 threads per 128 x 128 output tile and K
+// range: the threads stage 64-wide K slices of A and of B^T into shared
+// memory in the no-swizzle K-major layout (8-row x 16-byte core matrices:
+// K-adjacent ones 128 bytes apart, the next 8 rows 256 bytes on; a 16-wide K
+// step of a 128-row operand is 4 KB); one thread issues the four
+// tcgen05.mma.kind::f16 steps (M = N = 128, K = 16) into the CTA's 128 TMEM
+// columns and commits them to an mbarrier; after the last slice each warp
+// reads its 32 accumulator rows (TMEM lanes) back with tcgen05.ld.
 // ---------------------------------------------------------------------------
 
 struct GemmArgs {
@@ -138,94 +145,159 @@ struct GemmArgs {
   long long sbk, sbn;
   float* part;  // [splits][M][N]
   int M, N, K, kchunk;
+  int* err;     // set when a completion wait runs out
 };
 
-__device__ __forceinline__ void mma_bf16(float d[4], const uint32_t a[4], const uint32_t b[2]) {
-  asm volatile(
-      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
-      "{%0,%1,%2,%3};\n"
-      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
-      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+constexpr int kTM = 128, kTN = 128, kTK = 64;        // CTA tile; K per staged slice
+constexpr int kStepBytes = 128 * 16 * 2;              // one K = 16 step of a 128-row operand
+constexpr int kOpBytes = (kTK / 16) * kStepBytes;     // one staged operand slice (16 KB)
+// Dynamic shared memory per CTA: both operands plus room that caps an SM at
+// four CTAs, so that their TMEM allocations (128 of the 512 columns each)
+// never wait for one another.
+constexpr int kGemmSmem = 3 * kOpBytes;
+constexpr uint32_t kTmemCols = 128;
+// kind::f16 instruction descriptor: F32 accumulator (bits 4-5 = 1), BF16 A
+// and B (bits 7-9, 10-12 = 1), both K-major, N / 8 at bits 17-22, M / 16 at
+// bits 24-28.
+constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((kTN >> 3) << 17) | ((kTM >> 4) << 24);
+constexpr long long kWaitCycles = 2000000000LL;  // about a second at the SM clock
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+// Shared-memory matrix descriptor: start address, leading (K-direction) and
+// stride (row-direction) byte offsets, each in 16-byte units; bits 46-48 hold
+// the fixed value 1; no swizzle.
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+  return static_cast<uint64_t>((addr & 0x3FFFFu) >> 4) | (static_cast<uint64_t>((lbo >> 4) & 0x3FFFu) << 16) |
+         (static_cast<uint64_t>((sbo >> 4) & 0x3FFFu) << 32) | (static_cast<uint64_t>(1) << 46);
+}
+// Byte offset of element (row, k) of a staged slice (k < kTK).
+__device__ __forceinline__ uint32_t slice_off(int row, int k) {
+  return (k >> 4) * kStepBytes + (row >> 3) * 256 + ((k >> 3) & 1) * 128 + (row & 7) * 16 + (k & 7) * 2;
+}
+// Waits for completion phase `parity` of the mbarrier, at most kWaitCycles.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+  const long long t0 = clock64();
+  for (;;) {
+    uint32_t done;
+    asm volatile(
+        "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    if (done) return true;
+    if (clock64() - t0 > kWaitCycles) return false;
+  }
 }
 
-constexpr int kTM = 64, kTN = 64, kTK = 32, kPad = 8;
-
 __global__ void __launch_bounds__(128) k_gemm(GemmArgs g) {
-  __shared__ __align__(16) bf16 As[kTM][kTK + kPad];
-  __shared__ __align__(16) bf16 Bs[kTN][kTK + kPad];
+  extern __shared__ __align__(128) unsigned char gsm[];
+  __shared__ __align__(8) uint64_t mbar;
+  __shared__ uint32_t tslot;
+  unsigned char* sA = gsm;
+  unsigned char* sB = gsm + kOpBytes;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int gid = lane >> 2, tig = lane & 3;
-  const int wm = warp >> 1, wn = warp & 1;
   const long long m0 = static_cast<long long>(blockIdx.x) * kTM;
   const int n0 = blockIdx.y * kTN;
   const int kb0 = blockIdx.z * g.kchunk;
   const int kend = min(g.K, kb0 + g.kchunk);
   const bf16 zero = __float2bfloat16(0.f);
-  float acc[2][4][4];
-#pragma unroll
-  for (int i = 0; i < 2; ++i)
-#pragma unroll
-    for (int j = 0; j < 4; ++j)
-#pragma unroll
-      for (int r = 0; r < 4; ++r) acc[i][j][r] = 0.f;
 
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(&tslot)),
+                 "r"(kTmemCols));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  if (tid == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(&mbar)), "r"(1));
+    asm volatile("fence.mbarrier_init.release.cluster;");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  const uint32_t taddr = tslot;
+
+  bool ok = true;
+  uint32_t phase = 0;
+  int issued = 0;
   for (int kb = kb0; kb < kend; kb += kTK) {
+    // stage A(m0.., kb..) and B(kb.., n0..)^T, zeros outside the ranges;
+    // consecutive threads take the unit-stride direction
     for (int i = tid; i < kTM * kTK; i += 128) {
       const int r = g.sam == 1 ? (i % kTM) : (i / kTK);
       const int kk = g.sam == 1 ? (i / kTM) : (i % kTK);
       const long long m = m0 + r;
       const int k = kb + kk;
-      As[r][kk] = (m < g.M && k < kend) ? g.A[m * g.sam + k * g.sak] : zero;
+      *reinterpret_cast<bf16*>(sA + slice_off(r, kk)) = (m < g.M && k < kend) ? g.A[m * g.sam + k * g.sak] : zero;
     }
     for (int i = tid; i < kTN * kTK; i += 128) {
       const int r = g.sbn == 1 ? (i % kTN) : (i / kTK);
       const int kk = g.sbn == 1 ? (i / kTN) : (i % kTK);
       const int nn = n0 + r;
       const int k = kb + kk;
-      Bs[r][kk] = (nn < g.N && k < kend) ? g.B[static_cast<long long>(k) * g.sbk + static_cast<long long>(nn) * g.sbn]
-                                         : zero;
+      *reinterpret_cast<bf16*>(sB + slice_off(r, kk)) =
+          (nn < g.N && k < kend) ? g.B[static_cast<long long>(k) * g.sbk + static_cast<long long>(nn) * g.sbn]
+                                 : zero;
     }
+    // the tensor cores read shared memory through the async proxy
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     __syncthreads();
+    if (tid == 0) {
+      asm volatile("tcgen05.fence::after_thread_sync;");
 #pragma unroll
-    for (int ks = 0; ks < kTK; ks += 16) {
-      uint32_t a[2][4], b[4][2];
-#pragma unroll
-      for (int mi = 0; mi < 2; ++mi) {
-        const int row = wm * 32 + mi * 16 + gid;
-        a[mi][0] = *reinterpret_cast<const uint32_t*>(&As[row][ks + 2 * tig]);
-        a[mi][1] = *reinterpret_cast<const uint32_t*>(&As[row + 8][ks + 2 * tig]);
-        a[mi][2] = *reinterpret_cast<const uint32_t*>(&As[row][ks + 2 * tig + 8]);
-        a[mi][3] = *reinterpret_cast<const uint32_t*>(&As[row + 8][ks + 2 * tig + 8]);
+      for (int st = 0; st < kTK / 16; ++st) {
+        const uint64_t ad = smem_desc(smem_addr(sA + st * kStepBytes), 128, 256);
+        const uint64_t bd = smem_desc(smem_addr(sB + st * kStepBytes), 128, 256);
+        const uint32_t acc = (issued > 0 || st > 0) ? 1u : 0u;
+        asm volatile(
+            "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+            "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(taddr),
+            "l"(ad), "l"(bd), "r"(kIdesc), "r"(acc));
       }
-#pragma unroll
-      for (int ni = 0; ni < 4; ++ni) {
-        const int cn = wn * 32 + ni * 8 + gid;
-        b[ni][0] = *reinterpret_cast<const uint32_t*>(&Bs[cn][ks + 2 * tig]);
-        b[ni][1] = *reinterpret_cast<const uint32_t*>(&Bs[cn][ks + 2 * tig + 8]);
-      }
-#pragma unroll
-      for (int mi = 0; mi < 2; ++mi)
-#pragma unroll
-        for (int ni = 0; ni < 4; ++ni) mma_bf16(acc[mi][ni], a[mi], b[ni]);
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                       smem_addr(&mbar))
+                   : "memory");
     }
-    __syncthreads();
+    ++issued;
+    // the slice's products must finish before the next slice overwrites it
+    // (the outcome is made uniform across the CTA before anyone leaves)
+    ok = __syncthreads_and(mbar_wait(smem_addr(&mbar), phase)) != 0;
+    phase ^= 1u;
+    if (!ok) break;
   }
+  asm volatile("tcgen05.fence::after_thread_sync;");
+
+  // accumulator rows m0 + 32 warp + lane, 8 columns per load
   float* out = g.part + static_cast<long long>(blockIdx.z) * g.M * g.N;
+  const long long row = m0 + warp * 32 + lane;
+  for (int c = 0; c < kTN; c += 8) {
+    float v[8];
+    if (issued > 0 && ok) {
+      uint32_t r[8];
+      asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                   : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+                   : "r"(taddr + (static_cast<uint32_t>(warp * 32) << 16) + static_cast<uint32_t>(c)));
+      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
-  for (int mi = 0; mi < 2; ++mi)
+      for (int q = 0; q < 8; ++q) v[q] = __uint_as_float(r[q]);
+    } else {
 #pragma unroll
-    for (int ni = 0; ni < 4; ++ni) {
-      const long long row = m0 + wm * 32 + mi * 16 + gid;
-      const int cn = n0 + wn * 32 + ni * 8 + 2 * tig;
-#pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        const long long r = row + 8 * h;
-        if (r < g.M) {
-          if (cn < g.N) out[r * g.N + cn] = acc[mi][ni][2 * h];
-          if (cn + 1 < g.N) out[r * g.N + cn + 1] = acc[mi][ni][2 * h + 1];
-        }
-      }
+      for (int q = 0; q < 8; ++q) v[q] = ok ? 0.f : __int_as_float(0x7fc00000);  // empty K range: 0; timeout: NaN
     }
+    if (row < g.M) {
+#pragma unroll
+      for (int q = 0; q < 8; ++q)
+        if (n0 + c + q < g.N) out[row * g.N + n0 + c + q] = v[q];
+    }
+  }
+  if (!ok && tid == 0) {
+    atomicOr(g.err, 1);
+    mbar_wait(smem_addr(&mbar), phase ^ 1u);  // a last bounded wait for the products in flight
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(kTmemCols));
 }
 
 // ---------------------------------------------------------------------------
@@ -467,6 +539,7 @@ struct dlm_ws {
   int64_t part_cap = 0;
   double* loss = nullptr;  // [loss_cap]
   int64_t loss_cap = 0;
+  int* gemm_err = nullptr;  // set by a tensor-core product whose completion wait ran out (device)
 };
 
 namespace {
@@ -560,7 +633,8 @@ dlm_status gemm(dlm_ws* w, const bf16* A, long long sam, long long sak, const bf
     return DLM_OK;
   }
   dim3 grid(static_cast<unsigned>((M + kTM - 1) / kTM), static_cast<unsigned>((N + kTN - 1) / kTN), splits);
-  k_gemm<<<grid, 128, 0, w->stream>>>(g);
+  g.err = w->gemm_err;
+  k_gemm<<<grid, 128, kGemmSmem, w->stream>>>(g);
   WCK(cudaGetLastError());
   return DLM_OK;
 }
@@ -570,6 +644,19 @@ int last_splits(int64_t K, int splits) {
   kchunk = (kchunk + kTK - 1) / kTK * kTK;
   if (kchunk < kTK) kchunk = kTK;
   return static_cast<int>(std::max<int64_t>(1, (K + kchunk - 1) / kchunk));
+}
+
+// DLM_ERR_TIMEOUT when a tensor-core product's completion wait ran out
+// (the word is cleared for the next call).
+dlm_status check_gemm(dlm_ws* w) {
+  int h = 0;
+  WCK(cudaMemcpyAsync(&h, w->gemm_err, sizeof(int), cudaMemcpyDeviceToHost, w->stream));
+  WCK(cudaStreamSynchronize(w->stream));
+  if (h) {
+    WCK(cudaMemsetAsync(w->gemm_err, 0, sizeof(int), w->stream));
+    return wfail(DLM_ERR_TIMEOUT, "a tensor-core product did not complete in time");
+  }
+  return DLM_OK;
 }
 
 dlm_status refresh_bf16(dlm_ws* w) {
@@ -704,6 +791,8 @@ dlm_status dlm_ws_create(int32_t width, uint64_t seed, void* stream, dlm_ws** ou
   ck(walloc(&w->w3b, H));
   ck(walloc(&w->mu, kF));
   ck(walloc(&w->sd, kF));
+  ck(walloc(&w->gemm_err, 1));
+  if (s == DLM_OK) ck(cudaMemset(w->gemm_err, 0, sizeof(int)));
   if (s == DLM_OK) {
     ck(cudaMemcpy(w->theta, th.data(), sizeof(float) * w->P, cudaMemcpyHostToDevice));
     ck(cudaMemset(w->m, 0, sizeof(float) * w->P));
@@ -712,6 +801,7 @@ dlm_status dlm_ws_create(int32_t width, uint64_t seed, void* stream, dlm_ws** ou
     ck(cudaMemcpy(w->mu, zero.data(), sizeof(float) * kF, cudaMemcpyHostToDevice));
     ck(cudaMemcpy(w->sd, one.data(), sizeof(float) * kF, cudaMemcpyHostToDevice));
   }
+  if (s == DLM_OK) ck(cudaFuncSetAttribute(k_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, kGemmSmem));
   if (s == DLM_OK) s = refresh_bf16(w);
   if (s == DLM_OK) s = ensure_loss(w, 1);
   if (s == DLM_OK) {
@@ -786,7 +876,7 @@ dlm_status dlm_ws_loss_grad(dlm_ws* w, const float* X, const float* y, int64_t n
   if (loss) WCK(cudaMemcpyAsync(loss, w->loss, sizeof(double), cudaMemcpyDeviceToHost, w->stream));
   if (grad) WCK(cudaMemcpyAsync(grad, w->grad, sizeof(float) * w->P, cudaMemcpyDeviceToHost, w->stream));
   WCK(cudaStreamSynchronize(w->stream));
-  return DLM_OK;
+  return check_gemm(w);
 }
 
 dlm_status dlm_ws_train(dlm_ws* w, const float* X, const float* y, int64_t n, int32_t steps, float lr,
@@ -816,7 +906,7 @@ dlm_status dlm_ws_train(dlm_ws* w, const float* X, const float* y, int64_t n, in
     for (int32_t k = 0; k < steps; ++k) losses[k] = static_cast<float>(h[k]);
   }
   WCK(cudaStreamSynchronize(w->stream));
-  return DLM_OK;
+  return check_gemm(w);
 }
 
 dlm_status dlm_ws_predict(dlm_ws* w, const float* X, int64_t n, float* out) {
@@ -827,14 +917,14 @@ dlm_status dlm_ws_predict(dlm_ws* w, const float* X, int64_t n, float* out) {
   if (s != DLM_OK) return s;
   WCK(cudaMemcpyAsync(out, w->out, sizeof(float) * n, cudaMemcpyDeviceToDevice, w->stream));
   WCK(cudaStreamSynchronize(w->stream));
-  return DLM_OK;
+  return check_gemm(w);
 }
 
 void dlm_ws_destroy(dlm_ws* w) {
   if (!w) return;
   if (w->stream) cudaStreamSynchronize(w->stream);
   free_work(w);
-  void* ptrs[] = {w->theta, w->grad, w->m, w->v, w->W1b, w->W2b, w->w3b, w->mu, w->sd, w->part, w->loss};
+  void* ptrs[] = {w->theta, w->grad, w->m, w->v, w->W1b, w->W2b, w->w3b, w->mu, w->sd, w->part, w->loss, w->gemm_err};
   for (void* q : ptrs) cudaFree(q);
   if (w->own_stream && w->stream) cudaStreamDestroy(w->stream);
   delete w;

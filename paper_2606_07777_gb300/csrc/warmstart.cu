@@ -224,6 +224,7 @@ __global__ void __launch_bounds__(128) k_gemm(GemmArgs g) {
   for (int kb = kb0; kb < kend; kb += kTK) {
     // stage A(m0.., kb..) and B(kb.., n0..)^T, zeros outside the ranges;
     // consecutive threads take the unit-stride direction
+#pragma unroll 8
     for (int i = tid; i < kTM * kTK; i += 128) {
       const int r = g.sam == 1 ? (i % kTM) : (i / kTK);
       const int kk = g.sam == 1 ? (i / kTM) : (i % kTK);
@@ -231,6 +232,7 @@ __global__ void __launch_bounds__(128) k_gemm(GemmArgs g) {
       const int k = kb + kk;
       *reinterpret_cast<bf16*>(sA + slice_off(r, kk)) = (m < g.M && k < kend) ? g.A[m * g.sam + k * g.sak] : zero;
     }
+#pragma unroll 8
     for (int i = tid; i < kTN * kTK; i += 128) {
       const int r = g.sbn == 1 ? (i % kTN) : (i / kTK);
       const int kk = g.sbn == 1 ? (i / kTN) : (i % kTK);
@@ -570,9 +572,11 @@ void free_work(dlm_ws* w) {
 
 int last_splits(int64_t K, int splits);
 
+// Split-K ranges of about two staged slices each, so that the long products
+// (K = rows) spread over the SMs.
 int splits_for(int64_t K) {
-  const int64_t s = K / 512;
-  return static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(s, 128)));
+  const int64_t s = K / (2 * kTK);
+  return static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(s, 512)));
 }
 
 dlm_status ensure_part(dlm_ws* w, int64_t need) {

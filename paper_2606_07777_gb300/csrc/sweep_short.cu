@@ -111,11 +111,12 @@ __device__ __forceinline__ void short_slice(const InstDesc& D, const Seg& S, con
       const int k = 4 * g + e;
       const float y = ys[r.j[e]];
       if constexpr (KEEP) {
+        // padding: uh = -inf (c = +inf, a = 0); its ul (NaN) is never read,
+        // every later use being guarded by uh > tau
         const F2 u = u_pair(r.c[e], r.a[e], y);
-        const bool pad = r.c[e] == INFINITY;
-        uh[k] = pad ? -INFINITY : u.h;
-        ul[k] = pad ? 0.f : u.l;
-        v[k] = uh[k];
+        uh[k] = u.h;
+        ul[k] = u.l;
+        v[k] = u.h;
       } else {
         if constexpr (YK) yk[k] = y;
         v[k] = -fmaf(r.a[e], y, r.c[e]);
@@ -131,13 +132,13 @@ __device__ __forceinline__ void short_slice(const InstDesc& D, const Seg& S, con
   float tau = 0.f, taul = 0.f;
   bool single = false;
   if (!box && !none) {
-    // sort-based rule: r = the largest q + 1 with (q + 1) v_q > S_{q+1} - gamma z
+    // sort-based rule: r = the largest q + 1 with (q + 1) v_q - S_{q+1} > -gamma z
     float sm = 0.f, sr = v[0];
     int r = 1;
 #pragma unroll
     for (int q = 0; q < WC; ++q) {
       sm += v[q];
-      if (q > 0 && static_cast<float>(q + 1) * v[q] > sm - S.gz) {
+      if (q > 0 && fmaf(static_cast<float>(q + 1), v[q], -sm) > -S.gz) {
         r = q + 1;
         sr = sm;
       }

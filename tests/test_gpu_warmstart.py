@@ -102,6 +102,27 @@ def test_gradient_matches_oracle(dlm_lib):
     ws.close()
 
 
+@pytest.mark.parametrize("H,n", [(8, 300), (40, 1000), (136, 700), (256, 2500)])
+def test_widths_and_row_counts_match_oracle(dlm_lib, H, n):
+    # The tensor-core products use 128 x 128 output tiles and 64-wide K
+    # slices: widths below one tile (zero-padded columns), between one and two
+    # (two column tiles), two full tiles; row counts leaving a partial row
+    # tile, and split-K ranges of uneven length in the gradient products.
+    ws, P, X, y, mu, sd = ws_with_random_params(dlm_lib, H=H, seed=13, n=n)
+    out = ws.predict(torch.from_numpy(X).cuda()).cpu().numpy().astype(np.float64)
+    ref = mlp.predict(P, X.astype(np.float64), mu, sd, bf16_round=True)
+    err = np.abs(out - ref)
+    assert (err <= 5e-3 * (np.abs(ref) + 0.1)).all(), err.max()
+    loss, g = ws.loss_grad(torch.from_numpy(X).cuda(), torch.from_numpy(y).cuda())
+    rl, rg = mlp.loss_and_grad(P, X.astype(np.float64), y.astype(np.float64), mu, sd, bf16_round=True)
+    assert abs(loss - rl) <= 1e-4 * rl
+    G = ws.unpack(g)
+    for k in rg:
+        d = np.linalg.norm(G[k].astype(np.float64) - rg[k])
+        assert d <= 1e-2 * np.linalg.norm(rg[k]) + 1e-9, (k, d / np.linalg.norm(rg[k]))
+    ws.close()
+
+
 def test_adam_step_matches_oracle(dlm_lib):
     ws, P, X, y, mu, sd = ws_with_random_params(dlm_lib)
     Xd, yd = torch.from_numpy(X).cuda(), torch.from_numpy(y).cuda()

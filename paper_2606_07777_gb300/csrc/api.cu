@@ -231,6 +231,7 @@ InstDesc base_desc(const dlm_problem* p) {
   d.ca = p->lay.ca;
   d.orig_off = p->lay.orig_off;
   d.udeg = p->lay.udeg;
+  d.lead = p->lay.lead;
   d.nusers = p->lay.num_active_users;
   d.status = &p->state->status;
   d.scaleG = std::ldexp(1.0f, p->sG);
@@ -729,7 +730,7 @@ void free_problem(dlm_problem* p) {
   runner_free(p->run);
   cudaStream_t s = p->stream;
   void* pooled[] = {p->lay.slice_off, p->lay.slice_w, p->lay.col16, p->lay.ca, p->lay.orig_off,
-                    p->lay.udeg,      p->lay.n2,      p->a_ext};
+                    p->lay.udeg,      p->lay.lead,    p->lay.n2,  p->a_ext};
   for (void* q : pooled) dev_free(q, s);
   if (s) cudaStreamSynchronize(s);
   if (p->own_sums) {

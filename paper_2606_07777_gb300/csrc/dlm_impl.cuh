@@ -80,6 +80,7 @@ struct InstDesc {
   const void* ca;           // [padded nnz] interleaved (c, a): float2, or bf16 pair in a uint32
   const int64_t* orig_off;  // [users with edges] caller row start of each sorted user
   const int32_t* udeg;      // [users with edges] degree of each sorted user
+  const uint64_t* lead;     // [users with edges] caller positions of the row's lead edges (lead_caller_pos)
   int64_t nusers;           // users with edges (sorted users 0 .. nusers-1)
   int32_t* status;          // device error word (kStat* bits)
   const float* y;           // sweep point [J]
@@ -102,6 +103,38 @@ struct InstDesc {
   const void* a_ext;
   int64_t ext_stride;
 };
+
+// Lead order of a row in the slice layout (layout.cu): min(4, d) edges of
+// the row's lowest costs c, in ascending order of c, come first (among edges
+// of equal cost at the boundary, the one the layout's sorted insertion keeps);
+// the others follow in caller order.  A row's largest values u = -(c + a y) then tend
+// to come first, so the sweeps' first pass rarely has to insert later edges
+// into its record of the largest values.  `lead` packs the lead edges' caller
+// positions, 16 bits each (slot i at bits 16 i).  Returns the caller position
+// (0 .. d - 1) of slice position k of a row of d edges.
+__device__ __forceinline__ int lead_caller_pos(uint64_t lead, int k, int d) {
+  const int nl = d < 4 ? d : 4;
+  if (k < nl) return static_cast<int>((lead >> (16 * k)) & 0xFFFFu);
+  int p[4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) p[i] = i < nl ? static_cast<int>((lead >> (16 * i)) & 0xFFFFu) : 0x7FFFFFFF;
+  // ascending (a four-input network)
+#pragma unroll
+  for (int q = 0; q < 5; ++q) {
+    const int i = q == 0 ? 0 : q == 1 ? 2 : q == 2 ? 0 : q == 3 ? 1 : 1;
+    const int j = q == 0 ? 1 : q == 1 ? 3 : q == 2 ? 2 : q == 3 ? 3 : 2;
+    const int lo = min(p[i], p[j]), hi = max(p[i], p[j]);
+    p[i] = lo;
+    p[j] = hi;
+  }
+  // the (k - nl)-th position outside the lead set: step past every lead
+  // position at or below the candidate, in ascending order
+  int c = k - nl;
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+    if (p[i] <= c) ++c;
+  return c;
+}
 
 // A task: slices first, first + stride, ... (< end) of instance `inst`.  The
 // tasks of one CTA are contiguous and grouped by instance.
@@ -207,6 +240,7 @@ struct LayoutOut {
   void* ca = nullptr;            // [padded_nnz + 32]
   int64_t* orig_off = nullptr;   // [num_active_users + 32]
   int32_t* udeg = nullptr;       // [num_active_users + 32]
+  uint64_t* lead = nullptr;      // [num_active_users + 32] lead edges of each sorted row (lead_caller_pos)
   int64_t num_active_users = 0, nslices = 0, padded_nnz = 0;
   double* n2 = nullptr;          // [J] sum_i a_ij^2
   double n2max = 0;

@@ -45,8 +45,9 @@ __global__ void k_check(const void* a, int64_t n, bool bf16, int* flags, unsigne
 }
 
 // dst in slice order (layout.cu): edge k of sorted user u = 32 s + t sits at
-// slice_off[s] + sell_el(k, t, width[s] / 4); padding gets 0.
-__global__ void k_gather_ext(const int64_t* orig_off, const int32_t* udeg, const int64_t* slice_off,
+// slice_off[s] + sell_el(k, t, width[s] / 4) and is the row's caller edge
+// lead_caller_pos(lead[u], k, d); padding gets 0.
+__global__ void k_gather_ext(const int64_t* orig_off, const int32_t* udeg, const uint64_t* lead, const int64_t* slice_off,
                              const int32_t* width, int64_t nusers, int64_t nslices, const void* src, bool bf16,
                              void* dst) {
   const int lane = threadIdx.x & 31;
@@ -56,16 +57,18 @@ __global__ void k_gather_ext(const int64_t* orig_off, const int32_t* udeg, const
     const int64_t u = 32 * s + lane;
     const int64_t r = u < nusers ? orig_off[u] : 0;
     const int d = u < nusers ? udeg[u] : 0;
+    const uint64_t ld = u < nusers ? lead[u] : 0ull;
     const int w = width[s];
     const int w4 = w >> 2;
     const int64_t base = slice_off[s];
     for (int k = 0; k < w; ++k) {
       const int64_t e = k < 4 * w4 ? base + 4 * (32 * static_cast<int64_t>(k >> 2) + lane) + (k & 3)
                                    : base + 128 * static_cast<int64_t>(w4) + 32 * static_cast<int64_t>(k - 4 * w4) + lane;
+      const int64_t q = k < d ? r + lead_caller_pos(ld, k, d) : 0;
       if (bf16)
-        static_cast<uint16_t*>(dst)[e] = k < d ? static_cast<const uint16_t*>(src)[r + k] : static_cast<uint16_t>(0);
+        static_cast<uint16_t*>(dst)[e] = k < d ? static_cast<const uint16_t*>(src)[q] : static_cast<uint16_t>(0);
       else
-        static_cast<float*>(dst)[e] = k < d ? static_cast<const float*>(src)[r + k] : 0.f;
+        static_cast<float*>(dst)[e] = k < d ? static_cast<const float*>(src)[q] : 0.f;
     }
   }
 }
@@ -100,7 +103,7 @@ cudaError_t families_check(const void* a, int64_t n, bool bf16, int* flags, unsi
 cudaError_t families_gather(const LayoutOut& lay, const void* src, bool bf16, void* dst, cudaStream_t s) {
   if (lay.nslices == 0) return cudaSuccess;
   const int64_t g = (lay.nslices * 32 + 255) / 256;
-  k_gather_ext<<<static_cast<int>(g < 4096 ? g : 4096), 256, 0, s>>>(lay.orig_off, lay.udeg, lay.slice_off,
+  k_gather_ext<<<static_cast<int>(g < 4096 ? g : 4096), 256, 0, s>>>(lay.orig_off, lay.udeg, lay.lead, lay.slice_off,
                                                                     lay.slice_w, lay.num_active_users, lay.nslices,
                                                                     src, bf16, dst);
   return cudaGetLastError();

@@ -193,7 +193,20 @@ __global__ void k_slices(const int32_t* sdeg, int64_t nslices, int32_t* width, i
   }
 }
 
-// One warp per slice: lane t copies user t's row into column t of the slice.
+// The cost c of edge e as a float (bf16 bits widened exactly, or FP32).
+template <typename CA>
+__device__ __forceinline__ float cost_of(const void* c, int64_t e);
+template <>
+__device__ __forceinline__ float cost_of<float2>(const void* c, int64_t e) {
+  return static_cast<const float*>(c)[e];
+}
+template <>
+__device__ __forceinline__ float cost_of<uint32_t>(const void* c, int64_t e) {
+  return __uint_as_float(static_cast<uint32_t>(static_cast<const unsigned short*>(c)[e]) << 16);
+}
+
+// One warp per slice: lane t copies user t's row into column t of the slice,
+// in lead order (dlm_impl.cuh: the row's four lowest-cost edges first).
 // CA = float2 {c, a} (FP32) or uint32 (bf16 c low, bf16 a high).
 template <typename CA>
 __device__ __forceinline__ CA pack_ca(const void* c, const void* a, int64_t e);
@@ -220,7 +233,8 @@ __device__ __forceinline__ uint32_t pad_ca<uint32_t>() {
 template <typename CA>
 __global__ void k_gather(const int64_t* rp, const int32_t* col, const void* c, const void* a, const int32_t* perm,
                          const int32_t* sdeg, int64_t In, int64_t nslices, const int64_t* slice_off,
-                         const int32_t* width, uint16_t* col_o, CA* ca_o, int64_t* orig_off, int32_t* udeg) {
+                         const int32_t* width, uint16_t* col_o, CA* ca_o, int64_t* orig_off, int32_t* udeg,
+                         uint64_t* lead_o) {
   const int lane = threadIdx.x & 31;
   const int64_t w0 = (blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x) >> 5;
   const int64_t nwarps = (static_cast<int64_t>(gridDim.x) * blockDim.x) >> 5;
@@ -235,6 +249,29 @@ __global__ void k_gather(const int64_t* rp, const int32_t* col, const void* c, c
       orig_off[u] = r;
       udeg[u] = d;
     }
+    // lead edges: min(4, d) edges of the row's lowest costs, ascending, by a
+    // sorted insertion with strict comparisons (a deterministic choice among
+    // edges of equal cost)
+    float lv[4] = {INFINITY, INFINITY, INFINITY, INFINITY};
+    int lp[4] = {0, 0, 0, 0};
+    for (int k = 0; k < d && k < 0xFFFF; ++k) {  // positions fit 16 bits
+      float x = cost_of<CA>(c, r + k);
+      int xi = k;
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const bool lt = x < lv[q];
+        const float hv = lt ? lv[q] : x;
+        const int hi = lt ? lp[q] : xi;
+        lv[q] = lt ? x : lv[q];
+        lp[q] = lt ? xi : lp[q];
+        x = hv;
+        xi = hi;
+      }
+    }
+    uint64_t lead = 0;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) lead |= static_cast<uint64_t>(q < d ? lp[q] : 0xFFFF) << (16 * q);
+    if (u < In) lead_o[u] = lead;
     const int w = width[s];
     const int w4 = w >> 2;
     const int64_t base = slice_off[s];
@@ -242,8 +279,9 @@ __global__ void k_gather(const int64_t* rp, const int32_t* col, const void* c, c
       const bool v = k < d;
       const int64_t e = k < 4 * w4 ? base + 4 * (32 * static_cast<int64_t>(k >> 2) + lane) + (k & 3)
                                    : base + 128 * static_cast<int64_t>(w4) + 32 * static_cast<int64_t>(k - 4 * w4) + lane;
-      col_o[e] = v ? static_cast<uint16_t>(col[r + k]) : uint16_t(0);
-      ca_o[e] = v ? pack_ca<CA>(c, a, r + k) : pad_ca<CA>();
+      const int64_t src = v ? r + lead_caller_pos(lead, k, d) : 0;
+      col_o[e] = v ? static_cast<uint16_t>(col[src]) : uint16_t(0);
+      ca_o[e] = v ? pack_ca<CA>(c, a, src) : pad_ca<CA>();
     }
   }
 }
@@ -559,15 +597,16 @@ dlm_status build_layout(int64_t I, int64_t J, int64_t nnz, const int64_t* rp, co
   DLM_CK(dev_alloc(reinterpret_cast<void**>(&out->ca), 2 * vs * (out->padded_nnz + 32), s));
   DLM_CK(dev_alloc(reinterpret_cast<void**>(&out->orig_off), sizeof(int64_t) * (In + 32), s));
   DLM_CK(dev_alloc(reinterpret_cast<void**>(&out->udeg), sizeof(int32_t) * (In + 32), s));
+  DLM_CK(dev_alloc(reinterpret_cast<void**>(&out->lead), sizeof(uint64_t) * (In + 32), s));
   DLM_CK(cudaMemsetAsync(out->col16 + out->padded_nnz, 0, sizeof(uint16_t) * 64, s));
   if (ns > 0) {
     const int g = grid_for(ns * 32);
     if (bf16)
       k_gather<uint32_t><<<g, kT, 0, s>>>(rp, col, c, a, perm, sdeg, In, ns, out->slice_off, out->slice_w, out->col16,
-                                          static_cast<uint32_t*>(out->ca), out->orig_off, out->udeg);
+                                          static_cast<uint32_t*>(out->ca), out->orig_off, out->udeg, out->lead);
     else
       k_gather<float2><<<g, kT, 0, s>>>(rp, col, c, a, perm, sdeg, In, ns, out->slice_off, out->slice_w, out->col16,
-                                        static_cast<float2*>(out->ca), out->orig_off, out->udeg);
+                                        static_cast<float2*>(out->ca), out->orig_off, out->udeg, out->lead);
     DLM_CK(cudaGetLastError());
   }
 
@@ -648,6 +687,7 @@ done:
     dev_free(out->ca, s);
     dev_free(out->orig_off, s);
     dev_free(out->udeg, s);
+    dev_free(out->lead, s);
     dev_free(out->n2, s);
     out->slice_w = nullptr;
     out->slice_off = nullptr;
@@ -655,6 +695,7 @@ done:
     out->ca = nullptr;
     out->orig_off = nullptr;
     out->udeg = nullptr;
+    out->lead = nullptr;
     out->n2 = nullptr;
   }
   return st;

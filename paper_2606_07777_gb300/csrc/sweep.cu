@@ -472,6 +472,7 @@ __device__ __forceinline__ void finish_slice(const InstDesc& D, const Seg& S, co
       // x in the caller's order, every edge of the user
       const int64_t o = __ldg(D.orig_off + u);
       const int d = __ldg(D.udeg + u);
+      const uint64_t ld = __ldg(D.lead + u);  // slice position k is caller edge lead_caller_pos(ld, k, d)
       for (int k = 0; k < d; ++k) {
         float x = 0.f;
         if (mode == 1) {
@@ -483,7 +484,7 @@ __device__ __forceinline__ void finish_slice(const InstDesc& D, const Seg& S, co
           P::get(__ldg(ca0 + el), c, a);
           if (-fmaf(a, ys[j], c) > tau) x = x_general(S, box, tau, taul, c, a, ys[j]);
         }
-        D.xout[o + k] = x;
+        D.xout[o + lead_caller_pos(ld, k, d)] = x;
       }
     }
     wobj += static_cast<double>(ob);
@@ -508,18 +509,40 @@ __device__ __forceinline__ void do_slice(const InstDesc& D, const Seg& S, const 
   const typename P::IX* __restrict__ col0 = P::idx(D) + off;
   const typename P::T* __restrict__ ca0 = static_cast<const typename P::T*>(D.ca) + off;
   TopK<K> tk = topk_empty<K>();
-#pragma unroll 4
-  for (int g = 0; g < w4; ++g) {
-    const int q = 32 * g + lane;
-    int jj[4];
-    P::idx4(col0, q, jj);
-    float c[4], a[4];
-    P::get4(ca0, q, c, a);
+  // groups of four edges in chunks of CH groups: the chunk's loads are issued
+  // together, then each group is inserted unless no lane's group maximum tops
+  // its K-th largest value (then the insertions change no record: strict
+  // comparisons); the rows' lowest-cost edges come first (lead order,
+  // layout.cu), so most groups after the first are skipped by the warp
+  constexpr int CH = sizeof(typename P::T) == 4 ? 4 : 2;
+  auto insert_group = [&](int g, const int (&jj)[4], const float (&c)[4], const float (&a)[4]) {
+    float u[4];
 #pragma unroll
-    for (int e = 0; e < 4; ++e) {
-      const float u = -fmaf(a[e], ys[jj[e]], c[e]);
-      topk_insert<K>(u, 4 * g + e, tk);
+    for (int e = 0; e < 4; ++e) u[e] = -fmaf(a[e], ys[jj[e]], c[e]);
+    const float m4 = fmaxf(fmaxf(u[0], u[1]), fmaxf(u[2], u[3]));
+    if (__any_sync(kFull, m4 > tk.v[K - 1])) {
+#pragma unroll
+      for (int e = 0; e < 4; ++e) topk_insert<K>(u[e], 4 * g + e, tk);
     }
+  };
+  int g = 0;
+  for (; g + CH <= w4; g += CH) {
+    int jj[CH][4];
+    float c[CH][4], a[CH][4];
+#pragma unroll
+    for (int h = 0; h < CH; ++h) {
+      P::idx4(col0, 32 * (g + h) + lane, jj[h]);
+      P::get4(ca0, 32 * (g + h) + lane, c[h], a[h]);
+    }
+#pragma unroll
+    for (int h = 0; h < CH; ++h) insert_group(g + h, jj[h], c[h], a[h]);
+  }
+  for (; g < w4; ++g) {
+    int jj[4];
+    float c[4], a[4];
+    P::idx4(col0, 32 * g + lane, jj);
+    P::get4(ca0, 32 * g + lane, c, a);
+    insert_group(g, jj, c, a);
   }
   for (int k = 4 * w4; k < w; ++k) {
     const int el = 128 * w4 + 32 * (k - 4 * w4) + lane;

@@ -276,6 +276,7 @@ __device__ __forceinline__ void boxcut_slice(const InstDesc& D, const BSeg& S, c
       // x in the caller's order, every edge of the user
       const int64_t o = __ldg(D.orig_off + u);
       const int d = __ldg(D.udeg + u);
+      const uint64_t ld = __ldg(D.lead + u);  // slice position k is caller edge lead_caller_pos(ld, k, d)
       for (int k = 0; k < d; ++k) {
         const int el = sell_el(k, lane, w4);
         const int j = static_cast<int>(__ldg(col0 + el));
@@ -286,7 +287,7 @@ __device__ __forceinline__ void boxcut_slice(const InstDesc& D, const BSeg& S, c
           const F2 up = u_pair(c, a, ys[j]);
           x = fminf(fmaxf(((up.h - tau) + (up.l - taul)) * S.invg, 0.f), S.z);
         }
-        D.xout[o + k] = x;
+        D.xout[o + lead_caller_pos(ld, k, d)] = x;
       }
     }
     wobj += static_cast<double>(ob);

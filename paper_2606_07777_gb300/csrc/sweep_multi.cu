@@ -283,6 +283,7 @@ __device__ __forceinline__ void multi_slice(const InstDesc& D, const MSeg& S, co
       // x in the caller's order, every edge of the user
       const int64_t o = __ldg(D.orig_off + u);
       const int d = __ldg(D.udeg + u);
+      const uint64_t ld = __ldg(D.lead + u);  // slice position k is caller edge lead_caller_pos(ld, k, d)
       for (int k = 0; k < d; ++k) {
         float x = 0.f;
         if (mode == 1) {
@@ -291,7 +292,7 @@ __device__ __forceinline__ void multi_slice(const InstDesc& D, const MSeg& S, co
           load_edge<P, M>(D, S, off, k, lane, w4, bf16, j, c, a);
           if (u_of<M>(S, ys, j, c, a) > tau) x = x_of(S, box, tau, taul, u_pair_m<M>(S, ys, j, c, a));
         }
-        D.xout[o + k] = x;
+        D.xout[o + lead_caller_pos(ld, k, d)] = x;
       }
     }
     wobj += static_cast<double>(ob);

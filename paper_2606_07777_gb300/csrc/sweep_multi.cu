@@ -144,25 +144,54 @@ __device__ __forceinline__ void multi_slice(const InstDesc& D, const MSeg& S, co
 
   float v0 = -INFINITY, v1 = -INFINITY, v2 = -INFINITY, v3 = -INFINITY;
   int i0 = 0, i1 = 0, i2 = 0;
-  for (int g = 0; g < w4; ++g) {
-    const int q = 32 * g + lane;
-    const uint2 jv = __ldg(reinterpret_cast<const uint2*>(col0) + q);  // four 16-bit item indices
+  // Groups of four edges.  With two families, two groups' loads are issued
+  // together and a group is inserted only if some lane's largest value of the
+  // group tops its fourth largest (otherwise the insertions change no record:
+  // strict comparisons) -- most groups after the first, the rows'
+  // lowest-cost edges coming first (lead order, layout.cu).  With more
+  // families the chunk's registers would spill: one group at a time, all
+  // inserted.
+  struct Grp {
+    uint2 jv;  // four 16-bit item indices
     float c[4], a[M][4];
-    P::get4(ca0, q, c, a[0]);
+  };
+  auto load = [&](int g) {
+    Grp r;
+    const int q = 32 * g + lane;
+    r.jv = __ldg(reinterpret_cast<const uint2*>(col0) + q);
+    P::get4(ca0, q, r.c, r.a[0]);
 #pragma unroll
     for (int f = 1; f < M; ++f)
-      if (fam_on<M>(S, f)) ext_get4(ext0(f), q, bf16, a[f]);
-    const int jj[4] = {static_cast<int>(jv.x & 0xffffu), static_cast<int>(jv.x >> 16),
-                       static_cast<int>(jv.y & 0xffffu), static_cast<int>(jv.y >> 16)};
+      if (fam_on<M>(S, f)) ext_get4(ext0(f), q, bf16, r.a[f]);
+    return r;
+  };
+  auto insert = [&](int g, const Grp& r) {
+    const int jj[4] = {static_cast<int>(r.jv.x & 0xffffu), static_cast<int>(r.jv.x >> 16),
+                       static_cast<int>(r.jv.y & 0xffffu), static_cast<int>(r.jv.y >> 16)};
+    float u[4];
 #pragma unroll
     for (int e = 0; e < 4; ++e) {
-      float t = c[e];
+      float t = r.c[e];
 #pragma unroll
       for (int f = 0; f < M; ++f)
-        if (fam_on<M>(S, f)) t = fmaf(a[f][e], ys[f * S.J + jj[e]], t);
-      top4_insert(-t, 4 * g + e, v0, v1, v2, v3, i0, i1, i2);
+        if (fam_on<M>(S, f)) t = fmaf(r.a[f][e], ys[f * S.J + jj[e]], t);
+      u[e] = -t;
+    }
+    const float m4 = fmaxf(fmaxf(u[0], u[1]), fmaxf(u[2], u[3]));
+    if (M > 2 || __any_sync(kFull, m4 > v3)) {
+#pragma unroll
+      for (int e = 0; e < 4; ++e) top4_insert(u[e], 4 * g + e, v0, v1, v2, v3, i0, i1, i2);
+    }
+  };
+  int g = 0;
+  if (M <= 2) {
+    for (; g + 2 <= w4; g += 2) {
+      const Grp r0 = load(g), r1 = load(g + 1);
+      insert(g, r0);
+      insert(g + 1, r1);
     }
   }
+  for (; g < w4; ++g) insert(g, load(g));
   int j;
   float c, a[M];
   for (int k = 4 * w4; k < w; ++k) {

@@ -117,17 +117,65 @@ __device__ __forceinline__ void boxcut_slice(const InstDesc& D, const BSeg& S, c
   float sf = 0.f;
   int i0 = 0, i1 = 0, i2 = 0;
   {
-    int k = 0;
-    row_pass([&](int j, float c, float a) {
-      const float u = -fmaf(a, ys[j], c);
-      top4_insert(u, k++, v[0], v[1], v[2], v[3], i0, i1, i2);
+    // Groups of four edges, two groups' loads issued together (more spill);
+    // every edge updates the sets at tau = 0, and a group
+    // enters the record only if some lane's largest value of the group tops
+    // its fourth largest (otherwise the insertions change no record: strict
+    // comparisons) -- most groups after the first, the rows' lowest-cost edges
+    // coming first (lead order, layout.cu).  Edges are visited in order, so
+    // the sums are those of row_pass.
+    auto count = [&](float u) {
       if (u >= gz) {
         ++nu;
       } else if (u > 0.f) {
         ++nf;
         sf += u;
       }
-    });
+    };
+    auto group_in = [&](int g, uint2 jv, const float (&c)[4], const float (&a)[4]) {
+      const int jj[4] = {static_cast<int>(jv.x & 0xffffu), static_cast<int>(jv.x >> 16),
+                         static_cast<int>(jv.y & 0xffffu), static_cast<int>(jv.y >> 16)};
+      float u[4];
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        u[e] = -fmaf(a[e], ys[jj[e]], c[e]);
+        count(u[e]);
+      }
+      const float m4 = fmaxf(fmaxf(u[0], u[1]), fmaxf(u[2], u[3]));
+      if (__any_sync(kFull, m4 > v[3])) {
+#pragma unroll
+        for (int e = 0; e < 4; ++e) top4_insert(u[e], 4 * g + e, v[0], v[1], v[2], v[3], i0, i1, i2);
+      }
+    };
+    constexpr int CH = 2;
+    int g = 0;
+    for (; g + CH <= w4; g += CH) {
+      uint2 jv[CH];
+      float c[CH][4], a[CH][4];
+#pragma unroll
+      for (int h = 0; h < CH; ++h) {
+        const int q = 32 * (g + h) + lane;
+        jv[h] = __ldg(reinterpret_cast<const uint2*>(col0) + q);
+        V::get4(ca0, q, c[h], a[h]);
+      }
+#pragma unroll
+      for (int h = 0; h < CH; ++h) group_in(g + h, jv[h], c[h], a[h]);
+    }
+    for (; g < w4; ++g) {
+      const int q = 32 * g + lane;
+      const uint2 jv = __ldg(reinterpret_cast<const uint2*>(col0) + q);
+      float c[4], a[4];
+      V::get4(ca0, q, c, a);
+      group_in(g, jv, c, a);
+    }
+    for (int k = 4 * w4; k < w; ++k) {
+      const int el = 128 * w4 + 32 * (k - 4 * w4) + lane;
+      float c, a;
+      V::get(__ldg(ca0 + el), c, a);
+      const float u = -fmaf(a, ys[__ldg(col0 + el)], c);
+      count(u);
+      top4_insert(u, k, v[0], v[1], v[2], v[3], i0, i1, i2);
+    }
   }
   const float umax = v[0];
   float tau = 0.f, taul = 0.f;

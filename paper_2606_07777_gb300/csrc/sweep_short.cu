@@ -19,9 +19,11 @@
 // find the simplex threshold, as here): with the values sorted,
 // v_0 >= v_1 >= ..., the active count is the largest r with
 // r v_{r-1} > v_0 + ... + v_{r-1} - gamma z (FP32), and tau is then recomputed
-// over the r active edges in float-pair arithmetic, so that
-// x = (u - tau) / gamma keeps FP32 relative accuracy; one active edge with
-// tau >= 0 gets x = z exactly.  The inequality simplex takes max(tau, 0) (the
+// over the r active edges as v_0 plus an offset: the edges' values are float
+// pairs (c + a y evaluated exactly), and their differences from v_0, all within
+// gamma z of 0, are summed in FP32, so that x = (u - tau) / gamma is accurate
+// to FP32 relative to z whatever the size of u; one active edge with tau >= 0
+// gets x = z exactly.  The inequality simplex takes max(tau, 0) (the
 // early exit of Sec. 4.3); the box clips u / gamma to [0, z].  A row's
 // arithmetic involves no other row, so its result does not depend on the
 // mapping or on the other rows of its slice.
@@ -147,14 +149,18 @@ __device__ __forceinline__ void short_slice(const InstDesc& D, const Seg& S, con
     bool zero = !eq && tau <= 0.f;
     single = !zero && r == 1;
     if (!zero && !single) {
-      // the threshold over the active set in pair arithmetic (edge order)
-      F2 ps{0.f, 0.f};
+      // the threshold over the active set (edge order) as an offset from
+      // v_0: the active values lie within gamma z of v_0, so the FP32 sum of
+      // the differences u - v_0 (each u a float pair) is accurate to FP32
+      // relative to gamma z, as x = (u - tau) / gamma needs
+      const float v0 = v[0];
+      float sd = 0.f;
       int cnt = 0;
       if constexpr (KEEP) {
 #pragma unroll
         for (int k = 0; k < WC; ++k) {
           if (uh[k] > tau) {
-            ps = f2_add(ps, F2{uh[k], ul[k]});
+            sd += (uh[k] - v0) + ul[k];
             ++cnt;
           }
         }
@@ -166,18 +172,19 @@ __device__ __forceinline__ void short_slice(const InstDesc& D, const Seg& S, con
           for (int e = 0; e < 4; ++e) {
             const float y = YK ? yk[YK ? 4 * g + e : 0] : ys[rg.j[e]];
             if (-fmaf(rg.a[e], y, rg.c[e]) > tau) {
-              ps = f2_add(ps, u_pair(rg.c[e], rg.a[e], y));
+              const F2 u = u_pair(rg.c[e], rg.a[e], y);
+              sd += (u.h - v0) + u.l;
               ++cnt;
             }
           }
         }
       }
-      const F2 t2 = f2_threshold(ps, S.gz, S.gzl, cnt > 0 ? cnt : 1);
-      if (!eq && t2.h + t2.l <= 0.f) {
+      const float t = __fdiv_rn((sd - S.gz) - S.gzl, static_cast<float>(cnt > 0 ? cnt : 1));
+      if (!eq && v0 + t <= 0.f) {
         zero = true;
       } else {
-        tau = t2.h;
-        taul = t2.l;
+        tau = v0;
+        taul = t;
       }
     }
     if (zero) {
@@ -185,9 +192,14 @@ __device__ __forceinline__ void short_slice(const InstDesc& D, const Seg& S, con
       taul = 0.f;
     }
   }
-  // x on the active edges, their item sums and the row's objective
+  // x on the active edges, their item sums and the row's objective:
+  // x = (((u_h - tau) + u_l) - taul) / gamma on the edges with u above
+  // tau + taul, (tau, taul) being (v_0, the offset) after the refinement and
+  // (0, 0) at the inequality simplex's early exit and for the box
   float ob = 0.f;
-  unsigned long long cn = 0ull;
+  const float hg = 0.5f * S.gamma;
+  const float tt = tau + taul;
+  const float zc = box ? S.z : INFINITY;  // the box's upper bound
   if (!none) {
 #pragma unroll
     for (int g = 0; g < G; ++g) {
@@ -197,15 +209,23 @@ __device__ __forceinline__ void short_slice(const InstDesc& D, const Seg& S, con
         const int k = 4 * g + e;
         float x = 0.f;
         if constexpr (KEEP) {
-          if (uh[k] > tau) {
-            const float d = (uh[k] - tau) + (ul[k] - taul);
-            x = single ? S.z : box ? fminf(fmaxf(d * S.invg, 0.f), S.z) : fmaxf(d, 0.f) * S.invg;
+          if (uh[k] > tt) {
+            const float d = ((uh[k] - tau) + ul[k]) - taul;
+            x = single ? S.z : fminf(fmaxf(d * S.invg, 0.f), zc);
           }
         } else {
           const float y = YK ? yk[YK ? k : 0] : ys[rg.j[e]];
-          if (-fmaf(rg.a[e], y, rg.c[e]) > tau) x = single ? S.z : x_general(S, box, tau, taul, rg.c[e], rg.a[e], y);
+          if (-fmaf(rg.a[e], y, rg.c[e]) > tt) {
+            const F2 u = u_pair(rg.c[e], rg.a[e], y);
+            const float d = ((u.h - tau) + u.l) - taul;
+            x = single ? S.z : fminf(fmaxf(d * S.invg, 0.f), zc);
+          }
         }
-        if (x > 0.f) deposit<P, false>(S, rg.j[e], rg.c[e], rg.a[e], x, accG, nullptr, nullptr, ob, cn);
+        if (x > 0.f) {
+          // the item sum a x in 64-bit fixed point; the objective c x + gamma/2 x^2
+          atomicAdd(&accG[rg.j[e]], fixp(rg.a[e] * x, S.scaleG));
+          ob = fmaf(fmaf(hg, x, rg.c[e]), x, ob);
+        }
       }
     }
   }

@@ -4,7 +4,7 @@
 // pass streams the row and keeps its values u = -(c + a y) (with, for short
 // enough rows, each edge's value as a float pair or its dual); a sorting
 // network orders the values and the sort-based threshold rule finds the
-// active set in one scan; the pair-arithmetic refinement and the deposits read
+// active set in one scan; the threshold's refinement and the deposits read
 // the row's c, a and items again (from L1).  The general sweep (sweep.cu)
 // tracks the four (or eight) largest values and, for rows with more active
 // edges, iterates over the row, streaming it again for every pass -- the
@@ -47,10 +47,12 @@ __device__ __forceinline__ void sort_desc(float (&v)[N]) {
   }
 }
 
-// One slice of width w <= WC (a multiple of four): the lane's edges
-// 0 .. 4 w4 - 1 are w4 = w / 4 groups of four, the rest the slice's tail of
-// w - 4 w4 edges, stored edge-major (layout.cu); positions past w are
-// padding.
+// One slice of width w <= WC (the width class: 4, 6, 8, 10, 12, 16, 24 or
+// 32; the classes below 12 are two apart because the sort and every per-slot
+// pass cost in proportion to WC, and App. A's rows have about ten edges):
+// the lane's edges 0 .. 4 w4 - 1 are w4 = w / 4 groups of four, the rest the
+// slice's tail of w - 4 w4 edges, stored edge-major (layout.cu); positions
+// past w are padding.
 //
 // What the first pass keeps besides the sorted values depends on the width
 // (registers): up to 12 edges every edge's u as a float pair (uh, ul), so the
@@ -62,7 +64,7 @@ template <class P, int WC>
 __device__ __forceinline__ void short_slice(const InstDesc& D, const Seg& S, const float* __restrict__ ys,
                                             unsigned long long* accG, int64_t off, int w,
                                             unsigned long long& oq) {
-  constexpr int G = WC / 4;
+  constexpr int G = (WC + 3) / 4;  // groups of four; slots past WC are never read
   constexpr bool KEEP = WC <= 12;
   constexpr bool YK = WC > 12 && WC <= 16;
   const int lane = threadIdx.x & 31;
@@ -111,6 +113,7 @@ __device__ __forceinline__ void short_slice(const InstDesc& D, const Seg& S, con
 #pragma unroll
     for (int e = 0; e < 4; ++e) {
       const int k = 4 * g + e;
+      if (k >= WC) break;
       const float y = ys[r.j[e]];
       if constexpr (KEEP) {
         // padding: uh = -inf (c = +inf, a = 0); its ul (NaN) is never read,
@@ -170,6 +173,7 @@ __device__ __forceinline__ void short_slice(const InstDesc& D, const Seg& S, con
           const Grp rg = group(g);
 #pragma unroll
           for (int e = 0; e < 4; ++e) {
+            if (4 * g + e >= WC) break;
             const float y = YK ? yk[YK ? 4 * g + e : 0] : ys[rg.j[e]];
             if (-fmaf(rg.a[e], y, rg.c[e]) > tau) {
               const F2 u = u_pair(rg.c[e], rg.a[e], y);
@@ -207,6 +211,7 @@ __device__ __forceinline__ void short_slice(const InstDesc& D, const Seg& S, con
 #pragma unroll
       for (int e = 0; e < 4; ++e) {
         const int k = 4 * g + e;
+        if (k >= WC) break;
         float x = 0.f;
         if constexpr (KEEP) {
           if (uh[k] > tt) {
@@ -380,10 +385,14 @@ __global__ void __launch_bounds__(kSweepThreads, 1)
       short_slice<P, 24>(sD, S, ys, accG, off, w, oq);
     else if (w > 12)
       short_slice<P, 16>(sD, S, ys, accG, off, w, oq);
-    else if (w > 8)
+    else if (w > 10)
       short_slice<P, 12>(sD, S, ys, accG, off, w, oq);
-    else if (w > 4)
+    else if (w > 8)
+      short_slice<P, 10>(sD, S, ys, accG, off, w, oq);
+    else if (w > 6)
       short_slice<P, 8>(sD, S, ys, accG, off, w, oq);
+    else if (w > 4)
+      short_slice<P, 6>(sD, S, ys, accG, off, w, oq);
     else
       short_slice<P, 4>(sD, S, ys, accG, off, w, oq);
   }

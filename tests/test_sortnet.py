@@ -57,7 +57,9 @@ static bool check() {
   return true;
 }
 
-int main() { return (check<4>() && check<8>() && check<12>() && check<16>()) ? 0 : 1; }
+int main() {
+  return (check<4>() && check<6>() && check<8>() && check<10>() && check<12>() && check<16>()) ? 0 : 1;
+}
 """
 
 
@@ -73,5 +75,6 @@ def test_batcher_network_sorts(tmp_path):
     assert r.returncode == 0, r.stdout + r.stderr
     counts = dict(tuple(map(int, line.split())) for line in r.stdout.split("\n") if line.strip())
     # Batcher's odd-even merge sort: 5, 19 comparators for 4, 8 inputs (Knuth
-    # 5.3.4), 63 for 16; 42 for the 12-input restriction
-    assert counts == {4: 5, 8: 19, 12: 42, 16: 63}
+    # 5.3.4), 63 for 16; its restrictions to 6, 10 and 12 inputs keep 12, 32
+    # and 42 (the comparators that touch no input past n)
+    assert counts == {4: 5, 6: 12, 8: 19, 10: 32, 12: 42, 16: 63}

@@ -154,8 +154,11 @@ __global__ void __launch_bounds__(kStaticThreads) k_static_sweep(const int64_t* 
       m = warp_max(m);
       if (eq || m > 0.f) {
         tau = m - gz;
-        // every pass either stops or strictly shrinks the active set, so
-        // d + 1 passes always reach the fixed point
+        // the iteration stops once the threshold no longer rises (from the
+        // lower bound m - gamma z it cannot in exact arithmetic; in FP32 two
+        // sets whose thresholds round past each other would otherwise
+        // alternate), so every further pass strictly shrinks the active set
+        // and d + 1 passes always reach the stop
         int prevn = -1;
         for (int64_t it = 0; it <= d; ++it) {
           float sm = 0.f;
@@ -174,7 +177,7 @@ __global__ void __launch_bounds__(kStaticThreads) k_static_sweep(const int64_t* 
           if (cnt == prevn || cnt == 0) break;
           prevn = cnt;
           const float tn = __fdiv_rn(sm - gz, static_cast<float>(cnt));
-          if (tn == tau) break;
+          if (!(tn > tau)) break;
           tau = tn;
         }
         zero = !eq && tau <= 0.f;

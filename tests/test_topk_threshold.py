@@ -13,8 +13,11 @@ Michelot iteration, which can alternate between two active sets whose
 FP32 thresholds round past each other (values of 40 clustered within
 gamma z = 1e-3), reaches its pass cap only on such rows, whose x the cap's
 fallback (the threshold over the current set) keeps within the tolerance.
-The kernel is held to the oracle by the GPU parity tests; this test pins
-the arithmetic it follows on adversarial rows."""
+The allocation-free entry point (csrc/noalloc.cu), whose warp-per-user
+iteration stops once the threshold no longer rises, reaches that stop on
+every row within d + 1 passes, with x within the same tolerances.  The
+kernels are held to the oracle by the GPU tests; this test pins the
+arithmetic they follow on adversarial rows."""
 import numpy as np
 import pytest
 
@@ -193,3 +196,95 @@ def test_topk_threshold_matches_fp64_projection(kind, z, gamma):
             assert np.abs(x4.astype(np.float64) - x8).max() <= 8 * U * z + 4 * U * ref.max()
     print(f"kind={kind} gamma={gamma}: rows off the threshold, worst error / (8u z + 4u x) = {worst:.3f}; "
           f"rows at the pass cap: {capped}")
+
+
+def static_row_x(c, a, y, kind, z, gamma, monotone=True):
+    """x of one row by the allocation-free entry point's arithmetic
+    (noalloc.cu: the Michelot iteration from max u - gamma z, at most d + 1
+    passes), and whether the iteration stopped before that bound."""
+    g = np.float64(gamma)
+    gz = f32(g * z)
+    gzl = f32(g * z - np.float64(gz))
+    invg = f32(1.0 / g)
+    d = c.shape[0]
+    box, eq = kind == oracle.BOX, kind == oracle.SIMPLEX_EQ
+    u = np.array([fma_u(c[k], a[k], y[k]) for k in range(d)], F)
+    pairs = [u_pair(c[k], a[k], y[k]) for k in range(d)]
+    tau, taul, zero, stopped = f32(0), f32(0), box, True
+    if not box:
+        m = u.max()
+        if eq or m > 0:
+            tau = f32(m - gz)
+            prevn, stopped = -1, False
+            for _ in range(d + 1):
+                sel = u > tau
+                cnt = int(sel.sum())
+                sm = f32(0)
+                for k in range(d):
+                    if sel[k]:
+                        sm = f32(sm + u[k])
+                if cnt == prevn or cnt == 0:
+                    stopped = True
+                    break
+                prevn = cnt
+                tn = f32(f32(sm - gz) / f32(cnt))
+                if (not tn > tau) if monotone else tn == tau:
+                    stopped = True
+                    break
+                tau = tn
+            zero = not eq and tau <= 0
+            if not zero:
+                ps, cnt = (f32(0), f32(0)), 0
+                for k in range(d):
+                    if u[k] > tau:
+                        ps = f2_add(ps, pairs[k])
+                        cnt += 1
+                th, tl = f2_threshold(ps, gz, gzl, max(cnt, 1))
+                if not eq and f32(th + tl) <= 0:
+                    zero = True
+                else:
+                    tau, taul = th, tl
+        else:
+            zero = True
+    if zero:
+        tau, taul = f32(0), f32(0)
+    x = np.zeros(d, F)
+    for k in range(d):
+        if u[k] > tau:
+            h, l = pairs[k]
+            if box:
+                x[k] = min(max(f32(f32(h + l) * invg), F(0)), f32(z))
+            elif zero:
+                x[k] = max(f32(h + l), F(0)) * invg
+            else:
+                x[k] = max(f32(f32(h - tau) + f32(l - taul)), F(0)) * invg
+    return x, stopped
+
+
+@pytest.mark.parametrize("kind,z", [(oracle.SIMPLEX_LE, 1.0), (oracle.SIMPLEX_EQ, 0.7), (oracle.BOX, 0.6)])
+@pytest.mark.parametrize("gamma", [1e-2, 1e-3])
+def test_static_entry_point_iteration_stops_and_matches(kind, z, gamma):
+    # the allocation-free entry point stops its iteration once the threshold
+    # no longer rises: every row reaches that stop within d + 1 passes, with x
+    # within the tolerances above; the stop on equality alone lets rows
+    # alternate between two sets until the bound
+    rng = np.random.default_rng(60 + int(-np.log10(gamma)) + 7 * kind)
+    alternating = 0
+    for _ in range(300):
+        c, a, y = adversarial_row(rng, gamma, z)
+        x, stopped = static_row_x(c, a, y, kind, z, gamma)
+        assert stopped
+        alternating += not static_row_x(c, a, y, kind, z, gamma, monotone=False)[1]
+        u = -(c.astype(np.float64) + a.astype(np.float64) * y.astype(np.float64))
+        ref, theta = oracle.project(u / gamma, kind, z)
+        mag = np.abs(c.astype(np.float64)) + np.abs(a.astype(np.float64) * y)
+        thr = gamma * theta if kind != oracle.BOX else 0.0
+        near = np.abs(u - thr) <= 8 * U * mag.max()
+        if kind == oracle.BOX:
+            near |= np.abs(u - gamma * z) <= 8 * U * mag.max()
+        err = np.abs(x.astype(np.float64) - ref)
+        if near.any():
+            assert (err <= 2e-6 * z + 4 * U * ref + 16 * U * mag.max() / gamma).all(), (kind, gamma, u, ref, x)
+        else:
+            assert (err <= 8 * U * z + 4 * U * ref).all(), (kind, gamma, u, ref, x)
+    print(f"kind={kind} gamma={gamma}: rows the equality stop would leave alternating: {alternating}")
